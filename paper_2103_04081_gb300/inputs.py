@@ -1,0 +1,154 @@
+"""Seeded synthetic inputs: CP factor matrices, dense tensors, initial factors.
+
+This module only generates data. It holds none of the method's arithmetic,
+imports neither the CUDA binding nor the CPU oracle, and both sides of every
+parity test take their inputs from it.
+
+Recipe (the paper's own generator in Sec. 5.2 uses an unspecified
+``spread/magnitude`` function, so these stand in for its data):
+
+* factors ``A^(k)`` with i.i.d. N(0,1) entries (Sec. 5.2, "Data II" of the
+  variance study), optionally
+  - column-correlated: ``A = G chol(C)^T`` with ``C = (1-c) I + c 11^T``
+    (congruence c between columns),
+  - row-skewed: every row scaled by a lognormal(0,1) weight, so row norms
+    and leverage scores are uneven (the property importance sampling
+    exploits, Sec. 5.2);
+* ``X_true = [[A^(1),...,A^(N)]]`` (Sec. 1) and the observed tensor
+  ``X = X_true + noise * (||X_true|| / ||E||) * E`` with E i.i.d. N(0,1)
+  (Sec. 5.2);
+* initial factors ``A_0^(k)`` i.i.d. N(0,1) from a seed distinct from the data
+  seed (Sec. 5.2 "random initialization").
+
+Tensors are returned flat in column-major order (first index fastest), the
+order in which Eq. map enumerates the columns of every unfolding.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+_INIT_SALT = 0x5EED_1217
+
+
+def _gen(seed: int, device) -> torch.Generator:
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) & (2**63 - 1))
+    return g
+
+
+def factors(dims, R: int, seed: int, *, congruence: float = 0.0,
+            lognormal_rows: bool = False, device="cpu") -> list[torch.Tensor]:
+    """Ground-truth factor matrices (float64, shape (I_k, R)) on ``device``."""
+    g = _gen(seed, "cpu")
+    out = []
+    for I in dims:
+        A = torch.randn(int(I), R, generator=g, dtype=torch.float64)
+        if congruence:
+            C = (1.0 - congruence) * torch.eye(R, dtype=torch.float64) + congruence
+            A = A @ torch.linalg.cholesky(C).T
+        if lognormal_rows:
+            A = A * torch.exp(torch.randn(int(I), 1, generator=g, dtype=torch.float64))
+        out.append(A.to(device))
+    return out
+
+
+def init_factors(dims, R: int, seed: int, dtype=torch.float32) -> list[torch.Tensor]:
+    """Initial factors A_0^(k), i.i.d. N(0,1), seeded apart from the data."""
+    g = _gen(seed ^ _INIT_SALT, "cpu")
+    return [torch.randn(int(I), R, generator=g, dtype=torch.float64).to(dtype)
+            for I in dims]
+
+
+def _krp_rows(A: list[torch.Tensor], j0: int, j1: int) -> torch.Tensor:
+    """Rows j0..j1-1 of A^(N-1) (.) ... (.) A^(1) (first mode index fastest)."""
+    dims = [a.shape[0] for a in A]
+    j = torch.arange(j0, j1, device=A[0].device)
+    Z = torch.ones(j1 - j0, A[0].shape[1], dtype=A[0].dtype, device=A[0].device)
+    for a, I in zip(A, dims):
+        Z = Z * a[j % I]
+        j = j // I
+    return Z
+
+
+_STORE = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+
+
+def cp_tensor(A: list[torch.Tensor], noise: float, seed: int, x_dtype: str = "f64",
+              chunk_cols: int = 1 << 16, compute_dtype=torch.float64) -> torch.Tensor:
+    """Observed tensor X (flat, column-major) in the storage dtype ``x_dtype``.
+
+    Generated in column chunks of the mode-1 unfolding so that tensors of
+    several GB fit; the noise of chunk c comes from a generator seeded with
+    (seed, c), so the result does not depend on the device memory.
+    """
+    device = A[0].device
+    A = [a.to(compute_dtype) for a in A]
+    I0 = A[0].shape[0]
+    J = math.prod(a.shape[0] for a in A[1:])
+    out = torch.empty(I0 * J, dtype=_STORE[x_dtype], device=device)
+    ranges = [(c, j0, min(J, j0 + chunk_cols)) for c, j0 in enumerate(range(0, J, chunk_cols))]
+
+    def chunk(c, j0, j1):
+        Z = _krp_rows(A[1:], j0, j1)
+        xt = Z @ A[0].T                      # (j1-j0, I0): row j = column j of X_(1)
+        e = torch.randn(xt.shape, generator=_gen(seed * 1_000_003 + c, device),
+                        dtype=compute_dtype, device=device)
+        return xt, e
+
+    nt = ne = 0.0
+    if noise:
+        for c, j0, j1 in ranges:
+            xt, e = chunk(c, j0, j1)
+            nt += float((xt.double() ** 2).sum())
+            ne += float((e.double() ** 2).sum())
+        scale = noise * math.sqrt(nt) / math.sqrt(ne)
+    else:
+        scale = 0.0
+    for c, j0, j1 in ranges:
+        xt, e = chunk(c, j0, j1)
+        out[j0 * I0: j1 * I0] = (xt + scale * e).reshape(-1).to(out.dtype)
+    return out
+
+
+def to_numpy_fortran(x_flat: torch.Tensor, dims) -> np.ndarray:
+    """Host copy of a flat column-major tensor as a Fortran-ordered ndarray.
+
+    bf16 tensors come back as their uint16 bit patterns.
+    """
+    t = x_flat.detach().cpu()
+    if t.dtype == torch.bfloat16:
+        t = t.view(torch.int16)
+        arr = t.numpy().view(np.uint16)
+    else:
+        arr = t.numpy()
+    return arr.reshape(tuple(dims), order="F")
+
+
+def bf16_bits_to_f64(bits: np.ndarray) -> np.ndarray:
+    """Exact float64 values of bf16 bit patterns."""
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+# Workloads of the measurement plan: the paper's settings (Sec. 5) restated
+# at the sizes of the GB300 measurements.
+WORKLOADS = {
+    "c1_60cube_f64": dict(dims=(60, 60, 60), R=5, B=18, x_dtype="f64",
+                          sampling="euclidean", step="fixed", alpha=0.1, noise=1e-2,
+                          congruence=0.0, lognormal_rows=False, iters=300,
+                          data_seed=0, init_seed=1, sample_seed=0),
+    "c2_300cube_f32": dict(dims=(300, 300, 300), R=10, B=256, x_dtype="f32",
+                           sampling="euclidean", step="adagrad", eta=0.1, b=1e-12,
+                           noise=1e-2, congruence=0.8, lognormal_rows=True, iters=5000,
+                           data_seed=0, init_seed=1, sample_seed=0),
+    "c3_120pow4_bf16": dict(dims=(120, 120, 120, 120), R=20, B=1024, x_dtype="bf16",
+                            sampling="euclidean", step="adagrad", eta=0.1, b=1e-12,
+                            noise=1e-3, congruence=0.0, lognormal_rows=False,
+                            iters=2000, data_seed=0, init_seed=1, sample_seed=0),
+    "c4_1000cube_bf16": dict(dims=(1000, 1000, 1000), R=50, B=2048, x_dtype="bf16",
+                             sampling="euclidean", step="adagrad", eta=0.1, b=1e-12,
+                             noise=1e-2, congruence=0.0, lognormal_rows=True,
+                             iters=2000, data_seed=0, init_seed=1, sample_seed=0),
+}

@@ -1,0 +1,450 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test compares the oracle with an independent route: numpy's Philox
+bit generator, library QR / Khatri-Rao / reshapes, exhaustive enumeration of
+every mini-batch on tiny tensors (Thm 5, Thm 10, Table 1), closed forms of
+the updates and a hand-worked example under tests/golden/. None of them
+re-types the oracle's own formula.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.linalg import khatri_rao
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def explicit_Z(A, n):
+    """Z^(n) = A^(N) kr ... kr A^(n+1) kr A^(n-1) kr ... kr A^(1) (Eq. lsq_krp)."""
+    order = [k for k in reversed(range(len(A))) if k != n]
+    Z = A[order[0]]
+    for k in order[1:]:
+        Z = khatri_rao(Z, A[k])
+    return Z
+
+
+def unfold(X, n):
+    """Mode-n unfolding by a library reshape (Kolda & Bader ordering)."""
+    return np.moveaxis(X, n, 0).reshape(X.shape[n], -1, order="F")
+
+
+def rand_problem(dims, R, seed, noise=0.3):
+    rng = np.random.default_rng(seed)
+    A = [rng.standard_normal((d, R)) for d in dims]
+    X = np.einsum(",".join(f"{chr(105 + k)}r" for k in range(len(dims))) + "->"
+                  + "".join(chr(105 + k) for k in range(len(dims))), *A)
+    X = np.asfortranarray(X + noise * rng.standard_normal(dims))
+    return A, X
+
+
+# ------------------------------------------------------------------ #
+# Philox4x64-10 against numpy's implementation of the same generator   #
+# ------------------------------------------------------------------ #
+
+@pytest.mark.parametrize("ctr,key", [
+    ((1, 0, 0, 0), (0, 0)),
+    ((5, 7, 9, 11), (123, 456)),
+    ((2**64 - 1, 3, 0, 1), (2**63 + 5, 17)),
+    ((12345, 2**64 - 1, 2**32, 7), (0xDEADBEEF, 2**64 - 2)),
+])
+def test_philox_matches_numpy(orc, ctr, key):
+    # numpy's Philox increments its 256-bit counter before each block.
+    c = list(ctr)
+    c[0] -= 1
+    bg = np.random.Philox(key=np.array(key, dtype=np.uint64),
+                          counter=np.array(c, dtype=np.uint64))
+    assert orc.philox(ctr, key) == [int(v) for v in bg.random_raw(4)]
+
+
+def test_u53_range(orc):
+    assert orc.u53(0) == 0.0
+    assert orc.u53(2**64 - 1) == 1.0 - 2.0**-53
+    assert orc.u53(2**11) == 2.0**-53
+
+
+def test_mode_draw_uniform(orc):
+    """Alg. 4/5 draw n uniformly: chi-square over 30000 iterations."""
+    for N in (3, 4, 5):
+        counts = np.bincount([orc.mode_draw(11, t, N) for t in range(30000)], minlength=N)
+        assert counts.size == N
+        exp = 30000 / N
+        chi2 = ((counts - exp) ** 2 / exp).sum()
+        assert chi2 < 30.0, (N, counts)
+
+
+# ------------------------------------------------------------------ #
+# Eq. map / Eq. index_map: unfolding and KRP rows                      #
+# ------------------------------------------------------------------ #
+
+@pytest.mark.parametrize("dims", [(3, 4, 5), (2, 3, 4, 5)])
+def test_index_map_and_fiber_gather(orc, dims):
+    X = np.asfortranarray(np.arange(math.prod(dims), dtype=np.float64).reshape(dims, order="F"))
+    for n in range(len(dims)):
+        Xn = unfold(X, n)
+        others = [range(d) if k != n else [0] for k, d in enumerate(dims)]
+        for tup in itertools.product(*others):
+            j = orc.unfold_col(dims, n, tup)
+            fib = orc.gather_fiber(X, n, tup)
+            np.testing.assert_array_equal(fib, Xn[:, j])
+            # the column holds exactly the fiber X(i_1..:..i_N)
+            sl = list(tup)
+            sl[n] = slice(None)
+            np.testing.assert_array_equal(Xn[:, j], X[tuple(sl)])
+
+
+@pytest.mark.parametrize("dims", [(3, 4, 5), (2, 3, 4, 5)])
+def test_krp_row_and_cp_unfolding(orc, dims):
+    R = 3
+    A, _ = rand_problem(dims, R, 1, noise=0.0)
+    Xexact = np.einsum(",".join(f"{chr(105 + k)}r" for k in range(len(dims))) + "->"
+                       + "".join(chr(105 + k) for k in range(len(dims))), *A)
+    for n in range(len(dims)):
+        Z = explicit_Z(A, n)
+        # Kolda & Bader: X_(n) = A^(n) Z^(n)T for an exact CP tensor.
+        np.testing.assert_allclose(unfold(Xexact, n), A[n] @ Z.T, rtol=1e-12, atol=1e-12)
+        others = [range(d) if k != n else [0] for k, d in enumerate(dims)]
+        for tup in itertools.product(*others):
+            j = orc.unfold_col(dims, n, tup)
+            np.testing.assert_allclose(orc.krp_row(A, n, tup), Z[j], rtol=1e-15, atol=0)
+
+
+# ------------------------------------------------------------------ #
+# Sampling probabilities (Sec. 3.1)                                    #
+# ------------------------------------------------------------------ #
+
+def enumerate_batches(orc, cfg, n, X, A):
+    """(p_j, G_j) for every single-fiber batch (B = 1), column j of Eq. map."""
+    dims = cfg.dims
+    others = [range(d) if k != n else [-1] for k, d in enumerate(dims)]
+    out = {}
+    for tup in itertools.product(*others):
+        idx = np.array([tup], dtype=np.int64)
+        st, p, G = orc.gradient_for_batch(cfg, n, idx, X, A)
+        assert st == orc.OK
+        j = orc.unfold_col(dims, n, [max(v, 0) for v in tup])
+        out[j] = (p[0], G)
+    return out
+
+
+def test_euclidean_probabilities(orc):
+    dims, R = (3, 4, 5), 2
+    A, X = rand_problem(dims, R, 2)
+    cfg = orc.Config(dims=dims, R=R, B=1, sampling="euclidean")
+    for n in range(3):
+        Z = explicit_Z(A, n)
+        ps = enumerate_batches(orc, cfg, n, X, A)
+        assert abs(sum(p for p, _ in ps.values()) - 1.0) < 1e-14
+        others = [range(d) if k != n else [0] for k, d in enumerate(dims)]
+        for tup in itertools.product(*others):
+            j = orc.unfold_col(dims, n, tup)
+            rows = [np.linalg.norm(A[k][tup[k]]) ** 2 for k in range(3) if k != n]
+            fro = [np.linalg.norm(A[k]) ** 2 for k in range(3) if k != n]
+            # Eq. krp_euc_prob
+            assert ps[j][0] == pytest.approx(np.prod(rows) / np.prod(fro), rel=1e-14)
+            # Lemma 3
+            assert np.linalg.norm(Z[j]) ** 2 <= np.prod(rows) * (1 + 1e-14)
+
+
+def test_leverage_scores_match_qr(orc):
+    rng = np.random.default_rng(3)
+    for I, R in [(7, 1), (40, 5), (100, 20), (300, 50)]:
+        A = rng.standard_normal((I, R)) * np.exp(rng.standard_normal((I, 1)))
+        st, w = orc.weights("leverage", A)
+        assert st == orc.OK
+        Q, _ = np.linalg.qr(A)
+        np.testing.assert_allclose(w, (Q ** 2).sum(1), rtol=1e-9, atol=1e-13)
+        assert w.sum() == pytest.approx(R, rel=1e-12)       # sum of leverage = rank
+
+
+def test_leverage_rank_deficient_is_degenerate(orc):
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((20, 3))
+    A[:, 2] = A[:, 0]
+    st, _ = orc.weights("leverage", A)
+    assert st == orc.EDEGENERATE
+
+
+def test_leverage_probabilities_and_lemma1(orc):
+    dims, R = (6, 5, 7), 3
+    A, X = rand_problem(dims, R, 5)
+    cfg = orc.Config(dims=dims, R=R, B=1, sampling="leverage")
+    for n in range(3):
+        Z = explicit_Z(A, n)
+        Qz, _ = np.linalg.qr(Z)
+        lev_z = (Qz ** 2).sum(1)
+        lev = {k: (np.linalg.qr(A[k])[0] ** 2).sum(1) for k in range(3) if k != n}
+        ps = enumerate_batches(orc, cfg, n, X, A)
+        assert abs(sum(p for p, _ in ps.values()) - 1.0) < 1e-13
+        others = [range(d) if k != n else [0] for k, d in enumerate(dims)]
+        for tup in itertools.product(*others):
+            j = orc.unfold_col(dims, n, tup)
+            prod = np.prod([lev[k][tup[k]] for k in lev])
+            # Eq. krp_lev_prob with K = N-1 factors
+            assert ps[j][0] == pytest.approx(prod / R ** 2, rel=1e-9)
+            # Lemma 1
+            assert lev_z[j] <= prod * (1 + 1e-9)
+
+
+# ------------------------------------------------------------------ #
+# CDF and inverse-CDF draw                                             #
+# ------------------------------------------------------------------ #
+
+@pytest.mark.parametrize("I", [1, 2, 31, 32, 33, 1000, 1024, 1025, 40000])
+def test_cdf_exact_on_integers(orc, I):
+    rng = np.random.default_rng(I)
+    w = rng.integers(0, 1000, I).astype(np.float64)
+    np.testing.assert_array_equal(orc.cdf(w), np.cumsum(w))   # exact: integer sums
+
+
+@pytest.mark.parametrize("I", [33, 1000, 40000])
+def test_cdf_close_on_reals(orc, I):
+    rng = np.random.default_rng(I + 1)
+    w = np.exp(rng.standard_normal(I))
+    c = orc.cdf(w)
+    np.testing.assert_allclose(c, np.cumsum(w), rtol=1e-13)
+    assert np.all(np.diff(c) >= 0)
+
+
+def test_draw_intervals_and_zero_weights(orc):
+    w = np.array([0.0, 2.0, 0.0, 0.0, 1.0, 5.0, 0.0])
+    c = orc.cdf(w)
+    W = c[-1]
+    assert orc.draw(c, 0.0) == 1                       # first positive-weight row
+    for i in np.nonzero(w)[0]:
+        lo = c[i] - w[i]
+        mid = (lo + w[i] / 2) / W
+        assert orc.draw(c, mid) == i
+    us = np.linspace(0, 1, 20001)[:-1]
+    drawn = {orc.draw(c, u) for u in us}
+    assert drawn == {1, 4, 5}                          # zero-weight rows never drawn
+    assert orc.draw(c, 1.0 - 2.0**-53) == 5
+
+
+def test_sampler_frequencies_chi2(orc):
+    """Lemma 4: per-factor draws follow p_k(i) = ||A(i,:)||^2/||A||_F^2."""
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((50, 4)) * np.exp(rng.standard_normal((50, 1)))
+    st, w = orc.weights("euclidean", A)
+    np.testing.assert_allclose(w, (A ** 2).sum(1), rtol=1e-15)
+    c = orc.cdf(w)
+    p = (A ** 2).sum(1) / (A ** 2).sum()
+    n = 100000
+    draws = [orc.draw(c, orc.u53(orc.fiber_word(99, 3, f, 1))) for f in range(n)]
+    counts = np.bincount(draws, minlength=50)
+    exp = n * p
+    keep = exp > 5
+    chi2 = ((counts[keep] - exp[keep]) ** 2 / exp[keep]).sum()
+    dof = keep.sum() - 1
+    assert chi2 < dof + 6 * math.sqrt(2 * dof), (chi2, dof)
+
+
+# ------------------------------------------------------------------ #
+# Thm 5 (unbiased gradient) and Thm 10 / Table 1 (variance)             #
+# ------------------------------------------------------------------ #
+
+def full_gradient(A, X, n):
+    """Full LS gradient R Z with R = A Z^T - X_(n) (Sec. 2), by library ops."""
+    Z = explicit_Z(A, n)
+    Res = A[n] @ Z.T - unfold(X, n)
+    return Res, Z, Res @ Z
+
+
+CASES = [((3, 4, 5), 2, "euclidean"), ((3, 4, 5), 2, "leverage"),
+         ((3, 4, 5), 2, "uniform"), ((2, 3, 2, 3), 2, "euclidean"),
+         ((4, 3, 5), 1, "leverage")]
+
+
+@pytest.mark.parametrize("dims,R,sampling", CASES)
+def test_unbiased_gradient_thm5(orc, dims, R, sampling):
+    A, X = rand_problem(dims, R, 7)
+    cfg = orc.Config(dims=dims, R=R, B=1, sampling=sampling)
+    for n in range(len(dims)):
+        _, Z, grad = full_gradient(A, X, n)
+        Jn = Z.shape[0]
+        ps = enumerate_batches(orc, cfg, n, X, A)
+        EG = sum(p * G for p, G in ps.values())
+        # Eq. gradient1 taken literally: E[G] = (A Z^T Z - X_(n) Z) / J_n.
+        np.testing.assert_allclose(EG, grad / Jn, rtol=1e-11, atol=1e-13 * np.abs(grad).max())
+
+
+@pytest.mark.parametrize("dims,R,sampling", CASES[:3])
+def test_variance_thm10_table1(orc, dims, R, sampling):
+    A, X = rand_problem(dims, R, 8)
+    for n in range(len(dims)):
+        Res, Z, grad = full_gradient(A, X, n)
+        Jn = Z.shape[0]
+        cfg1 = orc.Config(dims=dims, R=R, B=1, sampling=sampling)
+        ps = enumerate_batches(orc, cfg1, n, X, A)
+        EG = grad / Jn
+        var1 = sum(p * np.sum((G - EG) ** 2) for p, G in ps.values())
+        rz = (Res ** 2).sum(0) * (Z ** 2).sum(1)         # ||R(:,j)||^2 ||Z(j,:)||^2
+        pj = np.array([ps[j][0] for j in range(Jn)])
+        # Thm 10, rescaled by 1/J_n^2 for the literal Eq. gradient1.
+        thm10 = (np.sum(rz / pj) - np.sum(grad ** 2)) / Jn ** 2
+        assert var1 == pytest.approx(thm10, rel=1e-10)
+        # Table 1, per distribution, in closed form (B = 1).
+        if sampling == "uniform":
+            tab = Jn * rz.sum() - np.sum(grad ** 2)
+        else:
+            if sampling == "leverage":
+                fac = {k: (np.linalg.qr(A[k])[0] ** 2).sum(1) for k in range(len(dims)) if k != n}
+                tot = R ** (len(dims) - 1)
+            else:
+                fac = {k: (A[k] ** 2).sum(1) for k in range(len(dims)) if k != n}
+                tot = np.prod([(A[k] ** 2).sum() for k in fac])
+            den = np.empty(Jn)
+            others = [range(d) if k != n else [0] for k, d in enumerate(dims)]
+            for tup in itertools.product(*others):
+                den[orc.unfold_col(dims, n, tup)] = np.prod([fac[k][tup[k]] for k in fac])
+            tab = tot * np.sum(rz / den) - np.sum(grad ** 2)
+        assert var1 == pytest.approx(tab / Jn ** 2, rel=1e-8)
+
+        # B = 2: independent draws halve the variance (Thm 10's 1/|F_n|).
+        if Jn <= 30:
+            cfg2 = orc.Config(dims=dims, R=R, B=2, sampling=sampling)
+            others = [range(d) if k != n else [-1] for k, d in enumerate(dims)]
+            tuples = list(itertools.product(*others))
+            E2 = np.zeros_like(EG)
+            V2 = 0.0
+            for t1 in tuples:
+                for t2 in tuples:
+                    st, p, G = orc.gradient_for_batch(cfg2, n, np.array([t1, t2]), X, A)
+                    w = p[0] * p[1]
+                    E2 += w * G
+                    V2 += w * np.sum((G - EG) ** 2)
+            np.testing.assert_allclose(E2, EG, rtol=1e-10, atol=1e-12 * np.abs(EG).max())
+            assert V2 == pytest.approx(thm10 / 2, rel=1e-9)
+
+
+def test_uniform_reduces_to_brascpd(orc):
+    """p = 1/J_n turns Eq. gradient1 into Alg. 2's (1/B)(A Zs^T Zs - Xs Zs)."""
+    dims, R, B = (4, 5, 6), 3, 7
+    A, X = rand_problem(dims, R, 9)
+    rng = np.random.default_rng(10)
+    cfg = orc.Config(dims=dims, R=R, B=B, sampling="uniform")
+    for n in range(3):
+        idx = np.stack([rng.integers(0, d, B) if k != n else -np.ones(B, int)
+                        for k, d in enumerate(dims)], 1)
+        st, p, G = orc.gradient_for_batch(cfg, n, idx, X, A)
+        Z = explicit_Z(A, n)
+        Xn = unfold(X, n)
+        cols = [orc.unfold_col(dims, n, np.maximum(row, 0)) for row in idx]
+        Zs, Xs = Z[cols], Xn[:, cols]
+        np.testing.assert_allclose(G, (A[n] @ Zs.T @ Zs - Xs @ Zs) / B, rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------------------ #
+# Updates, the hand-worked example and Tol                             #
+# ------------------------------------------------------------------ #
+
+def test_hand_worked_2x2x2(orc):
+    g = json.load(open(os.path.join(GOLDEN, "hand_2x2x2.json")))
+    dims = tuple(g["dims"])
+    A = [np.array(a, dtype=np.float64) for a in g["A"]]
+    X = np.full(dims, g["X_all_entries"], order="F")
+    cfg = orc.Config(dims=dims, R=1, B=1, sampling="euclidean", step="fixed", alpha=0.01)
+    st, p, G = orc.gradient_for_batch(cfg, g["n"], np.array(g["idx"]), X, A)
+    assert p[0] == pytest.approx(g["p_f"], rel=1e-15)
+    np.testing.assert_allclose(G, g["G"], rtol=1e-15)
+    An = A[0].copy()
+    orc.update(cfg, 0, An, None, G)
+    np.testing.assert_allclose(An, g["A_fixed_alpha_0.01"], rtol=1e-15)
+    cfg_ada = orc.Config(dims=dims, R=1, B=1, step="adagrad", eta=0.5, b=0.0)
+    An, Sn = A[0].copy(), np.zeros_like(A[0])
+    orc.update(cfg_ada, 0, An, Sn, G)
+    np.testing.assert_allclose(An, g["A_adagrad_eta_0.5_b_0"], rtol=1e-15)
+
+
+def test_adagrad_closed_form(orc):
+    """Eq. etaada with b=0: step 1 moves by eta*sign(G); step 2 by eta*G2/sqrt(G1^2+G2^2)."""
+    rng = np.random.default_rng(12)
+    A0 = rng.standard_normal((6, 3))
+    G1, G2 = rng.standard_normal((6, 3)), rng.standard_normal((6, 3))
+    cfg = orc.Config(dims=(6, 2, 2), R=3, B=1, step="adagrad", eta=0.3, b=0.0)
+    A, S = A0.copy(), np.zeros_like(A0)
+    orc.update(cfg, 0, A, S, G1)
+    np.testing.assert_allclose(A, A0 - 0.3 * np.sign(G1), rtol=1e-15)
+    orc.update(cfg, 1, A, S, G2)
+    np.testing.assert_allclose(A, A0 - 0.3 * np.sign(G1) - 0.3 * G2 / np.sqrt(G1 ** 2 + G2 ** 2),
+                               rtol=1e-14)
+    np.testing.assert_allclose(S, G1 ** 2 + G2 ** 2, rtol=1e-15)
+
+
+def test_decreasing_step(orc):
+    rng = np.random.default_rng(13)
+    A0, G = rng.standard_normal((5, 2)), rng.standard_normal((5, 2))
+    cfg = orc.Config(dims=(5, 2, 2), R=2, B=1, step="decay", beta=2.0, gamma=3.0)
+    A = A0.copy()
+    orc.update(cfg, 7, A, None, G)
+    np.testing.assert_allclose(A, A0 - (2.0 / 10.0) * G, rtol=1e-15)
+
+
+def test_tol_against_planted_residual(orc):
+    dims, R = (5, 6, 7), 3
+    A, _ = rand_problem(dims, R, 14, noise=0.0)
+    Xhat = np.einsum("ir,jr,kr->ijk", *A)
+    E = np.random.default_rng(15).standard_normal(dims) * 0.1
+    X = np.asfortranarray(Xhat + E)
+    tol, xx = orc.tol(X, A)
+    assert xx == pytest.approx(np.sum(X ** 2), rel=1e-13)
+    assert tol == pytest.approx(np.sum(E ** 2) / np.sum(X ** 2), rel=1e-10)
+    tol0, _ = orc.tol(np.asfortranarray(Xhat), A)
+    assert tol0 < 1e-28
+
+
+def test_zero_gradient_at_exact_solution(orc):
+    """Interpolation: with X = [[A]] every sampled gradient vanishes (Eq. gradient1)."""
+    dims, R = (6, 7, 8), 3
+    A, _ = rand_problem(dims, R, 16, noise=0.0)
+    X = np.asfortranarray(np.einsum("ir,jr,kr->ijk", *A))
+    for sampling in ("euclidean", "leverage", "uniform"):
+        cfg = orc.Config(dims=dims, R=R, B=5, sampling=sampling, step="fixed", alpha=0.1, seed=3)
+        Ac = [a.copy() for a in A]
+        for t in range(20):
+            out = orc.step(cfg, t, X, Ac)
+            assert out["status"] == orc.OK
+            assert np.abs(out["G"]).max() < 1e-12
+        for a, b in zip(Ac, A):
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("sampling", ["euclidean", "leverage"])
+def test_exact_recovery_from_perturbed_start(orc, sampling):
+    """Noiseless rank-R data, R_fit = R_true: fixed-step SGD recovers X (Tol -> 0)."""
+    dims, R = (8, 9, 10), 2
+    A, _ = rand_problem(dims, R, 17, noise=0.0)
+    X = np.asfortranarray(np.einsum("ir,jr,kr->ijk", *A))
+    rng = np.random.default_rng(18)
+    A0 = [a + 0.05 * rng.standard_normal(a.shape) for a in A]
+    cfg = orc.Config(dims=dims, R=R, B=16, sampling=sampling, step="fixed", alpha=0.2, seed=5)
+    tol0, _ = orc.tol(X, A0)
+    assert orc.run(cfg, 0, 6000, X, A0) == orc.OK
+    tol1, _ = orc.tol(X, A0)
+    assert tol0 > 1e-4
+    assert tol1 < 1e-20, tol1
+
+
+def test_step_records_batch_consistently(orc):
+    """orc_step's recorded (n, idx, p, G) are those of gradient_for_batch on the same state."""
+    dims, R, B = (7, 8, 9), 3, 11
+    A, X = rand_problem(dims, R, 19)
+    for sampling in ("euclidean", "leverage", "uniform"):
+        cfg = orc.Config(dims=dims, R=R, B=B, sampling=sampling, step="adagrad", seed=21)
+        Ac = [a.copy() for a in A]
+        S = [np.zeros_like(a) for a in A]
+        for t in range(5):
+            before = [a.copy() for a in Ac]
+            out = orc.step(cfg, t, X, Ac, S)
+            n = out["n"]
+            assert n == orc.mode_draw(21, t, 3)
+            assert np.all(out["idx"][:, n] == -1)
+            st, p, G = orc.gradient_for_batch(cfg, n, out["idx"], X, before)
+            np.testing.assert_array_equal(p, out["p"])
+            np.testing.assert_array_equal(G, out["G"])
+            for k in range(3):
+                if k != n:
+                    np.testing.assert_array_equal(Ac[k], before[k])
