@@ -1,0 +1,322 @@
+"""Throughput of BrawsCPD / AdawsCPD iterations on one or more GB300s.
+
+A step is one SGD iteration of the whole path (mode draw, importance
+sampling, sampled KRP rows, fiber gather, weighted gradient, AdaGrad step,
+CDF refresh) on the 1000^3 BF16 tensor, R = 50, B = 2048, Euclidean
+sampling. Inputs are synthetic (lognormal-scaled N(0,1) factors, 1e-2
+noise), generated on the device; the three mode replicas (6 GB) are far
+larger than L2, so no flush is needed between iterations.
+
+Prints one JSON line (rank 0). --impl reference times the FP64 CPU oracle on
+the same workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SGD iters/s & fiber-gather GB/s vs HBM peak; batched solves/s, p99 @ equal fit"
+DEFAULT_WORKLOAD = "c4_1000cube_bf16"
+KERNEL_SOURCES = ["paper_2103_04081_gb300/csrc/cpd_kernels.cu", "paper_2103_04081_gb300/csrc/cpd_tc.cu",
+                  "paper_2103_04081_gb300/csrc/cpd_device.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> tuple[dict, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def ncu_traffic(engine: str) -> float | None:
+    """DRAM bytes per launch of the gradient kernel from the committed ncu summary,
+    if that summary was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", f"grad_{engine}_c4_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m_hash = re.search(r"kernel_sources_sha256_16=(\w+)", txt)
+    m_b = re.search(r"dram_bytes_per_full_launch=([0-9.eE+]+)", txt)
+    if not m_hash or not m_b or m_hash.group(1) != kernel_hash():
+        return None
+    return float(m_b.group(1))
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return dist, rank, world, local
+    return None, 0, 1, 0
+
+
+def make_inputs(w: dict, rank: int, device: str):
+    from paper_2103_04081_gb300 import inputs as IN
+    A = IN.factors(w["dims"], w["R"], w["data_seed"] + rank, congruence=w["congruence"],
+                   lognormal_rows=w["lognormal_rows"], device=device)
+    X = IN.cp_tensor(A, w["noise"], w["data_seed"] + rank, w["x_dtype"])
+    A0 = IN.init_factors(w["dims"], w["R"], w["init_seed"] + rank,
+                         dtype=torch.float64 if w["x_dtype"] == "f64" else torch.float32)
+    return X, A0
+
+
+def cfg_kwargs(w: dict, rank: int, engine: str) -> dict:
+    return dict(dims=w["dims"], R=w["R"], B=w["B"], x_dtype=w["x_dtype"], sampling=w["sampling"],
+                step=w["step"], alpha=w.get("alpha", 0.1), eta=w.get("eta", 0.1), b=w.get("b", 1e-12),
+                seed=w["sample_seed"] + rank, engine=engine)
+
+
+def oracle_baseline(w: dict, X_dev: torch.Tensor, A0: list, budget_s: float) -> dict:
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    consecutive iterations from the same initial factors for about budget_s seconds."""
+    import numpy as np
+
+    from oracle import oracle as O
+    t0 = time.time()
+    if X_dev.dtype == torch.bfloat16:
+        xb = X_dev.cpu().view(torch.int16).numpy().view(np.uint16)
+    else:
+        xb = X_dev.cpu().numpy()
+    ocfg = O.Config(dims=tuple(w["dims"]), R=w["R"], B=w["B"], sampling=w["sampling"], step=w["step"],
+                    x_dtype=w["x_dtype"], alpha=w.get("alpha", 0.1), eta=w.get("eta", 0.1),
+                    b=w.get("b", 1e-12), seed=w["sample_seed"])
+    A = [a.double().numpy().copy() for a in A0]
+    S = [np.zeros_like(a) for a in A]
+    prep = time.time() - t0
+    O.run(ocfg, 0, 1, None, A, S, xbuf=xb)          # warm-up iteration
+    it, t1 = 0, time.time()
+    while time.time() - t1 < budget_s or it < 2:
+        st = O.run(ocfg, 1 + it, 1, None, A, S, xbuf=xb)
+        assert st == O.OK, st
+        it += 1
+    el = time.time() - t1
+    return {"value": it / el, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{it} consecutive oracle iterations of the {w['name']} workload "
+                      f"({el:.1f} s single-threaded FP64 C; host copy {prep:.1f} s not timed)"}
+
+
+def run_reference(args, w: dict) -> None:
+    dist, rank, world, local = dist_setup()
+    if rank != 0:
+        return
+    dev = f"cuda:{local}" if torch.cuda.is_available() else "cpu"
+    X, A0 = make_inputs(w, 0, dev)
+    budget = max(10.0, min(60.0, 1.0 * args.steps))
+    base = oracle_baseline(w, X, A0, budget)
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "iters/s",
+            "n_gpus": args.gpus, "steps": None, "warmup": 1, "ms_per_step": 1000.0 / base["value"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(w, "oracle"),
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": "iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_block(w: dict, engine: str) -> dict:
+    return {"workload": w["name"], "dims": list(w["dims"]), "R": w["R"], "B": w["B"],
+            "x_dtype": w["x_dtype"], "sampling": w["sampling"], "step": w["step"], "engine": engine,
+            "l2": "no flush: the mode-major tensor replicas (%.1f GB) are larger than L2" % (
+                len(w["dims"]) * torch.tensor(w["dims"]).prod().item() * (2 if w["x_dtype"] == "bf16" else 4) / 1e9)}
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=500)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tensor"])
+    ap.add_argument("--sampling", default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+
+    from paper_2103_04081_gb300 import inputs as IN
+    w = dict(IN.WORKLOADS[args.workload])
+    w["name"] = args.workload
+    if args.sampling:
+        w["sampling"] = args.sampling
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    from paper_2103_04081_gb300 import cpd as C
+    dist, rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    X, A0 = make_inputs(w, rank, dev)
+    kw = cfg_kwargs(w, rank, args.engine)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        dec = C.Decomposition(X, [a.to(dev) for a in A0], stream=stream, **kw)
+    desc = dec.describe()
+    engine = desc["engine"]
+    launches_per_iter = 2 + (2 if w["sampling"] == "leverage" else 0)
+
+    # warm-up (W iterations), then exactly K timed iterations
+    dec.sgd_iters(args.warmup, stream)
+    C.cpd_sync(dec.ctx, stream)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        dec.sgd_iters(args.steps, stream)
+        ev1.record(stream)
+        ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    C.cpd_sync(dec.ctx, stream)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = clk.summary()
+
+    # per-kernel duration of the gradient kernel: CUDA events around each launch
+    # on the launching stream, over a pass of the same iterations
+    C.cpd_profile(dec.ctx, True)
+    nprof = min(args.steps, 2000)
+    dec.sgd_iters(nprof, stream)
+    nlaunch, grad_ms = C.cpd_profile_read(dec.ctx, stream)
+    C.cpd_profile(dec.ctx, False)
+    fit, tol = dec.fit(stream)
+    dec.close()
+
+    iters_per_s = world * args.steps / (ms / 1e3)
+    esize = {"bf16": 2, "f32": 4, "f64": 8}[w["x_dtype"]]
+    In = sum(w["dims"]) / len(w["dims"])           # modes drawn uniformly
+    gather_bytes = w["B"] * In * esize               # algorithmic HBM bytes per gradient launch
+    peaks, src = measured_peaks()
+    achieved = gather_bytes / (grad_ms / 1e3) / 1e9
+    traffic = ncu_traffic(engine)
+
+    # end to end through the C-ABI with host buffers: upload X and A0 from pinned
+    # memory (cpd_init), K iterations, Tol, factors back to host
+    e2e = None
+    if rank == 0 or world > 1:
+        Xh = X.cpu().pin_memory()
+        A0h = [a.contiguous().pin_memory() for a in A0]
+        del X
+        torch.cuda.empty_cache()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            d2 = C.Decomposition(Xh, A0h, stream=stream, **kw)
+        d2.sgd_iters(args.steps, stream)
+        _, tol2 = d2.fit(stream)
+        Ah = d2.factors("cpu", stream)
+        t1 = time.perf_counter()
+        d2.close()
+        h2d = Xh.numel() * Xh.element_size() + sum(a.numel() * a.element_size() for a in A0h)
+        d2h = sum(a.numel() * a.element_size() for a in Ah) + 8
+        e2e = {"value": args.steps / (t1 - t0), "unit": "iters/s",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "seconds": t1 - t0, "note": "cpd_init from pinned host X + K iterations + cpd_fit + "
+                                           "cpd_get_factors to host, per iteration"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": iters_per_s, "unit": "iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if engine == "tensor" else ("f64" if w["x_dtype"] == "f64" else "f32"),
+        "data": "synthetic", "config": config_block(w, engine),
+        "gather_gbs_in_loop": gather_bytes * args.steps / (ms / 1e3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "kernel": "k_grad_tc" if engine == "tensor" else "k_grad_simt",
+                     "algorithmic_bytes_per_launch": gather_bytes, "mean_launch_ms": grad_ms,
+                     "timed_launches": nlaunch, "peak_source": src + " (hbm_gbs, of " + src + ")"},
+        "clocks": clocks, "gpu_launches": launches_per_iter * args.steps,
+        "e2e": e2e, "final_tol": tol, "launch": desc,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        Xc, A0c = make_inputs(w, 0, dev)
+        line["cpu_baseline"] = oracle_baseline(w, Xc, A0c, args.cpu_budget)
+        del Xc
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * cpd.h -- C ABI of libcpd, a GB300 (sm_103a) implementation of
+ * block-randomized weighted SGD with importance sampling for CP
+ * decomposition (BrawsCPD, Alg. 4, and AdawsCPD, Alg. 5, of Yu & Li,
+ * arXiv 2103.04081).
+ *
+ * The problem (Sec. 2, Eq. certain_criterion): given a dense N-way tensor X
+ * of size I_1 x ... x I_N and a rank R, find factor matrices A^(k) (I_k x R)
+ * minimising 1/2 ||X - [[A^(1), ..., A^(N)]]||_F^2. One iteration draws a
+ * mode n, draws B mode-n fibers by Euclidean- or leverage-based importance
+ * sampling (Alg. 3, Lemmas 2 and 4), forms the sampled Khatri-Rao rows and
+ * fibers (Alg. 1), the weighted stochastic gradient (Eq. gradient1) and
+ * updates A^(n) with a fixed (Eq. proposed), decreasing (Thm 9) or
+ * AdaGrad-style step (Eq. etaada / Eq. Aada).
+ *
+ * Conventions for every entry point:
+ *  - Indices are 0-based; the paper's are 1-based.
+ *  - X is dense and column-major (first index fastest): entry
+ *    (i_1, ..., i_N) sits at element offset sum_k i_k * prod_{m<k} I_m,
+ *    the order in which Eq. map numbers the columns of each unfolding.
+ *  - A factor matrix A^(k) is row-major I_k x R (row i contiguous).
+ *    Factors are double when x_dtype is CPD_F64 and float otherwise.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy stream).
+ *    Calls are ordered on that stream; a call that returns host data
+ *    synchronises it first.
+ *  - A location flag is CPD_HOST (pageable or pinned host memory) or
+ *    CPD_DEVICE (memory of the current CUDA device).
+ *  - Every call returns a cpd_status. On failure nothing is half-done
+ *    from the caller's point of view, and cpd_last_error() returns a
+ *    thread-local message. No C++ exception crosses the ABI.
+ *  - The library never falls back to the CPU: without a usable sm_103a
+ *    device, cpd_init returns CPD_ECUDA.
+ */
+#ifndef CPD_H
+#define CPD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CPD_MAX_MODES 8
+
+typedef enum {
+    CPD_OK = 0,
+    CPD_EINVAL = 1,       /* invalid argument or configuration            */
+    CPD_ENOMEM = 2,       /* device allocation failed / over the budget   */
+    CPD_ECUDA = 3,        /* CUDA runtime or driver error                 */
+    CPD_ETIMEOUT = 4,     /* a bounded device wait gave up                */
+    CPD_ENONFINITE = 5,   /* a gradient or factor became NaN / Inf        */
+    CPD_EDEGENERATE = 6,  /* a sampling distribution has no mass, or a
+                             leverage Gram matrix is not of full rank     */
+    CPD_EAGAIN = 7,       /* cpd_poll: request not finished yet           */
+    CPD_EBUSY = 8         /* server full; retry later                     */
+} cpd_status;
+
+enum { CPD_HOST = 0, CPD_DEVICE = 1 };
+
+/* Importance-sampling distribution of the per-factor row draws (Sec. 3.1). */
+enum {
+    CPD_SAMPLE_EUCLIDEAN = 0, /* p_k(i) = ||A^(k)(i,:)||^2 / ||A^(k)||_F^2, Lemma 4   */
+    CPD_SAMPLE_LEVERAGE = 1,  /* p_k(i) = l_i(A^(k)) / sum_i l_i, Lemma 2           */
+    CPD_SAMPLE_UNIFORM = 2    /* p_k(i) = 1 / I_k: BrasCPD / AdasCPD (Alg. 2)       */
+};
+
+/* Step rule (Sec. 3.2). */
+enum {
+    CPD_STEP_FIXED = 0,   /* A -= alpha G                      (Eq. proposed)   */
+    CPD_STEP_ADAGRAD = 1, /* S += G.^2; A -= eta G ./ sqrt(b + S) (Eq. etaada/Aada) */
+    CPD_STEP_DECAY = 2    /* A -= beta / (t + gamma) G            (Thm 9)        */
+};
+
+/* Storage type of the tensor entries. */
+enum { CPD_F64 = 0, CPD_F32 = 1, CPD_BF16 = 2 };
+
+typedef struct {
+    int32_t N;          /* number of modes, 3 <= N <= CPD_MAX_MODES                 */
+    int32_t R;          /* CP rank, 1 <= R <= 256                                   */
+    int32_t B;          /* mini-batch size |F_n|, 1 <= B <= 65536                    */
+    int32_t sampling;   /* CPD_SAMPLE_*                                             */
+    int32_t step;       /* CPD_STEP_*                                               */
+    int32_t x_dtype;    /* CPD_F64 / CPD_F32 / CPD_BF16                             */
+    int64_t dims[CPD_MAX_MODES]; /* I_1..I_N, each >= 1; leverage needs I_k > R   */
+    double alpha;       /* fixed step                                               */
+    double eta;         /* AdaGrad eta > 0                                          */
+    double b;           /* AdaGrad b >= 0                                           */
+    double beta;        /* decreasing step numerator                                */
+    double gamma;       /* decreasing step offset (t + gamma > 0)                   */
+    uint64_t seed;      /* key of the Philox4x64-10 draws                           */
+    int32_t engine;     /* 0 = automatic, 1 = CUDA-core gradient, 2 = tensor-core
+                           gradient (BF16 tensors only)                            */
+    int32_t reserved;   /* must be 0                                                */
+} cpd_config;
+
+typedef struct cpd_ctx cpd_ctx;
+
+/*
+ * cpd_init -- create a decomposition context (the inputs of Alg. 4 / Alg. 5:
+ * X, R, |F_n|, A_0, step parameters; Sec. 2 and Sec. 3.2).
+ *  cfg   : problem and method parameters (copied).
+ *  X     : the dense tensor, column-major, cfg->x_dtype entries, at x_loc.
+ *          Copied into device-resident, mode-major replicas owned by the
+ *          context (one per mode, so every mode-n fiber is contiguous);
+ *          X may be freed after the call returns.
+ *  A0    : array of N pointers, A0[k] row-major I_k x R (double for CPD_F64,
+ *          float otherwise), at a0_loc. Copied.
+ *  out   : receives the context. The iteration counter t starts at 0.
+ * Errors: CPD_EINVAL (bad cfg or NULL pointers; nothing is allocated),
+ *  CPD_ENOMEM, CPD_ECUDA, CPD_EDEGENERATE (a factor has no sampling mass, or
+ *  a leverage Gram matrix is singular). Synchronises `stream` before return.
+ */
+cpd_status cpd_init(const cpd_config *cfg, const void *X, int x_loc,
+                    const void *const *A0, int a0_loc, void *stream, cpd_ctx **out);
+
+/*
+ * cpd_sgd_iters -- run `iters` iterations t, t+1, ... of Alg. 4 / Alg. 5
+ * (mode draw, SKRP-ST-I of Alg. 3, Eq. gradient1, the configured step).
+ * Asynchronous: enqueued on `stream`; t advances by `iters` on the host
+ * immediately. Device-side faults (non-finite values, degenerate
+ * distributions) are recorded and reported by the next synchronising call.
+ * The random draws of iteration t depend only on (seed, t), so splitting a
+ * run into several calls gives bit-identical results.
+ */
+cpd_status cpd_sgd_iters(cpd_ctx *ctx, int64_t iters, void *stream);
+
+/*
+ * cpd_fit -- relative error of Sec. 5.2, Tol = ||[[A]] - X||_F^2 / ||X||_F^2,
+ * by one pass over the whole tensor with FP64 accumulation; fit = 1 - sqrt(Tol).
+ * Either output pointer may be NULL. Synchronises `stream`; returns a
+ * pending device fault (CPD_ENONFINITE, CPD_EDEGENERATE) if one occurred.
+ */
+cpd_status cpd_fit(cpd_ctx *ctx, double *fit, double *tol, void *stream);
+
+/*
+ * cpd_get_factors / cpd_set_factors -- copy the N factor matrices out of / into
+ * the context (the output of Alg. 4 / Alg. 5). `A` is an array of N pointers,
+ * each I_k x R row-major in the factor type, at `loc`. Setting factors
+ * rebuilds every sampling distribution. cpd_get_factors with CPD_HOST
+ * synchronises `stream`.
+ */
+cpd_status cpd_get_factors(cpd_ctx *ctx, void *const *A, int loc, void *stream);
+cpd_status cpd_set_factors(cpd_ctx *ctx, const void *const *A, int loc, void *stream);
+
+/*
+ * cpd_get_adagrad / cpd_set_adagrad -- the FP64 accumulators S^(k)
+ * (I_k x R row-major) of Eq. etaada, for checkpoint and resume.
+ */
+cpd_status cpd_get_adagrad(cpd_ctx *ctx, double *const *S, int loc, void *stream);
+cpd_status cpd_set_adagrad(cpd_ctx *ctx, const double *const *S, int loc, void *stream);
+
+/* cpd_get_iteration / cpd_set_iteration -- the iteration counter t. */
+cpd_status cpd_get_iteration(cpd_ctx *ctx, int64_t *t);
+cpd_status cpd_set_iteration(cpd_ctx *ctx, int64_t t);
+
+/*
+ * cpd_last_sample -- the mini-batch of the most recent iteration (Eq. idx,
+ * Eq. block_lev_prob): its mode n, idx (B x N row-major int32, column n set
+ * to -1) and the fiber probabilities p_f (B doubles). Host outputs; any may
+ * be NULL. Synchronises `stream`. Returns CPD_EINVAL before the first
+ * iteration.
+ */
+cpd_status cpd_last_sample(cpd_ctx *ctx, int32_t *n, int32_t *idx, double *p, void *stream);
+
+/*
+ * cpd_last_gradient -- G^(n) of the most recent iteration (Eq. gradient1),
+ * I_n x R row-major in the factor type, copied to host memory `G`.
+ * Synchronises `stream`.
+ */
+cpd_status cpd_last_gradient(cpd_ctx *ctx, void *G, void *stream);
+
+/*
+ * cpd_sync -- synchronise `stream` and return a pending device fault, if any
+ * (CPD_ENONFINITE, CPD_EDEGENERATE, CPD_ETIMEOUT), clearing it.
+ */
+cpd_status cpd_sync(cpd_ctx *ctx, void *stream);
+
+/*
+ * cpd_profile -- enable (1) or disable (0) per-kernel CUDA-event timing of the
+ * gradient kernel, recorded on the launching stream; cpd_profile_read
+ * returns the number of timed launches and their mean duration (ms) since
+ * the last enable, synchronising `stream`.
+ */
+cpd_status cpd_profile(cpd_ctx *ctx, int enable);
+cpd_status cpd_profile_read(cpd_ctx *ctx, int64_t *launches, double *mean_ms, void *stream);
+
+/*
+ * cpd_describe -- launch configuration chosen for the context, as a
+ * NUL-terminated JSON string in `buf` (at most `len` bytes).
+ */
+cpd_status cpd_describe(cpd_ctx *ctx, char *buf, size_t len);
+
+/* cpd_destroy -- free the context and everything it owns. NULL is a no-op. */
+cpd_status cpd_destroy(cpd_ctx *ctx);
+
+/* Thread-local description of the last failure on this thread. */
+const char *cpd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPD_H */

@@ -1,0 +1,273 @@
+"""Python binding of libcpd (include/cpd.h): argument marshalling only.
+
+The functions below carry the C names and forward to the library; every step
+of an iteration runs in the library's CUDA kernels. Importing this module
+loads ``libcpd.so`` from the package directory and raises if it has not been
+built (``python -m paper_2103_04081_gb300.build``): there is no CPU path.
+
+``Decomposition`` is a small convenience wrapper used by the tests and the
+bench; it keeps torch tensors only as device/host buffers.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcpd.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EDEGENERATE, EAGAIN, EBUSY = range(9)
+HOST, DEVICE = 0, 1
+SAMPLE = {"euclidean": 0, "leverage": 1, "uniform": 2}
+STEP = {"fixed": 0, "adagrad": 1, "decay": 2}
+XDT = {"f64": 0, "f32": 1, "bf16": 2}
+ENGINE = {"auto": 0, "simt": 1, "tensor": 2}
+MAX_MODES = 8
+
+
+class CpdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cpd status {status}: {msg}")
+        self.status = status
+
+
+class cpd_config(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int32), ("R", ctypes.c_int32), ("B", ctypes.c_int32),
+        ("sampling", ctypes.c_int32), ("step", ctypes.c_int32), ("x_dtype", ctypes.c_int32),
+        ("dims", ctypes.c_int64 * MAX_MODES),
+        ("alpha", ctypes.c_double), ("eta", ctypes.c_double), ("b", ctypes.c_double),
+        ("beta", ctypes.c_double), ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("engine", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it with "
+                           "`python -m paper_2103_04081_gb300.build` (there is no CPU fallback)")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    sig = {
+        "cpd_init": [ctypes.POINTER(cpd_config), P, I32, P, I32, P, ctypes.POINTER(P)],
+        "cpd_sgd_iters": [P, I64, P],
+        "cpd_fit": [P, P, P, P],
+        "cpd_get_factors": [P, P, I32, P],
+        "cpd_set_factors": [P, P, I32, P],
+        "cpd_get_adagrad": [P, P, I32, P],
+        "cpd_set_adagrad": [P, P, I32, P],
+        "cpd_get_iteration": [P, ctypes.POINTER(I64)],
+        "cpd_set_iteration": [P, I64],
+        "cpd_last_sample": [P, P, P, P, P],
+        "cpd_last_gradient": [P, P, P],
+        "cpd_sync": [P, P],
+        "cpd_profile": [P, I32],
+        "cpd_profile_read": [P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double), P],
+        "cpd_describe": [P, ctypes.c_char_p, ctypes.c_size_t],
+        "cpd_destroy": [P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.cpd_last_error.argtypes = []
+    lib.cpd_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _check(st: int) -> None:
+    if st != OK:
+        raise CpdError(st, _lib.cpd_last_error().decode())
+
+
+def make_config(dims, R, B, sampling="euclidean", step="adagrad", x_dtype="bf16", alpha=0.1,
+                eta=0.1, b=1e-12, beta=1.0, gamma=1.0, seed=0, engine="auto") -> cpd_config:
+    c = cpd_config()
+    c.N, c.R, c.B = len(dims), int(R), int(B)
+    c.sampling, c.step, c.x_dtype = SAMPLE[sampling], STEP[step], XDT[x_dtype]
+    for k, d in enumerate(dims):
+        c.dims[k] = int(d)
+    c.alpha, c.eta, c.b, c.beta, c.gamma = alpha, eta, b, beta, gamma
+    c.seed = int(seed) & (2**64 - 1)
+    c.engine = ENGINE[engine]
+    c.reserved = 0
+    return c
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptrs(ts) -> ctypes.Array:
+    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+def _loc(t: torch.Tensor) -> int:
+    return DEVICE if t.is_cuda else HOST
+
+
+# ---- C-ABI names -------------------------------------------------------
+
+def cpd_init(cfg: cpd_config, X: torch.Tensor, A0: list, stream=None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(_lib.cpd_init(ctypes.byref(cfg), X.data_ptr(), _loc(X), _ptrs(A0), _loc(A0[0]),
+                         _stream(stream), ctypes.byref(ctx)))
+    return ctx
+
+
+def cpd_sgd_iters(ctx, iters: int, stream=None) -> None:
+    _check(_lib.cpd_sgd_iters(ctx, int(iters), _stream(stream)))
+
+
+def cpd_fit(ctx, stream=None) -> tuple[float, float]:
+    fit, tol = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.cpd_fit(ctx, ctypes.byref(fit), ctypes.byref(tol), _stream(stream)))
+    return fit.value, tol.value
+
+
+def cpd_get_factors(ctx, out: list, stream=None) -> None:
+    _check(_lib.cpd_get_factors(ctx, _ptrs(out), _loc(out[0]), _stream(stream)))
+
+
+def cpd_set_factors(ctx, A: list, stream=None) -> None:
+    _check(_lib.cpd_set_factors(ctx, _ptrs(A), _loc(A[0]), _stream(stream)))
+
+
+def cpd_get_adagrad(ctx, out: list, stream=None) -> None:
+    _check(_lib.cpd_get_adagrad(ctx, _ptrs(out), _loc(out[0]), _stream(stream)))
+
+
+def cpd_set_adagrad(ctx, S: list, stream=None) -> None:
+    _check(_lib.cpd_set_adagrad(ctx, _ptrs(S), _loc(S[0]), _stream(stream)))
+
+
+def cpd_get_iteration(ctx) -> int:
+    t = ctypes.c_int64()
+    _check(_lib.cpd_get_iteration(ctx, ctypes.byref(t)))
+    return t.value
+
+
+def cpd_set_iteration(ctx, t: int) -> None:
+    _check(_lib.cpd_set_iteration(ctx, int(t)))
+
+
+def cpd_last_sample(ctx, N: int, B: int, stream=None):
+    n = ctypes.c_int32()
+    idx = torch.empty(B, N, dtype=torch.int32)
+    p = torch.empty(B, dtype=torch.float64)
+    _check(_lib.cpd_last_sample(ctx, ctypes.byref(n), idx.data_ptr(), p.data_ptr(), _stream(stream)))
+    return n.value, idx, p
+
+
+def cpd_last_gradient(ctx, In: int, R: int, dtype, stream=None) -> torch.Tensor:
+    G = torch.empty(In, R, dtype=dtype)
+    _check(_lib.cpd_last_gradient(ctx, G.data_ptr(), _stream(stream)))
+    return G
+
+
+def cpd_sync(ctx, stream=None) -> None:
+    _check(_lib.cpd_sync(ctx, _stream(stream)))
+
+
+def cpd_profile(ctx, enable: bool) -> None:
+    _check(_lib.cpd_profile(ctx, int(bool(enable))))
+
+
+def cpd_profile_read(ctx, stream=None) -> tuple[int, float]:
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    _check(_lib.cpd_profile_read(ctx, ctypes.byref(n), ctypes.byref(ms), _stream(stream)))
+    return n.value, ms.value
+
+
+def cpd_describe(ctx) -> dict:
+    buf = ctypes.create_string_buffer(1024)
+    _check(_lib.cpd_describe(ctx, buf, 1024))
+    return json.loads(buf.value.decode())
+
+
+def cpd_destroy(ctx) -> None:
+    _check(_lib.cpd_destroy(ctx))
+
+
+# ---- convenience wrapper -------------------------------------------------
+
+class Decomposition:
+    """One context: owns nothing on the Python side but the handle."""
+
+    def __init__(self, X: torch.Tensor, A0: list, stream=None, **cfg):
+        self.dims = tuple(int(d) for d in cfg["dims"])
+        self.R, self.B = int(cfg["R"]), int(cfg["B"])
+        self.x_dtype = cfg.get("x_dtype", "bf16")
+        self.fdtype = torch.float64 if self.x_dtype == "f64" else torch.float32
+        self.cfg = make_config(**cfg)
+        A0 = [a.to(self.fdtype).contiguous() for a in A0]
+        self.ctx = cpd_init(self.cfg, X.contiguous(), A0, stream)
+
+    def sgd_iters(self, iters: int, stream=None) -> None:
+        cpd_sgd_iters(self.ctx, iters, stream)
+
+    def fit(self, stream=None) -> tuple[float, float]:
+        return cpd_fit(self.ctx, stream)
+
+    def factors(self, device="cpu", stream=None) -> list:
+        out = [torch.empty(d, self.R, dtype=self.fdtype, device=device) for d in self.dims]
+        if device != "cpu":
+            out = [o.contiguous() for o in out]
+        cpd_get_factors(self.ctx, out, stream)
+        if device != "cpu":
+            torch.cuda.synchronize()
+        return out
+
+    def set_factors(self, A: list, stream=None) -> None:
+        cpd_set_factors(self.ctx, [a.to(self.fdtype).contiguous() for a in A], stream)
+
+    def adagrad(self) -> list:
+        out = [torch.empty(d, self.R, dtype=torch.float64) for d in self.dims]
+        cpd_get_adagrad(self.ctx, out)
+        return out
+
+    def set_adagrad(self, S: list) -> None:
+        cpd_set_adagrad(self.ctx, [s.to(torch.float64).contiguous() for s in S])
+
+    @property
+    def t(self) -> int:
+        return cpd_get_iteration(self.ctx)
+
+    @t.setter
+    def t(self, v: int) -> None:
+        cpd_set_iteration(self.ctx, v)
+
+    def last_sample(self):
+        return cpd_last_sample(self.ctx, len(self.dims), self.B)
+
+    def last_gradient(self):
+        n, _, _ = self.last_sample()
+        return n, cpd_last_gradient(self.ctx, self.dims[n], self.R, self.fdtype)
+
+    def sync(self) -> None:
+        cpd_sync(self.ctx)
+
+    def describe(self) -> dict:
+        return cpd_describe(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            cpd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,569 @@
+// C ABI of libcpd (declared and documented in include/cpd.h).
+//
+// The context owns every device buffer of one decomposition. Iterations are
+// device-driven (mode and draws follow from the device counter t), so a
+// fixed chunk of iterations is captured once into a CUDA graph and replayed;
+// a remainder runs as plain launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cpd.h"
+#include "cpd_internal.h"
+
+using namespace cpd;
+
+static thread_local std::string g_err;
+
+static cpd_status fail(cpd_status st, const std::string &msg)
+{
+    g_err = msg;
+    return st;
+}
+
+static cpd_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? CPD_ENOMEM : CPD_ECUDA;
+}
+
+#define CK(call)                                                      \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);           \
+    } while (0)
+
+static constexpr int kGraphChunk = 32;
+static constexpr int kProfSlots = 8192;
+
+struct cpd_ctx {
+    cpd_config cfg{};
+    int fbytes = 4;          // factor element size
+    int xbytes = 4;          // tensor element size
+    int device = 0;
+    int engine = kEngineSimt;
+    Problem<float> Pf{};
+    Problem<double> Pd{};
+    std::vector<void *> allocs;
+    int64_t t_host = 0;
+    int grid_grad = 0, grid_upd = 0;
+    size_t smem_grad = 0;
+    double *fit_partials = nullptr, *fit_out = nullptr;
+    double xnorm2 = 0.0;
+    int64_t imax = 0;
+    // graph replay of kGraphChunk iterations
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    // profiling
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
+    int prof_used = 0;
+    bool has_sample = false;
+
+    template <class F>
+    cudaError_t with_problem(F &&f)
+    {
+        return fbytes == 8 ? f(Pd) : f(Pf);
+    }
+};
+
+template <class T>
+static Problem<T> &problem(cpd_ctx *c);
+template <>
+Problem<float> &problem<float>(cpd_ctx *c) { return c->Pf; }
+template <>
+Problem<double> &problem<double>(cpd_ctx *c) { return c->Pd; }
+
+static cudaError_t dmalloc(cpd_ctx *c, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+    if (e == cudaSuccess) c->allocs.push_back(*p);
+    return e;
+}
+
+static void free_all(cpd_ctx *c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (void *p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+}
+
+static int64_t round8(int64_t v) { return (v + 7) / 8 * 8; }
+
+static cpd_status validate(const cpd_config *cfg)
+{
+    if (!cfg) return fail(CPD_EINVAL, "cfg is NULL");
+    if (cfg->N < 3 || cfg->N > CPD_MAX_MODES) return fail(CPD_EINVAL, "N must be in [3, 8]");
+    if (cfg->R < 1 || cfg->R > 256) return fail(CPD_EINVAL, "R must be in [1, 256]");
+    if (cfg->B < 1 || cfg->B > 65536) return fail(CPD_EINVAL, "B must be in [1, 65536]");
+    if (cfg->sampling < 0 || cfg->sampling > 2) return fail(CPD_EINVAL, "unknown sampling");
+    if (cfg->step < 0 || cfg->step > 2) return fail(CPD_EINVAL, "unknown step");
+    if (cfg->x_dtype < 0 || cfg->x_dtype > 2) return fail(CPD_EINVAL, "unknown x_dtype");
+    if (cfg->reserved != 0) return fail(CPD_EINVAL, "reserved must be 0");
+    if (cfg->engine < 0 || cfg->engine > 2) return fail(CPD_EINVAL, "unknown engine");
+    double total = 1.0;
+    for (int k = 0; k < cfg->N; ++k) {
+        if (cfg->dims[k] < 1 || cfg->dims[k] > (int64_t)1 << 31)
+            return fail(CPD_EINVAL, "every dim must be in [1, 2^31]");
+        if (cfg->sampling == CPD_SAMPLE_LEVERAGE && cfg->dims[k] <= cfg->R)
+            return fail(CPD_EINVAL, "leverage sampling needs I_k > R (Def. 3, Lemma 1)");
+        total *= (double)cfg->dims[k];
+    }
+    if (total > 9.0e15) return fail(CPD_EINVAL, "tensor too large");
+    if (cfg->step == CPD_STEP_ADAGRAD && !(cfg->eta > 0.0 && cfg->b >= 0.0))
+        return fail(CPD_EINVAL, "AdaGrad needs eta > 0 and b >= 0");
+    if (cfg->step == CPD_STEP_DECAY && !(cfg->gamma > 0.0))
+        return fail(CPD_EINVAL, "decreasing step needs gamma > 0");
+    if (cfg->engine == kEngineTensor && (cfg->x_dtype != CPD_BF16 || !tc_supported(cfg->R, 128)))
+        return fail(CPD_EINVAL, "tensor-core engine needs BF16 tensors and R <= 64");
+    return CPD_OK;
+}
+
+// Launch tiling: rb rows x fb fibers per CTA, about two waves of CTAs.
+template <class T>
+static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
+{
+    const cpd_config &g = c->cfg;
+    int64_t imax = 0;
+    for (int k = 0; k < g.N; ++k) imax = std::max<int64_t>(imax, g.dims[k]);
+    c->imax = imax;
+    if (c->engine == kEngineTensor) {
+        P.rb = 128;
+        P.fb = 64;
+    } else {
+        P.rb = (int)std::min<int64_t>(64, round8(imax));
+        int64_t pr_max = (imax + P.rb - 1) / P.rb;
+        int64_t target = 2LL * sm_count;
+        int64_t pf = std::max<int64_t>(1, (target + pr_max - 1) / pr_max);
+        pf = std::min<int64_t>(pf, std::max<int64_t>(1, (g.B + 15) / 16));
+        P.fb = (int)((g.B + pf - 1) / pf);
+        while (grad_smem_bytes(P) > 200 * 1024 && (P.fb > 8 || P.rb > 8)) {
+            if (P.fb > 8) P.fb = (P.fb + 1) / 2;
+            else P.rb = std::max(8, P.rb / 2);
+        }
+    }
+    P.pf = (g.B + P.fb - 1) / P.fb;
+    int maxpr = 0;
+    for (int k = 0; k < g.N; ++k) {
+        P.tile[k].pr = (int)((g.dims[k] + P.rb - 1) / P.rb);
+        maxpr = std::max(maxpr, P.tile[k].pr);
+    }
+    c->grid_grad = maxpr * P.pf;
+    const int rpc = std::max(1, kThreads / g.R);
+    c->grid_upd = (int)((imax + rpc - 1) / rpc);
+    c->smem_grad = c->engine == kEngineTensor ? 0 : grad_smem_bytes(P);
+}
+
+template <class T>
+static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *const *A0, int a0_loc,
+                             cudaStream_t s)
+{
+    const cpd_config &g = c->cfg;
+    Problem<T> &P = problem<T>(c);
+    P.N = g.N; P.R = g.R; P.B = g.B; P.sampling = g.sampling; P.step = g.step; P.x_dtype = g.x_dtype;
+    P.alpha = g.alpha; P.eta = g.eta; P.b = g.b; P.beta = g.beta; P.gamma = g.gamma;
+    P.seed = g.seed;
+    for (int k = 0; k < g.N; ++k) {
+        P.dims[k] = g.dims[k];
+        P.ld[k] = round8(g.dims[k]);
+        double J = 1.0;
+        for (int m = 0; m < g.N; ++m)
+            if (m != k) J *= (double)g.dims[m];
+        P.Jn[k] = J;
+    }
+    int sm_count = 152;
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (g.engine == 0)
+        c->engine = (g.x_dtype == CPD_BF16 && tc_supported(g.R, 128) && g.R >= 16) ? kEngineTensor : kEngineSimt;
+    else
+        c->engine = g.engine;
+    choose_tiles(c, P, sm_count);
+
+    // Tensor replicas (one per mode), built from a device copy of X.
+    int64_t total = 1;
+    for (int k = 0; k < g.N; ++k) total *= g.dims[k];
+    const size_t xb = (size_t)c->xbytes;
+    const void *Xd = X;
+    void *staging = nullptr;
+    if (x_loc == CPD_HOST) {
+        CK(cudaMalloc(&staging, total * xb));
+        CK(cudaMemcpyAsync(staging, X, total * xb, cudaMemcpyHostToDevice, s));
+        Xd = staging;
+    }
+    for (int k = 0; k < g.N; ++k) {
+        const size_t bytes = (size_t)(total / g.dims[k]) * P.ld[k] * xb;
+        void *rep;
+        cudaError_t e = dmalloc(c, &rep, bytes);
+        if (e != cudaSuccess) {
+            if (staging) cudaFree(staging);
+            return cuda_fail(e, "replica allocation");
+        }
+        if (P.ld[k] != g.dims[k]) CK(cudaMemsetAsync(rep, 0, bytes, s));
+        e = launch_build_replica(Xd, rep, (int)xb, g.N, g.dims, k, P.ld[k], s);
+        if (e != cudaSuccess) {
+            if (staging) cudaFree(staging);
+            return cuda_fail(e, "replica build");
+        }
+        P.rep[k] = rep;
+    }
+    if (staging) {
+        CK(cudaStreamSynchronize(s));
+        CK(cudaFree(staging));
+    }
+
+    // Factors, AdaGrad state, distributions.
+    for (int k = 0; k < g.N; ++k) {
+        const size_t fb = (size_t)g.dims[k] * g.R;
+        void *a, *S, *w, *cdf;
+        CK(dmalloc(c, &a, fb * sizeof(T)));
+        CK(dmalloc(c, &S, fb * sizeof(double)));
+        CK(dmalloc(c, &w, g.dims[k] * sizeof(double)));
+        CK(dmalloc(c, &cdf, g.dims[k] * sizeof(double)));
+        CK(cudaMemcpyAsync(a, A0[k], fb * sizeof(T),
+                           a0_loc == CPD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(S, 0, fb * sizeof(double), s));
+        P.A[k] = (T *)a; P.S[k] = (double *)S; P.w[k] = (double *)w; P.cdf[k] = (double *)cdf;
+    }
+    void *p;
+    CK(dmalloc(c, &p, sizeof(long long)));  P.t_dev = (long long *)p;
+    CK(dmalloc(c, &p, sizeof(int)));        P.n_last = (int *)p;
+    CK(dmalloc(c, &p, (size_t)g.B * g.N * sizeof(int)));  P.idx = (int *)p;
+    CK(dmalloc(c, &p, (size_t)g.B * sizeof(double)));     P.p = (double *)p;
+    CK(dmalloc(c, &p, (size_t)P.pf * g.R * c->imax * sizeof(T)));  P.part = (T *)p;
+    CK(dmalloc(c, &p, (size_t)(P.pf + 1) * g.R * g.R * sizeof(float)));  P.hpart = (float *)p;
+    CK(dmalloc(c, &p, (size_t)c->imax * g.R * sizeof(T)));  P.G = (T *)p;
+    CK(dmalloc(c, &p, (size_t)(c->imax / 31 + 64) * sizeof(double)));  P.scan_scratch = (double *)p;
+    CK(dmalloc(c, &p, (size_t)(2 * g.R * g.R + g.R + 8) * sizeof(double)));  P.lev_L = (double *)p;
+    CK(dmalloc(c, &p, sizeof(int)));  P.status = (int *)p;
+    CK(dmalloc(c, &p, 16 * sizeof(unsigned)));  P.counters = (unsigned *)p;
+    CK(dmalloc(c, &p, (size_t)fit_blocks() * sizeof(double)));  c->fit_partials = (double *)p;
+    CK(dmalloc(c, &p, sizeof(double)));  c->fit_out = (double *)p;
+    CK(cudaMemsetAsync(P.t_dev, 0, sizeof(long long), s));
+    CK(cudaMemsetAsync(P.n_last, 0xff, sizeof(int), s));
+    CK(cudaMemsetAsync(P.status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(P.counters, 0, 16 * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(P.G, 0, (size_t)c->imax * g.R * sizeof(T), s));
+    for (int k = 0; k < g.N; ++k) CK(launch_refresh_mode(P, k, s));
+    CK(launch_fit(P, c->fit_partials, fit_blocks(), c->fit_out, s, 1));
+    CK(cudaMemcpyAsync(&c->xnorm2, c->fit_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int st = 0;
+    CK(cudaMemcpy(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & kStDegenerate) return fail(CPD_EDEGENERATE, "a sampling distribution has no mass or a "
+                                                         "leverage Gram matrix is singular");
+    if (!(c->xnorm2 > 0.0)) return fail(CPD_EINVAL, "X is identically zero");
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_init(const cpd_config *cfg, const void *X, int x_loc, const void *const *A0,
+                               int a0_loc, void *stream, cpd_ctx **out)
+{
+    cpd_status st = validate(cfg);
+    if (st != CPD_OK) return st;
+    if (!X || !A0 || !out) return fail(CPD_EINVAL, "NULL argument");
+    for (int k = 0; k < cfg->N; ++k)
+        if (!A0[k]) return fail(CPD_EINVAL, "NULL factor pointer");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(CPD_ECUDA, "libcpd is built for sm_103a (GB300); this device is sm_" +
+                                   std::to_string(prop.major) + std::to_string(prop.minor));
+    cpd_ctx *c = new cpd_ctx();
+    c->cfg = *cfg;
+    c->device = dev;
+    c->fbytes = cfg->x_dtype == CPD_F64 ? 8 : 4;
+    c->xbytes = cfg->x_dtype == CPD_F64 ? 8 : (cfg->x_dtype == CPD_F32 ? 4 : 2);
+    cudaStream_t s = (cudaStream_t)stream;
+    st = c->fbytes == 8 ? init_typed<double>(c, X, x_loc, A0, a0_loc, s)
+                        : init_typed<float>(c, X, x_loc, A0, a0_loc, s);
+    if (st != CPD_OK) {
+        cudaStreamSynchronize(s);
+        free_all(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return CPD_OK;
+}
+
+template <class T>
+static cudaError_t run_plain(cpd_ctx *c, int64_t iters, cudaStream_t s)
+{
+    Problem<T> &P = problem<T>(c);
+    for (int64_t q = 0; q < iters; ++q) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c->profiling && c->prof_used < kProfSlots) {
+            e0 = c->ev[2 * c->prof_used];
+            e1 = c->ev[2 * c->prof_used + 1];
+            ++c->prof_used;
+        }
+        cudaError_t e = launch_iteration(P, c->grid_grad, c->grid_upd, c->smem_grad, s, c->engine, e0, e1);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <class T>
+static cudaError_t run_graph(cpd_ctx *c, int64_t chunks, cudaStream_t s)
+{
+    if (!c->graph || c->graph_stream != s) {
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+        cudaStream_t cap;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        cudaGraph_t g;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            Problem<T> &P = problem<T>(c);
+            for (int q = 0; q < kGraphChunk && e == cudaSuccess; ++q)
+                e = launch_iteration(P, c->grid_grad, c->grid_upd, c->smem_grad, cap, c->engine, nullptr,
+                                     nullptr);
+            cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&c->graph, g, 0);
+            cudaGraphDestroy(g);
+        }
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) return e;
+        c->graph_stream = s;
+    }
+    for (int64_t q = 0; q < chunks; ++q) {
+        cudaError_t e = cudaGraphLaunch(c->graph, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+extern "C" cpd_status cpd_sgd_iters(cpd_ctx *c, int64_t iters, void *stream)
+{
+    if (!c || iters < 0) return fail(CPD_EINVAL, "bad context or iteration count");
+    if (iters == 0) return CPD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (c->profiling) {
+        e = c->fbytes == 8 ? run_plain<double>(c, iters, s) : run_plain<float>(c, iters, s);
+    } else {
+        const int64_t chunks = iters / kGraphChunk, rem = iters % kGraphChunk;
+        e = cudaSuccess;
+        if (chunks) e = c->fbytes == 8 ? run_graph<double>(c, chunks, s) : run_graph<float>(c, chunks, s);
+        if (e == cudaSuccess && rem)
+            e = c->fbytes == 8 ? run_plain<double>(c, rem, s) : run_plain<float>(c, rem, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cpd_sgd_iters launch");
+    c->t_host += iters;
+    c->has_sample = true;
+    return CPD_OK;
+}
+
+static cpd_status read_status(cpd_ctx *c, cudaStream_t s)
+{
+    int *dst = c->fbytes == 8 ? c->Pd.status : c->Pf.status;
+    int st = 0;
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(&st, dst, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) CK(cudaMemset(dst, 0, sizeof(int)));
+    if (st & kStNonFinite) return fail(CPD_ENONFINITE, "a gradient or factor entry became NaN/Inf");
+    if (st & kStDegenerate)
+        return fail(CPD_EDEGENERATE, "a sampling distribution lost its mass or a Gram matrix is singular");
+    if (st & kStTimeout) return fail(CPD_ETIMEOUT, "a bounded device wait gave up");
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_sync(cpd_ctx *c, void *stream)
+{
+    if (!c) return fail(CPD_EINVAL, "NULL context");
+    return read_status(c, (cudaStream_t)stream);
+}
+
+extern "C" cpd_status cpd_fit(cpd_ctx *c, double *fit, double *tol, void *stream)
+{
+    if (!c) return fail(CPD_EINVAL, "NULL context");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = c->with_problem([&](auto &P) {
+        return launch_fit(P, c->fit_partials, fit_blocks(), c->fit_out, s, 0);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "fit launch");
+    double res = 0.0;
+    CK(cudaMemcpyAsync(&res, c->fit_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    cpd_status st = read_status(c, s);
+    const double tl = res / c->xnorm2;
+    if (tol) *tol = tl;
+    if (fit) *fit = 1.0 - std::sqrt(tl);
+    return st;
+}
+
+static cudaMemcpyKind kind_out(int loc) { return loc == CPD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
+static cudaMemcpyKind kind_in(int loc) { return loc == CPD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+
+extern "C" cpd_status cpd_get_factors(cpd_ctx *c, void *const *A, int loc, void *stream)
+{
+    if (!c || !A) return fail(CPD_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < c->cfg.N; ++k) {
+        if (!A[k]) return fail(CPD_EINVAL, "NULL factor pointer");
+        const void *src = c->fbytes == 8 ? (const void *)c->Pd.A[k] : (const void *)c->Pf.A[k];
+        CK(cudaMemcpyAsync(A[k], src, (size_t)c->cfg.dims[k] * c->cfg.R * c->fbytes, kind_out(loc), s));
+    }
+    if (loc == CPD_HOST) CK(cudaStreamSynchronize(s));
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_set_factors(cpd_ctx *c, const void *const *A, int loc, void *stream)
+{
+    if (!c || !A) return fail(CPD_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < c->cfg.N; ++k) {
+        if (!A[k]) return fail(CPD_EINVAL, "NULL factor pointer");
+        void *dst = c->fbytes == 8 ? (void *)c->Pd.A[k] : (void *)c->Pf.A[k];
+        CK(cudaMemcpyAsync(dst, A[k], (size_t)c->cfg.dims[k] * c->cfg.R * c->fbytes, kind_in(loc), s));
+    }
+    for (int k = 0; k < c->cfg.N; ++k) {
+        cudaError_t e = c->with_problem([&](auto &P) { return launch_refresh_mode(P, k, s); });
+        if (e != cudaSuccess) return cuda_fail(e, "distribution refresh");
+    }
+    return read_status(c, s);
+}
+
+extern "C" cpd_status cpd_get_adagrad(cpd_ctx *c, double *const *S, int loc, void *stream)
+{
+    if (!c || !S) return fail(CPD_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < c->cfg.N; ++k) {
+        const double *src = c->fbytes == 8 ? c->Pd.S[k] : c->Pf.S[k];
+        CK(cudaMemcpyAsync(S[k], src, (size_t)c->cfg.dims[k] * c->cfg.R * 8, kind_out(loc), s));
+    }
+    if (loc == CPD_HOST) CK(cudaStreamSynchronize(s));
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_set_adagrad(cpd_ctx *c, const double *const *S, int loc, void *stream)
+{
+    if (!c || !S) return fail(CPD_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < c->cfg.N; ++k) {
+        double *dst = c->fbytes == 8 ? c->Pd.S[k] : c->Pf.S[k];
+        CK(cudaMemcpyAsync(dst, S[k], (size_t)c->cfg.dims[k] * c->cfg.R * 8, kind_in(loc), s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_get_iteration(cpd_ctx *c, int64_t *t)
+{
+    if (!c || !t) return fail(CPD_EINVAL, "NULL argument");
+    *t = c->t_host;
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_set_iteration(cpd_ctx *c, int64_t t)
+{
+    if (!c || t < 0) return fail(CPD_EINVAL, "bad argument");
+    long long v = (long long)t;
+    long long *dst = c->fbytes == 8 ? c->Pd.t_dev : c->Pf.t_dev;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(dst, &v, sizeof v, cudaMemcpyHostToDevice));
+    c->t_host = t;
+    c->has_sample = false;
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_last_sample(cpd_ctx *c, int32_t *n, int32_t *idx, double *p, void *stream)
+{
+    if (!c) return fail(CPD_EINVAL, "NULL context");
+    if (!c->has_sample) return fail(CPD_EINVAL, "no iteration has run since the counter was set");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool d = c->fbytes == 8;
+    if (n) CK(cudaMemcpyAsync(n, d ? c->Pd.n_last : c->Pf.n_last, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (idx)
+        CK(cudaMemcpyAsync(idx, d ? c->Pd.idx : c->Pf.idx, (size_t)c->cfg.B * c->cfg.N * sizeof(int),
+                           cudaMemcpyDeviceToHost, s));
+    if (p)
+        CK(cudaMemcpyAsync(p, d ? c->Pd.p : c->Pf.p, (size_t)c->cfg.B * sizeof(double),
+                           cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_last_gradient(cpd_ctx *c, void *G, void *stream)
+{
+    if (!c || !G) return fail(CPD_EINVAL, "NULL argument");
+    if (!c->has_sample) return fail(CPD_EINVAL, "no iteration has run since the counter was set");
+    cudaStream_t s = (cudaStream_t)stream;
+    int n = 0;
+    const bool d = c->fbytes == 8;
+    CK(cudaMemcpyAsync(&n, d ? c->Pd.n_last : c->Pf.n_last, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (n < 0 || n >= c->cfg.N) return fail(CPD_EINVAL, "no completed iteration");
+    const void *src = d ? (const void *)c->Pd.G : (const void *)c->Pf.G;
+    CK(cudaMemcpyAsync(G, src, (size_t)c->cfg.dims[n] * c->cfg.R * c->fbytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_profile(cpd_ctx *c, int enable)
+{
+    if (!c) return fail(CPD_EINVAL, "NULL context");
+    if (enable && c->ev.empty()) {
+        c->ev.resize(2 * kProfSlots);
+        for (auto &e : c->ev) CK(cudaEventCreate(&e));
+    }
+    c->profiling = enable != 0;
+    c->prof_used = 0;
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_profile_read(cpd_ctx *c, int64_t *launches, double *mean_ms, void *stream)
+{
+    if (!c) return fail(CPD_EINVAL, "NULL context");
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    double tot = 0.0;
+    for (int q = 0; q < c->prof_used; ++q) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[2 * q], c->ev[2 * q + 1]));
+        tot += ms;
+    }
+    if (launches) *launches = c->prof_used;
+    if (mean_ms) *mean_ms = c->prof_used ? tot / c->prof_used : 0.0;
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_describe(cpd_ctx *c, char *buf, size_t len)
+{
+    if (!c || !buf || len == 0) return fail(CPD_EINVAL, "bad argument");
+    const int rb = c->fbytes == 8 ? c->Pd.rb : c->Pf.rb;
+    const int fb = c->fbytes == 8 ? c->Pd.fb : c->Pf.fb;
+    const int pf = c->fbytes == 8 ? c->Pd.pf : c->Pf.pf;
+    std::snprintf(buf, len,
+                  "{\"engine\": \"%s\", \"rows_per_cta\": %d, \"fibers_per_cta\": %d, \"fiber_groups\": %d, "
+                  "\"grad_grid\": %d, \"update_grid\": %d, \"grad_smem\": %zu, \"graph_chunk\": %d, "
+                  "\"xnorm2\": %.17g}",
+                  c->engine == kEngineTensor ? "tensor" : "simt", rb, fb, pf, c->grid_grad, c->grid_upd,
+                  c->smem_grad, kGraphChunk, c->xnorm2);
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_destroy(cpd_ctx *c)
+{
+    if (!c) return CPD_OK;
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+    return CPD_OK;
+}
+
+extern "C" const char *cpd_last_error(void) { return g_err.c_str(); }

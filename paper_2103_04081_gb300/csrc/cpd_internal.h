@@ -1,0 +1,90 @@
+// Internal declarations of libcpd shared by its translation units.
+//
+// Device-resident state of one decomposition (all of it lives in HBM for the
+// whole run; the host only launches work):
+//   rep[k]   mode-k-major replica of X: fiber j of the mode-k unfolding
+//            (Eq. map numbering) is contiguous at rep[k] + j * ld[k], so
+//            every sampled fiber is one contiguous, 16-byte-aligned run.
+//   A[k]     factor A^(k), row-major I_k x R, in the factor type T.
+//   S[k]     AdaGrad accumulators (FP64), Eq. etaada.
+//   w[k]     FP64 row weights (squared row norms or leverage scores).
+//   cdf[k]   FP64 inclusive prefix sums of w[k] in the canonical order.
+//   t_dev    the iteration counter; every kernel derives the mode n and the
+//            random draws of its iteration from (seed, *t_dev), so captured
+//            launches replay correctly.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cpd.h"
+
+namespace cpd {
+
+constexpr int kMaxModes = CPD_MAX_MODES;
+constexpr int kThreads = 256;
+
+// Device status bits, OR-ed into Problem::status and read at sync points.
+enum : int { kStNonFinite = 1, kStDegenerate = 2, kStTimeout = 4 };
+
+// Gradient engines.
+enum : int { kEngineSimt = 1, kEngineTensor = 2 };
+
+// Launch tiling of the gradient kernel for one mode n: CTA (gr, gf) handles
+// rows [gr*rb, gr*rb+rb) of A^(n) and fibers [gf*fb, gf*fb+fb) of the batch.
+struct ModeTile {
+    int pr;  // row tiles  = ceil(I_n / rb)
+};
+
+template <class T>
+struct Problem {
+    int N, R, B, sampling, step, x_dtype;
+    int rb, fb, pf;           // rows per CTA, fibers per CTA, fiber groups
+    int64_t dims[kMaxModes];
+    int64_t ld[kMaxModes];    // fiber stride of replica k (elements, multiple of 8)
+    double Jn[kMaxModes];     // J_n = prod_{k != n} I_k, as a double
+    ModeTile tile[kMaxModes];
+    const void *rep[kMaxModes];
+    T *A[kMaxModes];
+    double *S[kMaxModes];
+    double *w[kMaxModes];
+    double *cdf[kMaxModes];
+    double alpha, eta, b, beta, gamma;
+    unsigned long long seed;
+    long long *t_dev;         // iteration counter
+    int *n_last;              // mode of the last completed iteration
+    int *idx;                 // B x N, last batch (column n = -1)
+    double *p;                // B, last batch probabilities
+    T *part;                  // gradient partials [pf][R][I_n] (SIMT engine) or M partials
+    float *hpart;             // H partials [pf][R][R] (tensor engine)
+    T *G;                     // last gradient, I_n x R row-major
+    double *scan_scratch;     // canonical-scan level buffers
+    double *lev_L;            // leverage: Cholesky factor R x R + inverse pivots R
+    int *status;              // kSt* bits
+    unsigned *counters;       // last-block arrival counters (zero between launches)
+};
+
+// Launchers (cpd_kernels.cu). Every launcher enqueues on `stream` and
+// returns the launch error, if any.
+template <class T>
+cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd,
+                             size_t smem_grad, cudaStream_t stream, int engine,
+                             cudaEvent_t ev0, cudaEvent_t ev1);
+template <class T>
+cudaError_t launch_refresh_mode(const Problem<T> &P, int k, cudaStream_t stream);
+template <class T>
+cudaError_t launch_fit(const Problem<T> &P, double *partials, int nblocks,
+                       double *out2, cudaStream_t stream, int want_xnorm);
+cudaError_t launch_build_replica(const void *X, void *rep, int esize, int N,
+                                 const int64_t *dims, int n, int64_t ld,
+                                 cudaStream_t stream);
+template <class T>
+size_t grad_smem_bytes(const Problem<T> &P);
+int fit_blocks();
+
+// Tensor-core gradient engine (cpd_tc.cu).
+bool tc_supported(int R, int rb);
+cudaError_t launch_grad_tc(const Problem<float> &P, int grid, cudaStream_t stream);
+size_t tc_smem_bytes(const Problem<float> &P);
+
+}  // namespace cpd

@@ -1,0 +1,674 @@
+// Kernels of one BrawsCPD / AdawsCPD iteration (Alg. 4 / Alg. 5) and the
+// full-tensor relative error of Sec. 5.2.
+//
+// Per iteration (the mode n and all draws follow from (seed, *t_dev)):
+//   k_grad_simt   sampling (Alg. 3) + sampled KRP rows (Alg. 1, Eq. index_map)
+//                 + fiber gather (Alg. 1, Eq. map) + weighted gradient partials
+//                 (Eq. gradient1), split over (row tile, fiber group) CTAs;
+//   k_update      fixed-order reduction of the partials, the step
+//                 (Eq. proposed / Thm 9 / Eq. etaada-Aada), new Euclidean row
+//                 weights, and -- in the last CTA to finish -- the canonical
+//                 CDF rebuild of mode n and t += 1;
+//   k_gram, k_lev_rows   (leverage sampling only) Gram + Cholesky and the new
+//                 leverage scores of mode n, then the CDF rebuild and t += 1.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cpd_device.cuh"
+#include "cpd_internal.h"
+
+namespace cpd {
+
+namespace {
+
+// Shared-memory carve-up of the gradient kernel (all offsets 16-byte aligned).
+template <class T>
+struct GradSmem {
+    size_t idx, jcol, s, z, At, x, total;
+    __host__ __device__ GradSmem(int N, int R, int rb, int fb)
+    {
+        size_t o = 0;
+        idx = o;  o += align_up_h((size_t)fb * N * sizeof(int), 16);
+        jcol = o; o += align_up_h((size_t)fb * sizeof(long long), 16);
+        s = o;    o += align_up_h((size_t)fb * sizeof(T), 16);
+        z = o;    o += align_up_h((size_t)fb * R * sizeof(T), 16);
+        At = o;   o += align_up_h((size_t)R * rb * sizeof(T), 16);
+        x = o;    o += align_up_h((size_t)fb * rb * sizeof(T), 16);
+        total = o;
+    }
+    __host__ __device__ static size_t align_up_h(size_t v, size_t a) { return (v + a - 1) / a * a; }
+};
+
+// Draw the (N-1) x nf indices of this CTA's fibers (Alg. 3 "Randsample(I_k,
+// |F_n|, true, p_k)"): warps take 32-fiber chunks per mode k != n and run the
+// warp-cooperative search on cdf[k].
+template <class T>
+__device__ void draw_indices(const Problem<T> &P, long long t, int n, int f0, int nf, int *sidx)
+{
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const int chunks = (nf + 31) / 32;
+    for (int job = warp; job < chunks * P.N; job += nwarps) {
+        const int k = job / chunks, ch = job % chunks;
+        const int fl = ch * 32 + lane;
+        const bool act = fl < nf;
+        if (k == n) {
+            if (act) sidx[fl * P.N + k] = -1;
+            continue;
+        }
+        const long long Ik = P.dims[k];
+        unsigned long long x = act ? fiber_word(P.seed, t, (long long)(f0 + fl), k) : 0ULL;
+        long long i;
+        if (P.sampling == CPD_SAMPLE_UNIFORM) {
+            i = (long long)__umul64hi(x, (unsigned long long)Ik);
+        } else {
+            const double *c = P.cdf[k];
+            const double target = __dmul_rn(u53(x), __ldg(c + (Ik - 1)));
+            i = warp_search_cdf(c, Ik, target, act);
+        }
+        if (act) sidx[fl * P.N + k] = (int)i;
+    }
+}
+
+// p_f (Eq. block_lev_prob, product in ascending k) and the weight
+// s_f = 1 / (B J_n p_f) of the fiber's term in Eq. gradient1.
+template <class T>
+__device__ __forceinline__ double fiber_prob(const Problem<T> &P, int n, const int *row)
+{
+    double p = 1.0;
+    for (int k = 0; k < P.N; ++k) {
+        if (k == n) continue;
+        if (P.sampling == CPD_SAMPLE_UNIFORM) {
+            p = __dmul_rn(p, __ddiv_rn(1.0, (double)P.dims[k]));
+        } else {
+            const double W = __ldg(P.cdf[k] + (P.dims[k] - 1));
+            p = __dmul_rn(p, __ddiv_rn(__ldg(P.w[k] + row[k]), W));
+        }
+    }
+    return p;
+}
+
+template <class XT, class T>
+__device__ __forceinline__ T load_x(const XT *p) { return (T)to_float<XT>(*p); }
+template <>
+__device__ __forceinline__ double load_x<double, double>(const double *p) { return *p; }
+
+// Copy rows [r0, r0+rows) of fiber j (contiguous in the mode-n replica) into
+// shared memory as T, with 16-byte vector loads (rows are padded to 8).
+template <class XT, class T>
+__device__ __forceinline__ void gather_rows(const XT *__restrict__ rep, long long ld,
+                                            const long long *jcol, int nf, int r0, int rows,
+                                            int rb, T *sx)
+{
+    constexpr int V = 16 / sizeof(XT);
+    const int nv = (rows + V - 1) / V;
+    for (int e = threadIdx.x; e < nf * nv; e += blockDim.x) {
+        const int f = e / nv, q = e % nv;
+        const XT *src = rep + jcol[f] * ld + r0 + q * V;
+        const uint4 raw = __ldg(reinterpret_cast<const uint4 *>(src));
+        const XT *vals = reinterpret_cast<const XT *>(&raw);
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int i = q * V + u;
+            if (i < rows) sx[f * rb + i] = load_x<XT, T>(vals + u);
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Gradient partials, residual form. For this CTA's rows i and fibers f:
+//   res_if = s_f * (A^(n)(i,:) . z_f - x_f(i))          (one row of A Zs^T - Xs, weighted)
+//   part[gf][r][i] = sum_f res_if * z_f(r)
+// so that sum over fiber groups gives (A Zs^T D Zs - Xs D Zs) / (B J_n),
+// Eq. gradient1, without the cancellation of forming the two products apart.
+// ---------------------------------------------------------------------------
+template <class T, class XT>
+__global__ void __launch_bounds__(kThreads) k_grad_simt(const Problem<T> P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const long long t = *P.t_dev;
+    const int N = P.N, R = P.R, rb = P.rb, fb = P.fb;
+    const int n = mode_draw(P.seed, t, N);
+    const int pr = P.tile[n].pr;
+    const int gr = blockIdx.x % pr, gf = blockIdx.x / pr;
+    if (gf >= P.pf) return;
+    const long long In = P.dims[n];
+    const int r0 = gr * rb;
+    const int rows = (int)((In - r0) < rb ? (In - r0) : rb);
+    const int f0 = gf * fb;
+    const int nf = (P.B - f0) < fb ? (P.B - f0) : fb;
+
+    const GradSmem<T> L(N, R, rb, fb);
+    int *sidx = reinterpret_cast<int *>(smem + L.idx);
+    long long *jcol = reinterpret_cast<long long *>(smem + L.jcol);
+    T *ss = reinterpret_cast<T *>(smem + L.s);
+    T *sz = reinterpret_cast<T *>(smem + L.z);
+    T *sAt = reinterpret_cast<T *>(smem + L.At);
+    T *sx = reinterpret_cast<T *>(smem + L.x);
+
+    // 1. draws of Alg. 3
+    draw_indices(P, t, n, f0, nf, sidx);
+    // rows of A^(n) for the residual, transposed (conflict-free reads)
+    const T *An = P.A[n];
+    for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
+        const int i = e / R, r = e % R;
+        sAt[r * rb + i] = An[(long long)(r0 + i) * R + r];
+    }
+    __syncthreads();
+
+    // 2. fiber column j (Eq. map), probability p_f and weight s_f
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+        const int *row = sidx + f * N;
+        long long j = 0, Jp = 1;
+        for (int k = 0; k < N; ++k) {
+            if (k == n) continue;
+            j += (long long)row[k] * Jp;
+            Jp *= P.dims[k];
+        }
+        jcol[f] = j;
+        const double p = fiber_prob(P, n, row);
+        ss[f] = (T)__ddiv_rn(1.0, __dmul_rn(__dmul_rn((double)P.B, P.Jn[n]), p));
+        if (gr == 0) {
+            P.p[f0 + f] = p;
+            for (int k = 0; k < N; ++k) P.idx[(long long)(f0 + f) * N + k] = row[k];
+        }
+    }
+    // 3. sampled KRP rows z_f = Hadamard product of A^(k)(i_k,:), k != n (Alg. 1)
+    for (int e = threadIdx.x; e < nf * R; e += blockDim.x) {
+        const int f = e / R, r = e % R;
+        const int *row = sidx + f * N;
+        T z = (T)1;
+        for (int k = 0; k < N; ++k) {
+            if (k == n) continue;
+            z = z * P.A[k][(long long)row[k] * R + r];
+        }
+        sz[f * R + r] = z;
+    }
+    __syncthreads();
+
+    // 4. fiber gather from the mode-n replica (Alg. 1, X_(n)(:, F_n))
+    gather_rows<XT, T>(reinterpret_cast<const XT *>(P.rep[n]), P.ld[n], jcol, nf, r0, rows, rb, sx);
+    __syncthreads();
+
+    // 5. weighted residuals
+    for (int e = threadIdx.x; e < nf * rows; e += blockDim.x) {
+        const int f = e / rows, i = e % rows;
+        T acc = (T)0;
+        for (int r = 0; r < R; ++r) acc += sAt[r * rb + i] * sz[f * R + r];
+        sx[f * rb + i] = ss[f] * (acc - sx[f * rb + i]);
+    }
+    __syncthreads();
+
+    // 6. partial gradient of this fiber group, layout [gf][r][i]
+    T *out = P.part + (long long)gf * R * In;
+    for (int e = threadIdx.x; e < R * rows; e += blockDim.x) {
+        const int r = e / rows, i = e % rows;
+        T acc = (T)0;
+        for (int f = 0; f < nf; ++f) acc += sx[f * rb + i] * sz[f * R + r];
+        out[(long long)r * In + r0 + i] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reduction + step. CTA b owns rows [b*rpc, b*rpc+rpc) of A^(n).
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ double row_weight_euclid(const T *row, int R)
+{
+    double acc = 0.0;
+    for (int r = 0; r < R; ++r) acc = __fma_rn((double)row[r], (double)row[r], acc);
+    return acc;
+}
+
+// Rebuild cdf[k] from w[k] (one CTA); a distribution without mass is flagged.
+template <class T>
+__device__ void finish_cdf(const Problem<T> &P, int k)
+{
+    const long long Ik = P.dims[k];
+    block_scan32(P.w[k], Ik, P.cdf[k], P.scan_scratch);
+    if (threadIdx.x == 0) {
+        const double W = P.cdf[k][Ik - 1];
+        if (!(W > 0.0) || !isfinite(W)) atomicOr(P.status, kStDegenerate);
+    }
+}
+
+// Arrival counter: true in exactly one CTA, the last one to finish.
+__device__ __forceinline__ bool last_block(unsigned *counter)
+{
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(counter, 1u);
+        s_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P, int tensor_engine)
+{
+    __shared__ T s_new[kThreads];
+    __shared__ float sH[64 * 64];
+    const long long t = *P.t_dev;
+    const int N = P.N, R = P.R;
+    const int n = mode_draw(P.seed, t, N);
+    const long long In = P.dims[n];
+    const int rpc = kThreads / R > 0 ? kThreads / R : 1;
+    const int li = threadIdx.x / R, r = threadIdx.x % R;
+    const long long i = (long long)blockIdx.x * rpc + li;
+    const bool act = li < rpc && i < In;
+    T *An = P.A[n];
+    if (tensor_engine) {
+        // H = Z_S^T D Z_S, already reduced over fiber groups (R <= 64).
+        for (int e = threadIdx.x; e < R * R; e += blockDim.x) sH[e] = __ldcg(P.hpart + e);
+        __syncthreads();
+    }
+    if (act) {
+        T g = (T)0;
+        if (!tensor_engine) {
+            for (int q = 0; q < P.pf; ++q) g += P.part[((long long)q * R + r) * In + i];
+        } else {
+            // G = (A H - M) / (B J_n) with M, H reduced over fiber groups.
+            float m = 0.f;
+            for (int q = 0; q < P.pf; ++q) m += (float)P.part[((long long)q * R + r) * In + i];
+            float ah = 0.f;
+            for (int s = 0; s < R; ++s) ah += (float)An[i * R + s] * sH[s * R + r];
+            g = (T)(ah - m);
+        }
+        P.G[i * R + r] = g;
+        double a = (double)An[i * R + r];
+        if (P.step == CPD_STEP_ADAGRAD) {
+            double *Sp = P.S[n] + i * R + r;
+            const double gd = (double)g;
+            const double S = __fma_rn(gd, gd, *Sp);
+            *Sp = S;
+            a = a - P.eta * gd / sqrt(P.b + S);
+        } else {
+            const double alpha = (P.step == CPD_STEP_DECAY) ? P.beta / ((double)t + P.gamma) : P.alpha;
+            a = a - alpha * (double)g;
+        }
+        const T an = (T)a;
+        if (!isfinite((double)an) || !isfinite((double)g)) atomicOr(P.status, kStNonFinite);
+        An[i * R + r] = an;
+        s_new[threadIdx.x] = an;
+    }
+    __syncthreads();
+    if (P.sampling == CPD_SAMPLE_EUCLIDEAN && act && r == 0)
+        P.w[n][i] = row_weight_euclid(s_new + li * R, R);
+    if (!last_block(P.counters)) return;
+    if (P.sampling == CPD_SAMPLE_EUCLIDEAN) finish_cdf(P, n);
+    if (threadIdx.x == 0) {
+        P.counters[0] = 0;
+        if (P.sampling != CPD_SAMPLE_LEVERAGE) {
+            *P.n_last = n;
+            *P.t_dev = t + 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Leverage scores (Def. 3) in the canonical order: one warp per Gram entry
+// (32 strided partials, shuffle-down tree), the last CTA factors the Gram
+// matrix (left-looking Cholesky, k ascending) into P.lev_L.
+// k_mode < 0: the mode of the current iteration; else that mode.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mode)
+{
+    const long long t = *P.t_dev;
+    const int k = k_mode >= 0 ? k_mode : mode_draw(P.seed, t, P.N);
+    const int R = P.R;
+    const long long I = P.dims[k];
+    const T *A = P.A[k];
+    double *g = P.lev_L + R * R + R;  // Gram scratch after L and inv
+    const int lane = threadIdx.x & 31;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int npairs = R * (R + 1) / 2;
+    for (int pr = warp_global; pr < npairs; pr += (gridDim.x * blockDim.x) >> 5) {
+        int r = 0, rem = pr;
+        while (rem >= R - r) { rem -= R - r; ++r; }
+        const int s = r + rem;
+        double acc = 0.0;
+        for (long long i = lane; i < I; i += 32)
+            acc = __fma_rn((double)A[i * R + r], (double)A[i * R + s], acc);
+        for (int off = 16; off >= 1; off >>= 1)
+            acc = __dadd_rn(acc, __shfl_down_sync(0xffffffffu, acc, off));
+        if (lane == 0) {
+            g[r * R + s] = acc;
+            g[s * R + r] = acc;
+        }
+    }
+    if (!last_block(P.counters + 1)) return;
+    double *Lm = P.lev_L, *inv = P.lev_L + R * R;
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int j = 0; j < R; ++j) {
+        if (threadIdx.x == 0) {
+            double d = __ldcg(g + j * R + j);
+            for (int q = 0; q < j; ++q) d = __fma_rn(-Lm[j * R + q], Lm[j * R + q], d);
+            if (!(d > 0x1.0p-40 * __ldcg(g + j * R + j))) {
+                s_bad = 1;
+                d = 1.0;
+            }
+            Lm[j * R + j] = __dsqrt_rn(d);
+            inv[j] = __ddiv_rn(1.0, Lm[j * R + j]);
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) {
+            double v = __ldcg(g + i * R + j);
+            for (int q = 0; q < j; ++q) v = __fma_rn(-Lm[i * R + q], Lm[j * R + q], v);
+            Lm[i * R + j] = __dmul_rn(v, inv[j]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        P.counters[1] = 0;
+        if (s_bad) atomicOr(P.status, kStDegenerate);
+        P.lev_L[R * R + R + R * R] = s_bad ? 1.0 : 0.0;  // flag read by k_lev_rows
+    }
+}
+
+// l_i = ||L^{-1} a_i||^2 by forward substitution (k ascending), then the CDF
+// of the mode in the last CTA; advance = 1 closes the iteration (t += 1).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k_mode, int advance)
+{
+    const long long t = *P.t_dev;
+    const int k = k_mode >= 0 ? k_mode : mode_draw(P.seed, t, P.N);
+    const int R = P.R;
+    const long long I = P.dims[k];
+    const double *Lm = P.lev_L, *inv = P.lev_L + R * R;
+    const bool bad = __ldcg(P.lev_L + R * R + R + R * R) != 0.0;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (!bad && i < I) {
+        const T *a = P.A[k] + i * R;
+        double y[256];
+        double acc = 0.0;
+        for (int j = 0; j < R; ++j) {
+            double v = (double)a[j];
+            for (int q = 0; q < j; ++q) v = __fma_rn(-__ldcg(Lm + j * R + q), y[q], v);
+            y[j] = __dmul_rn(v, __ldcg(inv + j));
+            acc = __fma_rn(y[j], y[j], acc);
+        }
+        P.w[k][i] = acc;
+    }
+    if (!last_block(P.counters + 2)) return;
+    if (!bad) finish_cdf(P, k);
+    if (threadIdx.x == 0) {
+        P.counters[2] = 0;
+        if (advance) {
+            *P.n_last = k;
+            *P.t_dev = t + 1;
+        }
+    }
+}
+
+// Euclidean or uniform weights of mode k from scratch (initialisation and
+// cpd_set_factors), then its CDF.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_weights_euclid(const Problem<T> P, int k)
+{
+    const long long I = P.dims[k];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < I)
+        P.w[k][i] = (P.sampling == CPD_SAMPLE_UNIFORM) ? 1.0 : row_weight_euclid(P.A[k] + i * P.R, P.R);
+    if (!last_block(P.counters + 3)) return;
+    finish_cdf(P, k);
+    if (threadIdx.x == 0) P.counters[3] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Relative error (Sec. 5.2): sum over all entries of (x - x_hat)^2 with
+// x_hat(i, j) = A^(1)(i,:) . z_j, z_j the KRP row of mode-1 fiber j, read from
+// the mode-1 replica. FP64 accumulation, fixed-order reductions.
+// ---------------------------------------------------------------------------
+constexpr int kFitFibers = 16;
+
+template <class T, class XT>
+__global__ void __launch_bounds__(kThreads) k_fit(const Problem<T> P, double *partials, int want_xnorm)
+{
+    __shared__ T sz[kFitFibers * 256];
+    __shared__ double red[kThreads / 32];
+    const int N = P.N, R = P.R;
+    const long long I0 = P.dims[0];
+    long long J = 1;
+    for (int k = 1; k < N; ++k) J *= P.dims[k];
+    const XT *rep = reinterpret_cast<const XT *>(P.rep[0]);
+    const T *A0 = P.A[0];
+    double acc = 0.0;
+    for (long long j0 = (long long)blockIdx.x * kFitFibers; j0 < J; j0 += (long long)gridDim.x * kFitFibers) {
+        const int nfib = (J - j0) < kFitFibers ? (int)(J - j0) : kFitFibers;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nfib * R; e += blockDim.x) {
+            const int f = e / R, r = e % R;
+            long long j = j0 + f;
+            T z = (T)1;
+            for (int k = 1; k < N; ++k) {
+                const long long ik = j % P.dims[k];
+                j /= P.dims[k];
+                z = z * P.A[k][ik * R + r];
+            }
+            sz[f * R + r] = want_xnorm ? (T)0 : z;
+        }
+        __syncthreads();
+        for (long long i = threadIdx.x; i < I0; i += blockDim.x) {
+            T xh[kFitFibers];
+#pragma unroll
+            for (int f = 0; f < kFitFibers; ++f) xh[f] = (T)0;
+            if (!want_xnorm) {
+                for (int r = 0; r < R; ++r) {
+                    const T a = A0[i * R + r];
+#pragma unroll
+                    for (int f = 0; f < kFitFibers; ++f) xh[f] += a * sz[f * R + r];
+                }
+            }
+#pragma unroll
+            for (int f = 0; f < kFitFibers; ++f) {
+                if (f < nfib) {
+                    const T x = load_x<XT, T>(rep + (j0 + f) * P.ld[0] + i);
+                    const double d = (double)(x - xh[f]);
+                    acc = __fma_rn(d, d, acc);
+                }
+            }
+        }
+    }
+    for (int off = 16; off >= 1; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_fold(const double *partials, int n, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < n; ++q) s += partials[q];
+        *out = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Mode-n-major replica: X viewed as [I_post][I_n][I_pre] (column-major, i_pre
+// fastest) becomes [I_post][I_pre][ld] with i_n fastest, so fiber
+// j = i_pre + I_pre * i_post of the mode-n unfolding (Eq. map) is contiguous.
+// 32 x 32 tiles through shared memory keep both sides coalesced.
+// ---------------------------------------------------------------------------
+template <class E>
+__global__ void k_copy_padded(const E *__restrict__ X, E *__restrict__ Y, long long In, long long J,
+                              long long ld)
+{
+    const long long total = In * J;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long j = e / In, i = e % In;
+        Y[j * ld + i] = X[e];
+    }
+}
+
+template <class E>
+__global__ void k_replica(const E *__restrict__ X, E *__restrict__ Y, long long Ipre, long long In,
+                          long long Ipost, long long ld)
+{
+    __shared__ E tile[32][33];
+    const long long tiles_pre = (Ipre + 31) / 32, tiles_n = (In + 31) / 32;
+    const long long ntiles = tiles_pre * tiles_n * Ipost;
+    for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const long long post = tt / (tiles_pre * tiles_n);
+        const long long rem = tt % (tiles_pre * tiles_n);
+        const long long tn = rem / tiles_pre, tp = rem % tiles_pre;
+        __syncthreads();
+        for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+            const long long in = tn * 32 + y, ip = tp * 32 + threadIdx.x;
+            if (in < In && ip < Ipre) tile[y][threadIdx.x] = X[(post * In + in) * Ipre + ip];
+        }
+        __syncthreads();
+        for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+            const long long ip = tp * 32 + y, in = tn * 32 + threadIdx.x;
+            if (in < In && ip < Ipre) Y[(post * Ipre + ip) * ld + in] = tile[threadIdx.x][y];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <class T>
+size_t grad_smem_bytes(const Problem<T> &P)
+{
+    return GradSmem<T>(P.N, P.R, P.rb, P.fb).total;
+}
+
+template <class T, class XT>
+static cudaError_t launch_grad_simt(const Problem<T> &P, int grid, size_t smem, cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_grad_simt<T, XT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_grad_simt<T, XT><<<grid, kThreads, smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd, size_t smem_grad,
+                             cudaStream_t s, int engine, cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    cudaError_t e = cudaSuccess;
+    if (ev0) cudaEventRecord(ev0, s);
+    if (engine == kEngineTensor) {
+        if constexpr (sizeof(T) == 4) e = launch_grad_tc(P, grid_grad, s);
+        else e = cudaErrorInvalidValue;
+    } else {
+        if constexpr (sizeof(T) == 8) {
+            e = launch_grad_simt<T, double>(P, grid_grad, smem_grad, s);
+        } else {
+            if (P.x_dtype == CPD_F32) e = launch_grad_simt<T, float>(P, grid_grad, smem_grad, s);
+            else e = launch_grad_simt<T, __nv_bfloat16>(P, grid_grad, smem_grad, s);
+        }
+    }
+    if (ev1) cudaEventRecord(ev1, s);
+    if (e != cudaSuccess) return e;
+    k_update<T><<<grid_upd, kThreads, 0, s>>>(P, engine == kEngineTensor);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (P.sampling == CPD_SAMPLE_LEVERAGE) {
+        const int npairs = P.R * (P.R + 1) / 2;
+        k_gram<T><<<(npairs + 7) / 8, kThreads, 0, s>>>(P, -1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        long long Imax = 0;
+        for (int k = 0; k < P.N; ++k) Imax = P.dims[k] > Imax ? P.dims[k] : Imax;
+        k_lev_rows<T><<<(int)((Imax + kThreads - 1) / kThreads), kThreads, 0, s>>>(P, -1, 1);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+template <class T>
+cudaError_t launch_refresh_mode(const Problem<T> &P, int k, cudaStream_t s)
+{
+    const long long I = P.dims[k];
+    const int grid = (int)((I + kThreads - 1) / kThreads);
+    if (P.sampling == CPD_SAMPLE_LEVERAGE) {
+        const int npairs = P.R * (P.R + 1) / 2;
+        k_gram<T><<<(npairs + 7) / 8, kThreads, 0, s>>>(P, k);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_lev_rows<T><<<grid, kThreads, 0, s>>>(P, k, 0);
+    } else {
+        k_weights_euclid<T><<<grid, kThreads, 0, s>>>(P, k);
+    }
+    return cudaGetLastError();
+}
+
+int fit_blocks() { return 4 * 152; }
+
+template <class T>
+cudaError_t launch_fit(const Problem<T> &P, double *partials, int nblocks, double *out, cudaStream_t s,
+                       int want_xnorm)
+{
+    if constexpr (sizeof(T) == 8) {
+        k_fit<T, double><<<nblocks, kThreads, 0, s>>>(P, partials, want_xnorm);
+    } else {
+        if (P.x_dtype == CPD_F32) k_fit<T, float><<<nblocks, kThreads, 0, s>>>(P, partials, want_xnorm);
+        else k_fit<T, __nv_bfloat16><<<nblocks, kThreads, 0, s>>>(P, partials, want_xnorm);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_fold<<<1, 32, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_replica(const void *X, void *rep, int esize, int N, const int64_t *dims, int n,
+                                 int64_t ld, cudaStream_t s)
+{
+    long long pre = 1, post = 1;
+    for (int k = 0; k < n; ++k) pre *= dims[k];
+    for (int k = n + 1; k < N; ++k) post *= dims[k];
+    if (n == 0) {
+        const int grid = 152 * 8;
+        if (esize == 8)
+            k_copy_padded<double><<<grid, 256, 0, s>>>((const double *)X, (double *)rep, dims[0], post, ld);
+        else if (esize == 4)
+            k_copy_padded<float><<<grid, 256, 0, s>>>((const float *)X, (float *)rep, dims[0], post, ld);
+        else
+            k_copy_padded<unsigned short><<<grid, 256, 0, s>>>((const unsigned short *)X,
+                                                               (unsigned short *)rep, dims[0], post, ld);
+        return cudaGetLastError();
+    }
+    const dim3 block(32, 8);
+    const long long ntiles = ((pre + 31) / 32) * ((dims[n] + 31) / 32) * post;
+    const int grid = (int)(ntiles < 65535LL * 16 ? ntiles : 65535LL * 16);
+    if (esize == 8)
+        k_replica<double><<<grid, block, 0, s>>>((const double *)X, (double *)rep, pre, dims[n], post, ld);
+    else if (esize == 4)
+        k_replica<float><<<grid, block, 0, s>>>((const float *)X, (float *)rep, pre, dims[n], post, ld);
+    else
+        k_replica<unsigned short><<<grid, block, 0, s>>>((const unsigned short *)X, (unsigned short *)rep,
+                                                          pre, dims[n], post, ld);
+    return cudaGetLastError();
+}
+
+template size_t grad_smem_bytes<float>(const Problem<float> &);
+template size_t grad_smem_bytes<double>(const Problem<double> &);
+template cudaError_t launch_iteration<float>(const Problem<float> &, int, int, size_t, cudaStream_t, int,
+                                             cudaEvent_t, cudaEvent_t);
+template cudaError_t launch_iteration<double>(const Problem<double> &, int, int, size_t, cudaStream_t, int,
+                                              cudaEvent_t, cudaEvent_t);
+template cudaError_t launch_refresh_mode<float>(const Problem<float> &, int, cudaStream_t);
+template cudaError_t launch_refresh_mode<double>(const Problem<double> &, int, cudaStream_t);
+template cudaError_t launch_fit<float>(const Problem<float> &, double *, int, double *, cudaStream_t, int);
+template cudaError_t launch_fit<double>(const Problem<double> &, double *, int, double *, cudaStream_t, int);
+
+}  // namespace cpd

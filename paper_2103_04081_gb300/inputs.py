@@ -77,7 +77,7 @@ _STORE = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
 
 
 def cp_tensor(A: list[torch.Tensor], noise: float, seed: int, x_dtype: str = "f64",
-              chunk_cols: int = 1 << 16, compute_dtype=torch.float64) -> torch.Tensor:
+              chunk_cols: int = 1 << 16, compute_dtype=None) -> torch.Tensor:
     """Observed tensor X (flat, column-major) in the storage dtype ``x_dtype``.
 
     Generated in column chunks of the mode-1 unfolding so that tensors of
@@ -85,6 +85,8 @@ def cp_tensor(A: list[torch.Tensor], noise: float, seed: int, x_dtype: str = "f6
     (seed, c), so the result does not depend on the device memory.
     """
     device = A[0].device
+    if compute_dtype is None:  # FP64 on the host; FP32 (no TF32) on a GPU
+        compute_dtype = torch.float64 if device.type == "cpu" else torch.float32
     A = [a.to(compute_dtype) for a in A]
     I0 = A[0].shape[0]
     J = math.prod(a.shape[0] for a in A[1:])
@@ -151,4 +153,10 @@ WORKLOADS = {
                              sampling="euclidean", step="adagrad", eta=0.1, b=1e-12,
                              noise=1e-2, congruence=0.0, lognormal_rows=True,
                              iters=2000, data_seed=0, init_seed=1, sample_seed=0),
+    # Same kernel shapes as the 1000^3 workload on a smaller tensor (3 x 432 MB of
+    # replicas), for counter captures that must stay small.
+    "c4_shape_600cube_bf16": dict(dims=(600, 600, 600), R=50, B=2048, x_dtype="bf16",
+                                  sampling="euclidean", step="adagrad", eta=0.1, b=1e-12,
+                                  noise=1e-2, congruence=0.0, lognormal_rows=True,
+                                  iters=2000, data_seed=0, init_seed=1, sample_seed=0),
 }

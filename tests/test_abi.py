@@ -1,0 +1,68 @@
+"""The C-ABI library loads, exports every declared entry point and validates
+its arguments on the host (no GPU needed; no compute calls are made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"^\s*(?:cpd_status|const char\s*\*)\s*(cpd_\w+)\s*\(", txt, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def cpd():
+    from paper_2103_04081_gb300 import build
+    build.build()
+    from paper_2103_04081_gb300 import cpd as C
+    return C
+
+
+def test_exports_every_declared_symbol(cpd):
+    names = declared_symbols()
+    assert {"cpd_init", "cpd_sgd_iters", "cpd_fit", "cpd_destroy"} <= names
+    for name in sorted(names):
+        assert hasattr(cpd.lib(), name), name
+
+
+def _init_status(cpd, **kw):
+    import torch
+    cfg = cpd.make_config(**kw)
+    X = torch.zeros(8)
+    A0 = [torch.zeros(2, 1) for _ in kw["dims"]]
+    ctx = ctypes.c_void_p()
+    st = cpd.lib().cpd_init(ctypes.byref(cfg), X.data_ptr(), cpd.HOST,
+                            (ctypes.c_void_p * len(A0))(*[a.data_ptr() for a in A0]),
+                            cpd.HOST, None, ctypes.byref(ctx))
+    return st, cpd.lib().cpd_last_error().decode()
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(dims=(2, 2), R=1, B=1), "N must"),
+    (dict(dims=(2, 2, 2), R=0, B=1), "R must"),
+    (dict(dims=(2, 2, 2), R=1, B=0), "B must"),
+    (dict(dims=(3, 3, 3), R=3, B=1, sampling="leverage"), "I_k > R"),
+    (dict(dims=(2, 2, 2), R=1, B=1, step="adagrad", eta=0.0), "eta"),
+    (dict(dims=(2, 2, 2), R=1, B=1, step="decay", gamma=0.0), "gamma"),
+    (dict(dims=(2, 2, 2), R=1, B=1, x_dtype="f32", engine="tensor"), "tensor-core"),
+])
+def test_invalid_configs_rejected_on_host(cpd, kw, msg):
+    st, err = _init_status(cpd, **kw)
+    assert st == cpd.EINVAL
+    assert msg in err
+
+
+def test_no_cpu_fallback(cpd):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st, err = _init_status(cpd, dims=(2, 2, 2), R=1, B=1)
+    assert st == cpd.ECUDA, err

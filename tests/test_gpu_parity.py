@@ -1,0 +1,222 @@
+"""GPU path against the FP64 CPU oracle, through the C-ABI.
+
+Teacher forcing: before each checked iteration the oracle starts from the
+GPU's factors and AdaGrad state at the same t. The mode n, the sampled
+indices and the fiber probabilities p_f must agree bit for bit; the
+gradient and the updated factor within the dtype's tolerance (relative
+Frobenius norm): FP64 1e-11, FP32 1e-5, BF16 tensors on the CUDA-core engine
+1e-5, BF16 on the tensor-core engine 2e-2 (the tolerances stated for the
+method's precisions).
+"""
+import numpy as np
+import pytest
+import torch
+
+from helpers import TOL, make_problem, oracle_xbuf, rel, teacher_forced
+from paper_2103_04081_gb300 import inputs as IN
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cpd():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2103_04081_gb300 import build
+    build.build()
+    from paper_2103_04081_gb300 import cpd as C
+    return C
+
+
+def _ocfg(orc, dims, R, B, x_dtype, sampling, step, seed, **kw):
+    return orc.Config(dims=tuple(dims), R=R, B=B, sampling=sampling, step=step,
+                      x_dtype=x_dtype, seed=seed, alpha=kw.get("alpha", 0.1),
+                      eta=kw.get("eta", 0.1), b=kw.get("b", 1e-12), beta=kw.get("beta", 1.0),
+                      gamma=kw.get("gamma", 1.0))
+
+
+SMALL = [
+    # dims, R, B, x_dtype, sampling, step, extra
+    ((70, 61, 45), 5, 37, "f64", "euclidean", "fixed", {}),
+    ((150, 70, 33), 10, 100, "f32", "euclidean", "adagrad", {}),
+    ((90, 130, 40), 7, 64, "f32", "leverage", "adagrad", {}),
+    ((50, 60, 70), 4, 50, "f32", "uniform", "decay", dict(beta=0.01, gamma=2.0)),
+    ((40, 36, 30, 28), 12, 200, "bf16", "euclidean", "adagrad", {}),
+    ((33, 17, 9, 5, 3), 3, 20, "f32", "euclidean", "fixed", dict(alpha=0.05)),
+    ((65, 66, 67), 9, 1, "f32", "leverage", "fixed", dict(alpha=0.01)),
+]
+
+
+@pytest.mark.parametrize("dims,R,B,xdt,sampling,step,kw", SMALL)
+def test_teacher_forced_small(cpd, orc, dims, R, B, xdt, sampling, step, kw):
+    A, X, A0 = make_problem(dims, R, x_dtype=xdt, lognormal_rows=True)
+    seed = 1234
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype=xdt,
+                            sampling=sampling, step=step, seed=seed, engine="simt", **kw)
+    ocfg = _ocfg(orc, dims, R, B, xdt, sampling, step, seed, **kw)
+    tol = TOL[xdt]
+    worst = teacher_forced(dec, orc, ocfg, oracle_xbuf(X), 12, tol["G"], tol["A"])
+    print(dims, xdt, sampling, step, worst, dec.describe())
+    dec.close()
+
+
+def test_free_run_fp64_matches_oracle_c1(cpd, orc):
+    """The 60^3 FP64 workload, 300 fixed-step iterations free-running on both sides."""
+    w = IN.WORKLOADS["c1_60cube_f64"]
+    A, X, A0 = make_problem(w["dims"], w["R"], noise=w["noise"], x_dtype="f64")
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=w["dims"], R=w["R"], B=w["B"],
+                            x_dtype="f64", sampling="euclidean", step="fixed", alpha=0.1, seed=0)
+    dec.sgd_iters(w["iters"])
+    fit, tol_gpu = dec.fit()
+    ocfg = _ocfg(orc, w["dims"], w["R"], w["B"], "f64", "euclidean", "fixed", 0)
+    Ao = [a.double().numpy().copy() for a in A0]
+    xb = oracle_xbuf(X)
+    assert orc.run(ocfg, 0, w["iters"], None, Ao, xbuf=xb) == orc.OK
+    tol_orc, _ = orc.tol(xb, Ao, "f64", dims=w["dims"])
+    Ag = dec.factors()
+    for a, b in zip(Ag, Ao):
+        assert rel(a.numpy(), b) < 1e-9
+    assert abs(tol_gpu - tol_orc) < 1e-9 * max(1.0, tol_orc)
+    dec.close()
+
+
+@pytest.mark.parametrize("xdt,dims,R", [("f64", (30, 20, 25), 4), ("f32", (64, 50, 40), 6),
+                                        ("bf16", (48, 40, 36, 20), 5)])
+def test_fit_matches_oracle(cpd, orc, xdt, dims, R):
+    A, X, A0 = make_problem(dims, R, noise=0.1, x_dtype=xdt)
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=16, x_dtype=xdt,
+                            sampling="euclidean", step="adagrad", seed=3, engine="simt")
+    dec.sgd_iters(40)
+    fit, tol = dec.fit()
+    xb = oracle_xbuf(X)
+    tol_o, _ = orc.tol(xb, [a.double().numpy() for a in dec.factors()], xdt, dims=dims)
+    assert tol == pytest.approx(tol_o, rel=1e-9 if xdt == "f64" else 1e-5)
+    assert fit == pytest.approx(1 - np.sqrt(tol_o), rel=1e-5, abs=1e-6)
+    # exact factors of noiseless data: Tol is ~0
+    A2, X2, _ = make_problem(dims, R, noise=0.0, x_dtype=xdt)
+    dec2 = cpd.Decomposition(X2.cuda(), [a.cuda() for a in A2], dims=dims, R=R, B=16, x_dtype=xdt,
+                             sampling="euclidean", step="adagrad", seed=3)
+    _, tol2 = dec2.fit()
+    tol2_o, _ = orc.tol(oracle_xbuf(X2), [a.double().numpy() for a in dec2.factors()], xdt, dims=dims)
+    assert tol2 == pytest.approx(tol2_o, rel=1e-3, abs=1e-12)
+    dec.close()
+    dec2.close()
+
+
+def test_chunking_and_graph_replay_are_bitwise(cpd):
+    dims, R, B = (80, 70, 60), 6, 48
+    _, X, A0 = make_problem(dims, R, x_dtype="f32")
+    kw = dict(dims=dims, R=R, B=B, x_dtype="f32", sampling="leverage", step="adagrad", seed=9)
+    d1 = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], **kw)
+    d1.sgd_iters(100)                       # 3 graph replays + 4 plain launches
+    d2 = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], **kw)
+    for q in (1, 31, 32, 5, 31):            # mixed chunking
+        d2.sgd_iters(q)
+    assert d1.t == d2.t == 100
+    for a, b in zip(d1.factors(), d2.factors()):
+        assert torch.equal(a, b)
+    # checkpoint at 60, resume in a fresh context, continue to 100
+    d3 = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], **kw)
+    d3.sgd_iters(60)
+    A60, S60 = d3.factors(), d3.adagrad()
+    d4 = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], **kw)
+    d4.set_factors([a.cuda() for a in A60])
+    d4.set_adagrad(S60)
+    d4.t = 60
+    d4.sgd_iters(40)
+    for a, b in zip(d1.factors(), d4.factors()):
+        assert torch.equal(a, b)
+    for d in (d1, d2, d3, d4):
+        d.close()
+
+
+def test_exact_recovery_gpu(cpd):
+    """Noiseless rank-R data from a perturbed start: fixed-step SGD drives Tol to ~0."""
+    dims, R = (12, 14, 16), 2
+    A, X, _ = make_problem(dims, R, noise=0.0, x_dtype="f64")
+    g = torch.Generator().manual_seed(5)
+    A0 = [a + 0.05 * torch.randn(a.shape, generator=g, dtype=torch.float64) for a in A]
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=16, x_dtype="f64",
+                            sampling="euclidean", step="fixed", alpha=0.2, seed=5)
+    _, tol0 = dec.fit()
+    dec.sgd_iters(6000)
+    _, tol1 = dec.fit()
+    assert tol0 > 1e-4 and tol1 < 1e-20, (tol0, tol1)
+    dec.close()
+
+
+def test_degenerate_and_nonfinite_are_reported(cpd):
+    dims, R = (20, 21, 22), 3
+    _, X, A0 = make_problem(dims, R, x_dtype="f32")
+    A0z = [a.clone() for a in A0]
+    A0z[1].zero_()
+    with pytest.raises(cpd.CpdError) as e:
+        cpd.Decomposition(X.cuda(), [a.cuda() for a in A0z], dims=dims, R=R, B=8, x_dtype="f32",
+                          sampling="euclidean", step="fixed")
+    assert e.value.status == cpd.EDEGENERATE
+    A0r = [a.clone() for a in A0]
+    A0r[2][:, 1] = A0r[2][:, 0]
+    with pytest.raises(cpd.CpdError) as e:
+        cpd.Decomposition(X.cuda(), [a.cuda() for a in A0r], dims=dims, R=R, B=8, x_dtype="f32",
+                          sampling="leverage", step="fixed")
+    assert e.value.status == cpd.EDEGENERATE
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=8, x_dtype="f32",
+                            sampling="uniform", step="fixed", alpha=1e30)
+    dec.sgd_iters(3)
+    with pytest.raises(cpd.CpdError) as e:
+        dec.sync()
+    assert e.value.status == cpd.ENONFINITE
+    dec.close()
+
+
+def test_profile_events(cpd):
+    dims, R = (64, 64, 64), 8
+    _, X, A0 = make_problem(dims, R, x_dtype="f32")
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=64, x_dtype="f32",
+                            sampling="euclidean", step="adagrad")
+    cpd.cpd_profile(dec.ctx, True)
+    dec.sgd_iters(10)
+    n, ms = cpd.cpd_profile_read(dec.ctx)
+    assert n == 10 and 0 < ms < 10
+    cpd.cpd_profile(dec.ctx, False)
+    dec.close()
+
+
+# --------------------------------------------------------------------------
+# Full-size workloads, in the launch configuration the bench times: sampled
+# teacher-forced steps (the oracle gathers only the B sampled fibers).
+# --------------------------------------------------------------------------
+
+def _full(cpd, orc, name, sampling, steps, warm, engine="auto"):
+    w = IN.WORKLOADS[name]
+    dims, R, B, xdt = w["dims"], w["R"], w["B"], w["x_dtype"]
+    A = IN.factors(dims, R, w["data_seed"], congruence=w["congruence"],
+                   lognormal_rows=w["lognormal_rows"], device="cuda")
+    X = IN.cp_tensor(A, w["noise"], w["data_seed"], xdt)
+    A0 = IN.init_factors(dims, R, w["init_seed"])
+    dec = cpd.Decomposition(X, [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype=xdt,
+                            sampling=sampling, step=w["step"], eta=w.get("eta", 0.1),
+                            b=w.get("b", 1e-12), seed=w["sample_seed"], engine=engine)
+    xb = oracle_xbuf(X)
+    del X
+    desc = dec.describe()
+    dec.sgd_iters(warm)
+    key = "bf16_tensor" if desc["engine"] == "tensor" else xdt
+    ocfg = _ocfg(orc, dims, R, B, xdt, sampling, w["step"], w["sample_seed"],
+                 eta=w.get("eta", 0.1), b=w.get("b", 1e-12))
+    worst = teacher_forced(dec, orc, ocfg, xb, steps, TOL[key]["G"], TOL[key]["A"])
+    print(name, sampling, desc, worst)
+    dec.close()
+
+
+@pytest.mark.parametrize("sampling", ["euclidean", "leverage"])
+def test_full_c2_300cube_f32(cpd, orc, sampling):
+    _full(cpd, orc, "c2_300cube_f32", sampling, steps=4, warm=200)
+
+
+def test_full_c3_120pow4_bf16(cpd, orc):
+    _full(cpd, orc, "c3_120pow4_bf16", "euclidean", steps=4, warm=100)
+
+
+def test_full_c4_1000cube_bf16(cpd, orc):
+    _full(cpd, orc, "c4_1000cube_bf16", "euclidean", steps=3, warm=50)
