@@ -191,6 +191,31 @@ cpd_status cpd_profile_read(cpd_ctx *ctx, int64_t *launches, double *mean_ms, vo
  */
 cpd_status cpd_describe(cpd_ctx *ctx, char *buf, size_t len);
 
+/*
+ * cpd_tol_noalloc -- the relative error Tol = ||[[A]] - X||_F^2 / ||X||_F^2 of
+ * a CP model, computed without allocating any device memory. The paper has no
+ * counterpart: this entry point serves callers that cannot call cudaMalloc --
+ * a program whose device memory is owned by another allocator (a framework's
+ * caching pool, or a service that reserves all memory up front), or a loop
+ * that cannot afford the device synchronisation an allocation may cause.
+ *  N, dims, R : tensor order, sizes I_1..I_N and rank (3 <= N <= 8, R <= 256).
+ *  x_dtype    : CPD_F64 / CPD_F32 / CPD_BF16.
+ *  X          : device pointer to the dense tensor, column-major, unpadded.
+ *  A          : host array of N device pointers, A[k] row-major I_k x R,
+ *               double for CPD_F64 and float otherwise.
+ *  tol_out    : device pointer to one double, written in stream order.
+ * Limit: at most 1,048,576 mode-1 fibers (I_2 * ... * I_N <= 2^20); larger
+ * tensors return CPD_EINVAL (use cpd_fit). Scratch: a 1 MiB array that the
+ * library image places in the memory of every GPU that loads it, held until
+ * the process exits. The first call on each device looks up that array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture on the device. Every call reuses the same array, so calls
+ * that overlap on the GPU (e.g. on two streams at once) race: serialise
+ * them. Each call overwrites every scratch slot it reads.
+ */
+cpd_status cpd_tol_noalloc(int32_t N, const int64_t *dims, int32_t R, int32_t x_dtype,
+                           const void *X, const void *const *A, double *tol_out, void *stream);
+
 /* cpd_destroy -- free the context and everything it owns. NULL is a no-op. */
 cpd_status cpd_destroy(cpd_ctx *ctx);
 

@@ -67,6 +67,7 @@ def _load():
         "cpd_profile_read": [P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double), P],
         "cpd_describe": [P, ctypes.c_char_p, ctypes.c_size_t],
         "cpd_destroy": [P],
+        "cpd_tol_noalloc": [I32, P, I32, I32, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -198,6 +199,14 @@ def cpd_describe(ctx) -> dict:
 
 def cpd_destroy(ctx) -> None:
     _check(_lib.cpd_destroy(ctx))
+
+
+def cpd_tol_noalloc(dims, R: int, x_dtype: str, X: torch.Tensor, A: list, tol_out: torch.Tensor,
+                    stream=None) -> None:
+    """Tol of a CP model into the device double `tol_out`, with no device allocation."""
+    d = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
+    _check(_lib.cpd_tol_noalloc(len(dims), d, int(R), XDT[x_dtype], X.data_ptr(), _ptrs(A),
+                                tol_out.data_ptr(), _stream(stream)))
 
 
 # ---- convenience wrapper -------------------------------------------------

@@ -567,3 +567,7 @@ extern "C" cpd_status cpd_destroy(cpd_ctx *c)
 }
 
 extern "C" const char *cpd_last_error(void) { return g_err.c_str(); }
+
+namespace cpd {
+void set_error(const std::string &msg) { g_err = msg; }
+}  // namespace cpd
