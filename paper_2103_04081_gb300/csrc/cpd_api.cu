@@ -134,8 +134,14 @@ static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
     for (int k = 0; k < g.N; ++k) imax = std::max<int64_t>(imax, g.dims[k]);
     c->imax = imax;
     if (c->engine == kEngineTensor) {
+        // 128-row MMA tiles; fibers per CTA a multiple of 16 (the MMA K), about
+        // one wave of CTAs.
         P.rb = 128;
-        P.fb = 64;
+        const int64_t pr_max = (imax + P.rb - 1) / P.rb;
+        const int64_t pf = std::max<int64_t>(1, (sm_count + pr_max - 1) / pr_max);
+        int64_t fb = (g.B + pf - 1) / pf;
+        fb = (fb + 15) / 16 * 16;
+        P.fb = (int)std::min<int64_t>(128, std::max<int64_t>(16, fb));
     } else {
         P.rb = (int)std::min<int64_t>(64, round8(imax));
         int64_t pr_max = (imax + P.rb - 1) / P.rb;
@@ -157,7 +163,10 @@ static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
     c->grid_grad = maxpr * P.pf;
     const int rpc = std::max(1, kThreads / g.R);
     c->grid_upd = (int)((imax + rpc - 1) / rpc);
-    c->smem_grad = c->engine == kEngineTensor ? 0 : grad_smem_bytes(P);
+    if constexpr (sizeof(T) == 4)
+        c->smem_grad = c->engine == kEngineTensor ? tc_smem_bytes(P) : grad_smem_bytes(P);
+    else
+        c->smem_grad = grad_smem_bytes(P);
 }
 
 template <class T>

@@ -135,28 +135,27 @@ __device__ __forceinline__ long long warp_search_cdf(const double *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Canonical inclusive prefix sum ("scan32") of w[0..I) by one CTA: chunks of
-// 32 summed sequentially; chunk totals scanned recursively by the same rule;
-// offsets added top-down. scratch needs ceil(I/31) + 8 doubles. w is read
-// through L2 (other CTAs may have written it in this launch).
+// Canonical inclusive prefix sum ("scan32") by one CTA, in place on a[0..I):
+// chunks of 32 summed sequentially; chunk totals scanned recursively by the
+// same rule; offsets added top-down. `levels` needs ceil(I/31) + 8 doubles.
 // ---------------------------------------------------------------------------
-__device__ inline void block_scan32(const double *w, long long I, double *cdf, double *scratch)
+__device__ inline void scan32_inplace(double *a, long long I, double *levels)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (long long c = tid; c * 32 < I; c += nt) {
         double acc = 0.0;
         const long long hi = (c + 1) * 32 < I ? (c + 1) * 32 : I;
         for (long long e = c * 32; e < hi; ++e) {
-            acc = __dadd_rn(acc, __ldcg(w + e));
-            cdf[e] = acc;
+            acc = __dadd_rn(acc, a[e]);
+            a[e] = acc;
         }
     }
     double *lev[12];
     long long levn[12];
     int L = 0;
-    const double *src = cdf;
+    const double *src = a;
     long long cnt = I;
-    double *sp = scratch;
+    double *sp = levels;
     while (cnt > 32) {
         const long long nc = (cnt + 31) / 32;
         __syncthreads();
@@ -182,10 +181,29 @@ __device__ inline void block_scan32(const double *w, long long I, double *cdf, d
     }
     for (int l = L - 1; l >= 0; --l) {
         __syncthreads();
-        double *below = (l == 0) ? cdf : lev[l - 1];
+        double *below = (l == 0) ? a : lev[l - 1];
         const long long nb = (l == 0) ? I : levn[l - 1];
         for (long long e = 32 + tid; e < nb; e += nt)
             below[e] = __dadd_rn(lev[l][e / 32 - 1], below[e]);
+    }
+    __syncthreads();
+}
+
+// cdf[0..I) = scan32(w[0..I)). Staged through the shared buffer sm (cap
+// doubles) when it fits, else in global memory with `scratch` for the levels.
+// w is read through L2 (other CTAs of the launch may have written it).
+__device__ inline void block_scan32(const double *w, long long I, double *cdf, double *scratch,
+                                    double *sm, int cap)
+{
+    if (I + I / 31 + 16 <= cap) {
+        for (long long e = threadIdx.x; e < I; e += blockDim.x) sm[e] = __ldcg(w + e);
+        __syncthreads();
+        scan32_inplace(sm, I, sm + I);
+        for (long long e = threadIdx.x; e < I; e += blockDim.x) cdf[e] = sm[e];
+    } else {
+        for (long long e = threadIdx.x; e < I; e += blockDim.x) cdf[e] = __ldcg(w + e);
+        __syncthreads();
+        scan32_inplace(cdf, I, scratch);
     }
     __syncthreads();
 }
@@ -200,4 +218,76 @@ __device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 x)
     return __bfloat162float(x);
 }
 
+
+// ---------------------------------------------------------------------------
+// Sampling steps shared by both gradient engines.
+// ---------------------------------------------------------------------------
+// Draw the (N-1) x nf indices of this CTA's fibers (Alg. 3 "Randsample(I_k,
+// |F_n|, true, p_k)"): warps take 32-fiber chunks per mode k != n and run the
+// warp-cooperative search on cdf[k].
+template <class T>
+__device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int f0, int nf, int *sidx)
+{
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const int chunks = (nf + 31) / 32;
+    for (int job = warp; job < chunks * P.N; job += nwarps) {
+        const int k = job / chunks, ch = job % chunks;
+        const int fl = ch * 32 + lane;
+        const bool act = fl < nf;
+        if (k == n) {
+            if (act) sidx[fl * P.N + k] = -1;
+            continue;
+        }
+        const long long Ik = P.dims[k];
+        unsigned long long x = act ? fiber_word(P.seed, t, (long long)(f0 + fl), k) : 0ULL;
+        long long i;
+        if (P.sampling == CPD_SAMPLE_UNIFORM) {
+            i = (long long)__umul64hi(x, (unsigned long long)Ik);
+        } else {
+            const double *c = P.cdf[k];
+            const double target = __dmul_rn(u53(x), __ldg(c + (Ik - 1)));
+            i = warp_search_cdf(c, Ik, target, act);
+        }
+        if (act) sidx[fl * P.N + k] = (int)i;
+    }
+}
+
+// p_f (Eq. block_lev_prob, product in ascending k) and the weight
+// s_f = 1 / (B J_n p_f) of the fiber's term in Eq. gradient1.
+template <class T>
+__device__ __forceinline__ double fiber_prob(const Problem<T> &P, int n, const int *row)
+{
+    double p = 1.0;
+    for (int k = 0; k < P.N; ++k) {
+        if (k == n) continue;
+        if (P.sampling == CPD_SAMPLE_UNIFORM) {
+            p = __dmul_rn(p, __ddiv_rn(1.0, (double)P.dims[k]));
+        } else {
+            const double W = __ldg(P.cdf[k] + (P.dims[k] - 1));
+            p = __dmul_rn(p, __ddiv_rn(__ldg(P.w[k] + row[k]), W));
+        }
+    }
+    return p;
+}
+
+template <class XT, class T>
+__device__ __forceinline__ T load_x(const XT *p) { return (T)to_float<XT>(*p); }
+template <>
+__device__ __forceinline__ double load_x<double, double>(const double *p) { return *p; }
+
+
+// Arrival counter: true in exactly one CTA, the last one to finish.
+__device__ __forceinline__ bool last_block(unsigned *counter)
+{
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(counter, 1u);
+        s_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
 }  // namespace cpd

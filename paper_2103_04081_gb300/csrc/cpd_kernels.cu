@@ -40,59 +40,6 @@ struct GradSmem {
     __host__ __device__ static size_t align_up_h(size_t v, size_t a) { return (v + a - 1) / a * a; }
 };
 
-// Draw the (N-1) x nf indices of this CTA's fibers (Alg. 3 "Randsample(I_k,
-// |F_n|, true, p_k)"): warps take 32-fiber chunks per mode k != n and run the
-// warp-cooperative search on cdf[k].
-template <class T>
-__device__ void draw_indices(const Problem<T> &P, long long t, int n, int f0, int nf, int *sidx)
-{
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
-    const int chunks = (nf + 31) / 32;
-    for (int job = warp; job < chunks * P.N; job += nwarps) {
-        const int k = job / chunks, ch = job % chunks;
-        const int fl = ch * 32 + lane;
-        const bool act = fl < nf;
-        if (k == n) {
-            if (act) sidx[fl * P.N + k] = -1;
-            continue;
-        }
-        const long long Ik = P.dims[k];
-        unsigned long long x = act ? fiber_word(P.seed, t, (long long)(f0 + fl), k) : 0ULL;
-        long long i;
-        if (P.sampling == CPD_SAMPLE_UNIFORM) {
-            i = (long long)__umul64hi(x, (unsigned long long)Ik);
-        } else {
-            const double *c = P.cdf[k];
-            const double target = __dmul_rn(u53(x), __ldg(c + (Ik - 1)));
-            i = warp_search_cdf(c, Ik, target, act);
-        }
-        if (act) sidx[fl * P.N + k] = (int)i;
-    }
-}
-
-// p_f (Eq. block_lev_prob, product in ascending k) and the weight
-// s_f = 1 / (B J_n p_f) of the fiber's term in Eq. gradient1.
-template <class T>
-__device__ __forceinline__ double fiber_prob(const Problem<T> &P, int n, const int *row)
-{
-    double p = 1.0;
-    for (int k = 0; k < P.N; ++k) {
-        if (k == n) continue;
-        if (P.sampling == CPD_SAMPLE_UNIFORM) {
-            p = __dmul_rn(p, __ddiv_rn(1.0, (double)P.dims[k]));
-        } else {
-            const double W = __ldg(P.cdf[k] + (P.dims[k] - 1));
-            p = __dmul_rn(p, __ddiv_rn(__ldg(P.w[k] + row[k]), W));
-        }
-    }
-    return p;
-}
-
-template <class XT, class T>
-__device__ __forceinline__ T load_x(const XT *p) { return (T)to_float<XT>(*p); }
-template <>
-__device__ __forceinline__ double load_x<double, double>(const double *p) { return *p; }
-
 // Copy rows [r0, r0+rows) of fiber j (contiguous in the mode-n replica) into
 // shared memory as T, with 16-byte vector loads (rows are padded to 8).
 template <class XT, class T>
@@ -120,7 +67,7 @@ __device__ __forceinline__ void gather_rows(const XT *__restrict__ rep, long lon
 // ---------------------------------------------------------------------------
 // Gradient partials, residual form. For this CTA's rows i and fibers f:
 //   res_if = s_f * (A^(n)(i,:) . z_f - x_f(i))          (one row of A Zs^T - Xs, weighted)
-//   part[gf][r][i] = sum_f res_if * z_f(r)
+//   part[gf][i][r] = sum_f res_if * z_f(r)
 // so that sum over fiber groups gives (A Zs^T D Zs - Xs D Zs) / (B J_n),
 // Eq. gradient1, without the cancellation of forming the two products apart.
 // ---------------------------------------------------------------------------
@@ -201,13 +148,13 @@ __global__ void __launch_bounds__(kThreads) k_grad_simt(const Problem<T> P)
     }
     __syncthreads();
 
-    // 6. partial gradient of this fiber group, layout [gf][r][i]
+    // 6. partial gradient of this fiber group, layout [gf][i][r] (coalesced rows)
     T *out = P.part + (long long)gf * R * In;
     for (int e = threadIdx.x; e < R * rows; e += blockDim.x) {
-        const int r = e / rows, i = e % rows;
+        const int i = e / R, r = e % R;
         T acc = (T)0;
         for (int f = 0; f < nf; ++f) acc += sx[f * rb + i] * sz[f * R + r];
-        out[(long long)r * In + r0 + i] = acc;
+        out[(long long)(r0 + i) * R + r] = acc;
     }
 }
 
@@ -222,38 +169,26 @@ __device__ __forceinline__ double row_weight_euclid(const T *row, int R)
     return acc;
 }
 
+constexpr int kScanSmem = 4224;  // doubles of the shared scan buffer (I_k up to ~4080)
+
 // Rebuild cdf[k] from w[k] (one CTA); a distribution without mass is flagged.
 template <class T>
-__device__ void finish_cdf(const Problem<T> &P, int k)
+__device__ void finish_cdf(const Problem<T> &P, int k, double *sm)
 {
     const long long Ik = P.dims[k];
-    block_scan32(P.w[k], Ik, P.cdf[k], P.scan_scratch);
+    block_scan32(P.w[k], Ik, P.cdf[k], P.scan_scratch, sm, kScanSmem);
     if (threadIdx.x == 0) {
         const double W = P.cdf[k][Ik - 1];
         if (!(W > 0.0) || !isfinite(W)) atomicOr(P.status, kStDegenerate);
     }
 }
 
-// Arrival counter: true in exactly one CTA, the last one to finish.
-__device__ __forceinline__ bool last_block(unsigned *counter)
-{
-    __shared__ int s_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(counter, 1u);
-        s_last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (s_last) __threadfence();
-    return s_last != 0;
-}
-
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P, int tensor_engine)
 {
     __shared__ T s_new[kThreads];
-    __shared__ float sH[64 * 64];
+    __shared__ __align__(16) double s_buf[kScanSmem];   // H (tensor engine), then the scan
+    float *sH = reinterpret_cast<float *>(s_buf);
     const long long t = *P.t_dev;
     const int N = P.N, R = P.R;
     const int n = mode_draw(P.seed, t, N);
@@ -265,17 +200,18 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P, int ten
     T *An = P.A[n];
     if (tensor_engine) {
         // H = Z_S^T D Z_S, already reduced over fiber groups (R <= 64).
-        for (int e = threadIdx.x; e < R * R; e += blockDim.x) sH[e] = __ldcg(P.hpart + e);
+        const float *H = P.hpart + (long long)P.pf * R * R;
+        for (int e = threadIdx.x; e < R * R; e += blockDim.x) sH[e] = __ldcg(H + e);
         __syncthreads();
     }
     if (act) {
         T g = (T)0;
         if (!tensor_engine) {
-            for (int q = 0; q < P.pf; ++q) g += P.part[((long long)q * R + r) * In + i];
+            for (int q = 0; q < P.pf; ++q) g += P.part[((long long)q * In + i) * R + r];
         } else {
             // G = (A H - M) / (B J_n) with M, H reduced over fiber groups.
             float m = 0.f;
-            for (int q = 0; q < P.pf; ++q) m += (float)P.part[((long long)q * R + r) * In + i];
+            for (int q = 0; q < P.pf; ++q) m += (float)P.part[((long long)q * In + i) * R + r];
             float ah = 0.f;
             for (int s = 0; s < R; ++s) ah += (float)An[i * R + s] * sH[s * R + r];
             g = (T)(ah - m);
@@ -287,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P, int ten
             const double gd = (double)g;
             const double S = __fma_rn(gd, gd, *Sp);
             *Sp = S;
-            a = a - P.eta * gd / sqrt(P.b + S);
+            a = a - P.eta * gd * rsqrt(P.b + S);
         } else {
             const double alpha = (P.step == CPD_STEP_DECAY) ? P.beta / ((double)t + P.gamma) : P.alpha;
             a = a - alpha * (double)g;
@@ -301,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P, int ten
     if (P.sampling == CPD_SAMPLE_EUCLIDEAN && act && r == 0)
         P.w[n][i] = row_weight_euclid(s_new + li * R, R);
     if (!last_block(P.counters)) return;
-    if (P.sampling == CPD_SAMPLE_EUCLIDEAN) finish_cdf(P, n);
+    if (P.sampling == CPD_SAMPLE_EUCLIDEAN) finish_cdf(P, n, s_buf);
     if (threadIdx.x == 0) {
         P.counters[0] = 0;
         if (P.sampling != CPD_SAMPLE_LEVERAGE) {
@@ -399,7 +335,8 @@ __global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k
         P.w[k][i] = acc;
     }
     if (!last_block(P.counters + 2)) return;
-    if (!bad) finish_cdf(P, k);
+    __shared__ double s_scan[kScanSmem];
+    if (!bad) finish_cdf(P, k, s_scan);
     if (threadIdx.x == 0) {
         P.counters[2] = 0;
         if (advance) {
@@ -419,7 +356,8 @@ __global__ void __launch_bounds__(kThreads) k_weights_euclid(const Problem<T> P,
     if (i < I)
         P.w[k][i] = (P.sampling == CPD_SAMPLE_UNIFORM) ? 1.0 : row_weight_euclid(P.A[k] + i * P.R, P.R);
     if (!last_block(P.counters + 3)) return;
-    finish_cdf(P, k);
+    __shared__ double s_scan[kScanSmem];
+    finish_cdf(P, k, s_scan);
     if (threadIdx.x == 0) P.counters[3] = 0;
 }
 
@@ -551,12 +489,15 @@ size_t grad_smem_bytes(const Problem<T> &P)
 template <class T, class XT>
 static cudaError_t launch_grad_simt(const Problem<T> &P, int grid, size_t smem, cudaStream_t s)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_grad_simt<T, XT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    static size_t attr_bytes = 0;
+    if (smem > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_grad_simt<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        attr_bytes = smem;
     }
     k_grad_simt<T, XT><<<grid, kThreads, smem, s>>>(P);
     return cudaGetLastError();

@@ -60,6 +60,28 @@ def test_teacher_forced_small(cpd, orc, dims, R, B, xdt, sampling, step, kw):
     dec.close()
 
 
+TENSOR = [
+    # dims, R, B, sampling: ragged row tiles and fiber groups, R below and at 64
+    ((200, 150, 100), 50, 300, "euclidean"),
+    ((40, 36, 130, 28), 12, 77, "euclidean"),
+    ((129, 257, 70), 64, 2048, "leverage"),
+    ((300, 64, 90), 20, 1024, "uniform"),
+]
+
+
+@pytest.mark.parametrize("dims,R,B,sampling", TENSOR)
+def test_teacher_forced_tensor_engine(cpd, orc, dims, R, B, sampling):
+    A, X, A0 = make_problem(dims, R, x_dtype="bf16", lognormal_rows=True)
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype="bf16",
+                            sampling=sampling, step="adagrad", seed=77, engine="tensor")
+    assert dec.describe()["engine"] == "tensor"
+    ocfg = _ocfg(orc, dims, R, B, "bf16", sampling, "adagrad", 77)
+    tol = TOL["bf16_tensor"]
+    worst = teacher_forced(dec, orc, ocfg, oracle_xbuf(X), 10, tol["G"], tol["A"])
+    print(dims, R, B, sampling, "tensor", worst, dec.describe())
+    dec.close()
+
+
 def test_free_run_fp64_matches_oracle_c1(cpd, orc):
     """The 60^3 FP64 workload, 300 fixed-step iterations free-running on both sides."""
     w = IN.WORKLOADS["c1_60cube_f64"]
