@@ -32,20 +32,23 @@
  *
  * Canonical sampling arithmetic (bit-exactness of the sampled indices and
  * of p_f depends on it; a second, independent implementation on the GPU
- * follows the same order):
- *  - Euclidean row weight (Def. 5, Lemma 4): w_i = sum_r a_ir^2, r ascending,
- *    acc = fma(a_ir, a_ir, acc) from acc = 0.
- *  - Leverage row weight (Def. 3): Gram g_rs = sum_i a_ir a_is as 32 strided
- *    partials (rows i = p mod 32, ascending, fma) folded by the fixed tree
- *    p += p+off for off = 16,8,4,2,1; left-looking Cholesky g = L L^T with
- *    k ascending and inv_j = 1/L_jj; y = L^{-1} a_i by forward substitution
+ * follows the same definitions):
+ *  - Euclidean row weight (Def. 5, Lemma 4): w_i = sum_r a_ir^2 as 32 strided
+ *    partials (partial p takes r = p, p+32, ... ascending, acc = fma(a, a,
+ *    acc) from +0) folded by the fixed tree p += p+off for off = 16,8,4,2,1.
+ *  - Leverage row weight (Def. 3): Gram g_rs = sum_i a_ir a_is in the same
+ *    32-partial order over i; left-looking Cholesky g = L L^T with k
+ *    ascending and inv_j = 1/L_jj; y = L^{-1} a_i by forward substitution
  *    with k ascending; w_i = sum_j y_j^2 (fma, j ascending). A pivot at or
  *    below 2^-40 times its diagonal entry means "degenerate".
- *  - CDF: inclusive prefix sum "scan32": chunks of 32 summed sequentially,
- *    chunk totals scanned recursively by the same rule, offsets added.
- *  - Draw: u = (x >> 11) * 2^-53, target = u * W (W = cdf[I-1]),
- *    i = min{ i : target < cdf[i] }.  Uniform: i = floor(x * I / 2^64).
- *  - p_f = prod_{k != n, k ascending} (w_k[i_k] / W_k)  (uniform: 1/I_k).
+ *  - Fixed-point distribution: s = 61 - ceil(log2 I) - floor(log2 max_i w_i),
+ *    q_i = floor(w_i 2^s) (exact), Q = sum_i q_i < 2^62, cdf[i] = sum_{j<=i} q_j
+ *    as exact 64-bit integers. Rows whose weight is below 2^-(61-ceil(log2 I))
+ *    of the largest get q_i = 0 and are never drawn.
+ *  - Draw: i = min{ i : floor(x Q / 2^64) < cdf[i] } for the 64-bit Philox
+ *    word x (uniform sampling, q_i = 1: i = floor(x I / 2^64)).
+ *  - p_k(i) = (double)q_i / (double)Q (both conversions and the quotient
+ *    rounded to nearest); p_f = prod_{k != n, k ascending} p_k(i_k).
  *
  * Conventions (0-based in code, the paper is 1-based):
  *  - X dense, column-major (first index fastest): entry (i_0..i_{N-1}) at
@@ -115,9 +118,6 @@ void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* 53-bit uniform double in [0, 1). */
-double orc_u53(uint64_t x) { return (double)(x >> 11) * 0x1.0p-53; }
-
 /* Random word for the draw of fiber f in mode k at iteration t. */
 uint64_t orc_fiber_word(uint64_t seed, int64_t t, int64_t f, int k)
 {
@@ -142,14 +142,21 @@ int32_t orc_mode_draw(uint64_t seed, int64_t t, int32_t N)
 /* Per-factor row weights (Sec. 3.1).                                   */
 /* ------------------------------------------------------------------ */
 
-/* Def. 5 / Lemma 4 (beta = 1): w_i = ||A(i,:)||_2^2. */
+/* Def. 5 / Lemma 4 (beta = 1): w_i = ||A(i,:)||_2^2, canonical tree order. */
 void orc_weights_euclidean(const double *A, int64_t I, int32_t R, double *w)
 {
     for (int64_t i = 0; i < I; ++i) {
-        double acc = 0.0;
-        for (int32_t r = 0; r < R; ++r)
-            acc = fma(A[i * R + r], A[i * R + r], acc);
-        w[i] = acc;
+        double part[32];
+        for (int p = 0; p < 32; ++p) {
+            double acc = 0.0;
+            for (int32_t r = p; r < R; r += 32)
+                acc = fma(A[i * R + r], A[i * R + r], acc);
+            part[p] = acc;
+        }
+        for (int off = 16; off >= 1; off >>= 1)
+            for (int p = 0; p < off; ++p)
+                part[p] = part[p] + part[p + off];
+        w[i] = part[0];
     }
 }
 
@@ -225,46 +232,57 @@ int orc_weights_leverage(const double *A, int64_t I, int32_t R, double *w)
     return status;
 }
 
-/* Canonical inclusive prefix sum (scan32). */
-void orc_cdf(const double *w, int64_t I, double *cdf)
+static int ceil_log2_i64(int64_t v)
 {
-    if (I <= 0)
-        return;
-    int64_t nc = (I + 31) / 32;
-    for (int64_t c = 0; c < nc; ++c) {
-        double acc = 0.0;
-        int64_t hi = (c + 1) * 32 < I ? (c + 1) * 32 : I;
-        for (int64_t i = c * 32; i < hi; ++i) {
-            acc = acc + w[i];
-            cdf[i] = acc;
-        }
-    }
-    if (nc == 1)
-        return;
-    double *tot = (double *)malloc((size_t)nc * sizeof(double));
-    double *off = (double *)malloc((size_t)nc * sizeof(double));
-    for (int64_t c = 0; c < nc; ++c) {
-        int64_t last = (c + 1) * 32 < I ? (c + 1) * 32 - 1 : I - 1;
-        tot[c] = cdf[last];
-    }
-    orc_cdf(tot, nc, off);
-    for (int64_t c = 1; c < nc; ++c) {
-        int64_t hi = (c + 1) * 32 < I ? (c + 1) * 32 : I;
-        for (int64_t i = c * 32; i < hi; ++i)
-            cdf[i] = off[c - 1] + cdf[i];
-    }
-    free(tot);
-    free(off);
+    int L = 0;
+    while (((int64_t)1 << L) < v)
+        ++L;
+    return L;
 }
 
-/* Inverse-CDF draw (Def. 2): smallest i with u*W < cdf[i]. */
-int64_t orc_draw(const double *cdf, int64_t I, double u)
+/*
+ * Fixed-point sampling distribution of one factor from its row weights:
+ * q_i = floor(w_i 2^s) with s = 61 - ceil(log2 I) - floor(log2 max w), and
+ * cdf[i] = q_0 + ... + q_i (exact). Returns ORC_EDEGENERATE when a weight is
+ * negative or not finite, or when every q_i is 0.
+ */
+int orc_distribution(const double *w, int64_t I, uint64_t *cdf)
 {
-    double target = u * cdf[I - 1];
+    double wmax = 0.0;
+    for (int64_t i = 0; i < I; ++i) {
+        if (!(w[i] >= 0.0) || isinf(w[i]))
+            return ORC_EDEGENERATE;
+        if (w[i] > wmax)
+            wmax = w[i];
+    }
+    if (wmax == 0.0)
+        return ORC_EDEGENERATE;
+    int e;
+    frexp(wmax, &e);                 /* wmax in [2^(e-1), 2^e) */
+    const int s = 61 - ceil_log2_i64(I) - (e - 1);
+    uint64_t acc = 0;
+    for (int64_t i = 0; i < I; ++i) {
+        acc += (uint64_t)floor(ldexp(w[i], s));
+        cdf[i] = acc;
+    }
+    return acc > 0 ? ORC_OK : ORC_EDEGENERATE;
+}
+
+/* Inverse-CDF draw (Def. 2): smallest i with floor(x Q / 2^64) < cdf[i]. */
+int64_t orc_draw(const uint64_t *cdf, int64_t I, uint64_t x)
+{
+    const uint64_t target = mulhi64(x, cdf[I - 1]);
     for (int64_t i = 0; i < I; ++i)
         if (target < cdf[i])
             return i;
     return I - 1;
+}
+
+/* p_k(i) = q_i / Q, as doubles. */
+double orc_prob(const uint64_t *cdf, int64_t I, int64_t i)
+{
+    const uint64_t q = cdf[i] - (i > 0 ? cdf[i - 1] : 0);
+    return (double)q / (double)cdf[I - 1];
 }
 
 /* Row weights of one factor for the configured distribution. */
@@ -358,7 +376,7 @@ static int64_t j_count(const orc_cfg *c, int32_t n)
  * factors. w and cdf are arrays of N pointers to buffers of I_k doubles.
  */
 static int build_distributions(const orc_cfg *c, int32_t n, const double *const *A,
-                               double **w, double **cdf)
+                               double **w, uint64_t **cdf)
 {
     for (int32_t k = 0; k < c->N; ++k) {
         if (k == n)
@@ -366,26 +384,22 @@ static int build_distributions(const orc_cfg *c, int32_t n, const double *const 
         int st = orc_weights(c->sampling, A[k], c->dims[k], c->R, w[k]);
         if (st != ORC_OK)
             return st;
-        orc_cdf(w[k], c->dims[k], cdf[k]);
-        double W = cdf[k][c->dims[k] - 1];
-        if (!(W > 0.0) || !isfinite(W))
-            return ORC_EDEGENERATE;
+        st = orc_distribution(w[k], c->dims[k], cdf[k]);
+        if (st != ORC_OK)
+            return st;
     }
     return ORC_OK;
 }
 
 /* Eq. block_lev_prob: p_f as the product of the per-factor probabilities. */
 static double fiber_probability(const orc_cfg *c, int32_t n, const int64_t *idx,
-                                double *const *w, double *const *cdf)
+                                uint64_t *const *cdf)
 {
     double p = 1.0;
     for (int32_t k = 0; k < c->N; ++k) {
         if (k == n)
             continue;
-        if (c->sampling == ORC_SAMPLE_UNIFORM)
-            p = p * (1.0 / (double)c->dims[k]);
-        else
-            p = p * (w[k][idx[k]] / cdf[k][c->dims[k] - 1]);
+        p = p * orc_prob(cdf[k], c->dims[k], idx[k]);
     }
     return p;
 }
@@ -456,10 +470,11 @@ int orc_gradient_for_batch(const orc_cfg *c, int32_t n, const int64_t *idx,
 {
     int32_t N = c->N, R = c->R, B = c->B;
     int64_t In = c->dims[n];
-    double *w[ORC_MAXN] = {0}, *cdf[ORC_MAXN] = {0};
+    double *w[ORC_MAXN] = {0};
+    uint64_t *cdf[ORC_MAXN] = {0};
     for (int32_t k = 0; k < N; ++k) {
         w[k] = (double *)malloc((size_t)c->dims[k] * sizeof(double));
-        cdf[k] = (double *)malloc((size_t)c->dims[k] * sizeof(double));
+        cdf[k] = (uint64_t *)malloc((size_t)c->dims[k] * sizeof(uint64_t));
     }
     int st = build_distributions(c, n, A, w, cdf);
     double *Zs = (double *)malloc((size_t)B * R * sizeof(double));
@@ -467,7 +482,7 @@ int orc_gradient_for_batch(const orc_cfg *c, int32_t n, const int64_t *idx,
     if (st == ORC_OK) {
         for (int32_t f = 0; f < B; ++f) {
             const int64_t *row = idx + (int64_t)f * N;
-            p[f] = fiber_probability(c, n, row, w, cdf);
+            p[f] = fiber_probability(c, n, row, cdf);
             orc_krp_row(N, R, n, A, row, Zs + (int64_t)f * R);
             orc_gather_fiber(X, c->x_dtype, N, c->dims, n, row, Xs + (int64_t)f * In);
         }
@@ -498,10 +513,11 @@ int orc_step(const orc_cfg *c, int64_t t, const void *X, double *const *A,
         return ORC_EINVAL;
     int32_t n = orc_mode_draw(c->seed, t, N);
     int64_t In = c->dims[n];
-    double *w[ORC_MAXN] = {0}, *cdf[ORC_MAXN] = {0};
+    double *w[ORC_MAXN] = {0};
+    uint64_t *cdf[ORC_MAXN] = {0};
     for (int32_t k = 0; k < N; ++k) {
         w[k] = (double *)malloc((size_t)c->dims[k] * sizeof(double));
-        cdf[k] = (double *)malloc((size_t)c->dims[k] * sizeof(double));
+        cdf[k] = (uint64_t *)malloc((size_t)c->dims[k] * sizeof(uint64_t));
     }
     int64_t *idx = (int64_t *)malloc((size_t)B * N * sizeof(int64_t));
     double *p = (double *)malloc((size_t)B * sizeof(double));
@@ -514,18 +530,15 @@ int orc_step(const orc_cfg *c, int64_t t, const void *X, double *const *A,
                     idx[(int64_t)f * N + k] = -1;
                     continue;
                 }
-                uint64_t x = orc_fiber_word(c->seed, t, f, k);
-                if (c->sampling == ORC_SAMPLE_UNIFORM)
-                    idx[(int64_t)f * N + k] = (int64_t)mulhi64(x, (uint64_t)c->dims[k]);
-                else
-                    idx[(int64_t)f * N + k] = orc_draw(cdf[k], c->dims[k], orc_u53(x));
+                const uint64_t x = orc_fiber_word(c->seed, t, f, k);
+                idx[(int64_t)f * N + k] = orc_draw(cdf[k], c->dims[k], x);
             }
         }
         double *Zs = (double *)malloc((size_t)B * R * sizeof(double));
         double *Xs = (double *)malloc((size_t)B * In * sizeof(double));
         for (int32_t f = 0; f < B; ++f) {
             const int64_t *row = idx + (int64_t)f * N;
-            p[f] = fiber_probability(c, n, row, w, cdf);
+            p[f] = fiber_probability(c, n, row, cdf);
             orc_krp_row(N, R, n, (const double *const *)A, row, Zs + (int64_t)f * R);
             orc_gather_fiber(X, c->x_dtype, N, c->dims, n, row, Xs + (int64_t)f * In);
         }

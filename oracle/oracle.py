@@ -107,8 +107,6 @@ _dbl = ctypes.c_double
 
 def _declare(L):
     L.orc_philox4x64.argtypes = [_p, _p, _p]
-    L.orc_u53.argtypes = [_u64]
-    L.orc_u53.restype = _dbl
     L.orc_fiber_word.argtypes = [_u64, _i64, _i64, ctypes.c_int]
     L.orc_fiber_word.restype = _u64
     L.orc_mode_draw.argtypes = [_u64, _i64, _i32]
@@ -118,9 +116,12 @@ def _declare(L):
     L.orc_weights_leverage.restype = ctypes.c_int
     L.orc_weights.argtypes = [_i32, _p, _i64, _i32, _p]
     L.orc_weights.restype = ctypes.c_int
-    L.orc_cdf.argtypes = [_p, _i64, _p]
-    L.orc_draw.argtypes = [_p, _i64, _dbl]
+    L.orc_distribution.argtypes = [_p, _i64, _p]
+    L.orc_distribution.restype = ctypes.c_int
+    L.orc_draw.argtypes = [_p, _i64, _u64]
     L.orc_draw.restype = _i64
+    L.orc_prob.argtypes = [_p, _i64, _i64]
+    L.orc_prob.restype = _dbl
     L.orc_unfold_col.argtypes = [_i32, _p, _i32, _p]
     L.orc_unfold_col.restype = _i64
     L.orc_gather_fiber.argtypes = [_p, _i32, _i32, _p, _i32, _p, _p]
@@ -171,10 +172,6 @@ def philox(ctr, key) -> list:
     return [int(v) for v in o]
 
 
-def u53(x: int) -> float:
-    return lib().orc_u53(x)
-
-
 def fiber_word(seed: int, t: int, f: int, k: int) -> int:
     return lib().orc_fiber_word(seed, t, f, k)
 
@@ -190,16 +187,22 @@ def weights(sampling: str, A) -> tuple[int, np.ndarray]:
     return st, w
 
 
-def cdf(w) -> np.ndarray:
+def distribution(w) -> tuple[int, np.ndarray]:
+    """(status, cdf): the fixed-point sampling distribution of row weights w."""
     w = _f64(w)
-    out = np.empty_like(w)
-    lib().orc_cdf(_ptr(w), w.size, _ptr(out))
-    return out
+    out = np.zeros(w.size, dtype=np.uint64)
+    st = lib().orc_distribution(_ptr(w), w.size, _ptr(out))
+    return st, out
 
 
-def draw(c, u: float) -> int:
-    c = _f64(c)
-    return lib().orc_draw(_ptr(c), c.size, u)
+def draw(cdf: np.ndarray, x: int) -> int:
+    c = np.ascontiguousarray(cdf, dtype=np.uint64)
+    return lib().orc_draw(_ptr(c), c.size, int(x) & (2**64 - 1))
+
+
+def prob(cdf: np.ndarray, i: int) -> float:
+    c = np.ascontiguousarray(cdf, dtype=np.uint64)
+    return lib().orc_prob(_ptr(c), c.size, int(i))
 
 
 def unfold_col(dims, n: int, idx) -> int:

@@ -60,12 +60,6 @@ def test_philox_matches_numpy(orc, ctr, key):
     assert orc.philox(ctr, key) == [int(v) for v in bg.random_raw(4)]
 
 
-def test_u53_range(orc):
-    assert orc.u53(0) == 0.0
-    assert orc.u53(2**64 - 1) == 1.0 - 2.0**-53
-    assert orc.u53(2**11) == 2.0**-53
-
-
 def test_mode_draw_uniform(orc):
     """Alg. 4/5 draw n uniformly: chi-square over 30000 iterations."""
     for N in (3, 4, 5):
@@ -143,8 +137,8 @@ def test_euclidean_probabilities(orc):
             j = orc.unfold_col(dims, n, tup)
             rows = [np.linalg.norm(A[k][tup[k]]) ** 2 for k in range(3) if k != n]
             fro = [np.linalg.norm(A[k]) ** 2 for k in range(3) if k != n]
-            # Eq. krp_euc_prob
-            assert ps[j][0] == pytest.approx(np.prod(rows) / np.prod(fro), rel=1e-14)
+            # Eq. krp_euc_prob (up to the 2^-50 resolution of the fixed-point weights)
+            assert ps[j][0] == pytest.approx(np.prod(rows) / np.prod(fro), rel=1e-12)
             # Lemma 3
             assert np.linalg.norm(Z[j]) ** 2 <= np.prod(rows) * (1 + 1e-14)
 
@@ -190,38 +184,76 @@ def test_leverage_probabilities_and_lemma1(orc):
 
 
 # ------------------------------------------------------------------ #
-# CDF and inverse-CDF draw                                             #
+# Fixed-point distribution and inverse-CDF draw, against exact        #
+# big-integer / rational arithmetic                                   #
 # ------------------------------------------------------------------ #
 
-@pytest.mark.parametrize("I", [1, 2, 31, 32, 33, 1000, 1024, 1025, 40000])
-def test_cdf_exact_on_integers(orc, I):
+def exact_distribution(w):
+    """q_i = floor(w_i 2^s), s = 61 - ceil(log2 I) - floor(log2 max w), in Python integers."""
+    from fractions import Fraction
+    I = len(w)
+    wmax = max(w)
+    e = math.frexp(wmax)[1]
+    s = 61 - (I - 1).bit_length() - (e - 1)
+    q = [math.floor(Fraction(float(x)) * Fraction(2) ** s) for x in w]
+    cdf, acc = [], 0
+    for v in q:
+        acc += v
+        cdf.append(acc)
+    return q, cdf
+
+
+@pytest.mark.parametrize("I", [1, 2, 31, 32, 33, 1000, 1025, 40000])
+def test_distribution_exact(orc, I):
     rng = np.random.default_rng(I)
-    w = rng.integers(0, 1000, I).astype(np.float64)
-    np.testing.assert_array_equal(orc.cdf(w), np.cumsum(w))   # exact: integer sums
+    w = np.exp(3 * rng.standard_normal(I)) * (rng.random(I) > 0.1)
+    w[rng.integers(0, I)] = 5.0
+    if I > 3:
+        w[:3] = [1e-300, 5e-324, 0.0]          # tiny, subnormal and zero weights
+    st, c = orc.distribution(w)
+    assert st == orc.OK
+    q, cdf = exact_distribution(list(w))
+    assert [int(v) for v in c] == cdf
+    assert cdf[-1] < 2**62
+    for i in range(min(I, 50)):
+        assert orc.prob(c, i) == float(q[i]) / float(cdf[-1])
 
 
-@pytest.mark.parametrize("I", [33, 1000, 40000])
-def test_cdf_close_on_reals(orc, I):
-    rng = np.random.default_rng(I + 1)
-    w = np.exp(rng.standard_normal(I))
-    c = orc.cdf(w)
-    np.testing.assert_allclose(c, np.cumsum(w), rtol=1e-13)
-    assert np.all(np.diff(c) >= 0)
+def test_distribution_degenerate(orc):
+    assert orc.distribution(np.zeros(5))[0] == orc.EDEGENERATE
+    assert orc.distribution(np.array([1.0, np.nan]))[0] == orc.EDEGENERATE
+    assert orc.distribution(np.array([1.0, -2.0]))[0] == orc.EDEGENERATE
 
 
-def test_draw_intervals_and_zero_weights(orc):
-    w = np.array([0.0, 2.0, 0.0, 0.0, 1.0, 5.0, 0.0])
-    c = orc.cdf(w)
-    W = c[-1]
-    assert orc.draw(c, 0.0) == 1                       # first positive-weight row
-    for i in np.nonzero(w)[0]:
-        lo = c[i] - w[i]
-        mid = (lo + w[i] / 2) / W
-        assert orc.draw(c, mid) == i
-    us = np.linspace(0, 1, 20001)[:-1]
-    drawn = {orc.draw(c, u) for u in us}
-    assert drawn == {1, 4, 5}                          # zero-weight rows never drawn
-    assert orc.draw(c, 1.0 - 2.0**-53) == 5
+def test_draw_matches_bigint(orc):
+    import bisect
+    rng = np.random.default_rng(5)
+    w = np.array([0.0, 2.0, 0.0, 0.0, 1.0, 5.0, 0.0, 1e-30, 3.0])
+    st, c = orc.distribution(w)
+    cdf = [int(v) for v in c]
+    for x in list(rng.integers(0, 2**63, 2000, dtype=np.uint64)) + [0, 2**64 - 1, 2**63]:
+        x = int(x)
+        target = (x * cdf[-1]) >> 64
+        assert orc.draw(c, x) == bisect.bisect_right(cdf, target)
+    drawn = {orc.draw(c, int(x)) for x in rng.integers(0, 2**63, 20000, dtype=np.uint64) * 2}
+    assert drawn <= {1, 4, 5, 8} and {1, 4, 5} <= drawn      # zero-weight rows never drawn
+
+
+def test_uniform_weights_draw_is_multiply_high(orc):
+    for I in (1, 7, 1000, 12345):
+        st, c = orc.distribution(np.ones(I))
+        rng = np.random.default_rng(I)
+        for x in rng.integers(0, 2**63, 200, dtype=np.uint64):
+            x = int(x) * 2 + 1
+            assert orc.draw(c, x) == (x * I) >> 64
+            assert orc.prob(c, 0) == 1.0 / I
+
+
+def test_euclidean_weights_exact_on_integers(orc):
+    rng = np.random.default_rng(6)
+    A = rng.integers(-50, 50, (40, 77)).astype(np.float64)
+    st, w = orc.weights("euclidean", A)
+    np.testing.assert_array_equal(w, (A.astype(np.int64) ** 2).sum(1).astype(np.float64))
 
 
 def test_sampler_frequencies_chi2(orc):
@@ -230,10 +262,10 @@ def test_sampler_frequencies_chi2(orc):
     A = rng.standard_normal((50, 4)) * np.exp(rng.standard_normal((50, 1)))
     st, w = orc.weights("euclidean", A)
     np.testing.assert_allclose(w, (A ** 2).sum(1), rtol=1e-15)
-    c = orc.cdf(w)
+    st, c = orc.distribution(w)
     p = (A ** 2).sum(1) / (A ** 2).sum()
     n = 100000
-    draws = [orc.draw(c, orc.u53(orc.fiber_word(99, 3, f, 1))) for f in range(n)]
+    draws = [orc.draw(c, orc.fiber_word(99, 3, f, 1)) for f in range(n)]
     counts = np.bincount(draws, minlength=50)
     exp = n * p
     keep = exp > 5
