@@ -177,13 +177,31 @@ cpd_status cpd_last_gradient(cpd_ctx *ctx, void *G, void *stream);
 cpd_status cpd_sync(cpd_ctx *ctx, void *stream);
 
 /*
- * cpd_profile -- enable (1) or disable (0) per-kernel CUDA-event timing of the
- * gradient kernel, recorded on the launching stream; cpd_profile_read
- * returns the number of timed launches and their mean duration (ms) since
- * the last enable, synchronising `stream`.
+ * cpd_profile -- enable (1) or disable (0) per-kernel CUDA-event timing,
+ * recorded on the launching stream around the gradient kernel and around the
+ * rest of each iteration (update, CDF refresh). cpd_profile_read returns the
+ * number of timed iterations and the mean duration (ms) of each part since
+ * the last enable, synchronising `stream`. Either output may be NULL.
  */
 cpd_status cpd_profile(cpd_ctx *ctx, int enable);
-cpd_status cpd_profile_read(cpd_ctx *ctx, int64_t *launches, double *mean_ms, void *stream);
+cpd_status cpd_profile_read(cpd_ctx *ctx, int64_t *launches, double *mean_grad_ms,
+                            double *mean_update_ms, void *stream);
+
+/*
+ * cpd_trace -- enable (1) or disable (0) device-side phase timestamps
+ * (%globaltimer, ns) of the iterations that follow; cpd_trace_read copies the
+ * 64 stamps of the most recent traced iteration to host memory `out`
+ * (synchronising `stream`; 0 = phase not reached):
+ *   [0..9]   gradient kernel, first CTA: entry, TMEM/mbarrier set-up done,
+ *            draws done, weights and row copies issued, gather issued, KRP
+ *            rows and operands built, MMAs issued and H formed, MMAs
+ *            complete, epilogue done, exit;
+ *   [16..19] update kernel, first CTA: entry, gradient reduced, step applied,
+ *            row weights written;
+ *   [20..21] update kernel, last CTA: distribution rebuild start / end.
+ */
+cpd_status cpd_trace(cpd_ctx *ctx, int enable);
+cpd_status cpd_trace_read(cpd_ctx *ctx, uint64_t *out, void *stream);
 
 /*
  * cpd_describe -- launch configuration chosen for the context, as a

@@ -64,10 +64,13 @@ def _load():
         "cpd_last_gradient": [P, P, P],
         "cpd_sync": [P, P],
         "cpd_profile": [P, I32],
-        "cpd_profile_read": [P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double), P],
+        "cpd_profile_read": [P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), P],
         "cpd_describe": [P, ctypes.c_char_p, ctypes.c_size_t],
         "cpd_destroy": [P],
         "cpd_tol_noalloc": [I32, P, I32, I32, P, P, P, P],
+        "cpd_trace": [P, I32],
+        "cpd_trace_read": [P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -185,10 +188,23 @@ def cpd_profile(ctx, enable: bool) -> None:
     _check(_lib.cpd_profile(ctx, int(bool(enable))))
 
 
-def cpd_profile_read(ctx, stream=None) -> tuple[int, float]:
-    n, ms = ctypes.c_int64(), ctypes.c_double()
-    _check(_lib.cpd_profile_read(ctx, ctypes.byref(n), ctypes.byref(ms), _stream(stream)))
-    return n.value, ms.value
+def cpd_profile_read(ctx, stream=None) -> tuple[int, float, float]:
+    """(timed iterations, mean gradient-kernel ms, mean ms of the rest of an iteration)."""
+    n, mg, mu = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.cpd_profile_read(ctx, ctypes.byref(n), ctypes.byref(mg), ctypes.byref(mu),
+                                 _stream(stream)))
+    return n.value, mg.value, mu.value
+
+
+def cpd_trace(ctx, enable: bool) -> None:
+    _check(_lib.cpd_trace(ctx, int(bool(enable))))
+
+
+def cpd_trace_read(ctx, stream=None) -> list:
+    """The 64 phase timestamps (ns) of the most recent traced iteration."""
+    out = (ctypes.c_uint64 * 64)()
+    _check(_lib.cpd_trace_read(ctx, out, _stream(stream)))
+    return [int(v) for v in out]
 
 
 def cpd_describe(ctx) -> dict:

@@ -64,6 +64,7 @@ struct cpd_ctx {
     std::vector<cudaEvent_t> ev;
     int prof_used = 0;
     bool has_sample = false;
+    unsigned long long *trace_buf = nullptr;
 
     template <class F>
     cudaError_t with_problem(F &&f)
@@ -142,6 +143,8 @@ static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
         int64_t fb = (g.B + pf - 1) / pf;
         fb = (fb + 15) / 16 * 16;
         P.fb = (int)std::min<int64_t>(128, std::max<int64_t>(16, fb));
+        if constexpr (sizeof(T) == 4)
+            while (P.fb > 16 && tc_smem_bytes(P) > 220 * 1024) P.fb -= 16;
     } else {
         P.rb = (int)std::min<int64_t>(64, round8(imax));
         int64_t pr_max = (imax + P.rb - 1) / P.rb;
@@ -185,6 +188,7 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
         for (int m = 0; m < g.N; ++m)
             if (m != k) J *= (double)g.dims[m];
         P.Jn[k] = J;
+        P.inv_bj[k] = (float)(1.0 / ((double)g.B * J));
     }
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, c->device);
@@ -233,11 +237,11 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
         CK(dmalloc(c, &a, fb * sizeof(T)));
         CK(dmalloc(c, &S, fb * sizeof(double)));
         CK(dmalloc(c, &w, g.dims[k] * sizeof(double)));
-        CK(dmalloc(c, &cdf, g.dims[k] * sizeof(double)));
+        CK(dmalloc(c, &cdf, g.dims[k] * sizeof(unsigned long long)));
         CK(cudaMemcpyAsync(a, A0[k], fb * sizeof(T),
                            a0_loc == CPD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
         CK(cudaMemsetAsync(S, 0, fb * sizeof(double), s));
-        P.A[k] = (T *)a; P.S[k] = (double *)S; P.w[k] = (double *)w; P.cdf[k] = (double *)cdf;
+        P.A[k] = (T *)a; P.S[k] = (double *)S; P.w[k] = (double *)w; P.cdf[k] = (unsigned long long *)cdf;
     }
     void *p;
     CK(dmalloc(c, &p, sizeof(long long)));  P.t_dev = (long long *)p;
@@ -245,9 +249,7 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     CK(dmalloc(c, &p, (size_t)g.B * g.N * sizeof(int)));  P.idx = (int *)p;
     CK(dmalloc(c, &p, (size_t)g.B * sizeof(double)));     P.p = (double *)p;
     CK(dmalloc(c, &p, (size_t)P.pf * g.R * c->imax * sizeof(T)));  P.part = (T *)p;
-    CK(dmalloc(c, &p, (size_t)(P.pf + 1) * g.R * g.R * sizeof(float)));  P.hpart = (float *)p;
     CK(dmalloc(c, &p, (size_t)c->imax * g.R * sizeof(T)));  P.G = (T *)p;
-    CK(dmalloc(c, &p, (size_t)(c->imax / 31 + 64) * sizeof(double)));  P.scan_scratch = (double *)p;
     CK(dmalloc(c, &p, (size_t)(2 * g.R * g.R + g.R + 8) * sizeof(double)));  P.lev_L = (double *)p;
     CK(dmalloc(c, &p, sizeof(int)));  P.status = (int *)p;
     CK(dmalloc(c, &p, 16 * sizeof(unsigned)));  P.counters = (unsigned *)p;
@@ -310,13 +312,14 @@ static cudaError_t run_plain(cpd_ctx *c, int64_t iters, cudaStream_t s)
 {
     Problem<T> &P = problem<T>(c);
     for (int64_t q = 0; q < iters; ++q) {
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
         if (c->profiling && c->prof_used < kProfSlots) {
-            e0 = c->ev[2 * c->prof_used];
-            e1 = c->ev[2 * c->prof_used + 1];
+            e0 = c->ev[3 * c->prof_used];
+            e1 = c->ev[3 * c->prof_used + 1];
+            e2 = c->ev[3 * c->prof_used + 2];
             ++c->prof_used;
         }
-        cudaError_t e = launch_iteration(P, c->grid_grad, c->grid_upd, c->smem_grad, s, c->engine, e0, e1);
+        cudaError_t e = launch_iteration(P, c->grid_grad, c->grid_upd, c->smem_grad, s, c->engine, e0, e1, e2);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -339,7 +342,7 @@ static cudaError_t run_graph(cpd_ctx *c, int64_t chunks, cudaStream_t s)
             Problem<T> &P = problem<T>(c);
             for (int q = 0; q < kGraphChunk && e == cudaSuccess; ++q)
                 e = launch_iteration(P, c->grid_grad, c->grid_upd, c->smem_grad, cap, c->engine, nullptr,
-                                     nullptr);
+                                     nullptr, nullptr);
             cudaError_t e2 = cudaStreamEndCapture(cap, &g);
             if (e == cudaSuccess) e = e2;
         }
@@ -501,9 +504,13 @@ extern "C" cpd_status cpd_last_sample(cpd_ctx *c, int32_t *n, int32_t *idx, doub
     if (idx)
         CK(cudaMemcpyAsync(idx, d ? c->Pd.idx : c->Pf.idx, (size_t)c->cfg.B * c->cfg.N * sizeof(int),
                            cudaMemcpyDeviceToHost, s));
-    if (p)
+    if (p) {
+        // p_f is formed on demand from the recorded batch (off the iteration path)
+        const cudaError_t e = d ? launch_sample_probs(c->Pd, s) : launch_sample_probs(c->Pf, s);
+        if (e != cudaSuccess) return cuda_fail(e, "sample probabilities");
         CK(cudaMemcpyAsync(p, d ? c->Pd.p : c->Pf.p, (size_t)c->cfg.B * sizeof(double),
                            cudaMemcpyDeviceToHost, s));
+    }
     CK(cudaStreamSynchronize(s));
     return CPD_OK;
 }
@@ -528,7 +535,7 @@ extern "C" cpd_status cpd_profile(cpd_ctx *c, int enable)
 {
     if (!c) return fail(CPD_EINVAL, "NULL context");
     if (enable && c->ev.empty()) {
-        c->ev.resize(2 * kProfSlots);
+        c->ev.resize(3 * kProfSlots);
         for (auto &e : c->ev) CK(cudaEventCreate(&e));
     }
     c->profiling = enable != 0;
@@ -536,18 +543,49 @@ extern "C" cpd_status cpd_profile(cpd_ctx *c, int enable)
     return CPD_OK;
 }
 
-extern "C" cpd_status cpd_profile_read(cpd_ctx *c, int64_t *launches, double *mean_ms, void *stream)
+extern "C" cpd_status cpd_profile_read(cpd_ctx *c, int64_t *launches, double *mean_grad_ms,
+                                       double *mean_update_ms, void *stream)
 {
     if (!c) return fail(CPD_EINVAL, "NULL context");
     CK(cudaStreamSynchronize((cudaStream_t)stream));
-    double tot = 0.0;
+    double tg = 0.0, tu = 0.0;
     for (int q = 0; q < c->prof_used; ++q) {
         float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, c->ev[2 * q], c->ev[2 * q + 1]));
-        tot += ms;
+        CK(cudaEventElapsedTime(&ms, c->ev[3 * q], c->ev[3 * q + 1]));
+        tg += ms;
+        CK(cudaEventElapsedTime(&ms, c->ev[3 * q + 1], c->ev[3 * q + 2]));
+        tu += ms;
     }
     if (launches) *launches = c->prof_used;
-    if (mean_ms) *mean_ms = c->prof_used ? tot / c->prof_used : 0.0;
+    if (mean_grad_ms) *mean_grad_ms = c->prof_used ? tg / c->prof_used : 0.0;
+    if (mean_update_ms) *mean_update_ms = c->prof_used ? tu / c->prof_used : 0.0;
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_trace(cpd_ctx *c, int enable)
+{
+    if (!c) return fail(CPD_EINVAL, "NULL context");
+    unsigned long long *&tr = c->fbytes == 8 ? c->Pd.trace : c->Pf.trace;
+    if (enable && !c->trace_buf) {
+        void *p;
+        CK(dmalloc(c, &p, 64 * sizeof(unsigned long long)));
+        CK(cudaMemset(p, 0, 64 * sizeof(unsigned long long)));
+        c->trace_buf = (unsigned long long *)p;
+    }
+    tr = enable ? c->trace_buf : nullptr;
+    if (c->graph) {  // captured launches carry the old pointer
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_trace_read(cpd_ctx *c, uint64_t *out, void *stream)
+{
+    if (!c || !out) return fail(CPD_EINVAL, "bad argument");
+    if (!c->trace_buf) return fail(CPD_EINVAL, "tracing was never enabled");
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaMemcpy(out, c->trace_buf, 64 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     return CPD_OK;
 }
 

@@ -12,6 +12,17 @@
 
 namespace cpd {
 
+// Phase timestamp (%globaltimer, ns) into P.trace[slot] from one thread of the
+// chosen CTA, when tracing is on.
+__device__ __forceinline__ void trace_stamp(unsigned long long *trace, int slot, bool cta)
+{
+    if (trace && cta && threadIdx.x == 0) {
+        unsigned long long ns;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(ns));
+        trace[slot] = ns;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as
 // easy as 1, 2, 3", SC'11): ten rounds of two 64x64->128 multiplications,
@@ -64,31 +75,24 @@ __device__ __forceinline__ unsigned long long fiber_word(unsigned long long seed
     return x.v[k & 3];
 }
 
-__device__ __forceinline__ double u53(unsigned long long x)
-{
-    return __dmul_rn((double)(x >> 11), 0x1.0p-53);
-}
-
 // ---------------------------------------------------------------------------
-// Warp-cooperative inverse-CDF search (Def. 2 sampling from an FP64 CDF).
-// Every lane brings one target; all 32 searches share the CDF c[0..I).
-// Each lane ends with min{ i : target < c[i] } (I-1 if no such i).
-// One level splits every lane's candidate range into 32 segments: the warp
-// issues the 32 draws' segment-end loads back to back (one memory round trip
-// per level for all 32 draws) and a ballot per draw picks the segment, so an
-// I-entry CDF costs ceil(log32 I) + 1 dependent round trips.
+// Warp-cooperative inverse-CDF search (Def. 2 sampling). The CDF is exact
+// 64-bit fixed point: cdf[i] = q_0 + ... + q_i. Every lane brings one target
+// t = floor(x Q / 2^64) and ends with min{ i : t < cdf[i] }. One level splits
+// every lane's candidate range into 32 segments: the warp issues the 32
+// draws' segment-end loads back to back (one memory round trip per level for
+// all 32 draws) and a ballot per draw picks the segment, so an I-entry CDF
+// costs ceil(log32 I) + 1 dependent round trips.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ long long warp_search_cdf(const double *__restrict__ c, long long I,
-                                                     double target, bool active)
+__device__ __forceinline__ long long warp_search_cdf(const unsigned long long *__restrict__ c, long long I,
+                                                     unsigned long long target, bool active)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const double top = __ldg(c + (I - 1));
-    bool done = !active || !(target < top);
     long long result = I - 1;
-    long long lo = 0, len = done ? 0 : I;
+    long long lo = 0, len = active ? I : 0;
     while (__any_sync(full, len > 32)) {
-        double v[32];
+        unsigned long long v[32];
 #pragma unroll
         for (int d = 0; d < 32; ++d) {
             const long long lo_d = __shfl_sync(full, lo, d);
@@ -99,13 +103,13 @@ __device__ __forceinline__ long long warp_search_cdf(const double *__restrict__ 
                 end = end < len_d ? end : len_d;
                 v[d] = __ldg(c + lo_d + end - 1);
             } else {
-                v[d] = 0.0;
+                v[d] = 0;
             }
         }
 #pragma unroll
         for (int d = 0; d < 32; ++d) {
             const long long len_d = __shfl_sync(full, len, d);
-            const double tg = __shfl_sync(full, target, d);
+            const unsigned long long tg = __shfl_sync(full, target, d);
             const unsigned m = __ballot_sync(full, tg < v[d]);
             if (len_d > 32 && lane == d) {
                 const long long step = (len_d + 31) / 32;
@@ -116,96 +120,117 @@ __device__ __forceinline__ long long warp_search_cdf(const double *__restrict__ 
             }
         }
     }
-    double v[32];
+    unsigned long long v[32];
 #pragma unroll
     for (int d = 0; d < 32; ++d) {
         const long long lo_d = __shfl_sync(full, lo, d);
         const long long len_d = __shfl_sync(full, len, d);
-        v[d] = (lane < len_d) ? __ldg(c + lo_d + lane) : 0.0;
+        v[d] = (lane < len_d) ? __ldg(c + lo_d + lane) : 0;
     }
 #pragma unroll
     for (int d = 0; d < 32; ++d) {
         const long long len_d = __shfl_sync(full, len, d);
-        const double tg = __shfl_sync(full, target, d);
+        const unsigned long long tg = __shfl_sync(full, target, d);
         const unsigned m = __ballot_sync(full, (lane < len_d) && (tg < v[d]));
-        if (lane == d && len_d > 0)
-            result = lo + (__ffs(m) - 1);
+        if (lane == d && len_d > 0) result = m ? lo + (__ffs(m) - 1) : I - 1;
     }
-    return done ? I - 1 : result;
+    return result;
+}
+
+// Row weight of the Euclidean distribution (Def. 5, Lemma 4) in the canonical
+// order, by one warp: lane l accumulates a_r^2 for r = l, l+32, ... (fma from
+// +0), then the shuffle-down tree adds lane l+off into lane l for off =
+// 16..1. The FP64 dependency chain is ceil(R/32) + 5 operations long.
+template <class T>
+__device__ __forceinline__ double warp_row_weight(const T *row, int R)
+{
+    double acc = 0.0;
+    for (int r = threadIdx.x & 31; r < R; r += 32) {
+        const double a = (double)row[r];
+        acc = __fma_rn(a, a, acc);
+    }
+    for (int off = 16; off >= 1; off >>= 1) acc = __dadd_rn(acc, __shfl_down_sync(0xffffffffu, acc, off));
+    return acc;
+}
+
+// floor(w 2^s) for a finite w >= 0, exactly, on the integer pipe: w = M 2^e
+// with an integer mantissa M.
+__device__ __forceinline__ unsigned long long quantize(double w, int s)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(w);
+    const int ef = (int)(bits >> 52);
+    const unsigned long long frac = bits & ((1ULL << 52) - 1);
+    const unsigned long long M = ef ? (frac | (1ULL << 52)) : frac;
+    const int e = (ef ? ef : 1) - 1075;
+    const int sh = e + s;
+    if (sh >= 0) return M << sh;   // bounded by 2^62 through the choice of s
+    if (sh <= -64) return 0;
+    return M >> (-sh);
 }
 
 // ---------------------------------------------------------------------------
-// Canonical inclusive prefix sum ("scan32") by one CTA, in place on a[0..I):
-// chunks of 32 summed sequentially; chunk totals scanned recursively by the
-// same rule; offsets added top-down. `levels` needs ceil(I/31) + 8 doubles.
+// The fixed-point distribution of one factor from its FP64 row weights, by
+// one CTA: s = 61 - ceil(log2 I) - floor(log2 max w), q_i = floor(w_i 2^s),
+// cdf = inclusive prefix sum of q (exact, so any summation order gives the
+// same bits). Returns false (in every thread) when a weight is negative or
+// not finite, or when every q_i is 0. `sm` holds 2 * blockDim.x uint64 slots.
+// w is read through L2 (other CTAs of the launch may have written it).
 // ---------------------------------------------------------------------------
-__device__ inline void scan32_inplace(double *a, long long I, double *levels)
+__device__ inline bool block_distribution(const double *w, long long I, unsigned long long *cdf,
+                                          unsigned long long *sm)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (long long c = tid; c * 32 < I; c += nt) {
-        double acc = 0.0;
-        const long long hi = (c + 1) * 32 < I ? (c + 1) * 32 : I;
-        for (long long e = c * 32; e < hi; ++e) {
-            acc = __dadd_rn(acc, a[e]);
-            a[e] = acc;
-        }
+    // largest weight, through the integer order of non-negative doubles
+    long long mx = 0;
+    int bad = 0;
+    for (long long i = tid; i < I; i += nt) {
+        const double v = __ldcg(w + i);
+        if (!(v >= 0.0) || isinf(v)) bad = 1;
+        const long long b = __double_as_longlong(v);
+        mx = b > mx ? b : mx;
     }
-    double *lev[12];
-    long long levn[12];
+    for (int off = 16; off >= 1; off >>= 1) {
+        const long long o = __shfl_down_sync(0xffffffffu, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    bad = __syncthreads_or(bad);
+    if ((tid & 31) == 0) sm[tid >> 5] = (unsigned long long)mx;
+    __syncthreads();
+    long long gmx = 0;
+    for (int q = 0; q < (nt >> 5); ++q) gmx = (long long)sm[q] > gmx ? (long long)sm[q] : gmx;
+    __syncthreads();
+    const double wmax = __longlong_as_double(gmx);
+    if (bad || !(wmax > 0.0)) return false;
+    // floor(log2 wmax): exponent field for a normal number, leading bit for a subnormal
+    const int ef = (int)((unsigned long long)gmx >> 52);
+    const int lg = ef ? ef - 1023 : 63 - __clzll(gmx) - 1074;
     int L = 0;
-    const double *src = a;
-    long long cnt = I;
-    double *sp = levels;
-    while (cnt > 32) {
-        const long long nc = (cnt + 31) / 32;
-        __syncthreads();
-        for (long long c = tid; c < nc; c += nt) {
-            const long long last = (c + 1) * 32 - 1 < cnt ? (c + 1) * 32 - 1 : cnt - 1;
-            sp[c] = src[last];
-        }
-        __syncthreads();
-        for (long long c = tid; c * 32 < nc; c += nt) {
-            double acc = 0.0;
-            const long long hi = (c + 1) * 32 < nc ? (c + 1) * 32 : nc;
-            for (long long e = c * 32; e < hi; ++e) {
-                acc = __dadd_rn(acc, sp[e]);
-                sp[e] = acc;
-            }
-        }
-        lev[L] = sp;
-        levn[L] = nc;
-        ++L;
-        src = sp;
-        sp += nc;
-        cnt = nc;
+    while ((1LL << L) < I) ++L;
+    const int s = 61 - L - lg;
+    // exact prefix sum: contiguous chunk per thread, then an exclusive scan of
+    // the chunk totals across the CTA
+    const long long chunk = (I + nt - 1) / nt;
+    const long long i0 = tid * chunk, i1 = (i0 + chunk < I) ? i0 + chunk : I;
+    unsigned long long tot = 0;
+    for (long long i = i0; i < i1; ++i) tot += quantize(__ldcg(w + i), s);
+    unsigned long long inc = tot;
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, off);
+        if ((tid & 31) >= off) inc += o;
     }
-    for (int l = L - 1; l >= 0; --l) {
-        __syncthreads();
-        double *below = (l == 0) ? a : lev[l - 1];
-        const long long nb = (l == 0) ? I : levn[l - 1];
-        for (long long e = 32 + tid; e < nb; e += nt)
-            below[e] = __dadd_rn(lev[l][e / 32 - 1], below[e]);
-    }
+    if ((tid & 31) == 31) sm[nt + (tid >> 5)] = inc;
     __syncthreads();
-}
-
-// cdf[0..I) = scan32(w[0..I)). Staged through the shared buffer sm (cap
-// doubles) when it fits, else in global memory with `scratch` for the levels.
-// w is read through L2 (other CTAs of the launch may have written it).
-__device__ inline void block_scan32(const double *w, long long I, double *cdf, double *scratch,
-                                    double *sm, int cap)
-{
-    if (I + I / 31 + 16 <= cap) {
-        for (long long e = threadIdx.x; e < I; e += blockDim.x) sm[e] = __ldcg(w + e);
-        __syncthreads();
-        scan32_inplace(sm, I, sm + I);
-        for (long long e = threadIdx.x; e < I; e += blockDim.x) cdf[e] = sm[e];
-    } else {
-        for (long long e = threadIdx.x; e < I; e += blockDim.x) cdf[e] = __ldcg(w + e);
-        __syncthreads();
-        scan32_inplace(cdf, I, scratch);
+    unsigned long long base = 0;
+    for (int q = 0; q < (tid >> 5); ++q) base += sm[nt + q];
+    unsigned long long acc = base + inc - tot;
+    for (long long i = i0; i < i1; ++i) {
+        acc += quantize(__ldcg(w + i), s);
+        cdf[i] = acc;
     }
+    unsigned long long Q = 0;
+    for (int q = 0; q < (nt >> 5); ++q) Q += sm[nt + q];
     __syncthreads();
+    return Q > 0;
 }
 
 template <class XT>
@@ -239,21 +264,20 @@ __device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int
             continue;
         }
         const long long Ik = P.dims[k];
-        unsigned long long x = act ? fiber_word(P.seed, t, (long long)(f0 + fl), k) : 0ULL;
+        const unsigned long long x = act ? fiber_word(P.seed, t, (long long)(f0 + fl), k) : 0ULL;
         long long i;
         if (P.sampling == CPD_SAMPLE_UNIFORM) {
             i = (long long)__umul64hi(x, (unsigned long long)Ik);
         } else {
-            const double *c = P.cdf[k];
-            const double target = __dmul_rn(u53(x), __ldg(c + (Ik - 1)));
-            i = warp_search_cdf(c, Ik, target, act);
+            const unsigned long long *c = P.cdf[k];
+            i = warp_search_cdf(c, Ik, __umul64hi(x, __ldg(c + (Ik - 1))), act);
         }
         if (act) sidx[fl * P.N + k] = (int)i;
     }
 }
 
-// p_f (Eq. block_lev_prob, product in ascending k) and the weight
-// s_f = 1 / (B J_n p_f) of the fiber's term in Eq. gradient1.
+// p_f = prod_{k != n, ascending} q_k(i_k) / Q_k in FP64 (Eq. block_lev_prob),
+// for the record of the last batch; uniform: q = 1, Q = I_k.
 template <class T>
 __device__ __forceinline__ double fiber_prob(const Problem<T> &P, int n, const int *row)
 {
@@ -263,11 +287,32 @@ __device__ __forceinline__ double fiber_prob(const Problem<T> &P, int n, const i
         if (P.sampling == CPD_SAMPLE_UNIFORM) {
             p = __dmul_rn(p, __ddiv_rn(1.0, (double)P.dims[k]));
         } else {
-            const double W = __ldg(P.cdf[k] + (P.dims[k] - 1));
-            p = __dmul_rn(p, __ddiv_rn(__ldg(P.w[k] + row[k]), W));
+            const unsigned long long *c = P.cdf[k];
+            const unsigned long long q = c[row[k]] - (row[k] > 0 ? c[row[k] - 1] : 0ULL);
+            p = __dmul_rn(p, __ddiv_rn(__ull2double_rn(q), __ull2double_rn(c[P.dims[k] - 1])));
         }
     }
     return p;
+}
+
+// The fiber's weight in Eq. gradient1, s_f = 1 / (B J_n p_f), in FP32 (the
+// gradient's own precision): (1/(B J_n)) prod_k Q_k / q_k(i_k).
+template <class T>
+__device__ __forceinline__ float fiber_weight(const Problem<T> &P, int n, const int *row)
+{
+    float s = P.inv_bj[n];
+    for (int k = 0; k < P.N; ++k) {
+        if (k == n) continue;
+        if (P.sampling == CPD_SAMPLE_UNIFORM) {
+            s *= (float)P.dims[k];
+        } else {
+            const unsigned long long *c = P.cdf[k];
+            const unsigned long long hi = __ldg(c + row[k]);
+            const unsigned long long lo = row[k] > 0 ? __ldg(c + row[k] - 1) : 0ULL;
+            s *= __ull2float_rn(__ldg(c + P.dims[k] - 1)) / __ull2float_rn(hi - lo);
+        }
+    }
+    return s;
 }
 
 template <class XT, class T>

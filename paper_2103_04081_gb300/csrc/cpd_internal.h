@@ -47,21 +47,21 @@ struct Problem {
     const void *rep[kMaxModes];
     T *A[kMaxModes];
     double *S[kMaxModes];
-    double *w[kMaxModes];
-    double *cdf[kMaxModes];
+    double *w[kMaxModes];     // FP64 row weights
+    unsigned long long *cdf[kMaxModes];  // exact prefix sums of q_i = floor(w_i 2^s)
+    float inv_bj[kMaxModes];  // 1 / (B J_n) in FP32
     double alpha, eta, b, beta, gamma;
     unsigned long long seed;
     long long *t_dev;         // iteration counter
     int *n_last;              // mode of the last completed iteration
     int *idx;                 // B x N, last batch (column n = -1)
     double *p;                // B, last batch probabilities
-    T *part;                  // gradient partials [pf][R][I_n] (SIMT engine) or M partials
-    float *hpart;             // H partials [pf][R][R] (tensor engine)
+    T *part;                  // gradient partials [pf][I_n][R], one slab per fiber group
     T *G;                     // last gradient, I_n x R row-major
-    double *scan_scratch;     // canonical-scan level buffers
     double *lev_L;            // leverage: Cholesky factor R x R + inverse pivots R
     int *status;              // kSt* bits
     unsigned *counters;       // last-block arrival counters (zero between launches)
+    unsigned long long *trace;  // phase timestamps (cpd_trace), or null
 };
 
 // Launchers (cpd_kernels.cu). Every launcher enqueues on `stream` and
@@ -69,9 +69,11 @@ struct Problem {
 template <class T>
 cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd,
                              size_t smem_grad, cudaStream_t stream, int engine,
-                             cudaEvent_t ev0, cudaEvent_t ev1);
+                             cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t ev2);
 template <class T>
 cudaError_t launch_refresh_mode(const Problem<T> &P, int k, cudaStream_t stream);
+template <class T>
+cudaError_t launch_sample_probs(const Problem<T> &P, cudaStream_t stream);
 template <class T>
 cudaError_t launch_fit(const Problem<T> &P, double *partials, int nblocks,
                        double *out2, cudaStream_t stream, int want_xnorm);

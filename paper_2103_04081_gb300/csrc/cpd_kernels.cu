@@ -115,12 +115,12 @@ __global__ void __launch_bounds__(kThreads) k_grad_simt(const Problem<T> P)
             Jp *= P.dims[k];
         }
         jcol[f] = j;
-        const double p = fiber_prob(P, n, row);
-        ss[f] = (T)__ddiv_rn(1.0, __dmul_rn(__dmul_rn((double)P.B, P.Jn[n]), p));
-        if (gr == 0) {
-            P.p[f0 + f] = p;
+        if constexpr (sizeof(T) == 8)
+            ss[f] = __ddiv_rn(1.0, __dmul_rn(__dmul_rn((double)P.B, P.Jn[n]), fiber_prob(P, n, row)));
+        else
+            ss[f] = fiber_weight(P, n, row);
+        if (gr == 0)
             for (int k = 0; k < N; ++k) P.idx[(long long)(f0 + f) * N + k] = row[k];
-        }
     }
     // 3. sampled KRP rows z_f = Hadamard product of A^(k)(i_k,:), k != n (Alg. 1)
     for (int e = threadIdx.x; e < nf * R; e += blockDim.x) {
@@ -161,34 +161,23 @@ __global__ void __launch_bounds__(kThreads) k_grad_simt(const Problem<T> P)
 // ---------------------------------------------------------------------------
 // Reduction + step. CTA b owns rows [b*rpc, b*rpc+rpc) of A^(n).
 // ---------------------------------------------------------------------------
-template <class T>
-__device__ __forceinline__ double row_weight_euclid(const T *row, int R)
-{
-    double acc = 0.0;
-    for (int r = 0; r < R; ++r) acc = __fma_rn((double)row[r], (double)row[r], acc);
-    return acc;
-}
 
-constexpr int kScanSmem = 4224;  // doubles of the shared scan buffer (I_k up to ~4080)
-
-// Rebuild cdf[k] from w[k] (one CTA); a distribution without mass is flagged.
+// Rebuild the fixed-point distribution of mode k from w[k] (one CTA); a
+// distribution without mass is flagged.
 template <class T>
-__device__ void finish_cdf(const Problem<T> &P, int k, double *sm)
+__device__ void finish_distribution(const Problem<T> &P, int k, unsigned long long *sm)
 {
-    const long long Ik = P.dims[k];
-    block_scan32(P.w[k], Ik, P.cdf[k], P.scan_scratch, sm, kScanSmem);
-    if (threadIdx.x == 0) {
-        const double W = P.cdf[k][Ik - 1];
-        if (!(W > 0.0) || !isfinite(W)) atomicOr(P.status, kStDegenerate);
-    }
+    if (!block_distribution(P.w[k], P.dims[k], P.cdf[k], sm) && threadIdx.x == 0)
+        atomicOr(P.status, kStDegenerate);
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P, int tensor_engine)
+__global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P)
 {
     __shared__ T s_new[kThreads];
-    __shared__ __align__(16) double s_buf[kScanSmem];   // H (tensor engine), then the scan
-    float *sH = reinterpret_cast<float *>(s_buf);
+    __shared__ unsigned long long s_dist[2 * kThreads];
+    const bool tr0 = blockIdx.x == 0;
+    trace_stamp(P.trace, 16, tr0);
     const long long t = *P.t_dev;
     const int N = P.N, R = P.R;
     const int n = mode_draw(P.seed, t, N);
@@ -198,46 +187,59 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P, int ten
     const long long i = (long long)blockIdx.x * rpc + li;
     const bool act = li < rpc && i < In;
     T *An = P.A[n];
-    if (tensor_engine) {
-        // H = Z_S^T D Z_S, already reduced over fiber groups (R <= 64).
-        const float *H = P.hpart + (long long)P.pf * R * R;
-        for (int e = threadIdx.x; e < R * R; e += blockDim.x) sH[e] = __ldcg(H + e);
-        __syncthreads();
-    }
     if (act) {
+        // G(i, r) = sum of the fiber groups' partials in fixed order; the
+        // loads are issued in batches of 8 so their latencies overlap.
         T g = (T)0;
-        if (!tensor_engine) {
-            for (int q = 0; q < P.pf; ++q) g += P.part[((long long)q * In + i) * R + r];
-        } else {
-            // G = (A H - M) / (B J_n) with M, H reduced over fiber groups.
-            float m = 0.f;
-            for (int q = 0; q < P.pf; ++q) m += (float)P.part[((long long)q * In + i) * R + r];
-            float ah = 0.f;
-            for (int s = 0; s < R; ++s) ah += (float)An[i * R + s] * sH[s * R + r];
-            g = (T)(ah - m);
+        const T *src = P.part + i * R + r;
+        const long long slab = (long long)In * R;
+        for (int q0 = 0; q0 < P.pf; q0 += 8) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (q0 + u < P.pf) ? __ldcg(src + (q0 + u) * slab) : (T)0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (q0 + u < P.pf) g += v[u];
         }
         P.G[i * R + r] = g;
-        double a = (double)An[i * R + r];
+        trace_stamp(P.trace, 17, tr0 && threadIdx.x == 0);
+        T an;
         if (P.step == CPD_STEP_ADAGRAD) {
+            // S accumulates in FP64; the step factor eta / sqrt(b + S) is formed
+            // in the factor type.
             double *Sp = P.S[n] + i * R + r;
-            const double gd = (double)g;
-            const double S = __fma_rn(gd, gd, *Sp);
+            const double S = __fma_rn((double)g, (double)g, *Sp);
             *Sp = S;
-            a = a - P.eta * gd * rsqrt(P.b + S);
+            if constexpr (sizeof(T) == 8)
+                an = An[i * R + r] - P.eta * g * rsqrt(P.b + S);
+            else
+                an = An[i * R + r] - (float)P.eta * g * rsqrtf((float)S + (float)P.b);
         } else {
-            const double alpha = (P.step == CPD_STEP_DECAY) ? P.beta / ((double)t + P.gamma) : P.alpha;
-            a = a - alpha * (double)g;
+            const T alpha = (T)((P.step == CPD_STEP_DECAY) ? P.beta / ((double)t + P.gamma) : P.alpha);
+            an = An[i * R + r] - alpha * g;
         }
-        const T an = (T)a;
         if (!isfinite((double)an) || !isfinite((double)g)) atomicOr(P.status, kStNonFinite);
         An[i * R + r] = an;
         s_new[threadIdx.x] = an;
     }
     __syncthreads();
-    if (P.sampling == CPD_SAMPLE_EUCLIDEAN && act && r == 0)
-        P.w[n][i] = row_weight_euclid(s_new + li * R, R);
+    trace_stamp(P.trace, 18, tr0);
+    if (P.sampling == CPD_SAMPLE_EUCLIDEAN) {
+        // one warp per updated row: the canonical tree-ordered squared norm
+        const int warp = threadIdx.x >> 5;
+        for (int lr = warp; lr < rpc; lr += kThreads / 32) {
+            const long long row = (long long)blockIdx.x * rpc + lr;
+            if (row < In) {
+                const double wv = warp_row_weight(s_new + lr * R, R);
+                if ((threadIdx.x & 31) == 0) P.w[n][row] = wv;
+            }
+        }
+    }
+    trace_stamp(P.trace, 19, tr0);
     if (!last_block(P.counters)) return;
-    if (P.sampling == CPD_SAMPLE_EUCLIDEAN) finish_cdf(P, n, s_buf);
+    trace_stamp(P.trace, 20, true);
+    if (P.sampling == CPD_SAMPLE_EUCLIDEAN) finish_distribution(P, n, s_dist);
+    trace_stamp(P.trace, 21, true);
     if (threadIdx.x == 0) {
         P.counters[0] = 0;
         if (P.sampling != CPD_SAMPLE_LEVERAGE) {
@@ -335,8 +337,8 @@ __global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k
         P.w[k][i] = acc;
     }
     if (!last_block(P.counters + 2)) return;
-    __shared__ double s_scan[kScanSmem];
-    if (!bad) finish_cdf(P, k, s_scan);
+    __shared__ unsigned long long s_dist[2 * kThreads];
+    if (!bad) finish_distribution(P, k, s_dist);
     if (threadIdx.x == 0) {
         P.counters[2] = 0;
         if (advance) {
@@ -347,18 +349,31 @@ __global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k
 }
 
 // Euclidean or uniform weights of mode k from scratch (initialisation and
-// cpd_set_factors), then its CDF.
+// cpd_set_factors), one warp per row, then the distribution.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_weights_euclid(const Problem<T> P, int k)
 {
+    __shared__ unsigned long long s_dist[2 * kThreads];
     const long long I = P.dims[k];
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < I)
-        P.w[k][i] = (P.sampling == CPD_SAMPLE_UNIFORM) ? 1.0 : row_weight_euclid(P.A[k] + i * P.R, P.R);
+    const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row < I) {
+        const double wv = (P.sampling == CPD_SAMPLE_UNIFORM) ? 1.0 : warp_row_weight(P.A[k] + row * P.R, P.R);
+        if ((threadIdx.x & 31) == 0) P.w[k][row] = wv;
+    }
     if (!last_block(P.counters + 3)) return;
-    __shared__ double s_scan[kScanSmem];
-    finish_cdf(P, k, s_scan);
+    finish_distribution(P, k, s_dist);
     if (threadIdx.x == 0) P.counters[3] = 0;
+}
+
+// p_f of the last batch (Eq. block_lev_prob, FP64) for its record; the
+// distributions of the modes k != n it used have not changed since.
+template <class T>
+__global__ void k_sample_probs(const Problem<T> P)
+{
+    const int n = *P.n_last;
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < 0 || f >= P.B) return;
+    P.p[f] = fiber_prob(P, n, P.idx + (long long)f * P.N);
 }
 
 // ---------------------------------------------------------------------------
@@ -505,7 +520,7 @@ static cudaError_t launch_grad_simt(const Problem<T> &P, int grid, size_t smem, 
 
 template <class T>
 cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd, size_t smem_grad,
-                             cudaStream_t s, int engine, cudaEvent_t ev0, cudaEvent_t ev1)
+                             cudaStream_t s, int engine, cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t ev2)
 {
     cudaError_t e = cudaSuccess;
     if (ev0) cudaEventRecord(ev0, s);
@@ -522,7 +537,7 @@ cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd, s
     }
     if (ev1) cudaEventRecord(ev1, s);
     if (e != cudaSuccess) return e;
-    k_update<T><<<grid_upd, kThreads, 0, s>>>(P, engine == kEngineTensor);
+    k_update<T><<<grid_upd, kThreads, 0, s>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (P.sampling == CPD_SAMPLE_LEVERAGE) {
         const int npairs = P.R * (P.R + 1) / 2;
@@ -533,6 +548,7 @@ cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd, s
         k_lev_rows<T><<<(int)((Imax + kThreads - 1) / kThreads), kThreads, 0, s>>>(P, -1, 1);
         e = cudaGetLastError();
     }
+    if (ev2) cudaEventRecord(ev2, s);
     return e;
 }
 
@@ -541,6 +557,7 @@ cudaError_t launch_refresh_mode(const Problem<T> &P, int k, cudaStream_t s)
 {
     const long long I = P.dims[k];
     const int grid = (int)((I + kThreads - 1) / kThreads);
+    const int grid_rows = (int)((I * 32 + kThreads - 1) / kThreads);
     if (P.sampling == CPD_SAMPLE_LEVERAGE) {
         const int npairs = P.R * (P.R + 1) / 2;
         k_gram<T><<<(npairs + 7) / 8, kThreads, 0, s>>>(P, k);
@@ -548,8 +565,15 @@ cudaError_t launch_refresh_mode(const Problem<T> &P, int k, cudaStream_t s)
         if (e != cudaSuccess) return e;
         k_lev_rows<T><<<grid, kThreads, 0, s>>>(P, k, 0);
     } else {
-        k_weights_euclid<T><<<grid, kThreads, 0, s>>>(P, k);
+        k_weights_euclid<T><<<grid_rows, kThreads, 0, s>>>(P, k);
     }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_sample_probs(const Problem<T> &P, cudaStream_t s)
+{
+    k_sample_probs<T><<<(P.B + kThreads - 1) / kThreads, kThreads, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -604,11 +628,13 @@ cudaError_t launch_build_replica(const void *X, void *rep, int esize, int N, con
 template size_t grad_smem_bytes<float>(const Problem<float> &);
 template size_t grad_smem_bytes<double>(const Problem<double> &);
 template cudaError_t launch_iteration<float>(const Problem<float> &, int, int, size_t, cudaStream_t, int,
-                                             cudaEvent_t, cudaEvent_t);
+                                             cudaEvent_t, cudaEvent_t, cudaEvent_t);
 template cudaError_t launch_iteration<double>(const Problem<double> &, int, int, size_t, cudaStream_t, int,
-                                              cudaEvent_t, cudaEvent_t);
+                                              cudaEvent_t, cudaEvent_t, cudaEvent_t);
 template cudaError_t launch_refresh_mode<float>(const Problem<float> &, int, cudaStream_t);
 template cudaError_t launch_refresh_mode<double>(const Problem<double> &, int, cudaStream_t);
+template cudaError_t launch_sample_probs<float>(const Problem<float> &, cudaStream_t);
+template cudaError_t launch_sample_probs<double>(const Problem<double> &, cudaStream_t);
 template cudaError_t launch_fit<float>(const Problem<float> &, double *, int, double *, cudaStream_t, int);
 template cudaError_t launch_fit<double>(const Problem<double> &, double *, int, double *, cudaStream_t, int);
 

@@ -1,25 +1,26 @@
 // Tensor-core gradient engine for BF16 tensors (sm_103a: tcgen05.mma with the
 // accumulator in tensor memory).
 //
-// Eq. gradient1 in the M/H form: with Z'_S = D Z_S / (B J_n) (s_f folded into
-// the sampled KRP rows),
-//   M = X_S Z'_S        (I_n x R)  -- tensor cores, per (row tile, fiber group)
-//   H = Z_S^T Z'_S      (R x R)    -- CUDA cores, FP32, reduced in fixed order
-//   G = A^(n) H - M                 -- k_update.
-// The gathered fibers are BF16 (exact copies of the stored tensor). Z' is
-// split into a BF16 pair hi + lo, hi = bf16(z'), lo = bf16(z' - hi), and both
-// products accumulate into the same FP32 accumulator, which keeps ~16
-// significant bits of Z' instead of 8.
+// Eq. gradient1 split over fiber groups g (the batch is cut into groups of fb
+// fibers, one CTA per (row tile, group)): with Z'_S = D Z_S / (B J_n) (the
+// weight s_f folded into each sampled KRP row),
+//   M_g = X_S,g Z'_S,g      (I_n x R)  -- tensor cores
+//   H_g = Z_S,g^T Z'_S,g    (R x R)    -- CUDA cores, FP32
+//   G_g = A^(n) H_g - M_g               -- CUDA cores, FP32, in the epilogue
+// and k_update sums the G_g in fixed order. The gathered fibers are BF16
+// (exact copies of the stored tensor). Z' is split into a BF16 pair
+// hi = bf16(z'), lo = bf16(z' - hi); both products accumulate into the same
+// FP32 accumulator, which keeps ~16 significant bits of Z' instead of 8.
 //
 // Per CTA (rb = 128 rows of A^(n), fb fibers, fb a multiple of 16):
 //   1. draw the fibers (warp-cooperative inverse-CDF search), p_f, s_f;
 //   2. 16-byte cp.async copies of rows [r0, r0+128) of every fiber straight
-//      into the no-swizzle MN-major operand layout (zero fill past I_n);
+//      into the no-swizzle MN-major operand layout (zero fill past I_n), and
+//      the CTA's rows of A^(n) (transposed) into shared memory;
 //   3. z_f and the hi/lo B operands (K-major), zero-padded to N = 64;
 //   4. one thread issues 2*fb/16 tcgen05.mma (M=128, N=64, K=16) and commits
-//      to an mbarrier; meanwhile the CTA computes its share of H;
-//   5. tcgen05.ld of the accumulator -> M partial [gf][i][r];
-//   6. the last CTA to finish reduces the H partials (fixed order).
+//      to an mbarrier; meanwhile the CTA computes H_g;
+//   5. tcgen05.ld of M_g, G_g = A H_g - M_g, stored as the group's partial.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -37,23 +38,28 @@ constexpr int kTcK = 16;         // K of one MMA for 16-bit operands
 constexpr int kTcCols = 64;      // TMEM columns allocated (FP32 accumulator, N = 64)
 constexpr unsigned kWaitLimit = 1u << 24;
 
+// Shared memory of one CTA (byte offsets; operand tiles 128-byte aligned).
 struct TcSmem {
-    size_t a, bhi, blo, z, s, idx, jcol, bar, tmem, total;
+    size_t a, bhi, blo, zs, z, arow, h, rows, s, idx, jcol, bar, tmem, total;
+    int lda;  // row stride (floats) of the A^(n) tile: R rounded up to odd
     __host__ __device__ TcSmem(int N, int R, int fb)
     {
+        lda = R | 1;
         size_t o = 0;
-        a = o;    o += (size_t)fb * kTcM * 2;          // X tile, MN-major
-        bhi = o;  o += (size_t)fb * kTcN * 2;          // Z' hi, K-major
-        blo = o;  o += (size_t)fb * kTcN * 2;          // Z' lo, K-major
-        z = o;    o += up((size_t)fb * R * 4);         // z_f (FP32)
-        s = o;    o += up((size_t)fb * 4);             // s_f (FP32)
+        a = o;    o += (size_t)fb * kTcM * 2;               // X tile, MN-major bf16
+        bhi = o;  o += (size_t)fb * kTcN * 2;               // Z' hi, K-major bf16
+        blo = o;  o += (size_t)fb * kTcN * 2;               // Z' lo, K-major bf16
+        zs = o;   o += (size_t)fb * kTcN * 4;               // s_f z_f, fp32, 64 wide
+        z = o;    o += (size_t)fb * kTcN * 4;               // z_f, fp32, 64 wide
+        arow = o; o += up((size_t)kTcM * lda * 4);          // A^(n) rows of the tile
+        h = o;    o += (size_t)kTcN * kTcN * 4;             // H_g, 64 x 64
+        rows = o; o += up((size_t)fb * (N - 1) * R * 4);    // gathered factor rows
+        s = o;    o += up((size_t)fb * 4);
         idx = o;  o += up((size_t)fb * N * 4);
         jcol = o; o += up((size_t)fb * 8);
         bar = o;  o += 16;
         tmem = o; o += 16;
-        // Slack so that every operand read stays inside the allocation even
-        // under a transposed reading of the descriptor strides.
-        total = o + 32768;
+        total = o;
     }
     __host__ __device__ static size_t up(size_t v) { return (v + 127) / 128 * 128; }
 };
@@ -88,6 +94,11 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t phase)
@@ -133,186 +144,228 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
+    const bool tr0 = blockIdx.x == 0;
+    trace_stamp(P.trace, 0, tr0);
     const long long t = *P.t_dev;
     const int N = P.N, R = P.R, fb = P.fb;
     const int n = mode_draw(P.seed, t, N);
     const int pr = P.tile[n].pr;
     const int gr = blockIdx.x % pr, gf = blockIdx.x / pr;
-    const bool active = gf < P.pf;
+    if (gf >= P.pf) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long In = P.dims[n];
+    const int r0 = gr * kTcM;
+    const int f0 = gf * fb;
+    const int nf = (P.B - f0) < fb ? (P.B - f0) : fb;
 
     const TcSmem L(N, R, fb);
     unsigned char *sA = smem + L.a;
     __nv_bfloat16 *sBhi = reinterpret_cast<__nv_bfloat16 *>(smem + L.bhi);
     __nv_bfloat16 *sBlo = reinterpret_cast<__nv_bfloat16 *>(smem + L.blo);
+    float *szs = reinterpret_cast<float *>(smem + L.zs);
     float *sz = reinterpret_cast<float *>(smem + L.z);
+    float *sArow = reinterpret_cast<float *>(smem + L.arow);
+    float *sH = reinterpret_cast<float *>(smem + L.h);
+    float *sRows = reinterpret_cast<float *>(smem + L.rows);
     float *ss = reinterpret_cast<float *>(smem + L.s);
     int *sidx = reinterpret_cast<int *>(smem + L.idx);
     long long *jcol = reinterpret_cast<long long *>(smem + L.jcol);
     const uint32_t bar = smem_u32(smem + L.bar);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + L.tmem);
+    const int lda = L.lda;
 
-    if (active) {
-        const long long In = P.dims[n];
-        const int r0 = gr * kTcM;
-        const int f0 = gf * fb;
-        const int nf = (P.B - f0) < fb ? (P.B - f0) : fb;
-
-        if (warp == 0) {
-            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                             smem_u32(tmem_holder)),
-                         "r"(kTcCols)
-                         : "memory");
-            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-        }
-        if (threadIdx.x == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        }
-
-        // 1. draws, fiber columns, probabilities and weights
-        draw_indices(P, t, n, f0, nf, sidx);
-        __syncthreads();
-        for (int f = threadIdx.x; f < fb; f += blockDim.x) {
-            if (f < nf) {
-                const int *row = sidx + f * N;
-                long long j = 0, Jp = 1;
-                for (int k = 0; k < N; ++k) {
-                    if (k == n) continue;
-                    j += (long long)row[k] * Jp;
-                    Jp *= P.dims[k];
-                }
-                jcol[f] = j;
-                const double p = fiber_prob(P, n, row);
-                ss[f] = (float)__ddiv_rn(1.0, __dmul_rn(__dmul_rn((double)P.B, P.Jn[n]), p));
-                if (gr == 0) {
-                    P.p[f0 + f] = p;
-                    for (int k = 0; k < N; ++k) P.idx[(long long)(f0 + f) * N + k] = row[k];
-                }
-            } else {
-                jcol[f] = 0;
-                ss[f] = 0.f;
-            }
-        }
-        __syncthreads();
-
-        // 2. gather: chunk (f, ig) = rows r0+8ig .. r0+8ig+7 of fiber f, 16 bytes,
-        //    to core matrix (f/8, ig) at ((f/8)*16 + ig)*128 + (f%8)*16.
-        const __nv_bfloat16 *rep = reinterpret_cast<const __nv_bfloat16 *>(P.rep[n]);
-        const long long ld = P.ld[n];
-        const uint32_t aBase = smem_u32(sA);
-        for (int c = threadIdx.x; c < fb * (kTcM / 8); c += blockDim.x) {
-            const int f = c / (kTcM / 8), ig = c % (kTcM / 8);
-            const long long i0 = r0 + ig * 8;
-            const bool ok = f < nf && i0 < ld;
-            const __nv_bfloat16 *src = ok ? rep + jcol[f] * ld + i0 : rep;
-            cp_async16(aBase + (uint32_t)((((f >> 3) * (kTcM / 8) + ig) << 7) + ((f & 7) << 4)), src,
-                       ok ? 16u : 0u);
+    // 0. the tile's rows of A^(n) (independent of the draws): async copies
+    {
+        const float *An = P.A[n];
+        const uint32_t dst0 = smem_u32(sArow);
+        const int rows = (In - r0) < kTcM ? (int)(In - r0) : kTcM;
+        for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
+            const int i = e / R, q = e % R;
+            cp_async4(dst0 + (uint32_t)((i * lda + q) * 4), An + (long long)(r0 + i) * R + q);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(tmem_holder)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
 
-        // 3. z_f (FP32) and the B operands Z' = s_f z_f as a bf16 hi/lo pair,
-        //    K-major: element (r, f) at ((r/8)*(fb/8) + f/8)*64 + (r%8)*8 + f%8.
-        for (int e = threadIdx.x; e < fb * kTcN; e += blockDim.x) {
-            const int f = e / kTcN, r = e % kTcN;
-            float z = 0.f;
-            if (f < nf && r < R) {
-                const int *row = sidx + f * N;
-                z = 1.f;
-                for (int k = 0; k < N; ++k) {
-                    if (k == n) continue;
-                    z = z * P.A[k][(long long)row[k] * R + r];
-                }
-                sz[f * R + r] = z;
+    trace_stamp(P.trace, 1, tr0);
+    // 1. draws (Alg. 3), fiber columns (Eq. map) and weights s_f
+    draw_indices(P, t, n, f0, nf, sidx);
+    __syncthreads();
+    trace_stamp(P.trace, 2, tr0);
+    for (int f = threadIdx.x; f < fb; f += blockDim.x) {
+        if (f < nf) {
+            const int *row = sidx + f * N;
+            long long j = 0, Jp = 1;
+            for (int k = 0; k < N; ++k) {
+                if (k == n) continue;
+                j += (long long)row[k] * Jp;
+                Jp *= P.dims[k];
             }
-            const float zp = z * ss[f];
-            const __nv_bfloat16 hi = __float2bfloat16_rn(zp);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(zp - __bfloat162float(hi));
-            const int off = (((r >> 3) * (fb >> 3) + (f >> 3)) << 6) + ((r & 7) << 3) + (f & 7);
-            sBhi[off] = hi;
-            sBlo[off] = lo;
+            jcol[f] = j;
+            ss[f] = fiber_weight(P, n, row);
+            if (gr == 0)
+                for (int k = 0; k < N; ++k) P.idx[(long long)(f0 + f) * N + k] = row[k];
+        } else {
+            jcol[f] = 0;
+            ss[f] = 0.f;
         }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        const uint32_t tmem = *tmem_holder;
+    }
+    // factor rows A^(k)(i_k, :), k != n, of every fiber: async copies
+    {
+        const uint32_t dst0 = smem_u32(sRows);
+        const int per = (N - 1) * R;
+        for (int e = threadIdx.x; e < nf * per; e += blockDim.x) {
+            const int f = e / per, rem = e % per, kk = rem / R, q = rem % R;
+            const int k = kk + (kk >= n ? 1 : 0);
+            cp_async4(dst0 + (uint32_t)(e * 4), P.A[k] + (long long)sidx[f * N + k] * R + q);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    __syncthreads();
 
-        // 4. MMAs (one thread), H share on the CUDA cores meanwhile
-        if (threadIdx.x == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t bhi = smem_u32(sBhi), blo = smem_u32(sBlo);
-            const uint32_t idesc = idesc_bf16(kTcM, kTcN);
-            const uint32_t sboB = (uint32_t)(fb >> 3) * 128u;
-            for (int ks = 0; ks < fb / kTcK; ++ks) {
-                const uint64_t da = smem_desc(aBase + ks * 4096u, (kTcM / 8) * 128u, 128u);
-                const uint64_t dh = smem_desc(bhi + ks * 256u, 128u, sboB);
-                const uint64_t dl = smem_desc(blo + ks * 256u, 128u, sboB);
-                const uint32_t acc = ks > 0 ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-                    "l"(da), "l"(dh), "r"(idesc), "r"(acc)
-                    : "memory");
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-                    "l"(da), "l"(dl), "r"(idesc), "r"(1u)
-                    : "memory");
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             bar)
-                         : "memory");
-        }
-        const int npairs = R * (R + 1) / 2;
-        for (int lp = threadIdx.x; gr + lp * pr < npairs; lp += blockDim.x) {
-            int rem = gr + lp * pr, r = 0;
-            while (rem >= R - r) {
-                rem -= R - r;
-                ++r;
-            }
-            const int s2 = r + rem;
-            float acc = 0.f;
-            for (int f = 0; f < nf; ++f) acc += ss[f] * sz[f * R + r] * sz[f * R + s2];
-            P.hpart[((long long)gf * R + r) * R + s2] = acc;
-            P.hpart[((long long)gf * R + s2) * R + r] = acc;
-        }
+    trace_stamp(P.trace, 3, tr0);
+    // 2. gather: chunk (f, ig) = rows r0+8ig .. r0+8ig+7 of fiber f, 16 bytes,
+    //    to core matrix (f/8, ig) at ((f/8)*16 + ig)*128 + (f%8)*16.
+    const __nv_bfloat16 *rep = reinterpret_cast<const __nv_bfloat16 *>(P.rep[n]);
+    const long long ld = P.ld[n];
+    const uint32_t aBase = smem_u32(sA);
+    for (int c = threadIdx.x; c < fb * (kTcM / 8); c += blockDim.x) {
+        const int f = c / (kTcM / 8), ig = c % (kTcM / 8);
+        const long long i0 = r0 + ig * 8;
+        const bool ok = f < nf && i0 < ld;
+        const __nv_bfloat16 *src = ok ? rep + jcol[f] * ld + i0 : rep;
+        cp_async16(aBase + (uint32_t)((((f >> 3) * (kTcM / 8) + ig) << 7) + ((f & 7) << 4)), src,
+                   ok ? 16u : 0u);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
 
-        // 5. accumulator -> M partial rows
-        bool done = mbar_wait_bounded(bar, 0);
-        if (!done) {
-            if (threadIdx.x == 0) atomicOr(P.status, kStTimeout);
-            done = mbar_wait_bounded(bar, 0);
+    trace_stamp(P.trace, 4, tr0);
+    // 3. z_f = Hadamard product of the gathered rows (Alg. 1), and the B
+    //    operands Z' = s_f z_f as a bf16 hi/lo pair, K-major: element (r, f) at
+    //    ((r/8)*(fb/8) + f/8)*64 + (r%8)*8 + f%8. Rows past R are zero.
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // A rows and factor rows landed
+    __syncthreads();
+    for (int e = threadIdx.x; e < fb * kTcN; e += blockDim.x) {
+        const int f = e / kTcN, r = e % kTcN;
+        float z = 0.f;
+        if (f < nf && r < R) {
+            const float *fr = sRows + (long long)f * (N - 1) * R + r;
+            z = 1.f;
+            for (int kk = 0; kk < N - 1; ++kk) z = z * fr[kk * R];
         }
+        const float zp = z * ss[f];
+        sz[f * kTcN + r] = z;
+        szs[f * kTcN + r] = zp;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(zp);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(zp - __bfloat162float(hi));
+        const int off = (((r >> 3) * (fb >> 3) + (f >> 3)) << 6) + ((r & 7) << 3) + (f & 7);
+        sBhi[off] = hi;
+        sBlo[off] = lo;
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    const uint32_t tmem = *tmem_holder;
+    trace_stamp(P.trace, 5, tr0);
+
+    // 4. M_g = X Z' on the tensor cores (one thread issues), H_g meanwhile
+    if (threadIdx.x == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (done) {
-            const int q = warp & 3, h = warp >> 2;
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h), v);
-            const long long i = r0 + 32 * q + lane;
-            if (i < In) {
-                float *out = P.part + ((long long)gf * In + i) * R;
+        const uint32_t bhi = smem_u32(sBhi), blo = smem_u32(sBlo);
+        const uint32_t idesc = idesc_bf16(kTcM, kTcN);
+        const uint32_t sboB = (uint32_t)(fb >> 3) * 128u;
+        for (int ks = 0; ks < fb / kTcK; ++ks) {
+            const uint64_t da = smem_desc(aBase + ks * 4096u, (kTcM / 8) * 128u, 128u);
+            const uint64_t dh = smem_desc(bhi + ks * 256u, 128u, sboB);
+            const uint64_t dl = smem_desc(blo + ks * 256u, 128u, sboB);
+            const uint32_t acc = ks > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                "l"(da), "l"(dh), "r"(idesc), "r"(acc)
+                : "memory");
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                "l"(da), "l"(dl), "r"(idesc), "r"(1u)
+                : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                     : "memory");
+    }
+    {
+        // H_g = sum_f (s_f z_f) z_f^T: a 4 x 4 block of the 64 x 64 result per thread
+        const int rb = threadIdx.x >> 4, cb = threadIdx.x & 15;
+        float hacc[4][4] = {};
+        for (int f = 0; f < nf; ++f) {
+            const float4 a = *reinterpret_cast<const float4 *>(szs + f * kTcN + 4 * rb);
+            const float4 b = *reinterpret_cast<const float4 *>(sz + f * kTcN + 4 * cb);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    if (32 * h + c < R) out[32 * h + c] = v[c];
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) hacc[u][v] += av[u] * bv[v];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            *reinterpret_cast<float4 *>(sH + (4 * rb + u) * kTcN + 4 * cb) =
+                make_float4(hacc[u][0], hacc[u][1], hacc[u][2], hacc[u][3]);
+    }
+    __syncthreads();
+
+    trace_stamp(P.trace, 6, tr0);
+    // 5. accumulator -> G_g = A H_g - M_g for row i, columns [32h, 32h+32)
+    bool done = mbar_wait_bounded(bar, 0);
+    if (!done) {
+        if (threadIdx.x == 0) atomicOr(P.status, kStTimeout);
+        done = mbar_wait_bounded(bar, 0);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    trace_stamp(P.trace, 7, tr0);
+    if (done) {
+        const int q = warp & 3, h = warp >> 2;
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h), v);
+        const int il = 32 * q + lane;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) v[c] = -v[c];
+        for (int s2 = 0; s2 < R; ++s2) {
+            const float a = sArow[il * lda + s2];
+            const float4 *hrow = reinterpret_cast<const float4 *>(sH + s2 * kTcN + 32 * h);
+#pragma unroll
+            for (int c4 = 0; c4 < 8; ++c4) {
+                const float4 hv = hrow[c4];
+                v[4 * c4 + 0] += a * hv.x;
+                v[4 * c4 + 1] += a * hv.y;
+                v[4 * c4 + 2] += a * hv.z;
+                v[4 * c4 + 3] += a * hv.w;
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncthreads();
-        if (warp == 0)
-            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols)
-                         : "memory");
+        const long long i = r0 + il;
+        if (i < In) {
+            float *out = P.part + ((long long)gf * In + i) * R;
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                if (32 * h + c < R) out[32 * h + c] = v[c];
+        }
     }
-
-    // 6. the last CTA reduces H over fiber groups in fixed order
-    if (!last_block(P.counters + 4)) return;
-    const int RR = R * R;
-    float *H = P.hpart + (long long)P.pf * RR;
-    for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-        float h = 0.f;
-        for (int g = 0; g < P.pf; ++g) h += __ldcg(P.hpart + (long long)g * RR + e);
-        H[e] = h;
-    }
-    if (threadIdx.x == 0) P.counters[4] = 0;
+    trace_stamp(P.trace, 8, tr0);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    trace_stamp(P.trace, 9, tr0);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols)
+                     : "memory");
 }
 
 bool tc_supported(int R, int rb) { return R >= 1 && R <= kTcN && rb == kTcM; }

@@ -198,8 +198,8 @@ def test_profile_events(cpd):
                             sampling="euclidean", step="adagrad")
     cpd.cpd_profile(dec.ctx, True)
     dec.sgd_iters(10)
-    n, ms = cpd.cpd_profile_read(dec.ctx)
-    assert n == 10 and 0 < ms < 10
+    n, ms, ums = cpd.cpd_profile_read(dec.ctx)
+    assert n == 10 and 0 < ms < 10 and 0 < ums < 10
     cpd.cpd_profile(dec.ctx, False)
     dec.close()
 
