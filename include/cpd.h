@@ -196,6 +196,8 @@ cpd_status cpd_profile_read(cpd_ctx *ctx, int64_t *launches, double *mean_grad_m
  *            draws done, weights and row copies issued, gather issued, KRP
  *            rows and operands built, MMAs issued and H formed, MMAs
  *            complete, epilogue done, exit;
+ *   [10..15] gradient kernel detail: weights done, row copies issued, rows
+ *            landed, operands built, accumulator read, A H_g formed;
  *   [16..19] update kernel, first CTA: entry, gradient reduced, step applied,
  *            row weights written;
  *   [20..21] update kernel, last CTA: distribution rebuild start / end.

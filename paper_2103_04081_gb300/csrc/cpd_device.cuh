@@ -137,6 +137,42 @@ __device__ __forceinline__ long long warp_search_cdf(const unsigned long long *_
     return result;
 }
 
+// Warp-cooperative search over a CDF held in shared memory. The first level
+// is common to all 32 draws: lane l loads one splitter c[min((l+1)step, I)-1]
+// (step = ceil(I/32)), and each lane finds its segment by a binary search
+// over the 32 splitters through shuffles; the lane then finishes inside its
+// segment (at most step entries) with a binary search of its own.
+__device__ __forceinline__ long long warp_search_staged(const unsigned long long *c, long long I,
+                                                        unsigned long long target, bool active)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long step = (I + 31) / 32;
+    long long e = (long long)(lane + 1) * step;
+    e = (e < I ? e : I) - 1;
+    const unsigned long long split = c[e];
+    // segment = number of splitters <= target (splitter 31 = c[I-1] > target)
+    int seg = 0;
+#pragma unroll
+    for (int half = 16; half >= 1; half >>= 1) {
+        const unsigned long long v = __shfl_sync(full, split, seg + half - 1);
+        if (v <= target) seg += half;
+    }
+    long long lo = (long long)seg * step;
+    long long len = I - lo < step ? I - lo : step;
+    if (!active || len <= 0) return I - 1;
+    while (len > 1) {
+        const long long h = len >> 1;
+        if (target < c[lo + h - 1]) {
+            len = h;
+        } else {
+            lo += h;
+            len -= h;
+        }
+    }
+    return lo;
+}
+
 // Row weight of the Euclidean distribution (Def. 5, Lemma 4) in the canonical
 // order, by one warp: lane l accumulates a_r^2 for r = l, l+32, ... (fma from
 // +0), then the shuffle-down tree adds lane l+off into lane l for off =
@@ -176,15 +212,21 @@ __device__ __forceinline__ unsigned long long quantize(double w, int s)
 // not finite, or when every q_i is 0. `sm` holds 2 * blockDim.x uint64 slots.
 // w is read through L2 (other CTAs of the launch may have written it).
 // ---------------------------------------------------------------------------
-__device__ inline bool block_distribution(const double *w, long long I, unsigned long long *cdf,
-                                          unsigned long long *sm)
+__device__ inline bool block_distribution(const double *wg, long long I, unsigned long long *cdf,
+                                          unsigned long long *sm, double *wstage, long long wcap)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
+    const double *w = wg;
+    if (wstage && I <= wcap) {   // one coalesced pass through L2, then shared memory
+        for (long long i = tid; i < I; i += nt) wstage[i] = __ldcg(wg + i);
+        __syncthreads();
+        w = wstage;
+    }
     // largest weight, through the integer order of non-negative doubles
     long long mx = 0;
     int bad = 0;
     for (long long i = tid; i < I; i += nt) {
-        const double v = __ldcg(w + i);
+        const double v = w == wg ? __ldcg(w + i) : w[i];
         if (!(v >= 0.0) || isinf(v)) bad = 1;
         const long long b = __double_as_longlong(v);
         mx = b > mx ? b : mx;
@@ -212,7 +254,7 @@ __device__ inline bool block_distribution(const double *w, long long I, unsigned
     const long long chunk = (I + nt - 1) / nt;
     const long long i0 = tid * chunk, i1 = (i0 + chunk < I) ? i0 + chunk : I;
     unsigned long long tot = 0;
-    for (long long i = i0; i < i1; ++i) tot += quantize(__ldcg(w + i), s);
+    for (long long i = i0; i < i1; ++i) tot += quantize(w == wg ? __ldcg(w + i) : w[i], s);
     unsigned long long inc = tot;
     for (int off = 1; off < 32; off <<= 1) {
         const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, off);
@@ -224,7 +266,7 @@ __device__ inline bool block_distribution(const double *w, long long I, unsigned
     for (int q = 0; q < (tid >> 5); ++q) base += sm[nt + q];
     unsigned long long acc = base + inc - tot;
     for (long long i = i0; i < i1; ++i) {
-        acc += quantize(__ldcg(w + i), s);
+        acc += quantize(w == wg ? __ldcg(w + i) : w[i], s);
         cdf[i] = acc;
     }
     unsigned long long Q = 0;
@@ -248,12 +290,29 @@ __device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 x)
 // Sampling steps shared by both gradient engines.
 // ---------------------------------------------------------------------------
 // Draw the (N-1) x nf indices of this CTA's fibers (Alg. 3 "Randsample(I_k,
-// |F_n|, true, p_k)"): warps take 32-fiber chunks per mode k != n and run the
-// warp-cooperative search on cdf[k].
+// |F_n|, true, p_k)"). When the CDFs of the modes k != n fit the shared
+// buffer `stage` (cap entries) they are copied there first (one coalesced
+// pass) and searched there; otherwise the warp-cooperative multi-level
+// search runs on the global copies. Warps take 32-fiber chunks per mode.
 template <class T>
-__device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int f0, int nf, int *sidx)
+__device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int f0, int nf, int *sidx,
+                                    unsigned long long *stage, long long cap)
 {
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    long long need = 0, off[kMaxModes];
+    for (int k = 0; k < P.N; ++k) {
+        off[k] = need;
+        if (k != n) need += P.dims[k];
+    }
+    const bool staged = P.sampling != CPD_SAMPLE_UNIFORM && stage != nullptr && need <= cap;
+    if (staged) {
+        for (int k = 0; k < P.N; ++k) {
+            if (k == n) continue;
+            const unsigned long long *c = P.cdf[k];
+            for (long long i = threadIdx.x; i < P.dims[k]; i += blockDim.x) stage[off[k] + i] = __ldg(c + i);
+        }
+        __syncthreads();
+    }
     const int chunks = (nf + 31) / 32;
     for (int job = warp; job < chunks * P.N; job += nwarps) {
         const int k = job / chunks, ch = job % chunks;
@@ -268,6 +327,9 @@ __device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int
         long long i;
         if (P.sampling == CPD_SAMPLE_UNIFORM) {
             i = (long long)__umul64hi(x, (unsigned long long)Ik);
+        } else if (staged) {
+            const unsigned long long *c = stage + off[k];
+            i = warp_search_staged(c, Ik, __umul64hi(x, c[Ik - 1]), act);
         } else {
             const unsigned long long *c = P.cdf[k];
             i = warp_search_cdf(c, Ik, __umul64hi(x, __ldg(c + (Ik - 1))), act);

@@ -25,10 +25,11 @@ namespace {
 // Shared-memory carve-up of the gradient kernel (all offsets 16-byte aligned).
 template <class T>
 struct GradSmem {
-    size_t idx, jcol, s, z, At, x, total;
+    size_t idx, jcol, s, z, At, x, stage, total;
     __host__ __device__ GradSmem(int N, int R, int rb, int fb)
     {
         size_t o = 0;
+        stage = o; o += 2048 * 8;   // CDF staging for the draws
         idx = o;  o += align_up_h((size_t)fb * N * sizeof(int), 16);
         jcol = o; o += align_up_h((size_t)fb * sizeof(long long), 16);
         s = o;    o += align_up_h((size_t)fb * sizeof(T), 16);
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(kThreads) k_grad_simt(const Problem<T> P)
     T *sx = reinterpret_cast<T *>(smem + L.x);
 
     // 1. draws of Alg. 3
-    draw_indices(P, t, n, f0, nf, sidx);
+    draw_indices(P, t, n, f0, nf, sidx, reinterpret_cast<unsigned long long *>(smem + L.stage), 2048);
     // rows of A^(n) for the residual, transposed (conflict-free reads)
     const T *An = P.A[n];
     for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
@@ -164,10 +165,12 @@ __global__ void __launch_bounds__(kThreads) k_grad_simt(const Problem<T> P)
 
 // Rebuild the fixed-point distribution of mode k from w[k] (one CTA); a
 // distribution without mass is flagged.
+constexpr int kWStage = 4096;  // doubles of shared staging for the row weights
+
 template <class T>
-__device__ void finish_distribution(const Problem<T> &P, int k, unsigned long long *sm)
+__device__ void finish_distribution(const Problem<T> &P, int k, unsigned long long *sm, double *wstage)
 {
-    if (!block_distribution(P.w[k], P.dims[k], P.cdf[k], sm) && threadIdx.x == 0)
+    if (!block_distribution(P.w[k], P.dims[k], P.cdf[k], sm, wstage, kWStage) && threadIdx.x == 0)
         atomicOr(P.status, kStDegenerate);
 }
 
@@ -176,6 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P)
 {
     __shared__ T s_new[kThreads];
     __shared__ unsigned long long s_dist[2 * kThreads];
+    __shared__ double s_w[kWStage];
     const bool tr0 = blockIdx.x == 0;
     trace_stamp(P.trace, 16, tr0);
     const long long t = *P.t_dev;
@@ -189,16 +193,16 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P)
     T *An = P.A[n];
     if (act) {
         // G(i, r) = sum of the fiber groups' partials in fixed order; the
-        // loads are issued in batches of 8 so their latencies overlap.
+        // loads are issued in batches of 24 so their latencies overlap.
         T g = (T)0;
         const T *src = P.part + i * R + r;
         const long long slab = (long long)In * R;
-        for (int q0 = 0; q0 < P.pf; q0 += 8) {
-            T v[8];
+        for (int q0 = 0; q0 < P.pf; q0 += 24) {
+            T v[24];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = (q0 + u < P.pf) ? __ldcg(src + (q0 + u) * slab) : (T)0;
+            for (int u = 0; u < 24; ++u) v[u] = (q0 + u < P.pf) ? __ldcg(src + (q0 + u) * slab) : (T)0;
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
+            for (int u = 0; u < 24; ++u)
                 if (q0 + u < P.pf) g += v[u];
         }
         P.G[i * R + r] = g;
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P)
     trace_stamp(P.trace, 19, tr0);
     if (!last_block(P.counters)) return;
     trace_stamp(P.trace, 20, true);
-    if (P.sampling == CPD_SAMPLE_EUCLIDEAN) finish_distribution(P, n, s_dist);
+    if (P.sampling == CPD_SAMPLE_EUCLIDEAN) finish_distribution(P, n, s_dist, s_w);
     trace_stamp(P.trace, 21, true);
     if (threadIdx.x == 0) {
         P.counters[0] = 0;
@@ -338,7 +342,8 @@ __global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k
     }
     if (!last_block(P.counters + 2)) return;
     __shared__ unsigned long long s_dist[2 * kThreads];
-    if (!bad) finish_distribution(P, k, s_dist);
+    __shared__ double s_w[kWStage];
+    if (!bad) finish_distribution(P, k, s_dist, s_w);
     if (threadIdx.x == 0) {
         P.counters[2] = 0;
         if (advance) {
@@ -361,7 +366,8 @@ __global__ void __launch_bounds__(kThreads) k_weights_euclid(const Problem<T> P,
         if ((threadIdx.x & 31) == 0) P.w[k][row] = wv;
     }
     if (!last_block(P.counters + 3)) return;
-    finish_distribution(P, k, s_dist);
+    __shared__ double s_w[kWStage];
+    finish_distribution(P, k, s_dist, s_w);
     if (threadIdx.x == 0) P.counters[3] = 0;
 }
 

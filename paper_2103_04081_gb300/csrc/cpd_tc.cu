@@ -51,6 +51,9 @@ struct TcSmem {
         blo = o;  o += (size_t)fb * kTcN * 2;               // Z' lo, K-major bf16
         zs = o;   o += (size_t)fb * kTcN * 4;               // s_f z_f, fp32, 64 wide
         z = o;    o += (size_t)fb * kTcN * 4;               // z_f, fp32, 64 wide
+        // [a, arow) is dead once the MMAs are done: it stages the 128 x R
+        // G tile of the epilogue, so it must hold at least that much
+        if (o - a < (size_t)kTcM * R * 4) o = a + up((size_t)kTcM * R * 4);
         arow = o; o += up((size_t)kTcM * lda * 4);          // A^(n) rows of the tile
         h = o;    o += (size_t)kTcN * kTcN * 4;             // H_g, 64 x 64
         rows = o; o += up((size_t)fb * (N - 1) * R * 4);    // gathered factor rows
@@ -179,9 +182,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
         const float *An = P.A[n];
         const uint32_t dst0 = smem_u32(sArow);
         const int rows = (In - r0) < kTcM ? (int)(In - r0) : kTcM;
-        for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
-            const int i = e / R, q = e % R;
-            cp_async4(dst0 + (uint32_t)((i * lda + q) * 4), An + (long long)(r0 + i) * R + q);
+        for (int i = warp; i < rows; i += kThreads / 32) {
+            const float *src = An + (long long)(r0 + i) * R;
+            for (int q = lane; q < R; q += 32) cp_async4(dst0 + (uint32_t)((i * lda + q) * 4), src + q);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
@@ -198,8 +201,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
     }
 
     trace_stamp(P.trace, 1, tr0);
-    // 1. draws (Alg. 3), fiber columns (Eq. map) and weights s_f
-    draw_indices(P, t, n, f0, nf, sidx);
+    // 1. draws (Alg. 3), fiber columns (Eq. map) and weights s_f; the CDFs are
+    //    staged over the operand tiles, which are not written before the gather
+    draw_indices(P, t, n, f0, nf, sidx, reinterpret_cast<unsigned long long *>(sA),
+                 (long long)(L.z - L.a) / 8);
     __syncthreads();
     trace_stamp(P.trace, 2, tr0);
     for (int f = threadIdx.x; f < fb; f += blockDim.x) {
@@ -220,17 +225,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
             ss[f] = 0.f;
         }
     }
+    trace_stamp(P.trace, 10, tr0);
     // factor rows A^(k)(i_k, :), k != n, of every fiber: async copies
     {
+        // one warp per (fiber, mode) row; 8-byte copies when rows are 8-byte aligned
         const uint32_t dst0 = smem_u32(sRows);
-        const int per = (N - 1) * R;
-        for (int e = threadIdx.x; e < nf * per; e += blockDim.x) {
-            const int f = e / per, rem = e % per, kk = rem / R, q = rem % R;
+        for (int pr2 = warp; pr2 < nf * (N - 1); pr2 += kThreads / 32) {
+            const int f = pr2 / (N - 1), kk = pr2 % (N - 1);
             const int k = kk + (kk >= n ? 1 : 0);
-            cp_async4(dst0 + (uint32_t)(e * 4), P.A[k] + (long long)sidx[f * N + k] * R + q);
+            const float *src = P.A[k] + (long long)sidx[f * N + k] * R;
+            const uint32_t dst = dst0 + (uint32_t)(pr2 * R * 4);
+            if ((R & 1) == 0) {
+                for (int q = lane; q < R / 2; q += 32)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst + q * 8), "l"(src + 2 * q)
+                                 : "memory");
+            } else {
+                for (int q = lane; q < R; q += 32) cp_async4(dst + q * 4, src + q);
+            }
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
+    trace_stamp(P.trace, 11, tr0);
     __syncthreads();
 
     trace_stamp(P.trace, 3, tr0);
@@ -255,6 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
     //    ((r/8)*(fb/8) + f/8)*64 + (r%8)*8 + f%8. Rows past R are zero.
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // A rows and factor rows landed
     __syncthreads();
+    trace_stamp(P.trace, 12, tr0);
     for (int e = threadIdx.x; e < fb * kTcN; e += blockDim.x) {
         const int f = e / kTcN, r = e % kTcN;
         float z = 0.f;
@@ -272,6 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
         sBhi[off] = hi;
         sBlo[off] = lo;
     }
+    trace_stamp(P.trace, 13, tr0);
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
@@ -337,6 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h), v);
         const int il = 32 * q + lane;
+        trace_stamp(P.trace, 14, tr0);
 #pragma unroll
         for (int c = 0; c < 32; ++c) v[c] = -v[c];
         for (int s2 = 0; s2 < R; ++s2) {
@@ -351,13 +369,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
                 v[4 * c4 + 3] += a * hv.w;
             }
         }
-        const long long i = r0 + il;
-        if (i < In) {
-            float *out = P.part + ((long long)gf * In + i) * R;
+        trace_stamp(P.trace, 15, tr0);
+        float *tile = reinterpret_cast<float *>(sA);   // operands are dead: stage the 128 x R tile
 #pragma unroll
-            for (int c = 0; c < 32; ++c)
-                if (32 * h + c < R) out[32 * h + c] = v[c];
-        }
+        for (int c = 0; c < 32; ++c)
+            if (32 * h + c < R) tile[il * R + 32 * h + c] = v[c];
+    }
+    __syncthreads();
+    if (done) {
+        // the tile's rows are contiguous in the partial slab: coalesced stores
+        const int rows = (In - r0) < kTcM ? (int)(In - r0) : kTcM;
+        float *out = P.part + ((long long)gf * In + r0) * R;
+        const float *tile = reinterpret_cast<const float *>(sA);
+        for (int e = threadIdx.x; e < rows * R; e += blockDim.x) out[e] = tile[e];
     }
     trace_stamp(P.trace, 8, tr0);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
