@@ -200,7 +200,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=500)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tensor"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tensor", "cluster"])
     ap.add_argument("--sampling", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -255,7 +255,7 @@ def main() -> None:
     C.cpd_profile(dec.ctx, True)
     nprof = min(args.steps, 2000)
     dec.sgd_iters(nprof, stream)
-    nlaunch, grad_ms = C.cpd_profile_read(dec.ctx, stream)
+    nlaunch, grad_ms, upd_ms = C.cpd_profile_read(dec.ctx, stream)
     C.cpd_profile(dec.ctx, False)
     fit, tol = dec.fit(stream)
     dec.close()
@@ -298,14 +298,15 @@ def main() -> None:
         "metric": METRIC, "value": iters_per_s, "unit": "iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if engine == "tensor" else ("f64" if w["x_dtype"] == "f64" else "f32"),
+        "dtype": "bf16" if engine in ("tensor", "cluster") else ("f64" if w["x_dtype"] == "f64" else "f32"),
         "data": "synthetic", "config": config_block(w, engine),
         "gather_gbs_in_loop": gather_bytes * args.steps / (ms / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "kernel": "k_grad_tc" if engine == "tensor" else "k_grad_simt",
+                     "kernel": {"tensor": "k_grad_tc", "cluster": "k_grad_tcc"}.get(engine, "k_grad_simt"),
                      "algorithmic_bytes_per_launch": gather_bytes, "mean_launch_ms": grad_ms,
-                     "timed_launches": nlaunch, "peak_source": src + " (hbm_gbs, of " + src + ")"},
+                     "timed_launches": nlaunch, "peak_source": src + " (hbm_gbs, of " + src + ")",
+                     "update_mean_ms": upd_ms},
         "clocks": clocks, "gpu_launches": launches_per_iter * args.steps,
         "e2e": e2e, "final_tol": tol, "launch": desc,
     }

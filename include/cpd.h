@@ -90,7 +90,9 @@ typedef struct {
     double gamma;       /* decreasing step offset (t + gamma > 0)                   */
     uint64_t seed;      /* key of the Philox4x64-10 draws                           */
     int32_t engine;     /* 0 = automatic, 1 = CUDA-core gradient, 2 = tensor-core
-                           gradient (BF16 tensors only)                            */
+                           gradient, one CTA per tile, 3 = tensor-core gradient,
+                           one thread-block cluster per fiber group (2 and 3:
+                           BF16 tensors, R <= 64; 3: every I_k <= 1024)         */
     int32_t reserved;   /* must be 0                                                */
 } cpd_config;
 

@@ -23,7 +23,7 @@ HOST, DEVICE = 0, 1
 SAMPLE = {"euclidean": 0, "leverage": 1, "uniform": 2}
 STEP = {"fixed": 0, "adagrad": 1, "decay": 2}
 XDT = {"f64": 0, "f32": 1, "bf16": 2}
-ENGINE = {"auto": 0, "simt": 1, "tensor": 2}
+ENGINE = {"auto": 0, "simt": 1, "tensor": 2, "cluster": 3}
 MAX_MODES = 8
 
 

@@ -65,6 +65,7 @@ struct cpd_ctx {
     int prof_used = 0;
     bool has_sample = false;
     unsigned long long *trace_buf = nullptr;
+    int max_clusters = 0;
 
     template <class F>
     cudaError_t with_problem(F &&f)
@@ -107,7 +108,7 @@ static cpd_status validate(const cpd_config *cfg)
     if (cfg->step < 0 || cfg->step > 2) return fail(CPD_EINVAL, "unknown step");
     if (cfg->x_dtype < 0 || cfg->x_dtype > 2) return fail(CPD_EINVAL, "unknown x_dtype");
     if (cfg->reserved != 0) return fail(CPD_EINVAL, "reserved must be 0");
-    if (cfg->engine < 0 || cfg->engine > 2) return fail(CPD_EINVAL, "unknown engine");
+    if (cfg->engine < 0 || cfg->engine > 3) return fail(CPD_EINVAL, "unknown engine");
     double total = 1.0;
     for (int k = 0; k < cfg->N; ++k) {
         if (cfg->dims[k] < 1 || cfg->dims[k] > (int64_t)1 << 31)
@@ -121,8 +122,14 @@ static cpd_status validate(const cpd_config *cfg)
         return fail(CPD_EINVAL, "AdaGrad needs eta > 0 and b >= 0");
     if (cfg->step == CPD_STEP_DECAY && !(cfg->gamma > 0.0))
         return fail(CPD_EINVAL, "decreasing step needs gamma > 0");
-    if (cfg->engine == kEngineTensor && (cfg->x_dtype != CPD_BF16 || !tc_supported(cfg->R, 128)))
+    if ((cfg->engine == kEngineTensor || cfg->engine == kEngineTensorCluster) &&
+        (cfg->x_dtype != CPD_BF16 || !tc_supported(cfg->R, 128)))
         return fail(CPD_EINVAL, "tensor-core engine needs BF16 tensors and R <= 64");
+    if (cfg->engine == kEngineTensorCluster) {
+        int64_t imax = 0;
+        for (int k = 0; k < cfg->N; ++k) imax = std::max<int64_t>(imax, cfg->dims[k]);
+        if ((imax + 127) / 128 > 8) return fail(CPD_EINVAL, "cluster engine needs every I_k <= 1024");
+    }
     return CPD_OK;
 }
 
@@ -134,7 +141,28 @@ static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
     int64_t imax = 0;
     for (int k = 0; k < g.N; ++k) imax = std::max<int64_t>(imax, g.dims[k]);
     c->imax = imax;
-    if (c->engine == kEngineTensor) {
+    P.cs = 1;
+    if (c->engine == kEngineTensorCluster) {
+        if constexpr (sizeof(T) == 4) {
+            // one cluster of ceil(I_max / 128) CTAs per fiber group; as many
+            // groups as clusters fit at once, fibers per group a multiple of 16
+            P.rb = 128;
+            P.cs = (int)((imax + P.rb - 1) / P.rb);
+            P.fb = 128;
+            const int maxc = tcc_max_clusters(P);
+            if (maxc < 1) {   // no such cluster can be co-scheduled: per-CTA engine
+                c->engine = kEngineTensor;
+                choose_tiles(c, P, sm_count);
+                return;
+            }
+            int64_t pf = std::max<int64_t>(1, std::min<int64_t>(maxc, (g.B + 15) / 16));
+            int64_t fb = (g.B + pf - 1) / pf;
+            fb = (fb + 15) / 16 * 16;
+            P.fb = (int)std::min<int64_t>(256, std::max<int64_t>(16, fb));
+            while (P.fb > 16 && tcc_smem_bytes(P) > 220 * 1024) P.fb -= 16;
+            c->max_clusters = maxc;
+        }
+    } else if (c->engine == kEngineTensor) {
         // 128-row MMA tiles; fibers per CTA a multiple of 16 (the MMA K), about
         // one wave of CTAs.
         P.rb = 128;
@@ -163,11 +191,13 @@ static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
         P.tile[k].pr = (int)((g.dims[k] + P.rb - 1) / P.rb);
         maxpr = std::max(maxpr, P.tile[k].pr);
     }
-    c->grid_grad = maxpr * P.pf;
+    c->grid_grad = (c->engine == kEngineTensorCluster ? P.cs : maxpr) * P.pf;
     const int rpc = std::max(1, kThreads / g.R);
     c->grid_upd = (int)((imax + rpc - 1) / rpc);
     if constexpr (sizeof(T) == 4)
-        c->smem_grad = c->engine == kEngineTensor ? tc_smem_bytes(P) : grad_smem_bytes(P);
+        c->smem_grad = c->engine == kEngineTensorCluster ? tcc_smem_bytes(P)
+                       : c->engine == kEngineTensor      ? tc_smem_bytes(P)
+                                                         : grad_smem_bytes(P);
     else
         c->smem_grad = grad_smem_bytes(P);
 }
@@ -192,10 +222,14 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     }
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, c->device);
-    if (g.engine == 0)
-        c->engine = (g.x_dtype == CPD_BF16 && tc_supported(g.R, 128) && g.R >= 16) ? kEngineTensor : kEngineSimt;
-    else
+    if (g.engine == 0) {
+        int64_t imax = 0;
+        for (int k = 0; k < g.N; ++k) imax = std::max<int64_t>(imax, g.dims[k]);
+        const bool tc = g.x_dtype == CPD_BF16 && tc_supported(g.R, 128) && g.R >= 16;
+        c->engine = !tc ? kEngineSimt : ((imax + 127) / 128 <= 8 ? kEngineTensorCluster : kEngineTensor);
+    } else {
         c->engine = g.engine;
+    }
     choose_tiles(c, P, sm_count);
 
     // Tensor replicas (one per mode), built from a device copy of X.
@@ -598,9 +632,11 @@ extern "C" cpd_status cpd_describe(cpd_ctx *c, char *buf, size_t len)
     std::snprintf(buf, len,
                   "{\"engine\": \"%s\", \"rows_per_cta\": %d, \"fibers_per_cta\": %d, \"fiber_groups\": %d, "
                   "\"grad_grid\": %d, \"update_grid\": %d, \"grad_smem\": %zu, \"graph_chunk\": %d, "
+                  "\"cluster\": %d, \"max_clusters\": %d, "
                   "\"xnorm2\": %.17g}",
-                  c->engine == kEngineTensor ? "tensor" : "simt", rb, fb, pf, c->grid_grad, c->grid_upd,
-                  c->smem_grad, kGraphChunk, c->xnorm2);
+                  c->engine == kEngineTensorCluster ? "cluster" : c->engine == kEngineTensor ? "tensor" : "simt",
+                  rb, fb, pf, c->grid_grad, c->grid_upd,
+                  c->smem_grad, kGraphChunk, c->fbytes == 8 ? 1 : c->Pf.cs, c->max_clusters, c->xnorm2);
     return CPD_OK;
 }
 

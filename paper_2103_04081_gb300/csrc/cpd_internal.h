@@ -28,7 +28,7 @@ constexpr int kThreads = 256;
 enum : int { kStNonFinite = 1, kStDegenerate = 2, kStTimeout = 4 };
 
 // Gradient engines.
-enum : int { kEngineSimt = 1, kEngineTensor = 2 };
+enum : int { kEngineSimt = 1, kEngineTensor = 2, kEngineTensorCluster = 3 };
 
 // Launch tiling of the gradient kernel for one mode n: CTA (gr, gf) handles
 // rows [gr*rb, gr*rb+rb) of A^(n) and fibers [gf*fb, gf*fb+fb) of the batch.
@@ -40,6 +40,7 @@ template <class T>
 struct Problem {
     int N, R, B, sampling, step, x_dtype;
     int rb, fb, pf;           // rows per CTA, fibers per CTA, fiber groups
+    int cs;                   // CTAs per cluster (clustered tensor-core engine)
     int64_t dims[kMaxModes];
     int64_t ld[kMaxModes];    // fiber stride of replica k (elements, multiple of 8)
     double Jn[kMaxModes];     // J_n = prod_{k != n} I_k, as a double
@@ -84,9 +85,13 @@ template <class T>
 size_t grad_smem_bytes(const Problem<T> &P);
 int fit_blocks();
 
-// Tensor-core gradient engine (cpd_tc.cu).
+// Tensor-core gradient engines (cpd_tc.cu: one CTA per tile; cpd_tcc.cu:
+// one cluster per fiber group).
 bool tc_supported(int R, int rb);
 cudaError_t launch_grad_tc(const Problem<float> &P, int grid, cudaStream_t stream);
 size_t tc_smem_bytes(const Problem<float> &P);
+cudaError_t launch_grad_tcc(const Problem<float> &P, int grid, cudaStream_t stream);
+size_t tcc_smem_bytes(const Problem<float> &P);
+int tcc_max_clusters(const Problem<float> &P);
 
 }  // namespace cpd

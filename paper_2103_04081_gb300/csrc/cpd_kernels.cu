@@ -530,9 +530,11 @@ cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd, s
 {
     cudaError_t e = cudaSuccess;
     if (ev0) cudaEventRecord(ev0, s);
-    if (engine == kEngineTensor) {
-        if constexpr (sizeof(T) == 4) e = launch_grad_tc(P, grid_grad, s);
-        else e = cudaErrorInvalidValue;
+    if (engine == kEngineTensor || engine == kEngineTensorCluster) {
+        if constexpr (sizeof(T) == 4)
+            e = engine == kEngineTensor ? launch_grad_tc(P, grid_grad, s) : launch_grad_tcc(P, grid_grad, s);
+        else
+            e = cudaErrorInvalidValue;
     } else {
         if constexpr (sizeof(T) == 8) {
             e = launch_grad_simt<T, double>(P, grid_grad, smem_grad, s);

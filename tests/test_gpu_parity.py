@@ -69,16 +69,17 @@ TENSOR = [
 ]
 
 
+@pytest.mark.parametrize("engine", ["tensor", "cluster"])
 @pytest.mark.parametrize("dims,R,B,sampling", TENSOR)
-def test_teacher_forced_tensor_engine(cpd, orc, dims, R, B, sampling):
+def test_teacher_forced_tensor_engine(cpd, orc, dims, R, B, sampling, engine):
     A, X, A0 = make_problem(dims, R, x_dtype="bf16", lognormal_rows=True)
     dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype="bf16",
-                            sampling=sampling, step="adagrad", seed=77, engine="tensor")
-    assert dec.describe()["engine"] == "tensor"
+                            sampling=sampling, step="adagrad", seed=77, engine=engine)
+    assert dec.describe()["engine"] == engine
     ocfg = _ocfg(orc, dims, R, B, "bf16", sampling, "adagrad", 77)
     tol = TOL["bf16_tensor"]
     worst = teacher_forced(dec, orc, ocfg, oracle_xbuf(X), 10, tol["G"], tol["A"])
-    print(dims, R, B, sampling, "tensor", worst, dec.describe())
+    print(dims, R, B, sampling, engine, worst, dec.describe())
     dec.close()
 
 
@@ -223,7 +224,7 @@ def _full(cpd, orc, name, sampling, steps, warm, engine="auto"):
     del X
     desc = dec.describe()
     dec.sgd_iters(warm)
-    key = "bf16_tensor" if desc["engine"] == "tensor" else xdt
+    key = "bf16_tensor" if desc["engine"] in ("tensor", "cluster") else xdt
     ocfg = _ocfg(orc, dims, R, B, xdt, sampling, w["step"], w["sample_seed"],
                  eta=w.get("eta", 0.1), b=w.get("b", 1e-12))
     worst = teacher_forced(dec, orc, ocfg, xb, steps, TOL[key]["G"], TOL[key]["A"])
