@@ -268,7 +268,7 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     for (int k = 0; k < g.N; ++k) {
         const size_t fb = (size_t)g.dims[k] * g.R;
         void *a, *S, *w, *cdf;
-        CK(dmalloc(c, &a, fb * sizeof(T)));
+        CK(dmalloc(c, &a, fb * sizeof(T) + 64));   // tail room for 16-byte bulk copies of row blocks
         CK(dmalloc(c, &S, fb * sizeof(double)));
         CK(dmalloc(c, &w, g.dims[k] * sizeof(double)));
         CK(dmalloc(c, &cdf, g.dims[k] * sizeof(unsigned long long)));
@@ -286,6 +286,25 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     CK(dmalloc(c, &p, (size_t)c->imax * g.R * sizeof(T)));  P.G = (T *)p;
     CK(dmalloc(c, &p, (size_t)(2 * g.R * g.R + g.R + 8) * sizeof(double)));  P.lev_L = (double *)p;
     CK(dmalloc(c, &p, sizeof(int)));  P.status = (int *)p;
+    CK(dmalloc(c, &p, sizeof(int)));  P.dirty = (int *)p;
+    CK(cudaMemsetAsync(P.dirty, 0xff, sizeof(int), s));
+    {
+        // CDF rebuilds are deferred to the next gradient kernel when every
+        // mode's companions fit its staging buffer
+        long long cap = kSimtStageCap;
+        if constexpr (sizeof(T) == 4) {
+            if (c->engine == kEngineTensor) cap = tc_stage_cap(P);
+            if (c->engine == kEngineTensorCluster) cap = tcc_stage_cap(P);
+        }
+        long long need = 0;
+        for (int n = 0; n < g.N; ++n) {
+            long long nd = 0;
+            for (int k = 0; k < g.N; ++k)
+                if (k != n) nd += g.dims[k];
+            need = std::max(need, nd);
+        }
+        P.defer_cdf = (g.sampling == CPD_SAMPLE_EUCLIDEAN && need <= cap) ? 1 : 0;
+    }
     CK(dmalloc(c, &p, 16 * sizeof(unsigned)));  P.counters = (unsigned *)p;
     CK(dmalloc(c, &p, (size_t)fit_blocks() * sizeof(double)));  c->fit_partials = (double *)p;
     CK(dmalloc(c, &p, sizeof(double)));  c->fit_out = (double *)p;
@@ -482,6 +501,7 @@ extern "C" cpd_status cpd_set_factors(cpd_ctx *c, const void *const *A, int loc,
         cudaError_t e = c->with_problem([&](auto &P) { return launch_refresh_mode(P, k, s); });
         if (e != cudaSuccess) return cuda_fail(e, "distribution refresh");
     }
+    CK(cudaMemsetAsync(c->fbytes == 8 ? c->Pd.dirty : c->Pf.dirty, 0xff, sizeof(int), s));   // all CDFs fresh
     return read_status(c, s);
 }
 
@@ -632,11 +652,12 @@ extern "C" cpd_status cpd_describe(cpd_ctx *c, char *buf, size_t len)
     std::snprintf(buf, len,
                   "{\"engine\": \"%s\", \"rows_per_cta\": %d, \"fibers_per_cta\": %d, \"fiber_groups\": %d, "
                   "\"grad_grid\": %d, \"update_grid\": %d, \"grad_smem\": %zu, \"graph_chunk\": %d, "
-                  "\"cluster\": %d, \"max_clusters\": %d, "
+                  "\"cluster\": %d, \"max_clusters\": %d, \"deferred_cdf\": %d, "
                   "\"xnorm2\": %.17g}",
                   c->engine == kEngineTensorCluster ? "cluster" : c->engine == kEngineTensor ? "tensor" : "simt",
                   rb, fb, pf, c->grid_grad, c->grid_upd,
-                  c->smem_grad, kGraphChunk, c->fbytes == 8 ? 1 : c->Pf.cs, c->max_clusters, c->xnorm2);
+                  c->smem_grad, kGraphChunk, c->fbytes == 8 ? 1 : c->Pf.cs, c->max_clusters,
+                  c->fbytes == 8 ? c->Pd.defer_cdf : c->Pf.defer_cdf, c->xnorm2);
     return CPD_OK;
 }
 

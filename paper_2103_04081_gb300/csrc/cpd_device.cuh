@@ -204,6 +204,63 @@ __device__ __forceinline__ unsigned long long quantize(double w, int s)
     return M >> (-sh);
 }
 
+// In place: `a` holds the bit patterns of the FP64 row weights w[0..I) on
+// entry and the fixed-point CDF (same definition as block_distribution) on
+// exit. Each thread transforms a contiguous chunk, reading every weight
+// before overwriting it. `sm` holds 2 * blockDim.x uint64 slots. Returns
+// false in every thread when the distribution has no mass.
+__device__ inline bool block_distribution_inplace(unsigned long long *a, long long I, unsigned long long *sm)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    long long mx = 0;
+    int bad = 0;
+    for (long long i = tid; i < I; i += nt) {
+        const double v = __longlong_as_double((long long)a[i]);
+        if (!(v >= 0.0) || isinf(v)) bad = 1;
+        const long long b = (long long)a[i];
+        mx = b > mx ? b : mx;
+    }
+    for (int off = 16; off >= 1; off >>= 1) {
+        const long long o = __shfl_down_sync(0xffffffffu, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    bad = __syncthreads_or(bad);
+    if ((tid & 31) == 0) sm[tid >> 5] = (unsigned long long)mx;
+    __syncthreads();
+    long long gmx = 0;
+    for (int q = 0; q < (nt >> 5); ++q) gmx = (long long)sm[q] > gmx ? (long long)sm[q] : gmx;
+    __syncthreads();
+    const double wmax = __longlong_as_double(gmx);
+    if (bad || !(wmax > 0.0)) return false;
+    const int ef = (int)((unsigned long long)gmx >> 52);
+    const int lg = ef ? ef - 1023 : 63 - __clzll(gmx) - 1074;
+    int L = 0;
+    while ((1LL << L) < I) ++L;
+    const int s = 61 - L - lg;
+    const long long chunk = (I + nt - 1) / nt;
+    const long long i0 = tid * chunk, i1 = (i0 + chunk < I) ? i0 + chunk : I;
+    unsigned long long tot = 0;
+    for (long long i = i0; i < i1; ++i) tot += quantize(__longlong_as_double((long long)a[i]), s);
+    unsigned long long inc = tot;
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, off);
+        if ((tid & 31) >= off) inc += o;
+    }
+    if ((tid & 31) == 31) sm[nt + (tid >> 5)] = inc;
+    __syncthreads();
+    unsigned long long acc = 0;
+    for (int q = 0; q < (tid >> 5); ++q) acc += sm[nt + q];
+    acc += inc - tot;
+    for (long long i = i0; i < i1; ++i) {
+        acc += quantize(__longlong_as_double((long long)a[i]), s);
+        a[i] = acc;
+    }
+    unsigned long long Q = 0;
+    for (int q = 0; q < (nt >> 5); ++q) Q += sm[nt + q];
+    __syncthreads();
+    return Q > 0;
+}
+
 // ---------------------------------------------------------------------------
 // The fixed-point distribution of one factor from its FP64 row weights, by
 // one CTA: s = 61 - ceil(log2 I) - floor(log2 max w), q_i = floor(w_i 2^s),
@@ -294,9 +351,15 @@ __device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 x)
 // buffer `stage` (cap entries) they are copied there first (one coalesced
 // pass) and searched there; otherwise the warp-cooperative multi-level
 // search runs on the global copies. Warps take 32-fiber chunks per mode.
+//
+// When CDF rebuilds are deferred (P.defer_cdf), the mode updated last
+// (*P.dirty) has only fresh row weights: its CDF is rebuilt here, in the
+// staging buffer, from those weights (scratch: `dsm`, 2 * blockDim.x uint64),
+// and the CTA with blockIdx.x == 0 stores it for later iterations.
 template <class T>
 __device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int f0, int nf, int *sidx,
-                                    unsigned long long *stage, long long cap)
+                                    unsigned long long *stage, long long cap,
+                                    unsigned long long *dsm = nullptr)
 {
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
     long long need = 0, off[kMaxModes];
@@ -306,12 +369,26 @@ __device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int
     }
     const bool staged = P.sampling != CPD_SAMPLE_UNIFORM && stage != nullptr && need <= cap;
     if (staged) {
+        const int dirty = P.defer_cdf ? *P.dirty : -1;
         for (int k = 0; k < P.N; ++k) {
             if (k == n) continue;
-            const unsigned long long *c = P.cdf[k];
-            for (long long i = threadIdx.x; i < P.dims[k]; i += blockDim.x) stage[off[k] + i] = __ldg(c + i);
+            if (k == dirty) {
+                const unsigned long long *wb = reinterpret_cast<const unsigned long long *>(P.w[k]);
+                for (long long i = threadIdx.x; i < P.dims[k]; i += blockDim.x) stage[off[k] + i] = __ldcg(wb + i);
+            } else {
+                const unsigned long long *c = P.cdf[k];
+                for (long long i = threadIdx.x; i < P.dims[k]; i += blockDim.x) stage[off[k] + i] = __ldg(c + i);
+            }
         }
         __syncthreads();
+        if (dirty >= 0 && dirty != n) {
+            unsigned long long *c = stage + off[dirty];
+            if (!block_distribution_inplace(c, P.dims[dirty], dsm)) {
+                if (threadIdx.x == 0) atomicOr(P.status, kStDegenerate);
+            } else if (blockIdx.x == 0) {
+                for (long long i = threadIdx.x; i < P.dims[dirty]; i += blockDim.x) P.cdf[dirty][i] = c[i];
+            }
+        }
     }
     const int chunks = (nf + 31) / 32;
     for (int job = warp; job < chunks * P.N; job += nwarps) {
@@ -357,6 +434,24 @@ __device__ __forceinline__ double fiber_prob(const Problem<T> &P, int n, const i
     return p;
 }
 
+// fiber_prob on the staged CDFs (stage == nullptr: the global ones).
+template <class T>
+__device__ __forceinline__ double fiber_prob_staged(const Problem<T> &P, int n, const int *row,
+                                                    const unsigned long long *stage)
+{
+    if (!stage) return fiber_prob(P, n, row);
+    double p = 1.0;
+    long long off = 0;
+    for (int k = 0; k < P.N; ++k) {
+        if (k == n) continue;
+        const unsigned long long *c = stage + off;
+        const unsigned long long q = c[row[k]] - (row[k] > 0 ? c[row[k] - 1] : 0ULL);
+        p = __dmul_rn(p, __ddiv_rn(__ull2double_rn(q), __ull2double_rn(c[P.dims[k] - 1])));
+        off += P.dims[k];
+    }
+    return p;
+}
+
 // The fiber's weight in Eq. gradient1, s_f = 1 / (B J_n p_f), in FP32 (the
 // gradient's own precision): (1/(B J_n)) prod_k Q_k / q_k(i_k).
 template <class T>
@@ -375,6 +470,38 @@ __device__ __forceinline__ float fiber_weight(const Problem<T> &P, int n, const 
         }
     }
     return s;
+}
+
+// s_f from CDFs staged in shared memory by draw_indices (modes k != n in
+// ascending order, I_k entries each); same arithmetic as fiber_weight.
+template <class T>
+__device__ __forceinline__ float fiber_weight_staged(const Problem<T> &P, int n, const int *row,
+                                                     const unsigned long long *stage)
+{
+    float s = P.inv_bj[n];
+    long long off = 0;
+    for (int k = 0; k < P.N; ++k) {
+        if (k == n) continue;
+        if (P.sampling == CPD_SAMPLE_UNIFORM) {
+            s *= (float)P.dims[k];
+        } else {
+            const unsigned long long *c = stage + off;
+            const unsigned long long q = c[row[k]] - (row[k] > 0 ? c[row[k] - 1] : 0ULL);
+            s *= __ull2float_rn(c[P.dims[k] - 1]) / __ull2float_rn(q);
+        }
+        off += P.dims[k];
+    }
+    return s;
+}
+
+// True when draw_indices staged the CDFs of every mode k != n in `cap` slots.
+template <class T>
+__device__ __forceinline__ bool cdfs_staged(const Problem<T> &P, int n, long long cap)
+{
+    long long need = 0;
+    for (int k = 0; k < P.N; ++k)
+        if (k != n) need += P.dims[k];
+    return P.sampling != CPD_SAMPLE_UNIFORM && need <= cap;
 }
 
 template <class XT, class T>

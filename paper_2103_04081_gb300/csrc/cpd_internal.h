@@ -61,6 +61,9 @@ struct Problem {
     T *G;                     // last gradient, I_n x R row-major
     double *lev_L;            // leverage: Cholesky factor R x R + inverse pivots R
     int *status;              // kSt* bits
+    int *dirty;               // mode whose global CDF is stale (-1: none); the next
+                              // gradient kernel rebuilds it while staging the CDFs
+    int defer_cdf;            // 1: CDF rebuilds are deferred that way
     unsigned *counters;       // last-block arrival counters (zero between launches)
     unsigned long long *trace;  // phase timestamps (cpd_trace), or null
 };
@@ -93,5 +96,8 @@ size_t tc_smem_bytes(const Problem<float> &P);
 cudaError_t launch_grad_tcc(const Problem<float> &P, int grid, cudaStream_t stream);
 size_t tcc_smem_bytes(const Problem<float> &P);
 int tcc_max_clusters(const Problem<float> &P);
+long long tc_stage_cap(const Problem<float> &P);
+long long tcc_stage_cap(const Problem<float> &P);
+constexpr long long kSimtStageCap = 2048;
 
 }  // namespace cpd

@@ -25,11 +25,12 @@ namespace {
 // Shared-memory carve-up of the gradient kernel (all offsets 16-byte aligned).
 template <class T>
 struct GradSmem {
-    size_t idx, jcol, s, z, At, x, stage, total;
+    size_t idx, jcol, s, z, At, x, stage, dsm, total;
     __host__ __device__ GradSmem(int N, int R, int rb, int fb)
     {
         size_t o = 0;
         stage = o; o += 2048 * 8;   // CDF staging for the draws
+        dsm = o;   o += 2 * kThreads * 8;   // scratch of an in-place CDF rebuild
         idx = o;  o += align_up_h((size_t)fb * N * sizeof(int), 16);
         jcol = o; o += align_up_h((size_t)fb * sizeof(long long), 16);
         s = o;    o += align_up_h((size_t)fb * sizeof(T), 16);
@@ -97,7 +98,9 @@ __global__ void __launch_bounds__(kThreads) k_grad_simt(const Problem<T> P)
     T *sx = reinterpret_cast<T *>(smem + L.x);
 
     // 1. draws of Alg. 3
-    draw_indices(P, t, n, f0, nf, sidx, reinterpret_cast<unsigned long long *>(smem + L.stage), 2048);
+    unsigned long long *stage = reinterpret_cast<unsigned long long *>(smem + L.stage);
+    draw_indices(P, t, n, f0, nf, sidx, stage, 2048, reinterpret_cast<unsigned long long *>(smem + L.dsm));
+    const bool staged = cdfs_staged(P, n, 2048);
     // rows of A^(n) for the residual, transposed (conflict-free reads)
     const T *An = P.A[n];
     for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
@@ -117,9 +120,9 @@ __global__ void __launch_bounds__(kThreads) k_grad_simt(const Problem<T> P)
         }
         jcol[f] = j;
         if constexpr (sizeof(T) == 8)
-            ss[f] = __ddiv_rn(1.0, __dmul_rn(__dmul_rn((double)P.B, P.Jn[n]), fiber_prob(P, n, row)));
+            ss[f] = __ddiv_rn(1.0, __dmul_rn(__dmul_rn((double)P.B, P.Jn[n]), fiber_prob_staged(P, n, row, staged ? stage : nullptr)));
         else
-            ss[f] = fiber_weight(P, n, row);
+            ss[f] = staged ? fiber_weight_staged(P, n, row, stage) : fiber_weight(P, n, row);
         if (gr == 0)
             for (int k = 0; k < N; ++k) P.idx[(long long)(f0 + f) * N + k] = row[k];
     }
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P)
 {
     __shared__ T s_new[kThreads];
     __shared__ unsigned long long s_dist[2 * kThreads];
-    __shared__ double s_w[kWStage];
+    __shared__ __align__(16) double s_w[kWStage];       // last CTA: staged row weights
     const bool tr0 = blockIdx.x == 0;
     trace_stamp(P.trace, 16, tr0);
     const long long t = *P.t_dev;
@@ -242,11 +245,12 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P)
     trace_stamp(P.trace, 19, tr0);
     if (!last_block(P.counters)) return;
     trace_stamp(P.trace, 20, true);
-    if (P.sampling == CPD_SAMPLE_EUCLIDEAN) finish_distribution(P, n, s_dist, s_w);
+    if (P.sampling == CPD_SAMPLE_EUCLIDEAN && !P.defer_cdf) finish_distribution(P, n, s_dist, s_w);
     trace_stamp(P.trace, 21, true);
     if (threadIdx.x == 0) {
         P.counters[0] = 0;
         if (P.sampling != CPD_SAMPLE_LEVERAGE) {
+            if (P.sampling == CPD_SAMPLE_EUCLIDEAN && P.defer_cdf) *P.dirty = n;
             *P.n_last = n;
             *P.t_dev = t + 1;
         }

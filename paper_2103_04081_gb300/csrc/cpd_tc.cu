@@ -128,8 +128,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
     trace_stamp(P.trace, 1, tr0);
     // 1. draws (Alg. 3), fiber columns (Eq. map) and weights s_f; the CDFs are
     //    staged over the operand tiles, which are not written before the gather
-    draw_indices(P, t, n, f0, nf, sidx, reinterpret_cast<unsigned long long *>(sA),
-                 (long long)(L.z - L.a) / 8);
+    const long long cap = (long long)(L.zs - L.a) / 8;
+    draw_indices(P, t, n, f0, nf, sidx, reinterpret_cast<unsigned long long *>(sA), cap,
+                 reinterpret_cast<unsigned long long *>(szs));
+    const bool staged = cdfs_staged(P, n, cap);
     __syncthreads();
     trace_stamp(P.trace, 2, tr0);
     for (int f = threadIdx.x; f < fb; f += blockDim.x) {
@@ -142,7 +144,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
                 Jp *= P.dims[k];
             }
             jcol[f] = j;
-            ss[f] = fiber_weight(P, n, row);
+            ss[f] = staged ? fiber_weight_staged(P, n, row, reinterpret_cast<const unsigned long long *>(sA))
+                           : fiber_weight(P, n, row);
             if (gr == 0)
                 for (int k = 0; k < N; ++k) P.idx[(long long)(f0 + f) * N + k] = row[k];
         } else {
@@ -320,6 +323,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
 bool tc_supported(int R, int rb) { return R >= 1 && R <= kTcN && rb == kTcM; }
 
 size_t tc_smem_bytes(const Problem<float> &P) { return TcSmem(P.N, P.R, P.fb).total; }
+
+long long tc_stage_cap(const Problem<float> &P)
+{
+    const TcSmem L(P.N, P.R, P.fb);
+    return (long long)(L.zs - L.a) / 8;
+}
 
 cudaError_t launch_grad_tc(const Problem<float> &P, int grid, cudaStream_t s)
 {

@@ -3,27 +3,20 @@
 // Same arithmetic as the per-CTA engine (Eq. gradient1 as G_g = A H_g - M_g
 // per fiber group g, M_g = X_S,g Z'_S,g on tcgen05, Z' as a bf16 hi/lo pair),
 // but one cluster of cs CTAs handles one fiber group: CTA `rank` owns the
-// row tile [128 rank, 128 rank + 128) of A^(n) and 1/cs of the group's
-// fibers. Everything the row tiles of a group share -- the draws, the
-// sampled KRP rows z_f, the B operands and H_g -- is computed once, in
-// slices: each CTA draws and builds the operands of its own fibers and
-// writes them into every CTA of the cluster through distributed shared
-// memory; each CTA forms H over its own fibers, and CTA `rank` sums rows
-// r = rank (mod cs) of those partials across the cluster (ascending rank,
-// read through DSMEM) and writes the finished rows into every CTA.
-//
-// Phases of one CTA:
-//   0. t, n; async copy of its A^(n) rows; TMEM / mbarrier set-up; early
-//      arrival on the cluster barrier.
-//   1. draws of its own fibers (Alg. 3), their columns (Eq. map) and weights.
-//   2. its fibers' factor rows (async), then z_f, s_f z_f and the hi/lo B
-//      operands, stored into all CTAs of the cluster (DSMEM), after the
-//      early barrier has completed (every CTA has started).
-//   3. cluster barrier: all fibers' columns and operands are everywhere.
-//   4. gather of its rows of every fiber (cp.async, MN-major operand layout);
-//      its slice of H_g, stored into all CTAs; MMAs; cluster barrier.
-//   5. accumulator -> G_g = A H_g - M_g for its rows, staged and stored
-//      coalesced as the group's partial.
+// row tile [128 rank, 128 rank + 128) of A^(n) and a slice of fpc of the
+// group's fb fibers. Everything the row tiles of a group share is computed
+// once, in slices, and moved between the CTAs' shared memories by bulk async
+// copies (cp.async.bulk shared::cta -> shared::cluster) that complete on the
+// receiving CTA's mbarrier:
+//   - each CTA draws its fibers (Alg. 3), forms their columns (Eq. map),
+//     weights and sampled KRP rows (Alg. 1), and the B operands of its slice,
+//     and sends the slice (B hi/lo, columns, weights) to every other CTA;
+//   - each CTA forms H over its own fibers; CTA d owns rows [d hr, d hr + hr)
+//     of H_g, receives those rows of every CTA's partial, sums them in
+//     ascending rank and sends the finished rows to every other CTA.
+// The A^(n) rows of the tile arrive by one global -> shared bulk copy. One
+// cluster barrier after all receptions guarantees that no source buffer is
+// reused while a copy could still read it.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -42,12 +35,12 @@ constexpr int kK = 16;    // MMA K for 16-bit operands
 constexpr int kCols = 64; // TMEM columns
 
 struct TccSmem {
-    size_t a, bhi, blo, zo, zso, hp, arow, h, rows, jcol, s, idx, bar, tmem, total;
-    int lda, fpc;
+    size_t a, bhi, blo, zo, zso, hp, hrecv, arow, h, rows, jcol, s, idx, bar, tmem, total;
+    int fpc, hr;
     __host__ __device__ TccSmem(int N, int R, int fb, int cs)
     {
-        lda = R | 1;
-        fpc = ((fb + cs - 1) / cs + 7) / 8 * 8;   // own fibers per CTA, multiple of 8
+        fpc = ((fb + cs - 1) / cs + 7) / 8 * 8;   // fiber slots per CTA, multiple of 8
+        hr = (kN + cs - 1) / cs;                 // rows of H_g owned per CTA
         size_t o = 0;
         a = o;    o += (size_t)fb * kM * 2;                 // X tile (also CDF staging)
         bhi = o;  o += (size_t)fb * kN * 2;                 // Z' hi, K-major
@@ -55,19 +48,33 @@ struct TccSmem {
         zo = o;   o += up((size_t)fpc * kN * 4);            // own z_f, [fiber][64]
         zso = o;  o += up((size_t)fpc * kN * 4);            // own s_f z_f
         hp = o;   o += (size_t)kN * kN * 4;                 // H over own fibers
+        hrecv = o; o += up((size_t)cs * hr * kN * 4);       // owned rows of every CTA's partial
         if (o - a < (size_t)kM * R * 4) o = a + up((size_t)kM * R * 4);   // epilogue tile staging
-        arow = o; o += up((size_t)kM * lda * 4);            // A^(n) rows of the tile
+        arow = o; o += up((size_t)kM * R * 4 + 16);         // A^(n) rows of the tile (bulk copy)
         h = o;    o += (size_t)kN * kN * 4;                 // H_g
         rows = o; o += up((size_t)fpc * (N - 1) * R * 4);   // own fibers' factor rows
         jcol = o; o += up((size_t)fb * 8);
         s = o;    o += up((size_t)fb * 4);
         idx = o;  o += up((size_t)fpc * N * 4);
-        bar = o;  o += 16;
+        bar = o;  o += 64;                                  // mbarriers: mma, a, x, hp, h
         tmem = o; o += 16;
         total = o;
     }
     __host__ __device__ static size_t up(size_t v) { return (v + 127) / 128 * 128; }
 };
+
+// Fiber slots [c fpc, c fpc + nslot(c)) of CTA c (zero-padded past nf).
+__device__ __forceinline__ int nslot(int c, int fpc, int fb)
+{
+    const int v = fb - c * fpc;
+    return v < 0 ? 0 : (v < fpc ? v : fpc);
+}
+
+__device__ __forceinline__ int hrows(int d, int hr)
+{
+    const int v = kN - d * hr;
+    return v < 0 ? 0 : (v < hr ? v : hr);
+}
 
 }  // namespace
 
@@ -85,75 +92,88 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
     const long long In = P.dims[n];
     const int r0 = rank * kM;
     const bool has_rows = r0 < In;
+    const int nrows = has_rows ? ((In - r0) < kM ? (int)(In - r0) : kM) : 0;
     const int f0 = gf * fb;
     const int nf = (P.B - f0) < fb ? (P.B - f0) : fb;
 
     const TccSmem L(N, R, fb, cs);
     unsigned char *sA = smem + L.a;
+    __nv_bfloat16 *sBhi = reinterpret_cast<__nv_bfloat16 *>(smem + L.bhi);
+    __nv_bfloat16 *sBlo = reinterpret_cast<__nv_bfloat16 *>(smem + L.blo);
     float *sArow = reinterpret_cast<float *>(smem + L.arow);
     float *sH = reinterpret_cast<float *>(smem + L.h);
+    float *sHp = reinterpret_cast<float *>(smem + L.hp);
+    float *sHr = reinterpret_cast<float *>(smem + L.hrecv);
     float *sRows = reinterpret_cast<float *>(smem + L.rows);
     float *sZo = reinterpret_cast<float *>(smem + L.zo);
     float *sZso = reinterpret_cast<float *>(smem + L.zso);
-    float *sHp = reinterpret_cast<float *>(smem + L.hp);
     long long *jcol = reinterpret_cast<long long *>(smem + L.jcol);
     float *ss = reinterpret_cast<float *>(smem + L.s);
     int *sidx = reinterpret_cast<int *>(smem + L.idx);
-    const uint32_t bar = smem_u32(smem + L.bar);
+    const uint32_t bar_mma = smem_u32(smem + L.bar), bar_a = bar_mma + 8, bar_x = bar_mma + 16,
+                   bar_hp = bar_mma + 24, bar_h = bar_mma + 32;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + L.tmem);
-    const int lda = L.lda, fpc = L.fpc;
-    const int fo0 = rank * fpc;                                   // own fibers [fo0, fo0+nown)
+    const int fpc = L.fpc, hr = L.hr;
+    const int fo0 = rank * fpc;
+    const int myslots = nslot(rank, fpc, fb);
     const int nown = nf - fo0 < 0 ? 0 : (nf - fo0 < fpc ? nf - fo0 : fpc);
+    const int nb8 = myslots / 8;
 
-    // 0. own A^(n) rows (async), TMEM and mbarrier, early cluster arrival
-    if (has_rows) {
-        const float *An = P.A[n];
-        const uint32_t dst0 = smem_u32(sArow);
-        const int rows = (In - r0) < kM ? (int)(In - r0) : kM;
-        for (int i = warp; i < rows; i += kThreads / 32) {
-            const float *src = An + (long long)(r0 + i) * R;
-            for (int q = lane; q < R; q += 32) cp_async4(dst0 + (uint32_t)((i * lda + q) * 4), src + q);
+    // 0. mbarriers with the byte counts this CTA will receive; A^(n) rows by
+    //    one bulk copy; TMEM; early cluster arrival
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 5; ++q) mbar_init(bar_mma + 8 * q, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        uint32_t bx = 0, bh = 0;
+        for (int c = 0; c < cs; ++c) {
+            if (c == rank) continue;
+            bx += 2u * 8u * (uint32_t)(nslot(c, fpc, fb) / 8) * 128u + (uint32_t)nslot(c, fpc, fb) * 12u;
+            bh += (uint32_t)hrows(c, hr) * kN * 4u;
         }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        if (warp == 0) {
-            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                             smem_u32(tmem_holder)),
-                         "r"(kCols)
-                         : "memory");
-            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-        }
-        if (threadIdx.x == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        mbar_expect_tx(bar_x, bx);
+        mbar_expect_tx(bar_hp, (uint32_t)(cs - 1) * (uint32_t)hrows(rank, hr) * kN * 4u);
+        mbar_expect_tx(bar_h, bh);
+        if (has_rows) {
+            const uint32_t bytes = (uint32_t)((nrows * R * 4 + 15) / 16 * 16);
+            mbar_expect_tx(bar_a, bytes);
+            bulk_g2s(smem_u32(sArow), P.A[n] + (long long)r0 * R, bytes, bar_a);
+        } else {
+            mbar_expect_tx(bar_a, 0);
         }
     }
-    cluster_arrive();   // no remote store reaches this CTA before everyone has started
+    if (has_rows && warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_holder)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    cluster_arrive();   // released once every CTA's mbarriers are initialised
     trace_stamp(P.trace, 1, tr0);
 
-    // 1. own fibers: draws (CDFs staged in the X-tile region, written by no
-    //    other CTA), columns, weights
-    draw_indices(P, t, n, f0 + fo0, nown, sidx, reinterpret_cast<unsigned long long *>(sA),
-                 (long long)(fb * kM * 2) / 8);
+    // 1. own fibers: draws (CDFs staged in the X-tile region), columns, weights
+    unsigned long long *stage = reinterpret_cast<unsigned long long *>(sA);
+    const long long cap = (long long)(fb * kM * 2) / 8;
+    draw_indices(P, t, n, f0 + fo0, nown, sidx, stage, cap, reinterpret_cast<unsigned long long *>(sZo));
     __syncthreads();
     trace_stamp(P.trace, 2, tr0);
-    const uint32_t jcol_l = smem_u32(jcol), ss_l = smem_u32(ss);
-    long long myj = 0;
-    float mys = 0.f;
-    if (threadIdx.x < nown) {
+    const bool staged = cdfs_staged(P, n, cap);
+    if (threadIdx.x < myslots) {
         const int f = threadIdx.x;
-        const int *row = sidx + f * N;
-        long long Jp = 1;
-        for (int k = 0; k < N; ++k) {
-            if (k == n) continue;
-            myj += (long long)row[k] * Jp;
-            Jp *= P.dims[k];
+        long long j = 0;
+        float w = 0.f;
+        if (f < nown) {
+            const int *row = sidx + f * N;
+            long long Jp = 1;
+            for (int k = 0; k < N; ++k) {
+                if (k == n) continue;
+                j += (long long)row[k] * Jp;
+                Jp *= P.dims[k];
+            }
+            w = staged ? fiber_weight_staged(P, n, row, stage) : fiber_weight(P, n, row);
+            for (int k = 0; k < N; ++k) P.idx[(long long)(f0 + fo0 + f) * N + k] = row[k];
         }
-        mys = fiber_weight(P, n, row);
-        for (int k = 0; k < N; ++k) P.idx[(long long)(f0 + fo0 + f) * N + k] = row[k];
-    }
-    if (threadIdx.x < fpc && fo0 + (int)threadIdx.x < fb) {
-        jcol[fo0 + threadIdx.x] = myj;   // local copies for the operand build below
-        ss[fo0 + threadIdx.x] = mys;
+        jcol[fo0 + f] = j;
+        ss[fo0 + f] = w;
     }
     {
         // own fibers' factor rows, one warp per (fiber, mode) row
@@ -173,67 +193,74 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
     trace_stamp(P.trace, 10, tr0);
-    asm volatile("cp.async.wait_all;\n" ::: "memory");     // A rows and factor rows
+
+    // 2. z_f, s_f z_f (own, local) and the own slice of the B operands
+    for (int job = threadIdx.x; job < kN * nb8; job += blockDim.x) {
+        const int r = job % kN, b = job / kN;
+        __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int fl = 8 * b + u;
+            float v = 0.f;
+            if (fl < nown && r < R) {
+                const float *fr = sRows + (long long)fl * (N - 1) * R + r;
+                v = 1.f;
+                for (int kk = 0; kk < N - 1; ++kk) v = v * fr[kk * R];
+            }
+            const float zs = v * ss[fo0 + fl];
+            sZo[fl * kN + r] = v;
+            sZso[fl * kN + r] = zs;
+            hi[u] = __float2bfloat16_rn(zs);
+            lo[u] = __float2bfloat16_rn(zs - __bfloat162float(hi[u]));
+        }
+        const int f = fo0 + 8 * b;
+        const int off = (((r >> 3) * (fb >> 3) + (f >> 3)) << 6) + ((r & 7) << 3);
+        *reinterpret_cast<uint4 *>(sBhi + off) = *reinterpret_cast<uint4 *>(hi);
+        *reinterpret_cast<uint4 *>(sBlo + off) = *reinterpret_cast<uint4 *>(lo);
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     trace_stamp(P.trace, 11, tr0);
-
-    // 2. operands of the own fibers, into every CTA of the cluster
-    cluster_wait();
-    if (threadIdx.x < fpc && fo0 + (int)threadIdx.x < fb) {
-        const int f = fo0 + threadIdx.x;
-        for (int d = 0; d < cs; ++d) {
-            if (d == rank) continue;
-            st_cluster_u64(map_shared(jcol_l + (uint32_t)(f * 8), d), (unsigned long long)myj);
-            st_cluster_u32(map_shared(ss_l + (uint32_t)(f * 4), d), __float_as_uint(mys));
-        }
-    }
-    {
-        const uint32_t bhi_l = smem_u32(smem + L.bhi), blo_l = smem_u32(smem + L.blo);
-        const int nb8 = fpc / 8;
-        for (int job = threadIdx.x; job < kN * nb8; job += blockDim.x) {
-            const int r = job % kN, b = job / kN;
-            if (fo0 + 8 * b >= fb) continue;
-            __nv_bfloat16 hi[8], lo[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int fl = 8 * b + u;
-                float v = 0.f;
-                if (fl < nown && r < R) {
-                    const float *fr = sRows + (long long)fl * (N - 1) * R + r;
-                    v = 1.f;
-                    for (int kk = 0; kk < N - 1; ++kk) v = v * fr[kk * R];
-                }
-                const float zs = fl < nown ? v * ss[fo0 + fl] : 0.f;
-                sZo[fl * kN + r] = v;
-                sZso[fl * kN + r] = zs;
-                hi[u] = __float2bfloat16_rn(zs);
-                lo[u] = __float2bfloat16_rn(zs - __bfloat162float(hi[u]));
-            }
-            const int f = fo0 + 8 * b;
-            const uint32_t boff = (uint32_t)(((((r >> 3) * (fb >> 3) + (f >> 3)) << 6) + ((r & 7) << 3)) * 2);
-            const uint4 vh = *reinterpret_cast<uint4 *>(hi), vl = *reinterpret_cast<uint4 *>(lo);
-            for (int d = 0; d < cs; ++d) {
-                st_cluster_v4(map_shared(bhi_l + boff, d), vh);
-                st_cluster_v4(map_shared(blo_l + boff, d), vl);
+    cluster_wait();     // every CTA's mbarriers exist: sends may start
+    if (warp == 0 && cs > 1) {
+        // own slice -> every other CTA: 8 row groups x (hi, lo), columns, weights
+        const uint32_t bhi_l = smem_u32(sBhi), blo_l = smem_u32(sBlo);
+        const uint32_t j_l = smem_u32(jcol), s_l = smem_u32(ss);
+        const int per = 18;
+        for (int task = lane; task < (cs - 1) * per; task += 32) {
+            const int di = task / per, q = task % per;
+            const int d = di + (di >= rank ? 1 : 0);
+            const uint32_t mb = map_shared(bar_x, d);
+            if (nb8 == 0) continue;
+            if (q < 16) {
+                const int rg = q & 7;
+                const uint32_t base = (q < 8) ? bhi_l : blo_l;
+                const uint32_t off = (uint32_t)((rg * (fb >> 3) + (fo0 >> 3)) * 128);
+                bulk_s2s(map_shared(base + off, d), base + off, (uint32_t)nb8 * 128u, mb);
+            } else if (q == 16) {
+                bulk_s2s(map_shared(j_l + fo0 * 8, d), j_l + fo0 * 8, (uint32_t)myslots * 8u, mb);
+            } else {
+                bulk_s2s(map_shared(s_l + fo0 * 4, d), s_l + fo0 * 4, (uint32_t)myslots * 4u, mb);
             }
         }
     }
-    __syncthreads();
-    // H over the own fibers: 16 entries (one row, 16 columns) per thread
+    // H over the own fibers (all 64 x 64): one row, 16 columns per thread
     {
         const int r = threadIdx.x >> 2, c0 = 16 * (threadIdx.x & 3);
         float acc[16] = {};
         for (int fl = 0; fl < nown; ++fl) {
-            const float a = sZso[fl * kN + r];
+            const float av = sZso[fl * kN + r];
             const float4 *b4 = reinterpret_cast<const float4 *>(sZo + fl * kN + c0);
 #pragma unroll
             for (int q4 = 0; q4 < 4; ++q4) {
                 const float4 y = b4[q4];
-                acc[4 * q4 + 0] += a * y.x;
-                acc[4 * q4 + 1] += a * y.y;
-                acc[4 * q4 + 2] += a * y.z;
-                acc[4 * q4 + 3] += a * y.w;
+                acc[4 * q4 + 0] += av * y.x;
+                acc[4 * q4 + 1] += av * y.y;
+                acc[4 * q4 + 2] += av * y.z;
+                acc[4 * q4 + 3] += av * y.w;
             }
         }
 #pragma unroll
@@ -241,12 +268,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
             *reinterpret_cast<float4 *>(sHp + r * kN + c0 + 4 * q4) =
                 make_float4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]);
     }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 1 && cs > 1) {
+        // rows [d hr, d hr + hrows(d)) of the partial -> owner d, slot `rank`
+        const uint32_t hp_l = smem_u32(sHp), hr_l = smem_u32(sHr);
+        for (int di = lane; di < cs - 1; di += 32) {
+            const int d = di + (di >= rank ? 1 : 0);
+            const int nr = hrows(d, hr);
+            if (nr == 0) continue;
+            bulk_s2s(map_shared(hr_l + (uint32_t)(rank * hr * kN * 4), d), hp_l + (uint32_t)(d * hr * kN * 4),
+                     (uint32_t)nr * kN * 4u, map_shared(bar_hp, d));
+        }
+    }
     trace_stamp(P.trace, 3, tr0);
-    cluster_arrive();
-    cluster_wait();
-    trace_stamp(P.trace, 4, tr0);
 
-    // 4. gather of this tile's rows of every fiber
+    // 3. fibers' columns and operands of the whole group have arrived: gather
+    bool ok = mbar_wait_bounded(bar_x, 0);
+    trace_stamp(P.trace, 4, tr0);
     const uint32_t aBase = smem_u32(sA);
     if (has_rows) {
         const __nv_bfloat16 *rep = reinterpret_cast<const __nv_bfloat16 *>(P.rep[n]);
@@ -254,24 +293,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
         for (int c = threadIdx.x; c < fb * (kM / 8); c += blockDim.x) {
             const int f = c / (kM / 8), ig = c % (kM / 8);
             const long long i0 = r0 + ig * 8;
-            const bool ok = f < nf && i0 < ld;
-            const __nv_bfloat16 *src = ok ? rep + jcol[f] * ld + i0 : rep;
+            const bool inb = f < nf && i0 < ld;
+            const __nv_bfloat16 *src = inb ? rep + jcol[f] * ld + i0 : rep;
             cp_async16(aBase + (uint32_t)((((f >> 3) * (kM / 8) + ig) << 7) + ((f & 7) << 4)), src,
-                       ok ? 16u : 0u);
+                       inb ? 16u : 0u);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-    // rows r = rank, rank + cs, ... of H_g: the cluster's partials summed in
-    // ascending rank, written into every CTA
+    // owned rows of H_g: partials of every CTA summed in ascending rank
+    ok = mbar_wait_bounded(bar_hp, 0) && ok;
     {
-        const uint32_t h_l = smem_u32(sH), hp_l = smem_u32(sHp);
-        const int nrows = (kN - rank + cs - 1) / cs;
-        for (int e = threadIdx.x; e < nrows * kN; e += blockDim.x) {
-            const int r = rank + cs * (e / kN), c = e % kN;
-            const uint32_t off = (uint32_t)((r * kN + c) * 4);
+        const int nr = hrows(rank, hr);
+        for (int e = threadIdx.x; e < nr * kN; e += blockDim.x) {
+            const int rl = e / kN, c = e % kN, r = rank * hr + rl;
             float acc = 0.f;
-            for (int d = 0; d < cs; ++d) acc += ld_cluster_f32(map_shared(hp_l + off, d));
-            for (int d = 0; d < cs; ++d) st_cluster_u32(map_shared(h_l + off, d), __float_as_uint(acc));
+            for (int q = 0; q < cs; ++q)
+                acc += (q == rank) ? sHp[r * kN + c] : sHr[(q * hr + rl) * kN + c];
+            sH[r * kN + c] = acc;
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (warp == 0 && cs > 1 && nr > 0) {
+            const uint32_t h_l = smem_u32(sH) + (uint32_t)(rank * hr * kN * 4);
+            for (int di = lane; di < cs - 1; di += 32) {
+                const int d = di + (di >= rank ? 1 : 0);
+                bulk_s2s(map_shared(h_l, d), h_l, (uint32_t)nr * kN * 4u, map_shared(bar_h, d));
+            }
         }
     }
     trace_stamp(P.trace, 5, tr0);
@@ -281,9 +328,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         tmem = *tmem_holder;
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && ok) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t bhi = smem_u32(smem + L.bhi), blo = smem_u32(smem + L.blo);
+            const uint32_t bhi = smem_u32(sBhi), blo = smem_u32(sBlo);
             const uint32_t idesc = idesc_bf16(kM, kN);
             const uint32_t sboB = (uint32_t)(fb >> 3) * 128u;
             for (int ks = 0; ks < fb / kK; ++ks) {
@@ -303,20 +350,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             bar)
+                             bar_mma)
                          : "memory");
         }
     }
-    cluster_arrive();   // H_g slices written
+    ok = mbar_wait_bounded(bar_h, 0) && ok;
+    ok = mbar_wait_bounded(bar_a, 0) && ok;
+    if (!ok && threadIdx.x == 0) atomicOr(P.status, kStTimeout);
+    cluster_arrive();   // every CTA has received everything: no copy reads our buffers any more
     cluster_wait();
     trace_stamp(P.trace, 6, tr0);
 
-    // 5. G_g = A H_g - M_g for this tile's rows
+    // 4. G_g = A H_g - M_g for this tile's rows
     if (has_rows) {
-        bool done = mbar_wait_bounded(bar, 0);
-        if (!done) {
+        bool done = ok && mbar_wait_bounded(bar_mma, 0);
+        if (!done && ok) {
             if (threadIdx.x == 0) atomicOr(P.status, kStTimeout);
-            done = mbar_wait_bounded(bar, 0);
+            done = mbar_wait_bounded(bar_mma, 0);
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         trace_stamp(P.trace, 7, tr0);
@@ -330,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
 #pragma unroll
             for (int c = 0; c < 32; ++c) v[c] = -v[c];
             for (int s2 = 0; s2 < R; ++s2) {
-                const float a = sArow[il * lda + s2];
+                const float a = sArow[il * R + s2];
                 const float4 *hrow = reinterpret_cast<const float4 *>(sH + s2 * kN + 32 * hh);
 #pragma unroll
                 for (int c4 = 0; c4 < 8; ++c4) {
@@ -342,15 +392,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
                 }
             }
             trace_stamp(P.trace, 15, tr0);
+            // the staging region holds only dead operands (the MMAs are complete)
 #pragma unroll
             for (int c = 0; c < 32; ++c)
                 if (32 * hh + c < R) tile[il * R + 32 * hh + c] = v[c];
         }
         __syncthreads();
         if (done) {
-            const int rows = (In - r0) < kM ? (int)(In - r0) : kM;
             float *out = P.part + ((long long)gf * In + r0) * R;
-            for (int e = threadIdx.x; e < rows * R; e += blockDim.x) out[e] = tile[e];
+            for (int e = threadIdx.x; e < nrows * R; e += blockDim.x) out[e] = tile[e];
         }
         trace_stamp(P.trace, 8, tr0);
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -363,6 +413,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
 }
 
 size_t tcc_smem_bytes(const Problem<float> &P) { return TccSmem(P.N, P.R, P.fb, P.cs).total; }
+
+long long tcc_stage_cap(const Problem<float> &P) { return (long long)P.fb * kM * 2 / 8; }
 
 // The kernel's dynamic shared-memory limit, raised (never lowered) as needed;
 // the one place that sets it, so the recorded value is the attribute's.
