@@ -136,6 +136,15 @@ cpd_status cpd_sgd_iters(cpd_ctx *ctx, int64_t iters, void *stream);
 cpd_status cpd_fit(cpd_ctx *ctx, double *fit, double *tol, void *stream);
 
 /*
+ * cpd_fit_start / cpd_fit_poll -- the same Tol as cpd_fit without blocking:
+ * cpd_fit_start enqueues the full-tensor pass on `stream` and returns;
+ * cpd_fit_poll returns CPD_EAGAIN until that pass has finished, then the
+ * fit and Tol of the most recent cpd_fit_start (either pointer may be NULL).
+ */
+cpd_status cpd_fit_start(cpd_ctx *ctx, void *stream);
+cpd_status cpd_fit_poll(cpd_ctx *ctx, double *fit, double *tol);
+
+/*
  * cpd_get_factors / cpd_set_factors -- copy the N factor matrices out of / into
  * the context (the output of Alg. 4 / Alg. 5). `A` is an array of N pointers,
  * each I_k x R row-major in the factor type, at `loc`. Setting factors
@@ -237,6 +246,63 @@ cpd_status cpd_describe(cpd_ctx *ctx, char *buf, size_t len);
  */
 cpd_status cpd_tol_noalloc(int32_t N, const int64_t *dims, int32_t R, int32_t x_dtype,
                            const void *X, const void *const *A, double *tol_out, void *stream);
+
+/*
+ * Serving: many decompositions on one GPU. A server admits submitted
+ * requests (each one a full run of Alg. 4 / Alg. 5 until a fit target or an
+ * iteration cap, Sec. 5.2 stopping rule) first-fit against a device-memory
+ * budget and a limit on concurrent requests, runs every admitted request on
+ * a stream of its own so that their kernels overlap, checks each request's
+ * fit every fit_every iterations without blocking the others, and frees a
+ * request's memory as soon as it stops. A request's results do not depend on
+ * what else runs: every kernel's arithmetic is independent of the mix.
+ */
+typedef struct cpd_server cpd_server;
+
+typedef struct {
+    size_t hbm_budget;    /* device bytes admitted requests may hold
+                             (0: 85% of the free memory at creation)          */
+    int32_t max_active;   /* requests running at once (0: 32)                  */
+    int32_t fit_every;    /* iterations between fit checks (0: 250)            */
+    int32_t reserved[2];  /* must be 0                                         */
+} cpd_server_config;
+
+typedef struct {
+    int32_t status;       /* CPD_OK, or the failure that stopped the request   */
+    int32_t done;         /* 1 once the request has stopped                    */
+    int32_t reached;      /* 1 when the fit target was reached                 */
+    int32_t pad;
+    int64_t iters;        /* iterations run                                    */
+    double fit, tol;      /* at the last check (Sec. 5.2)                      */
+    double t_submit, t_start, t_done; /* seconds on the server's clock         */
+} cpd_result;
+
+/* cpd_server_create -- a server on the current CUDA device (one worker thread). */
+cpd_status cpd_server_create(const cpd_server_config *cfg, cpd_server **out);
+
+/*
+ * cpd_submit -- queue one decomposition: cfg, X and A0 as for cpd_init (X and
+ * A0 must stay valid until cpd_poll reports the request done); it stops when
+ * fit >= stop_fit or after max_iters iterations. Returns its ticket.
+ * CPD_ENOMEM if the request can never fit the budget.
+ */
+cpd_status cpd_submit(cpd_server *srv, const cpd_config *cfg, const void *X, int x_loc,
+                      const void *const *A0, int a0_loc, double stop_fit, int64_t max_iters,
+                      uint64_t *ticket);
+
+/*
+ * cpd_poll -- the state of a request; CPD_EAGAIN while it runs or waits (out
+ * is still filled). Once done, returns its status and, if A_out is not NULL,
+ * copies its N factor matrices into the host buffers A_out[k] (I_k x R).
+ */
+cpd_status cpd_poll(cpd_server *srv, uint64_t ticket, cpd_result *out, void *const *A_out);
+
+/* cpd_server_wait -- block until every submitted request is done, or
+ * CPD_EAGAIN after timeout_s seconds (timeout_s <= 0: no limit). */
+cpd_status cpd_server_wait(cpd_server *srv, double timeout_s);
+
+/* cpd_server_destroy -- stop the worker (running requests are abandoned) and free. */
+cpd_status cpd_server_destroy(cpd_server *srv);
 
 /* cpd_destroy -- free the context and everything it owns. NULL is a no-op. */
 cpd_status cpd_destroy(cpd_ctx *ctx);

@@ -44,6 +44,18 @@ class cpd_config(ctypes.Structure):
     ]
 
 
+class cpd_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int32),
+                ("fit_every", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+class cpd_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("done", ctypes.c_int32), ("reached", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("iters", ctypes.c_int64), ("fit", ctypes.c_double),
+                ("tol", ctypes.c_double), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise RuntimeError(f"{_LIB_PATH} is missing: build it with "
@@ -54,6 +66,8 @@ def _load():
         "cpd_init": [ctypes.POINTER(cpd_config), P, I32, P, I32, P, ctypes.POINTER(P)],
         "cpd_sgd_iters": [P, I64, P],
         "cpd_fit": [P, P, P, P],
+        "cpd_fit_start": [P, P],
+        "cpd_fit_poll": [P, P, P],
         "cpd_get_factors": [P, P, I32, P],
         "cpd_set_factors": [P, P, I32, P],
         "cpd_get_adagrad": [P, P, I32, P],
@@ -69,6 +83,12 @@ def _load():
         "cpd_describe": [P, ctypes.c_char_p, ctypes.c_size_t],
         "cpd_destroy": [P],
         "cpd_tol_noalloc": [I32, P, I32, I32, P, P, P, P],
+        "cpd_server_create": [ctypes.POINTER(cpd_server_config), ctypes.POINTER(P)],
+        "cpd_submit": [P, ctypes.POINTER(cpd_config), P, I32, P, I32, ctypes.c_double, I64,
+                       ctypes.POINTER(ctypes.c_uint64)],
+        "cpd_poll": [P, ctypes.c_uint64, ctypes.POINTER(cpd_result), P],
+        "cpd_server_wait": [P, ctypes.c_double],
+        "cpd_server_destroy": [P],
         "cpd_trace": [P, I32],
         "cpd_trace_read": [P, P, P],
     }
@@ -137,6 +157,20 @@ def cpd_sgd_iters(ctx, iters: int, stream=None) -> None:
 def cpd_fit(ctx, stream=None) -> tuple[float, float]:
     fit, tol = ctypes.c_double(), ctypes.c_double()
     _check(_lib.cpd_fit(ctx, ctypes.byref(fit), ctypes.byref(tol), _stream(stream)))
+    return fit.value, tol.value
+
+
+def cpd_fit_start(ctx, stream=None) -> None:
+    _check(_lib.cpd_fit_start(ctx, _stream(stream)))
+
+
+def cpd_fit_poll(ctx):
+    """(fit, tol), or None while the pass started by cpd_fit_start is running."""
+    fit, tol = ctypes.c_double(), ctypes.c_double()
+    st = _lib.cpd_fit_poll(ctx, ctypes.byref(fit), ctypes.byref(tol))
+    if st == EAGAIN:
+        return None
+    _check(st)
     return fit.value, tol.value
 
 
@@ -223,6 +257,46 @@ def cpd_tol_noalloc(dims, R: int, x_dtype: str, X: torch.Tensor, A: list, tol_ou
     d = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
     _check(_lib.cpd_tol_noalloc(len(dims), d, int(R), XDT[x_dtype], X.data_ptr(), _ptrs(A),
                                 tol_out.data_ptr(), _stream(stream)))
+
+
+def cpd_server_create(hbm_budget: int = 0, max_active: int = 0, fit_every: int = 0):
+    cfg = cpd_server_config()
+    cfg.hbm_budget, cfg.max_active, cfg.fit_every = int(hbm_budget), int(max_active), int(fit_every)
+    srv = ctypes.c_void_p()
+    _check(_lib.cpd_server_create(ctypes.byref(cfg), ctypes.byref(srv)))
+    return srv
+
+
+def cpd_submit(srv, cfg: cpd_config, X: torch.Tensor, A0: list, stop_fit: float, max_iters: int) -> int:
+    ticket = ctypes.c_uint64()
+    _check(_lib.cpd_submit(srv, ctypes.byref(cfg), X.data_ptr(), _loc(X), _ptrs(A0), _loc(A0[0]),
+                           float(stop_fit), int(max_iters), ctypes.byref(ticket)))
+    return ticket.value
+
+
+def cpd_poll(srv, ticket: int, A_out: list | None = None):
+    """(status, result dict); status EAGAIN while the request runs or waits."""
+    res = cpd_result()
+    st = _lib.cpd_poll(srv, ticket, ctypes.byref(res), _ptrs(A_out) if A_out else None)
+    if st not in (OK, EAGAIN):
+        msg = _lib.cpd_last_error().decode()
+    else:
+        msg = ""
+    d = {f: getattr(res, f) for f, _ in cpd_result._fields_ if f != "pad"}
+    d["message"] = msg
+    return st, d
+
+
+def cpd_server_wait(srv, timeout_s: float = 0.0) -> bool:
+    st = _lib.cpd_server_wait(srv, float(timeout_s))
+    if st == EAGAIN:
+        return False
+    _check(st)
+    return True
+
+
+def cpd_server_destroy(srv) -> None:
+    _check(_lib.cpd_server_destroy(srv))
 
 
 # ---- convenience wrapper -------------------------------------------------

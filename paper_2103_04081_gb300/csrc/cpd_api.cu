@@ -66,6 +66,10 @@ struct cpd_ctx {
     bool has_sample = false;
     unsigned long long *trace_buf = nullptr;
     int max_clusters = 0;
+    cudaStream_t home = nullptr;     // stream of cpd_init: allocations and frees
+    cudaEvent_t fit_event = nullptr; // cpd_fit_start / cpd_fit_poll
+    double *fit_host = nullptr;      // pinned copy of the residual sum
+    bool fit_started = false;
 
     template <class F>
     cudaError_t with_problem(F &&f)
@@ -81,9 +85,12 @@ Problem<float> &problem<float>(cpd_ctx *c) { return c->Pf; }
 template <>
 Problem<double> &problem<double>(cpd_ctx *c) { return c->Pd; }
 
+// Device buffers come from the stream-ordered allocator on the context's
+// stream, so creating and destroying contexts never synchronises the device
+// (other decompositions keep running).
 static cudaError_t dmalloc(cpd_ctx *c, void **p, size_t bytes)
 {
-    cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+    cudaError_t e = cudaMallocAsync(p, bytes < 16 ? 16 : bytes, c->home);
     if (e == cudaSuccess) c->allocs.push_back(*p);
     return e;
 }
@@ -92,8 +99,11 @@ static void free_all(cpd_ctx *c)
 {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-    for (void *p : c->allocs) cudaFree(p);
+    if (c->fit_event) cudaEventDestroy(c->fit_event);
+    if (c->fit_host) cudaFreeHost(c->fit_host);
+    for (void *p : c->allocs) cudaFreeAsync(p, c->home);
     c->allocs.clear();
+    cudaStreamSynchronize(c->home);
 }
 
 static int64_t round8(int64_t v) { return (v + 7) / 8 * 8; }
@@ -239,7 +249,7 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     const void *Xd = X;
     void *staging = nullptr;
     if (x_loc == CPD_HOST) {
-        CK(cudaMalloc(&staging, total * xb));
+        CK(cudaMallocAsync(&staging, total * xb, s));
         CK(cudaMemcpyAsync(staging, X, total * xb, cudaMemcpyHostToDevice, s));
         Xd = staging;
     }
@@ -248,21 +258,18 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
         void *rep;
         cudaError_t e = dmalloc(c, &rep, bytes);
         if (e != cudaSuccess) {
-            if (staging) cudaFree(staging);
+            if (staging) cudaFreeAsync(staging, s);
             return cuda_fail(e, "replica allocation");
         }
         if (P.ld[k] != g.dims[k]) CK(cudaMemsetAsync(rep, 0, bytes, s));
         e = launch_build_replica(Xd, rep, (int)xb, g.N, g.dims, k, P.ld[k], s);
         if (e != cudaSuccess) {
-            if (staging) cudaFree(staging);
+            if (staging) cudaFreeAsync(staging, s);
             return cuda_fail(e, "replica build");
         }
         P.rep[k] = rep;
     }
-    if (staging) {
-        CK(cudaStreamSynchronize(s));
-        CK(cudaFree(staging));
-    }
+    if (staging) CK(cudaFreeAsync(staging, s));
 
     // Factors, AdaGrad state, distributions.
     for (int k = 0; k < g.N; ++k) {
@@ -348,6 +355,7 @@ extern "C" cpd_status cpd_init(const cpd_config *cfg, const void *X, int x_loc, 
     c->fbytes = cfg->x_dtype == CPD_F64 ? 8 : 4;
     c->xbytes = cfg->x_dtype == CPD_F64 ? 8 : (cfg->x_dtype == CPD_F32 ? 4 : 2);
     cudaStream_t s = (cudaStream_t)stream;
+    c->home = s;
     st = c->fbytes == 8 ? init_typed<double>(c, X, x_loc, A0, a0_loc, s)
                         : init_typed<float>(c, X, x_loc, A0, a0_loc, s);
     if (st != CPD_OK) {
@@ -470,6 +478,44 @@ extern "C" cpd_status cpd_fit(cpd_ctx *c, double *fit, double *tol, void *stream
     if (tol) *tol = tl;
     if (fit) *fit = 1.0 - std::sqrt(tl);
     return st;
+}
+
+extern "C" cpd_status cpd_fit_start(cpd_ctx *c, void *stream)
+{
+    if (!c) return fail(CPD_EINVAL, "NULL context");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->fit_event) {
+        CK(cudaEventCreateWithFlags(&c->fit_event, cudaEventDisableTiming));
+        CK(cudaMallocHost((void **)&c->fit_host, 2 * sizeof(double)));   // residual, status word
+    }
+    cudaError_t e = c->with_problem([&](auto &P) {
+        return launch_fit(P, c->fit_partials, fit_blocks(), c->fit_out, s, 0);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "fit launch");
+    CK(cudaMemcpyAsync(c->fit_host, c->fit_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->fit_host + 1, c->fbytes == 8 ? c->Pd.status : c->Pf.status, sizeof(int),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->fit_event, s));
+    c->fit_started = true;
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_fit_poll(cpd_ctx *c, double *fit, double *tol)
+{
+    if (!c) return fail(CPD_EINVAL, "NULL context");
+    if (!c->fit_started) return fail(CPD_EINVAL, "no fit was started");
+    const cudaError_t q = cudaEventQuery(c->fit_event);
+    if (q == cudaErrorNotReady) return CPD_EAGAIN;
+    if (q != cudaSuccess) return cuda_fail(q, "fit event");
+    const double tl = *c->fit_host / c->xnorm2;
+    if (tol) *tol = tl;
+    if (fit) *fit = 1.0 - std::sqrt(tl);
+    int st = 0;
+    std::memcpy(&st, c->fit_host + 1, sizeof(int));
+    if (st & kStNonFinite) return fail(CPD_ENONFINITE, "a gradient or factor entry became NaN/Inf");
+    if (st & kStDegenerate) return fail(CPD_EDEGENERATE, "a sampling distribution lost its mass");
+    if (st & kStTimeout) return fail(CPD_ETIMEOUT, "a bounded device wait gave up");
+    return CPD_OK;
 }
 
 static cudaMemcpyKind kind_out(int loc) { return loc == CPD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
@@ -669,6 +715,18 @@ extern "C" cpd_status cpd_destroy(cpd_ctx *c)
     delete c;
     return CPD_OK;
 }
+
+// Destroy without a device-wide synchronisation: the caller guarantees that
+// all of the context's work was enqueued on its home stream (the server).
+namespace cpd {
+void destroy_on_home_stream(cpd_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->home);
+    free_all(c);
+    delete c;
+}
+}  // namespace cpd
 
 extern "C" const char *cpd_last_error(void) { return g_err.c_str(); }
 

@@ -1,0 +1,335 @@
+// Serving loop of libcpd (declared in include/cpd.h): many decompositions on
+// one GPU, admitted by a device-memory budget, each on its own stream.
+//
+// One worker thread owns all device work. Per round it
+//   1. admits queued requests first-fit while the memory budget and the
+//      concurrency limit allow (cpd_init on a fresh non-blocking stream);
+//   2. for every running request whose previous fit check has finished,
+//      enqueues the iterations up to its next check and an asynchronous fit
+//      (cpd_sgd_iters + cpd_fit_start), so each stream always has a bounded
+//      amount of queued work and the streams overlap on the GPU;
+//   3. retires requests whose check met the target or whose cap is reached:
+//      factors copied out, context freed with stream-ordered frees.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "cpd.h"
+#include "cpd_internal.h"
+
+namespace cpd {
+void set_error(const std::string &msg);
+void destroy_on_home_stream(cpd_ctx *c);
+}  // namespace cpd
+
+using namespace cpd;
+
+namespace {
+
+double now_s()
+{
+    using clk = std::chrono::steady_clock;
+    static const clk::time_point t0 = clk::now();
+    return std::chrono::duration<double>(clk::now() - t0).count();
+}
+
+// Device bytes a request may hold: the mode-major replicas, factors and their
+// state, the gradient partials (upper bound) and a fixed allowance.
+size_t estimate_bytes(const cpd_config &g)
+{
+    const size_t xb = g.x_dtype == CPD_F64 ? 8 : (g.x_dtype == CPD_F32 ? 4 : 2);
+    const size_t fb = g.x_dtype == CPD_F64 ? 8 : 4;
+    double total = 1.0;
+    int64_t imax = 0, isum = 0;
+    for (int k = 0; k < g.N; ++k) {
+        total *= (double)g.dims[k];
+        imax = std::max<int64_t>(imax, g.dims[k]);
+        isum += g.dims[k];
+    }
+    double bytes = 0.0;
+    for (int k = 0; k < g.N; ++k) {
+        const double ld = (double)((g.dims[k] + 7) / 8 * 8);
+        bytes += total / (double)g.dims[k] * ld * (double)xb;
+    }
+    bytes += (double)isum * g.R * (fb + 8) + (double)isum * 16;
+    bytes += 608.0 * g.R * (double)imax * fb;   // partial slabs, bound of the tile chooser
+    bytes += 8.0 * 1024 * 1024;
+    return (size_t)bytes;
+}
+
+struct Request {
+    uint64_t ticket = 0;
+    cpd_config cfg{};
+    const void *X = nullptr;
+    int x_loc = 0;
+    std::vector<const void *> A0;
+    int a0_loc = 0;
+    double stop_fit = 1.0;
+    int64_t max_iters = 0;
+    size_t bytes = 0;
+    cpd_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    bool fit_pending = false;
+    int64_t next_check = 0;
+    cpd_result res{};
+    std::vector<std::vector<unsigned char>> factors;
+};
+
+}  // namespace
+
+struct cpd_server {
+    cpd_server_config cfg{};
+    int device = 0;
+    size_t budget = 0, used = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::vector<std::shared_ptr<Request>> active;
+    std::map<uint64_t, std::shared_ptr<Request>> all;
+    size_t unfinished = 0;
+    std::thread worker;
+};
+
+static void finish(cpd_server *srv, const std::shared_ptr<Request> &r, cpd_status st)
+{
+    r->res.status = st;
+    if (r->ctx) {
+        if (st == CPD_OK) {
+            std::vector<void *> ptrs;
+            const size_t fbytes = r->cfg.x_dtype == CPD_F64 ? 8 : 4;
+            r->factors.resize(r->cfg.N);
+            for (int k = 0; k < r->cfg.N; ++k) {
+                r->factors[k].resize((size_t)r->cfg.dims[k] * r->cfg.R * fbytes);
+                ptrs.push_back(r->factors[k].data());
+            }
+            const cpd_status g = cpd_get_factors(r->ctx, ptrs.data(), CPD_HOST, r->stream);
+            if (g != CPD_OK) r->res.status = g;
+        }
+        destroy_on_home_stream(r->ctx);
+        r->ctx = nullptr;
+    }
+    if (r->stream) {
+        cudaStreamDestroy(r->stream);
+        r->stream = nullptr;
+    }
+    std::lock_guard<std::mutex> lock(srv->mu);
+    r->res.t_done = now_s();
+    r->res.done = 1;
+    srv->used -= r->bytes;
+    --srv->unfinished;
+    srv->cv_done.notify_all();
+}
+
+static void worker_loop(cpd_server *srv)
+{
+    cudaSetDevice(srv->device);
+    const int fit_every = srv->cfg.fit_every > 0 ? srv->cfg.fit_every : 250;
+    const size_t max_active = srv->cfg.max_active > 0 ? (size_t)srv->cfg.max_active : 32;
+    for (;;) {
+        // 1. admission (first fit in submission order)
+        std::vector<std::shared_ptr<Request>> admit;
+        {
+            std::unique_lock<std::mutex> lock(srv->mu);
+            if (srv->stop) break;
+            if (srv->queue.empty() && srv->active.empty())
+                srv->cv_work.wait(lock, [&] { return srv->stop || !srv->queue.empty(); });
+            if (srv->stop) break;
+            for (auto it = srv->queue.begin(); it != srv->queue.end() && srv->active.size() + admit.size() < max_active;) {
+                if (srv->used + (*it)->bytes <= srv->budget) {
+                    srv->used += (*it)->bytes;
+                    admit.push_back(*it);
+                    it = srv->queue.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        for (auto &r : admit) {
+            r->res.t_start = now_s();
+            cpd_status st = CPD_OK;
+            if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess) st = CPD_ECUDA;
+            if (st == CPD_OK) st = cpd_init(&r->cfg, r->X, r->x_loc, r->A0.data(), r->a0_loc, r->stream, &r->ctx);
+            if (st != CPD_OK) {
+                finish(srv, r, st);
+                continue;
+            }
+            r->next_check = std::min<int64_t>(fit_every, r->max_iters);
+            srv->active.push_back(r);
+        }
+        // 2./3. progress every running request
+        bool progressed = !admit.empty();
+        for (size_t q = 0; q < srv->active.size();) {
+            auto r = srv->active[q];
+            bool retire = false;
+            cpd_status st = CPD_OK;
+            if (r->fit_pending) {
+                double fit = 0.0, tol = 0.0;
+                st = cpd_fit_poll(r->ctx, &fit, &tol);
+                if (st == CPD_EAGAIN) {
+                    ++q;
+                    continue;
+                }
+                progressed = true;
+                r->fit_pending = false;
+                r->res.fit = fit;
+                r->res.tol = tol;
+                if (st != CPD_OK) {
+                    retire = true;
+                } else if (fit >= r->stop_fit) {
+                    r->res.reached = 1;
+                    retire = true;
+                } else if (r->res.iters >= r->max_iters) {
+                    retire = true;
+                } else {
+                    r->next_check = std::min<int64_t>(r->res.iters + fit_every, r->max_iters);
+                }
+            }
+            if (!retire && !r->fit_pending) {
+                const int64_t chunk = r->next_check - r->res.iters;
+                st = cpd_sgd_iters(r->ctx, chunk, r->stream);
+                if (st == CPD_OK) st = cpd_fit_start(r->ctx, r->stream);
+                if (st != CPD_OK) {
+                    retire = true;
+                } else {
+                    r->res.iters += chunk;
+                    r->fit_pending = true;
+                    progressed = true;
+                }
+            }
+            if (retire) {
+                finish(srv, r, st);
+                srv->active.erase(srv->active.begin() + q);
+            } else {
+                ++q;
+            }
+        }
+        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    for (auto &r : srv->active) finish(srv, r, CPD_EBUSY);
+    srv->active.clear();
+}
+
+extern "C" cpd_status cpd_server_create(const cpd_server_config *cfg, cpd_server **out)
+{
+    if (!out) {
+        set_error("NULL output");
+        return CPD_EINVAL;
+    }
+    auto *srv = new cpd_server();
+    if (cfg) srv->cfg = *cfg;
+    if (srv->cfg.reserved[0] || srv->cfg.reserved[1]) {
+        delete srv;
+        set_error("reserved fields must be 0");
+        return CPD_EINVAL;
+    }
+    if (cudaGetDevice(&srv->device) != cudaSuccess) {
+        delete srv;
+        set_error("no CUDA device");
+        return CPD_ECUDA;
+    }
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete srv;
+        set_error("cudaMemGetInfo failed");
+        return CPD_ECUDA;
+    }
+    srv->budget = srv->cfg.hbm_budget ? srv->cfg.hbm_budget : (size_t)(0.85 * (double)free_b);
+    srv->worker = std::thread(worker_loop, srv);
+    *out = srv;
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_submit(cpd_server *srv, const cpd_config *cfg, const void *X, int x_loc,
+                                 const void *const *A0, int a0_loc, double stop_fit, int64_t max_iters,
+                                 uint64_t *ticket)
+{
+    if (!srv || !cfg || !X || !A0 || !ticket || max_iters < 1 || cfg->N < 1 || cfg->N > CPD_MAX_MODES) {
+        set_error("invalid argument");
+        return CPD_EINVAL;
+    }
+    auto r = std::make_shared<Request>();
+    r->cfg = *cfg;
+    r->X = X;
+    r->x_loc = x_loc;
+    r->A0.assign(A0, A0 + cfg->N);
+    r->a0_loc = a0_loc;
+    r->stop_fit = stop_fit;
+    r->max_iters = max_iters;
+    r->bytes = estimate_bytes(*cfg);
+    if (r->bytes > srv->budget) {
+        set_error("request needs " + std::to_string(r->bytes) + " bytes, over the server budget");
+        return CPD_ENOMEM;
+    }
+    std::lock_guard<std::mutex> lock(srv->mu);
+    r->ticket = srv->next_ticket++;
+    r->res.t_submit = now_s();
+    srv->queue.push_back(r);
+    srv->all[r->ticket] = r;
+    ++srv->unfinished;
+    srv->cv_work.notify_all();
+    *ticket = r->ticket;
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_poll(cpd_server *srv, uint64_t ticket, cpd_result *out, void *const *A_out)
+{
+    if (!srv) {
+        set_error("NULL server");
+        return CPD_EINVAL;
+    }
+    std::shared_ptr<Request> r;
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        auto it = srv->all.find(ticket);
+        if (it == srv->all.end()) {
+            set_error("unknown ticket");
+            return CPD_EINVAL;
+        }
+        r = it->second;
+        if (out) *out = r->res;
+        if (!r->res.done) return CPD_EAGAIN;
+    }
+    if (A_out && r->res.status == CPD_OK)
+        for (int k = 0; k < r->cfg.N; ++k)
+            if (A_out[k]) std::copy(r->factors[k].begin(), r->factors[k].end(), static_cast<unsigned char *>(A_out[k]));
+    return (cpd_status)r->res.status;
+}
+
+extern "C" cpd_status cpd_server_wait(cpd_server *srv, double timeout_s)
+{
+    if (!srv) {
+        set_error("NULL server");
+        return CPD_EINVAL;
+    }
+    std::unique_lock<std::mutex> lock(srv->mu);
+    auto pred = [&] { return srv->unfinished == 0; };
+    if (timeout_s <= 0) {
+        srv->cv_done.wait(lock, pred);
+        return CPD_OK;
+    }
+    return srv->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), pred) ? CPD_OK : CPD_EAGAIN;
+}
+
+extern "C" cpd_status cpd_server_destroy(cpd_server *srv)
+{
+    if (!srv) return CPD_OK;
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        srv->stop = true;
+        srv->cv_work.notify_all();
+    }
+    if (srv->worker.joinable()) srv->worker.join();
+    delete srv;
+    return CPD_OK;
+}
