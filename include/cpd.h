@@ -93,7 +93,12 @@ typedef struct {
                            gradient, one CTA per tile, 3 = tensor-core gradient,
                            one thread-block cluster per fiber group (2 and 3:
                            BF16 tensors, R <= 64; 3: every I_k <= 1024)         */
-    int32_t reserved;   /* must be 0                                                */
+    int32_t max_ctas;   /* 0: size the gradient grid for the whole GPU; > 0: use at
+                           most about this many CTAs per gradient launch (fewer
+                           fiber groups, more fibers per CTA), so that several
+                           decompositions share the GPU. Part of the arithmetic:
+                           the grouping of the batch fixes the summation order of
+                           the gradient partials.                                */
 } cpd_config;
 
 typedef struct cpd_ctx cpd_ctx;
@@ -256,6 +261,11 @@ cpd_status cpd_tol_noalloc(int32_t N, const int64_t *dims, int32_t R, int32_t x_
  * fit every fit_every iterations without blocking the others, and frees a
  * request's memory as soon as it stops. A request's results do not depend on
  * what else runs: every kernel's arithmetic is independent of the mix.
+ * Throughput: give requests a CTA cap (cpd_config.max_ctas, e.g. 8) so that
+ * many fit on the GPU at once, and let the process use 32 hardware work
+ * queues (environment CUDA_DEVICE_MAX_CONNECTIONS=32, set before the CUDA
+ * context is created); with the default 8, streams share queues and
+ * serialise.
  */
 typedef struct cpd_server cpd_server;
 
@@ -263,7 +273,8 @@ typedef struct {
     size_t hbm_budget;    /* device bytes admitted requests may hold
                              (0: 85% of the free memory at creation)          */
     int32_t max_active;   /* requests running at once (0: 32)                  */
-    int32_t fit_every;    /* iterations between fit checks (0: 250)            */
+    int32_t fit_every;    /* iterations between fit checks (0: 250; a multiple
+                             of 32 keeps every iteration in replayed graphs)  */
     int32_t reserved[2];  /* must be 0                                         */
 } cpd_server_config;
 

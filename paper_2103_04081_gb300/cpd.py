@@ -40,7 +40,7 @@ class cpd_config(ctypes.Structure):
         ("dims", ctypes.c_int64 * MAX_MODES),
         ("alpha", ctypes.c_double), ("eta", ctypes.c_double), ("b", ctypes.c_double),
         ("beta", ctypes.c_double), ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64),
-        ("engine", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("engine", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
     ]
 
 
@@ -114,7 +114,8 @@ def _check(st: int) -> None:
 
 
 def make_config(dims, R, B, sampling="euclidean", step="adagrad", x_dtype="bf16", alpha=0.1,
-                eta=0.1, b=1e-12, beta=1.0, gamma=1.0, seed=0, engine="auto") -> cpd_config:
+                eta=0.1, b=1e-12, beta=1.0, gamma=1.0, seed=0, engine="auto",
+                max_ctas=0) -> cpd_config:
     c = cpd_config()
     c.N, c.R, c.B = len(dims), int(R), int(B)
     c.sampling, c.step, c.x_dtype = SAMPLE[sampling], STEP[step], XDT[x_dtype]
@@ -123,7 +124,7 @@ def make_config(dims, R, B, sampling="euclidean", step="adagrad", x_dtype="bf16"
     c.alpha, c.eta, c.b, c.beta, c.gamma = alpha, eta, b, beta, gamma
     c.seed = int(seed) & (2**64 - 1)
     c.engine = ENGINE[engine]
-    c.reserved = 0
+    c.max_ctas = int(max_ctas)
     return c
 
 

@@ -117,7 +117,7 @@ static cpd_status validate(const cpd_config *cfg)
     if (cfg->sampling < 0 || cfg->sampling > 2) return fail(CPD_EINVAL, "unknown sampling");
     if (cfg->step < 0 || cfg->step > 2) return fail(CPD_EINVAL, "unknown step");
     if (cfg->x_dtype < 0 || cfg->x_dtype > 2) return fail(CPD_EINVAL, "unknown x_dtype");
-    if (cfg->reserved != 0) return fail(CPD_EINVAL, "reserved must be 0");
+    if (cfg->max_ctas < 0) return fail(CPD_EINVAL, "max_ctas must be >= 0");
     if (cfg->engine < 0 || cfg->engine > 3) return fail(CPD_EINVAL, "unknown engine");
     double total = 1.0;
     for (int k = 0; k < cfg->N; ++k) {
@@ -166,6 +166,7 @@ static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
                 return;
             }
             int64_t pf = std::max<int64_t>(1, std::min<int64_t>(maxc, (g.B + 15) / 16));
+            if (g.max_ctas > 0) pf = std::max<int64_t>(1, std::min<int64_t>(pf, g.max_ctas / P.cs));
             int64_t fb = (g.B + pf - 1) / pf;
             fb = (fb + 15) / 16 * 16;
             P.fb = (int)std::min<int64_t>(256, std::max<int64_t>(16, fb));
@@ -177,7 +178,8 @@ static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
         // one wave of CTAs.
         P.rb = 128;
         const int64_t pr_max = (imax + P.rb - 1) / P.rb;
-        const int64_t pf = std::max<int64_t>(1, (sm_count + pr_max - 1) / pr_max);
+        const int64_t ctas = g.max_ctas > 0 ? std::min<int64_t>(g.max_ctas, sm_count) : sm_count;
+        const int64_t pf = std::max<int64_t>(1, (ctas + pr_max - 1) / pr_max);
         int64_t fb = (g.B + pf - 1) / pf;
         fb = (fb + 15) / 16 * 16;
         P.fb = (int)std::min<int64_t>(128, std::max<int64_t>(16, fb));
@@ -186,7 +188,7 @@ static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
     } else {
         P.rb = (int)std::min<int64_t>(64, round8(imax));
         int64_t pr_max = (imax + P.rb - 1) / P.rb;
-        int64_t target = 2LL * sm_count;
+        int64_t target = g.max_ctas > 0 ? std::min<int64_t>(g.max_ctas, 2LL * sm_count) : 2LL * sm_count;
         int64_t pf = std::max<int64_t>(1, (target + pr_max - 1) / pr_max);
         pf = std::min<int64_t>(pf, std::max<int64_t>(1, (g.B + 15) / 16));
         P.fb = (int)((g.B + pf - 1) / pf);
@@ -343,12 +345,13 @@ extern "C" cpd_status cpd_init(const cpd_config *cfg, const void *X, int x_loc, 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    cudaDeviceProp prop;
-    e = cudaGetDeviceProperties(&prop, dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
-    if (prop.major != 10 || prop.minor != 3)
+    int cc_major = 0, cc_minor = 0;
+    e = cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    if (cc_major != 10 || cc_minor != 3)
         return fail(CPD_ECUDA, "libcpd is built for sm_103a (GB300); this device is sm_" +
-                                   std::to_string(prop.major) + std::to_string(prop.minor));
+                                   std::to_string(cc_major) + std::to_string(cc_minor));
     cpd_ctx *c = new cpd_ctx();
     c->cfg = *cfg;
     c->device = dev;

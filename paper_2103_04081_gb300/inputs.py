@@ -160,3 +160,29 @@ WORKLOADS = {
                                   noise=1e-2, congruence=0.0, lognormal_rows=True,
                                   iters=2000, data_seed=0, init_seed=1, sample_seed=0),
 }
+
+
+def serve_requests(n: int, rate: float = 200.0, seed: int = 0) -> list[dict]:
+    """The request stream of the serving workload.
+
+    Arrivals form a Poisson process of ``rate`` per second (exponential gaps
+    from ``seed``; the first request arrives at 0). Request i draws, from its
+    own generator (seed, i): 3 or 4 modes with equal odds, mode sizes uniform
+    in [50, 400] for 3-way tensors and in [50, 90] for 4-way ones (so that no
+    4-way tensor is larger than the largest 3-way one, 90^4 ~ 400^3), and a
+    rank uniform in {5, ..., 32}. Its data, initial factors and sampling use
+    seed i.
+    """
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, n)
+    arrive = np.concatenate([[0.0], np.cumsum(gaps[1:])])
+    out = []
+    for i in range(n):
+        r = np.random.default_rng([seed, i])
+        N = 3 if r.random() < 0.5 else 4
+        hi = 400 if N == 3 else 90
+        dims = tuple(int(v) for v in r.integers(50, hi + 1, N))
+        R = int(r.integers(5, 33))
+        out.append(dict(i=i, arrival=float(arrive[i]), N=N, dims=dims, R=R, noise=1e-2,
+                        data_seed=i, init_seed=i, sample_seed=i))
+    return out

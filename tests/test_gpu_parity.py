@@ -83,6 +83,37 @@ def test_teacher_forced_tensor_engine(cpd, orc, dims, R, B, sampling, engine):
     dec.close()
 
 
+@pytest.mark.parametrize("engine,xdt,dims,R,B", [
+    ("simt", "f32", (150, 70, 33), 10, 512),
+    ("simt", "bf16", (60, 70, 55, 40), 8, 300),
+    ("tensor", "bf16", (300, 200, 100), 24, 512),
+    ("cluster", "bf16", (400, 250, 130), 32, 512),
+])
+@pytest.mark.parametrize("max_ctas", [1, 8])
+def test_max_ctas_bounds_grid_and_keeps_parity(cpd, orc, engine, xdt, dims, R, B, max_ctas):
+    """A CTA cap regroups the batch into fewer, larger fiber groups; the result
+    still follows the oracle (same draws bit-exact, gradient within tolerance)."""
+    A, X, A0 = make_problem(dims, R, x_dtype=xdt, lognormal_rows=True)
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype=xdt,
+                            sampling="euclidean", step="adagrad", seed=5, engine=engine,
+                            max_ctas=max_ctas)
+    d = dec.describe()
+    assert d["engine"] == engine
+    assert d["fiber_groups"] == -(-B // d["fibers_per_cta"])
+    full = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype=xdt,
+                             sampling="euclidean", step="adagrad", seed=5, engine=engine)
+    d0 = full.describe()
+    full.close()
+    # fewer, larger fiber groups than the whole-GPU tiling (the per-CTA fiber
+    # limits of each engine still apply)
+    assert d["fiber_groups"] < d0["fiber_groups"] and d["grad_grid"] < d0["grad_grid"]
+    ocfg = _ocfg(orc, dims, R, B, xdt, "euclidean", "adagrad", 5)
+    tol = TOL["bf16_tensor"] if engine != "simt" else TOL[xdt]
+    worst = teacher_forced(dec, orc, ocfg, oracle_xbuf(X), 6, tol["G"], tol["A"])
+    print(engine, dims, max_ctas, worst, d)
+    dec.close()
+
+
 def test_free_run_fp64_matches_oracle_c1(cpd, orc):
     """The 60^3 FP64 workload, 300 fixed-step iterations free-running on both sides."""
     w = IN.WORKLOADS["c1_60cube_f64"]

@@ -20,18 +20,20 @@ def cpd():
 
 
 REQS = [
-    ((60, 70, 80), 5, "bf16", 96, "euclidean"),
-    ((90, 50, 40, 30), 8, "bf16", 128, "euclidean"),
-    ((120, 110, 100), 16, "bf16", 256, "euclidean"),
-    ((64, 64, 64), 10, "f32", 64, "leverage"),
-    ((200, 150, 30), 32, "bf16", 512, "euclidean"),
-    ((45, 55, 65, 35), 12, "f32", 100, "uniform"),
+    # dims, R, x_dtype, B, sampling, max_ctas
+    ((60, 70, 80), 5, "bf16", 96, "euclidean", 0),
+    ((90, 50, 40, 30), 8, "bf16", 128, "euclidean", 4),
+    ((120, 110, 100), 16, "bf16", 256, "euclidean", 0),
+    ((64, 64, 64), 10, "f32", 64, "leverage", 0),
+    ((200, 150, 30), 32, "bf16", 512, "euclidean", 8),
+    ((45, 55, 65, 35), 12, "f32", 100, "uniform", 2),
 ]
 
 
-def _make(C, dims, R, xdt, B, sampling, seed):
+def _make(C, dims, R, xdt, B, sampling, seed, max_ctas=0):
     _, X, A0 = make_problem(dims, R, noise=1e-2, x_dtype=xdt, seed=seed, init_seed=seed + 100)
-    cfg = C.make_config(dims, R, B, sampling=sampling, step="adagrad", x_dtype=xdt, seed=seed)
+    cfg = C.make_config(dims, R, B, sampling=sampling, step="adagrad", x_dtype=xdt, seed=seed,
+                        max_ctas=max_ctas)
     fdt = torch.float32 if xdt != "f64" else torch.float64
     return cfg, X.cuda(), [a.to(fdt).cuda() for a in A0]
 
@@ -39,19 +41,19 @@ def _make(C, dims, R, xdt, B, sampling, seed):
 def test_concurrent_requests_match_solo_runs(cpd):
     srv = cpd.cpd_server_create(max_active=8, fit_every=100)
     inputs, tickets = [], []
-    for q, (dims, R, xdt, B, sampling) in enumerate(REQS):
-        cfg, X, A0 = _make(cpd, dims, R, xdt, B, sampling, 10 + q)
-        inputs.append((dims, R, xdt, B, sampling, cfg, X, A0))
+    for q, (dims, R, xdt, B, sampling, mc) in enumerate(REQS):
+        cfg, X, A0 = _make(cpd, dims, R, xdt, B, sampling, 10 + q, mc)
+        inputs.append((dims, R, xdt, B, sampling, mc, cfg, X, A0))
         tickets.append(cpd.cpd_submit(srv, cfg, X, A0, stop_fit=2.0, max_iters=300 + 50 * q))
     assert cpd.cpd_server_wait(srv, 300.0)
-    for (dims, R, xdt, B, sampling, cfg, X, A0), tk in zip(inputs, tickets):
+    for (dims, R, xdt, B, sampling, mc, cfg, X, A0), tk in zip(inputs, tickets):
         fdt = torch.float32 if xdt != "f64" else torch.float64
         out = [torch.empty(d, R, dtype=fdt) for d in dims]
         st, res = cpd.cpd_poll(srv, tk, out)
         assert st == cpd.OK and res["done"] == 1, res
         assert res["reached"] == 0 and res["iters"] > 0
         solo = cpd.Decomposition(X, A0, dims=dims, R=R, B=B, x_dtype=xdt, sampling=sampling,
-                                 step="adagrad", seed=cfg.seed)
+                                 step="adagrad", seed=cfg.seed, max_ctas=mc)
         solo.sgd_iters(res["iters"])
         for a, b in zip(out, solo.factors()):
             assert torch.equal(a, b)
