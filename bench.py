@@ -118,15 +118,35 @@ class Clocks:
 
 
 def dist_setup():
+    """One process per GPU (replicas: every rank runs its own decomposition).
+    NCCL when GPUs are present, gloo otherwise (host-side tests)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
         return dist, rank, world, local
     return None, 0, 1, 0
+
+
+def max_over_ranks(dist, value: float, device: str) -> float:
+    """The slowest rank's time: the job is done when every replica is."""
+    if not dist:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, max_ms: float) -> float:
+    """Iterations per second over all replicas (weak scaling: each rank runs
+    `steps` iterations of its own decomposition)."""
+    return world * steps / (max_ms / 1e3)
 
 
 def make_inputs(w: dict, rank: int, device: str):
@@ -366,10 +386,8 @@ def main() -> None:
         ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
     C.cpd_sync(dec.ctx, stream)
+    ms = max_over_ranks(dist, ms, dev)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     torch.cuda.synchronize()
     clocks = clk.summary()
@@ -384,7 +402,7 @@ def main() -> None:
     fit, tol = dec.fit(stream)
     dec.close()
 
-    iters_per_s = world * args.steps / (ms / 1e3)
+    iters_per_s = whole_job_rate(world, args.steps, ms)
     esize = {"bf16": 2, "f32": 4, "f64": 8}[w["x_dtype"]]
     In = sum(w["dims"]) / len(w["dims"])           # modes drawn uniformly
     gather_bytes = w["B"] * In * esize               # algorithmic HBM bytes per gradient launch
