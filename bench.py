@@ -216,7 +216,8 @@ def run_reference(args, w: dict) -> None:
 # the fewest iterations in a sweep of B in {256, 512, 1024, 2048} x eta in
 # {0.1, 0.2} over the first 24 requests, each run alone.
 SERVE = dict(requests=512, rate=200.0, stop_fit=0.98, max_iters=20000, fit_every=256,
-             sampling="euclidean", step="adagrad", eta=0.2, b=1e-12, B=512, max_ctas=8)
+             sampling="euclidean", step="adagrad", eta=0.2, b=1e-12, B=512, max_ctas=8,
+             engine_r16="tensor", grouping=True)
 
 
 def serve_batch(q: dict) -> int:
@@ -261,14 +262,15 @@ def serve_bench(dev: str, n_req: int, n_plain: int, max_active: int) -> dict:
     from paper_2103_04081_gb300 import inputs as IN
     reqs = IN.serve_requests(n_req, rate=SERVE["rate"], seed=0)
     data = serve_inputs(reqs, dev, "bf16")
-    srv = C.cpd_server_create(max_active=max_active, fit_every=SERVE["fit_every"])
+    srv = C.cpd_server_create(max_active=max_active, fit_every=SERVE["fit_every"], grouping=SERVE["grouping"])
     tickets = []
     t0 = time.perf_counter()
     for q, (X, A0) in zip(reqs, data):
         delay = t0 + q["arrival"] - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        tickets.append(C.cpd_submit(srv, serve_cfg(q, "bf16", max_ctas=SERVE["max_ctas"]), X, A0,
+        engine = SERVE["engine_r16"] if q["R"] >= 16 else "simt"
+        tickets.append(C.cpd_submit(srv, serve_cfg(q, "bf16", engine, SERVE["max_ctas"]), X, A0,
                                     SERVE["stop_fit"], SERVE["max_iters"]))
     finished = C.cpd_server_wait(srv, 600.0)
     t1 = time.perf_counter()
@@ -323,7 +325,9 @@ def serve_bench(dev: str, n_req: int, n_plain: int, max_active: int) -> dict:
             "rule": {"stop_fit": SERVE["stop_fit"], "max_iters": SERVE["max_iters"],
                      "fit_every": SERVE["fit_every"], "sampling": SERVE["sampling"],
                      "step": SERVE["step"], "eta": SERVE["eta"], "B": SERVE["B"],
-                     "max_ctas": SERVE["max_ctas"], "max_active": max_active}}
+                     "max_ctas": SERVE["max_ctas"], "max_active": max_active,
+                     "engine": "per-CTA tensor cores for R >= 16 (%s), CUDA cores below" % SERVE["engine_r16"],
+                     "grouped_launches": SERVE["grouping"]}}
 
 
 def config_block(w: dict, engine: str) -> dict:

@@ -275,7 +275,13 @@ typedef struct {
     int32_t max_active;   /* requests running at once (0: 32)                  */
     int32_t fit_every;    /* iterations between fit checks (0: 250; a multiple
                              of 32 keeps every iteration in replayed graphs)  */
-    int32_t reserved[2];  /* must be 0                                         */
+    int32_t no_grouping;  /* 0: requests that use the CUDA-core or per-CTA
+                             tensor-core engine (and no leverage sampling) run
+                             in grouped launches (cpd_group_*), one group per
+                             lane of same-dtype, same-engine requests; others
+                             run on streams of their own. 1: every request on
+                             a stream of its own.                             */
+    int32_t reserved;     /* must be 0                                         */
 } cpd_server_config;
 
 typedef struct {
@@ -317,6 +323,35 @@ cpd_status cpd_server_destroy(cpd_server *srv);
 
 /* cpd_destroy -- free the context and everything it owns. NULL is a no-op. */
 cpd_status cpd_destroy(cpd_ctx *ctx);
+
+/*
+ * Groups -- advance many decompositions with one gradient launch and one
+ * update launch per iteration (batched execution of Alg. 4 / Alg. 5 over
+ * independent problems; the paper runs one problem at a time). Every member
+ * runs exactly the CTAs, tiling and arithmetic it runs alone, so after
+ * cpd_group_iters(g, T) each member's state is bitwise what cpd_sgd_iters(T)
+ * on that context alone gives.
+ *
+ * cpd_group_create -- group G contexts (array of G distinct handles, borrowed:
+ *  they must outlive the group). Members must share the tensor dtype and the
+ *  gradient engine, which must be the CUDA-core (1) or the per-CTA
+ *  tensor-core (2) engine, and none may sample by leverage. The members'
+ *  launch state is captured at creation (later cpd_trace / cpd_profile
+ *  changes do not reach the group). Allocates a few hundred bytes per member
+ *  on `stream` and synchronises it.
+ *  Errors: CPD_EINVAL (NULL, duplicate or incompatible members), CPD_ENOMEM,
+ *  CPD_ECUDA.
+ * cpd_group_iters -- run `iters` iterations of every member, enqueued on
+ *  `stream` (graph-replayed chunks). Asynchronous. The caller orders this
+ *  stream after any work still pending on the members' own streams, and
+ *  the members' later calls (cpd_fit, cpd_get_factors, ...) after it.
+ * cpd_group_destroy -- synchronise the last stream the group used and free
+ *  it; the member contexts are untouched.
+ */
+typedef struct cpd_group cpd_group;
+cpd_status cpd_group_create(cpd_ctx *const *ctxs, int32_t G, void *stream, cpd_group **out);
+cpd_status cpd_group_iters(cpd_group *group, int64_t iters, void *stream);
+cpd_status cpd_group_destroy(cpd_group *group);
 
 /* Thread-local description of the last failure on this thread. */
 const char *cpd_last_error(void);

@@ -46,7 +46,8 @@ class cpd_config(ctypes.Structure):
 
 class cpd_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int32),
-                ("fit_every", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("fit_every", ctypes.c_int32), ("no_grouping", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class cpd_result(ctypes.Structure):
@@ -89,6 +90,9 @@ def _load():
         "cpd_poll": [P, ctypes.c_uint64, ctypes.POINTER(cpd_result), P],
         "cpd_server_wait": [P, ctypes.c_double],
         "cpd_server_destroy": [P],
+        "cpd_group_create": [P, I32, P, ctypes.POINTER(P)],
+        "cpd_group_iters": [P, I64, P],
+        "cpd_group_destroy": [P],
         "cpd_trace": [P, I32],
         "cpd_trace_read": [P, P, P],
     }
@@ -260,9 +264,11 @@ def cpd_tol_noalloc(dims, R: int, x_dtype: str, X: torch.Tensor, A: list, tol_ou
                                 tol_out.data_ptr(), _stream(stream)))
 
 
-def cpd_server_create(hbm_budget: int = 0, max_active: int = 0, fit_every: int = 0):
+def cpd_server_create(hbm_budget: int = 0, max_active: int = 0, fit_every: int = 0,
+                      grouping: bool = True):
     cfg = cpd_server_config()
     cfg.hbm_budget, cfg.max_active, cfg.fit_every = int(hbm_budget), int(max_active), int(fit_every)
+    cfg.no_grouping = 0 if grouping else 1
     srv = ctypes.c_void_p()
     _check(_lib.cpd_server_create(ctypes.byref(cfg), ctypes.byref(srv)))
     return srv
@@ -298,6 +304,22 @@ def cpd_server_wait(srv, timeout_s: float = 0.0) -> bool:
 
 def cpd_server_destroy(srv) -> None:
     _check(_lib.cpd_server_destroy(srv))
+
+
+def cpd_group_create(ctxs: list, stream=None):
+    """One grouped launch per iteration for all of `ctxs` (borrowed handles)."""
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    grp = ctypes.c_void_p()
+    _check(_lib.cpd_group_create(arr, len(ctxs), _stream(stream), ctypes.byref(grp)))
+    return grp
+
+
+def cpd_group_iters(grp, iters: int, stream=None) -> None:
+    _check(_lib.cpd_group_iters(grp, int(iters), _stream(stream)))
+
+
+def cpd_group_destroy(grp) -> None:
+    _check(_lib.cpd_group_destroy(grp))
 
 
 # ---- convenience wrapper -------------------------------------------------

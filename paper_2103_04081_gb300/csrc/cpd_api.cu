@@ -735,4 +735,168 @@ extern "C" const char *cpd_last_error(void) { return g_err.c_str(); }
 
 namespace cpd {
 void set_error(const std::string &msg) { g_err = msg; }
+int ctx_engine(const cpd_ctx *c) { return c->engine; }
 }  // namespace cpd
+
+// ---------------------------------------------------------------------------
+// Groups: many contexts advanced by one gradient launch and one update
+// launch per iteration (each member runs exactly its own CTAs and arithmetic).
+// ---------------------------------------------------------------------------
+struct cpd_group {
+    int fbytes = 4, x_dtype = 0, engine = 0, G = 0;
+    std::vector<cpd_ctx *> members;
+    void *dP = nullptr;      // device array of the members' Problem structs
+    int *dcta = nullptr;     // cta_grad[G + 1] followed by cta_upd[G + 1]
+    GroupLaunch<float> Lf{};
+    GroupLaunch<double> Ld{};
+    cudaStream_t home = nullptr;          // stream of creation: allocation and free
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    cudaStream_t last = nullptr;          // last stream work was enqueued on
+};
+
+template <class T>
+static GroupLaunch<T> &group_launch(cpd_group *g);
+template <>
+GroupLaunch<float> &group_launch<float>(cpd_group *g) { return g->Lf; }
+template <>
+GroupLaunch<double> &group_launch<double>(cpd_group *g) { return g->Ld; }
+
+template <class T>
+static cpd_status group_build(cpd_group *g, cudaStream_t s)
+{
+    std::vector<Problem<T>> hp(g->G);
+    std::vector<int> cta(2 * (g->G + 1), 0);
+    size_t smem = 0;
+    for (int q = 0; q < g->G; ++q) {
+        cpd_ctx *c = g->members[q];
+        hp[q] = problem<T>(c);
+        cta[q + 1] = cta[q] + c->grid_grad;
+        cta[g->G + 1 + q + 1] = cta[g->G + 1 + q] + c->grid_upd;
+        smem = std::max(smem, c->smem_grad);
+    }
+    CK(cudaMallocAsync(&g->dP, sizeof(Problem<T>) * g->G, s));
+    CK(cudaMallocAsync((void **)&g->dcta, sizeof(int) * cta.size(), s));
+    CK(cudaMemcpyAsync(g->dP, hp.data(), sizeof(Problem<T>) * g->G, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(g->dcta, cta.data(), sizeof(int) * cta.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));   // the host staging vectors go out of scope
+    GroupLaunch<T> L{};
+    L.P = (const Problem<T> *)g->dP;
+    L.cta_grad = g->dcta;
+    L.cta_upd = g->dcta + g->G + 1;
+    L.G = g->G;
+    L.grid_grad = cta[g->G];
+    L.grid_upd = cta[2 * g->G + 1];
+    L.engine = g->engine;
+    L.x_dtype = g->x_dtype;
+    L.smem_grad = smem;
+    group_launch<T>(g) = L;
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_group_create(cpd_ctx *const *ctxs, int32_t G, void *stream, cpd_group **out)
+{
+    if (!ctxs || !out || G < 1) return fail(CPD_EINVAL, "NULL argument or empty group");
+    cpd_ctx *c0 = ctxs[0];
+    if (!c0) return fail(CPD_EINVAL, "NULL context");
+    for (int q = 0; q < G; ++q) {
+        cpd_ctx *c = ctxs[q];
+        if (!c) return fail(CPD_EINVAL, "NULL context");
+        for (int r = 0; r < q; ++r)
+            if (ctxs[r] == c) return fail(CPD_EINVAL, "a context appears twice in the group");
+        if (c->engine != kEngineSimt && c->engine != kEngineTensor)
+            return fail(CPD_EINVAL, "grouped launches take CUDA-core or per-CTA tensor-core contexts only");
+        if (c->cfg.sampling == CPD_SAMPLE_LEVERAGE)
+            return fail(CPD_EINVAL, "grouped launches do not take leverage sampling");
+        if (c->fbytes != c0->fbytes || c->cfg.x_dtype != c0->cfg.x_dtype || c->engine != c0->engine ||
+            c->device != c0->device)
+            return fail(CPD_EINVAL, "group members differ in tensor dtype, engine or device");
+    }
+    auto *g = new cpd_group();
+    g->fbytes = c0->fbytes;
+    g->x_dtype = c0->cfg.x_dtype;
+    g->engine = c0->engine;
+    g->G = G;
+    g->members.assign(ctxs, ctxs + G);
+    g->home = (cudaStream_t)stream;
+    g->last = g->home;
+    const cpd_status st = g->fbytes == 8 ? group_build<double>(g, g->home) : group_build<float>(g, g->home);
+    if (st != CPD_OK) {
+        cudaStreamSynchronize(g->home);
+        if (g->dP) cudaFreeAsync(g->dP, g->home);
+        if (g->dcta) cudaFreeAsync(g->dcta, g->home);
+        cudaStreamSynchronize(g->home);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return CPD_OK;
+}
+
+template <class T>
+static cudaError_t group_run(cpd_group *g, int64_t iters, cudaStream_t s)
+{
+    const GroupLaunch<T> &L = group_launch<T>(g);
+    const int64_t chunks = iters / kGraphChunk, rem = iters % kGraphChunk;
+    if (chunks) {
+        if (!g->graph || g->graph_stream != s) {
+            if (g->graph) {
+                cudaGraphExecDestroy(g->graph);
+                g->graph = nullptr;
+            }
+            cudaStream_t cap;
+            cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return e;
+            cudaGraph_t gr;
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (int q = 0; q < kGraphChunk && e == cudaSuccess; ++q) e = launch_group_iteration(L, cap);
+                cudaError_t e2 = cudaStreamEndCapture(cap, &gr);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) {
+                e = cudaGraphInstantiate(&g->graph, gr, 0);
+                cudaGraphDestroy(gr);
+            }
+            cudaStreamDestroy(cap);
+            if (e != cudaSuccess) return e;
+            g->graph_stream = s;
+        }
+        for (int64_t q = 0; q < chunks; ++q) {
+            cudaError_t e = cudaGraphLaunch(g->graph, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    for (int64_t q = 0; q < rem; ++q) {
+        cudaError_t e = launch_group_iteration(L, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+extern "C" cpd_status cpd_group_iters(cpd_group *g, int64_t iters, void *stream)
+{
+    if (!g || iters < 0) return fail(CPD_EINVAL, "bad group or iteration count");
+    if (iters == 0) return CPD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaError_t e = g->fbytes == 8 ? group_run<double>(g, iters, s) : group_run<float>(g, iters, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cpd_group_iters launch");
+    g->last = s;
+    for (cpd_ctx *c : g->members) {
+        c->t_host += iters;
+        c->has_sample = true;
+    }
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_group_destroy(cpd_group *g)
+{
+    if (!g) return CPD_OK;
+    cudaStreamSynchronize(g->last);
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    cudaFreeAsync(g->dP, g->home);
+    cudaFreeAsync(g->dcta, g->home);
+    cudaStreamSynchronize(g->home);
+    delete g;
+    return CPD_OK;
+}

@@ -355,11 +355,12 @@ __device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 x)
 // When CDF rebuilds are deferred (P.defer_cdf), the mode updated last
 // (*P.dirty) has only fresh row weights: its CDF is rebuilt here, in the
 // staging buffer, from those weights (scratch: `dsm`, 2 * blockDim.x uint64),
-// and the CTA with blockIdx.x == 0 stores it for later iterations.
+// and the one CTA of the launch that passes `writer` stores it for later
+// iterations.
 template <class T>
 __device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int f0, int nf, int *sidx,
-                                    unsigned long long *stage, long long cap,
-                                    unsigned long long *dsm = nullptr)
+                                    unsigned long long *stage, long long cap, unsigned long long *dsm,
+                                    bool writer)
 {
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
     long long need = 0, off[kMaxModes];
@@ -385,7 +386,7 @@ __device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int
             unsigned long long *c = stage + off[dirty];
             if (!block_distribution_inplace(c, P.dims[dirty], dsm)) {
                 if (threadIdx.x == 0) atomicOr(P.status, kStDegenerate);
-            } else if (blockIdx.x == 0) {
+            } else if (writer) {
                 for (long long i = threadIdx.x; i < P.dims[dirty]; i += blockDim.x) P.cdf[dirty][i] = c[i];
             }
         }
@@ -510,18 +511,49 @@ template <>
 __device__ __forceinline__ double load_x<double, double>(const double *p) { return *p; }
 
 
-// Arrival counter: true in exactly one CTA, the last one to finish.
-__device__ __forceinline__ bool last_block(unsigned *counter)
+// Arrival counter: true in exactly one of the nblk CTAs that work on one
+// problem, the last one to finish.
+__device__ __forceinline__ bool last_block(unsigned *counter, unsigned nblk)
 {
     __shared__ int s_last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(counter, 1u);
-        s_last = (prev == gridDim.x - 1);
+        s_last = (prev == nblk - 1);
     }
     __syncthreads();
     if (s_last) __threadfence();
     return s_last != 0;
+}
+
+__device__ __forceinline__ bool last_block(unsigned *counter) { return last_block(counter, gridDim.x); }
+
+// Grouped launches: one launch runs the CTAs of G problems back to back;
+// problem g owns CTAs [cta0[g], cta0[g+1]). Returns g (binary search by one
+// thread) and copies problem g into `sp` for the whole CTA.
+template <class T>
+__device__ __forceinline__ int group_member(const Problem<T> *__restrict__ Ps, const int *__restrict__ cta0,
+                                            int G, Problem<T> &sp)
+{
+    __shared__ int s_g;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = G - 1;
+        const int b = (int)blockIdx.x;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(cta0 + mid) <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        s_g = lo;
+    }
+    __syncthreads();
+    const int g = s_g;
+    static_assert(sizeof(Problem<T>) % 8 == 0, "Problem is copied in 8-byte words");
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(Ps + g);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sp);
+    for (int q = threadIdx.x; q < (int)(sizeof(Problem<T>) / 8); q += blockDim.x) dst[q] = __ldg(src + q);
+    __syncthreads();
+    return g;
 }
 }  // namespace cpd

@@ -68,12 +68,28 @@ struct Problem {
     unsigned long long *trace;  // phase timestamps (cpd_trace), or null
 };
 
+// A group of problems advanced by grouped launches: problem g owns CTAs
+// [cta_grad[g], cta_grad[g+1]) of the gradient launch and [cta_upd[g],
+// cta_upd[g+1]) of the update launch, and runs exactly the CTAs it would run
+// alone. All members share T, the tensor dtype and the engine (CUDA-core or
+// per-CTA tensor-core), and none samples by leverage.
+template <class T>
+struct GroupLaunch {
+    const Problem<T> *P;      // device array of G problems
+    const int *cta_grad;      // device, G + 1 prefix sums
+    const int *cta_upd;       // device, G + 1 prefix sums
+    int G, grid_grad, grid_upd, engine, x_dtype;
+    size_t smem_grad;         // largest member's dynamic shared memory
+};
+
 // Launchers (cpd_kernels.cu). Every launcher enqueues on `stream` and
 // returns the launch error, if any.
 template <class T>
 cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd,
                              size_t smem_grad, cudaStream_t stream, int engine,
                              cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t ev2);
+template <class T>
+cudaError_t launch_group_iteration(const GroupLaunch<T> &L, cudaStream_t stream);
 template <class T>
 cudaError_t launch_refresh_mode(const Problem<T> &P, int k, cudaStream_t stream);
 template <class T>
@@ -92,6 +108,7 @@ int fit_blocks();
 // one cluster per fiber group).
 bool tc_supported(int R, int rb);
 cudaError_t launch_grad_tc(const Problem<float> &P, int grid, cudaStream_t stream);
+cudaError_t launch_grad_tc_group(const GroupLaunch<float> &L, cudaStream_t stream);
 size_t tc_smem_bytes(const Problem<float> &P);
 cudaError_t launch_grad_tcc(const Problem<float> &P, int grid, cudaStream_t stream);
 size_t tcc_smem_bytes(const Problem<float> &P);

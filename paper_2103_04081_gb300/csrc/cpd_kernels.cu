@@ -73,15 +73,16 @@ __device__ __forceinline__ void gather_rows(const XT *__restrict__ rep, long lon
 // so that sum over fiber groups gives (A Zs^T D Zs - Xs D Zs) / (B J_n),
 // Eq. gradient1, without the cancellation of forming the two products apart.
 // ---------------------------------------------------------------------------
+// `bid` is the CTA's index among the CTAs of this problem.
 template <class T, class XT>
-__global__ void __launch_bounds__(kThreads) k_grad_simt(const Problem<T> P)
+__device__ __forceinline__ void grad_simt_body(const Problem<T> &P, int bid)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const long long t = *P.t_dev;
     const int N = P.N, R = P.R, rb = P.rb, fb = P.fb;
     const int n = mode_draw(P.seed, t, N);
     const int pr = P.tile[n].pr;
-    const int gr = blockIdx.x % pr, gf = blockIdx.x / pr;
+    const int gr = bid % pr, gf = bid / pr;
     if (gf >= P.pf) return;
     const long long In = P.dims[n];
     const int r0 = gr * rb;
@@ -99,7 +100,8 @@ __global__ void __launch_bounds__(kThreads) k_grad_simt(const Problem<T> P)
 
     // 1. draws of Alg. 3
     unsigned long long *stage = reinterpret_cast<unsigned long long *>(smem + L.stage);
-    draw_indices(P, t, n, f0, nf, sidx, stage, 2048, reinterpret_cast<unsigned long long *>(smem + L.dsm));
+    draw_indices(P, t, n, f0, nf, sidx, stage, 2048, reinterpret_cast<unsigned long long *>(smem + L.dsm),
+                 bid == 0);
     const bool staged = cdfs_staged(P, n, 2048);
     // rows of A^(n) for the residual, transposed (conflict-free reads)
     const T *An = P.A[n];
@@ -162,6 +164,22 @@ __global__ void __launch_bounds__(kThreads) k_grad_simt(const Problem<T> P)
     }
 }
 
+template <class T, class XT>
+__global__ void __launch_bounds__(kThreads) k_grad_simt(const Problem<T> P)
+{
+    grad_simt_body<T, XT>(P, (int)blockIdx.x);
+}
+
+// One launch for a group of problems (see group_member).
+template <class T, class XT>
+__global__ void __launch_bounds__(kThreads) k_grad_simt_group(const Problem<T> *__restrict__ Ps,
+                                                              const int *__restrict__ cta0, int G)
+{
+    __shared__ __align__(16) Problem<T> sp;
+    const int g = group_member(Ps, cta0, G, sp);
+    grad_simt_body<T, XT>(sp, (int)blockIdx.x - __ldg(cta0 + g));
+}
+
 // ---------------------------------------------------------------------------
 // Reduction + step. CTA b owns rows [b*rpc, b*rpc+rpc) of A^(n).
 // ---------------------------------------------------------------------------
@@ -177,13 +195,14 @@ __device__ void finish_distribution(const Problem<T> &P, int k, unsigned long lo
         atomicOr(P.status, kStDegenerate);
 }
 
+// `bid` / `nblk`: the CTA's index among, and the number of, this problem's CTAs.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P)
+__device__ __forceinline__ void update_body(const Problem<T> &P, int bid, unsigned nblk)
 {
     __shared__ T s_new[kThreads];
     __shared__ unsigned long long s_dist[2 * kThreads];
     __shared__ __align__(16) double s_w[kWStage];       // last CTA: staged row weights
-    const bool tr0 = blockIdx.x == 0;
+    const bool tr0 = bid == 0;
     trace_stamp(P.trace, 16, tr0);
     const long long t = *P.t_dev;
     const int N = P.N, R = P.R;
@@ -191,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P)
     const long long In = P.dims[n];
     const int rpc = kThreads / R > 0 ? kThreads / R : 1;
     const int li = threadIdx.x / R, r = threadIdx.x % R;
-    const long long i = (long long)blockIdx.x * rpc + li;
+    const long long i = (long long)bid * rpc + li;
     const bool act = li < rpc && i < In;
     T *An = P.A[n];
     if (act) {
@@ -235,7 +254,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P)
         // one warp per updated row: the canonical tree-ordered squared norm
         const int warp = threadIdx.x >> 5;
         for (int lr = warp; lr < rpc; lr += kThreads / 32) {
-            const long long row = (long long)blockIdx.x * rpc + lr;
+            const long long row = (long long)bid * rpc + lr;
             if (row < In) {
                 const double wv = warp_row_weight(s_new + lr * R, R);
                 if ((threadIdx.x & 31) == 0) P.w[n][row] = wv;
@@ -243,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P)
         }
     }
     trace_stamp(P.trace, 19, tr0);
-    if (!last_block(P.counters)) return;
+    if (!last_block(P.counters, nblk)) return;
     trace_stamp(P.trace, 20, true);
     if (P.sampling == CPD_SAMPLE_EUCLIDEAN && !P.defer_cdf) finish_distribution(P, n, s_dist, s_w);
     trace_stamp(P.trace, 21, true);
@@ -255,6 +274,22 @@ __global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P)
             *P.t_dev = t + 1;
         }
     }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_update(const Problem<T> P)
+{
+    update_body<T>(P, (int)blockIdx.x, gridDim.x);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_update_group(const Problem<T> *__restrict__ Ps,
+                                                           const int *__restrict__ cta0, int G)
+{
+    __shared__ __align__(16) Problem<T> sp;
+    const int g = group_member(Ps, cta0, G, sp);
+    const int b0 = __ldg(cta0 + g);
+    update_body<T>(sp, (int)blockIdx.x - b0, (unsigned)(__ldg(cta0 + g + 1) - b0));
 }
 
 // ---------------------------------------------------------------------------
@@ -564,6 +599,45 @@ cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd, s
     return e;
 }
 
+template <class T, class XT>
+static cudaError_t launch_grad_simt_group(const GroupLaunch<T> &L, cudaStream_t s)
+{
+    static size_t attr_bytes = 0;
+    if (L.smem_grad > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_grad_simt_group<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)L.smem_grad);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        attr_bytes = L.smem_grad;
+    }
+    k_grad_simt_group<T, XT><<<L.grid_grad, kThreads, L.smem_grad, s>>>(L.P, L.cta_grad, L.G);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_group_iteration(const GroupLaunch<T> &L, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (L.engine == kEngineTensor) {
+        if constexpr (sizeof(T) == 4) e = launch_grad_tc_group(L, s);
+        else e = cudaErrorInvalidValue;
+    } else if (L.engine == kEngineSimt) {
+        if constexpr (sizeof(T) == 8) {
+            e = launch_grad_simt_group<T, double>(L, s);
+        } else {
+            if (L.x_dtype == CPD_F32) e = launch_grad_simt_group<T, float>(L, s);
+            else e = launch_grad_simt_group<T, __nv_bfloat16>(L, s);
+        }
+    } else {
+        e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    k_update_group<T><<<L.grid_upd, kThreads, 0, s>>>(L.P, L.cta_upd, L.G);
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_refresh_mode(const Problem<T> &P, int k, cudaStream_t s)
 {
@@ -643,6 +717,8 @@ template cudaError_t launch_iteration<float>(const Problem<float> &, int, int, s
                                              cudaEvent_t, cudaEvent_t, cudaEvent_t);
 template cudaError_t launch_iteration<double>(const Problem<double> &, int, int, size_t, cudaStream_t, int,
                                               cudaEvent_t, cudaEvent_t, cudaEvent_t);
+template cudaError_t launch_group_iteration<float>(const GroupLaunch<float> &, cudaStream_t);
+template cudaError_t launch_group_iteration<double>(const GroupLaunch<double> &, cudaStream_t);
 template cudaError_t launch_refresh_mode<float>(const Problem<float> &, int, cudaStream_t);
 template cudaError_t launch_refresh_mode<double>(const Problem<double> &, int, cudaStream_t);
 template cudaError_t launch_sample_probs<float>(const Problem<float> &, cudaStream_t);

@@ -1,14 +1,19 @@
 // Serving loop of libcpd (declared in include/cpd.h): many decompositions on
-// one GPU, admitted by a device-memory budget, each on its own stream.
+// one GPU, admitted by a device-memory budget.
 //
 // One worker thread owns all device work. Per round it
 //   1. admits queued requests first-fit while the memory budget and the
 //      concurrency limit allow (cpd_init on a fresh non-blocking stream);
-//   2. for every running request whose previous fit check has finished,
-//      enqueues the iterations up to its next check and an asynchronous fit
-//      (cpd_sgd_iters + cpd_fit_start), so each stream always has a bounded
-//      amount of queued work and the streams overlap on the GPU;
-//   3. retires requests whose check met the target or whose cap is reached:
+//   2. steps the lanes: requests of one class (tensor dtype and engine, no
+//      leverage sampling) share a lane whose rounds advance all members with
+//      grouped launches (one gradient and one update launch per iteration
+//      for the whole lane), then start every member's fit; members leave and
+//      join between rounds. Two lanes per class overlap one lane's host work
+//      with the other's GPU work;
+//   3. steps the requests that cannot be grouped, each on its own stream:
+//      iterations up to its next check and an asynchronous fit, so every
+//      stream has a bounded amount of queued work and the streams overlap;
+//   4. retires requests whose check met the target or whose cap is reached:
 //      factors copied out, context freed with stream-ordered frees.
 #include <cuda_runtime.h>
 
@@ -29,6 +34,7 @@
 namespace cpd {
 void set_error(const std::string &msg);
 void destroy_on_home_stream(cpd_ctx *c);
+int ctx_engine(const cpd_ctx *c);
 }  // namespace cpd
 
 using namespace cpd;
@@ -86,6 +92,21 @@ struct Request {
 
 }  // namespace
 
+// A lane advances a set of same-class requests (same tensor dtype and
+// engine) with grouped launches on its own stream: rounds of `chunk`
+// iterations of every member, then every member's asynchronous fit, then an
+// event. Members join and leave between rounds.
+struct Lane {
+    int fbytes = 4, x_dtype = 0, engine = 0;
+    std::vector<std::shared_ptr<Request>> members, joining;
+    cpd_group *grp = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false, changed = false;
+};
+
+constexpr int kLanesPerClass = 2;
+
 struct cpd_server {
     cpd_server_config cfg{};
     int device = 0;
@@ -95,7 +116,9 @@ struct cpd_server {
     bool stop = false;
     uint64_t next_ticket = 1;
     std::deque<std::shared_ptr<Request>> queue;
-    std::vector<std::shared_ptr<Request>> active;
+    std::vector<std::shared_ptr<Request>> active;   // requests on streams of their own
+    std::vector<std::unique_ptr<Lane>> lanes;
+    size_t running = 0;                             // admitted and not finished
     std::map<uint64_t, std::shared_ptr<Request>> all;
     size_t unfinished = 0;
     std::thread worker;
@@ -127,8 +150,109 @@ static void finish(cpd_server *srv, const std::shared_ptr<Request> &r, cpd_statu
     r->res.t_done = now_s();
     r->res.done = 1;
     srv->used -= r->bytes;
+    --srv->running;
     --srv->unfinished;
     srv->cv_done.notify_all();
+}
+
+// The outcome of a finished fit check: true if the request stops.
+static bool after_fit(const std::shared_ptr<Request> &r, cpd_status st, double fit, double tol,
+                      cpd_status *why)
+{
+    r->res.fit = fit;
+    r->res.tol = tol;
+    *why = st;
+    if (st != CPD_OK) return true;
+    if (fit >= r->stop_fit) {
+        r->res.reached = 1;
+        return true;
+    }
+    return r->res.iters >= r->max_iters;
+}
+
+static Lane *pick_lane(cpd_server *srv, const std::shared_ptr<Request> &r, int engine)
+{
+    const int fbytes = r->cfg.x_dtype == CPD_F64 ? 8 : 4;
+    Lane *best = nullptr;
+    int found = 0;
+    for (auto &l : srv->lanes) {
+        if (l->fbytes != fbytes || l->x_dtype != r->cfg.x_dtype || l->engine != engine) continue;
+        ++found;
+        if (!best || l->members.size() + l->joining.size() < best->members.size() + best->joining.size())
+            best = l.get();
+    }
+    if (found < kLanesPerClass && (!best || !best->members.empty() || !best->joining.empty())) {
+        auto l = std::make_unique<Lane>();
+        l->fbytes = fbytes;
+        l->x_dtype = r->cfg.x_dtype;
+        l->engine = engine;
+        if (cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        if (cudaEventCreateWithFlags(&l->done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaStreamDestroy(l->stream);
+            return nullptr;
+        }
+        best = l.get();
+        srv->lanes.push_back(std::move(l));
+    }
+    return best;
+}
+
+// One scheduling step of a lane; returns true if it changed anything.
+static bool step_lane(cpd_server *srv, Lane &l, int fit_every)
+{
+    if (l.busy) {
+        if (cudaEventQuery(l.done) == cudaErrorNotReady) return false;
+        l.busy = false;
+        for (size_t q = 0; q < l.members.size();) {
+            auto m = l.members[q];
+            double fit = 0.0, tol = 0.0;
+            cpd_status st = cpd_fit_poll(m->ctx, &fit, &tol);
+            cpd_status why = CPD_OK;
+            if (after_fit(m, st, fit, tol, &why)) {
+                finish(srv, m, why);
+                l.members.erase(l.members.begin() + q);
+                l.changed = true;
+            } else {
+                ++q;
+            }
+        }
+    }
+    if (!l.joining.empty()) {
+        l.members.insert(l.members.end(), l.joining.begin(), l.joining.end());
+        l.joining.clear();
+        l.changed = true;
+    }
+    if (l.changed && l.grp) {
+        cpd_group_destroy(l.grp);
+        l.grp = nullptr;
+    }
+    if (l.members.empty()) {
+        l.changed = false;
+        return true;
+    }
+    cpd_status st = CPD_OK;
+    if (!l.grp) {
+        std::vector<cpd_ctx *> ctxs;
+        for (auto &m : l.members) ctxs.push_back(m->ctx);
+        st = cpd_group_create(ctxs.data(), (int32_t)ctxs.size(), l.stream, &l.grp);
+        l.changed = false;
+    }
+    int64_t chunk = fit_every;
+    for (auto &m : l.members) chunk = std::min<int64_t>(chunk, m->max_iters - m->res.iters);
+    if (st == CPD_OK) st = cpd_group_iters(l.grp, chunk, l.stream);
+    for (size_t q = 0; q < l.members.size() && st == CPD_OK; ++q) st = cpd_fit_start(l.members[q]->ctx, l.stream);
+    if (st == CPD_OK && cudaEventRecord(l.done, l.stream) != cudaSuccess) st = CPD_ECUDA;
+    if (st != CPD_OK) {
+        cudaStreamSynchronize(l.stream);
+        if (l.grp) cpd_group_destroy(l.grp);
+        l.grp = nullptr;
+        for (auto &m : l.members) finish(srv, m, st);
+        l.members.clear();
+        return true;
+    }
+    for (auto &m : l.members) m->res.iters += chunk;
+    l.busy = true;
+    return true;
 }
 
 static void worker_loop(cpd_server *srv)
@@ -142,12 +266,13 @@ static void worker_loop(cpd_server *srv)
         {
             std::unique_lock<std::mutex> lock(srv->mu);
             if (srv->stop) break;
-            if (srv->queue.empty() && srv->active.empty())
+            if (srv->queue.empty() && srv->running == 0)
                 srv->cv_work.wait(lock, [&] { return srv->stop || !srv->queue.empty(); });
             if (srv->stop) break;
-            for (auto it = srv->queue.begin(); it != srv->queue.end() && srv->active.size() + admit.size() < max_active;) {
+            for (auto it = srv->queue.begin(); it != srv->queue.end() && srv->running < max_active;) {
                 if (srv->used + (*it)->bytes <= srv->budget) {
                     srv->used += (*it)->bytes;
+                    ++srv->running;
                     admit.push_back(*it);
                     it = srv->queue.erase(it);
                 } else {
@@ -164,36 +289,36 @@ static void worker_loop(cpd_server *srv)
                 finish(srv, r, st);
                 continue;
             }
-            r->next_check = std::min<int64_t>(fit_every, r->max_iters);
-            srv->active.push_back(r);
+            const int engine = ctx_engine(r->ctx);
+            const bool groupable = !srv->cfg.no_grouping && r->cfg.sampling != CPD_SAMPLE_LEVERAGE &&
+                                   (engine == kEngineSimt || engine == kEngineTensor);
+            Lane *lane = groupable ? pick_lane(srv, r, engine) : nullptr;
+            if (lane) {
+                lane->joining.push_back(r);
+            } else {
+                r->next_check = std::min<int64_t>(fit_every, r->max_iters);
+                srv->active.push_back(r);
+            }
         }
-        // 2./3. progress every running request
         bool progressed = !admit.empty();
+        // 2. lanes of grouped requests
+        for (auto &l : srv->lanes) progressed |= step_lane(srv, *l, fit_every);
+        // 3. requests on streams of their own
         for (size_t q = 0; q < srv->active.size();) {
             auto r = srv->active[q];
             bool retire = false;
             cpd_status st = CPD_OK;
             if (r->fit_pending) {
                 double fit = 0.0, tol = 0.0;
-                st = cpd_fit_poll(r->ctx, &fit, &tol);
-                if (st == CPD_EAGAIN) {
+                const cpd_status ps = cpd_fit_poll(r->ctx, &fit, &tol);
+                if (ps == CPD_EAGAIN) {
                     ++q;
                     continue;
                 }
                 progressed = true;
                 r->fit_pending = false;
-                r->res.fit = fit;
-                r->res.tol = tol;
-                if (st != CPD_OK) {
-                    retire = true;
-                } else if (fit >= r->stop_fit) {
-                    r->res.reached = 1;
-                    retire = true;
-                } else if (r->res.iters >= r->max_iters) {
-                    retire = true;
-                } else {
-                    r->next_check = std::min<int64_t>(r->res.iters + fit_every, r->max_iters);
-                }
+                retire = after_fit(r, ps, fit, tol, &st);
+                if (!retire) r->next_check = std::min<int64_t>(r->res.iters + fit_every, r->max_iters);
             }
             if (!retire && !r->fit_pending) {
                 const int64_t chunk = r->next_check - r->res.iters;
@@ -218,6 +343,15 @@ static void worker_loop(cpd_server *srv)
     }
     for (auto &r : srv->active) finish(srv, r, CPD_EBUSY);
     srv->active.clear();
+    for (auto &l : srv->lanes) {
+        cudaStreamSynchronize(l->stream);
+        if (l->grp) cpd_group_destroy(l->grp);
+        for (auto &m : l->members) finish(srv, m, CPD_EBUSY);
+        for (auto &m : l->joining) finish(srv, m, CPD_EBUSY);
+        cudaEventDestroy(l->done);
+        cudaStreamDestroy(l->stream);
+    }
+    srv->lanes.clear();
 }
 
 extern "C" cpd_status cpd_server_create(const cpd_server_config *cfg, cpd_server **out)
@@ -228,9 +362,9 @@ extern "C" cpd_status cpd_server_create(const cpd_server_config *cfg, cpd_server
     }
     auto *srv = new cpd_server();
     if (cfg) srv->cfg = *cfg;
-    if (srv->cfg.reserved[0] || srv->cfg.reserved[1]) {
+    if (srv->cfg.reserved || srv->cfg.no_grouping < 0 || srv->cfg.no_grouping > 1) {
         delete srv;
-        set_error("reserved fields must be 0");
+        set_error("reserved must be 0 and no_grouping 0 or 1");
         return CPD_EINVAL;
     }
     if (cudaGetDevice(&srv->device) != cudaSuccess) {

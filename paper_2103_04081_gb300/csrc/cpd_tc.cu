@@ -69,16 +69,17 @@ struct TcSmem {
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
+// `bid` is the CTA's index among the CTAs of this problem.
+__device__ __forceinline__ void grad_tc_body(const Problem<float> &P, int bid)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const bool tr0 = blockIdx.x == 0;
+    const bool tr0 = bid == 0;
     trace_stamp(P.trace, 0, tr0);
     const long long t = *P.t_dev;
     const int N = P.N, R = P.R, fb = P.fb;
     const int n = mode_draw(P.seed, t, N);
     const int pr = P.tile[n].pr;
-    const int gr = blockIdx.x % pr, gf = blockIdx.x / pr;
+    const int gr = bid % pr, gf = bid / pr;
     if (gf >= P.pf) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long In = P.dims[n];
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
     //    staged over the operand tiles, which are not written before the gather
     const long long cap = (long long)(L.zs - L.a) / 8;
     draw_indices(P, t, n, f0, nf, sidx, reinterpret_cast<unsigned long long *>(sA), cap,
-                 reinterpret_cast<unsigned long long *>(szs));
+                 reinterpret_cast<unsigned long long *>(szs), bid == 0);
     const bool staged = cdfs_staged(P, n, cap);
     __syncthreads();
     trace_stamp(P.trace, 2, tr0);
@@ -318,6 +319,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols)
                      : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const Problem<float> P)
+{
+    grad_tc_body(P, (int)blockIdx.x);
+}
+
+// One launch for a group of problems (see group_member).
+__global__ void __launch_bounds__(kThreads, 1) k_grad_tc_group(const Problem<float> *__restrict__ Ps,
+                                                               const int *__restrict__ cta0, int G)
+{
+    __shared__ __align__(16) Problem<float> sp;
+    const int g = group_member(Ps, cta0, G, sp);
+    grad_tc_body(sp, (int)blockIdx.x - __ldg(cta0 + g));
+}
+
+cudaError_t launch_grad_tc_group(const GroupLaunch<float> &L, cudaStream_t s)
+{
+    static size_t attr_bytes = 0;
+    if (L.smem_grad > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_grad_tc_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)L.smem_grad);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        attr_bytes = L.smem_grad;
+    }
+    k_grad_tc_group<<<L.grid_grad, kThreads, L.smem_grad, s>>>(L.P, L.cta_grad, L.G);
+    return cudaGetLastError();
 }
 
 bool tc_supported(int R, int rb) { return R >= 1 && R <= kTcN && rb == kTcM; }

@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
     // 1. own fibers: draws (CDFs staged in the X-tile region), columns, weights
     unsigned long long *stage = reinterpret_cast<unsigned long long *>(sA);
     const long long cap = (long long)(fb * kM * 2) / 8;
-    draw_indices(P, t, n, f0 + fo0, nown, sidx, stage, cap, reinterpret_cast<unsigned long long *>(sZo));
+    draw_indices(P, t, n, f0 + fo0, nown, sidx, stage, cap, reinterpret_cast<unsigned long long *>(sZo),
+                 blockIdx.x == 0);
     __syncthreads();
     trace_stamp(P.trace, 2, tr0);
     const bool staged = cdfs_staged(P, n, cap);

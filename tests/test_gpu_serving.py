@@ -93,3 +93,48 @@ def test_fit_target_stops_a_request(cpd):
     assert st == cpd.OK and res["reached"] == 1 and res["fit"] >= 0.999
     assert res["iters"] < 50000 and res["iters"] % 100 == 0
     cpd.cpd_server_destroy(srv)
+
+
+def test_grouped_and_per_stream_serving_agree(cpd):
+    """The same requests served with grouped launches and with a stream per
+    request end bitwise alike (and like a solo run)."""
+    reqs = [
+        ((70, 60, 50), 6, "bf16", 128, "simt", 4),
+        ((80, 40, 30, 20), 9, "bf16", 200, "simt", 0),
+        ((150, 120, 90), 24, "bf16", 512, "tensor", 8),
+        ((100, 90, 80), 16, "bf16", 256, "tensor", 2),
+        ((60, 50, 40), 5, "f32", 64, "simt", 0),
+        ((90, 80, 70), 20, "bf16", 300, "tensor", 0),
+    ]
+    made = []
+    for q, (dims, R, xdt, B, engine, mc) in enumerate(reqs):
+        _, X, A0 = make_problem(dims, R, noise=1e-2, x_dtype=xdt, seed=60 + q, init_seed=160 + q)
+        cfg = cpd.make_config(dims, R, B, step="adagrad", x_dtype=xdt, seed=60 + q, engine=engine,
+                              max_ctas=mc)
+        made.append((dims, R, xdt, B, engine, mc, cfg, X.cuda(), [a.cuda() for a in A0]))
+    outs = {}
+    for grouping in (True, False):
+        srv = cpd.cpd_server_create(max_active=8, fit_every=64, grouping=grouping)
+        tks = [cpd.cpd_submit(srv, m[6], m[7], m[8], stop_fit=2.0, max_iters=200 + 30 * q)
+               for q, m in enumerate(made)]
+        assert cpd.cpd_server_wait(srv, 300.0)
+        res = []
+        for m, tk in zip(made, tks):
+            out = [torch.empty(d, m[1], dtype=torch.float32) for d in m[0]]
+            st, r = cpd.cpd_poll(srv, tk, out)
+            assert st == cpd.OK, r
+            res.append((r["iters"], r["tol"], out))
+        cpd.cpd_server_destroy(srv)
+        outs[grouping] = res
+    for (it1, tol1, o1), (it2, tol2, o2), m in zip(outs[True], outs[False], made):
+        assert it1 == it2
+        assert tol1 == tol2
+        for a, b in zip(o1, o2):
+            assert torch.equal(a, b)
+        dims, R, xdt, B, engine, mc, cfg, X, A0 = m
+        solo = cpd.Decomposition(X, A0, dims=dims, R=R, B=B, x_dtype=xdt, step="adagrad",
+                                 seed=cfg.seed, engine=engine, max_ctas=mc)
+        solo.sgd_iters(it1)
+        for a, b in zip(o1, solo.factors()):
+            assert torch.equal(a, b)
+        solo.close()
