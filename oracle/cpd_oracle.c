@@ -68,6 +68,7 @@ enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_EDEGENERATE = 6 };
 enum { ORC_SAMPLE_EUCLIDEAN = 0, ORC_SAMPLE_LEVERAGE = 1, ORC_SAMPLE_UNIFORM = 2 };
 enum { ORC_STEP_FIXED = 0, ORC_STEP_ADAGRAD = 1, ORC_STEP_DECAY = 2 };
 enum { ORC_X_F64 = 0, ORC_X_F32 = 1, ORC_X_BF16 = 2 };
+enum { ORC_CONSTRAINT_NONE = 0, ORC_CONSTRAINT_NONNEG = 1 };
 
 typedef struct {
     int32_t N;
@@ -83,6 +84,8 @@ typedef struct {
     double beta;   /* decreasing step alpha_t = beta/(t+gamma)  */
     double gamma;  /*   (Thm 9)                                 */
     uint64_t seed;
+    int32_t constraint;  /* ORC_CONSTRAINT_*                         */
+    int32_t pad;
 } orc_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -440,7 +443,18 @@ void orc_gradient(int64_t In, int32_t R, int32_t B, int64_t Jn, const double *An
  * Eq. proposed (fixed alpha, or the decreasing alpha_t = beta/(t+gamma) of
  * Thm 9) and Eq. etaada / Eq. Aada (AdaGrad-style step, accumulator S
  * including the current gradient).
+ *
+ * Nonnegative variant (Sec. 5, Table 5 / Fig. 2, generalised "as in" Fu et
+ * al.'s BrasCPD, whose constrained step is a projected gradient step): after
+ * the step every entry is projected onto the constraint set A >= 0, i.e. the
+ * Euclidean projection max(0, a). A NaN stays NaN.
  */
+static double project(const orc_cfg *c, double a)
+{
+    if (c->constraint == ORC_CONSTRAINT_NONNEG && a < 0.0) return 0.0;
+    return a;
+}
+
 void orc_update(const orc_cfg *c, int64_t t, int64_t In, double *An, double *Sn,
                 const double *G)
 {
@@ -449,7 +463,7 @@ void orc_update(const orc_cfg *c, int64_t t, int64_t In, double *An, double *Sn,
         for (int64_t q = 0; q < In * R; ++q) {
             Sn[q] = Sn[q] + G[q] * G[q];
             double eta = c->eta / sqrt(c->b + Sn[q]);
-            An[q] = An[q] - eta * G[q];
+            An[q] = project(c, An[q] - eta * G[q]);
         }
         return;
     }
@@ -457,7 +471,7 @@ void orc_update(const orc_cfg *c, int64_t t, int64_t In, double *An, double *Sn,
     if (c->step == ORC_STEP_DECAY)
         alpha = c->beta / ((double)t + c->gamma);
     for (int64_t q = 0; q < In * R; ++q)
-        An[q] = An[q] - alpha * G[q];
+        An[q] = project(c, An[q] - alpha * G[q]);
 }
 
 /*

@@ -29,6 +29,7 @@ MAXN = 8
 SAMPLE = {"euclidean": 0, "leverage": 1, "uniform": 2}
 STEP = {"fixed": 0, "adagrad": 1, "decay": 2}
 XDT = {"f64": 0, "f32": 1, "bf16": 2}
+CONSTRAINT = {"none": 0, "nonneg": 1}
 OK, EINVAL, EDEGENERATE = 0, 1, 6
 
 
@@ -63,6 +64,7 @@ class _Cfg(ctypes.Structure):
         ("alpha", ctypes.c_double), ("eta", ctypes.c_double),
         ("b", ctypes.c_double), ("beta", ctypes.c_double),
         ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("constraint", ctypes.c_int32), ("pad", ctypes.c_int32),
     ]
 
 
@@ -81,6 +83,7 @@ class Config:
     beta: float = 1.0
     gamma: float = 1.0
     seed: int = 0
+    constraint: str = "none"
     extra: dict = field(default_factory=dict)
 
     def c(self) -> _Cfg:
@@ -93,6 +96,7 @@ class Config:
         for k, d in enumerate(self.dims):
             cfg.dims[k] = int(d)
         cfg.alpha, cfg.eta, cfg.b = self.alpha, self.eta, self.b
+        cfg.constraint = CONSTRAINT[self.constraint]
         cfg.beta, cfg.gamma = self.beta, self.gamma
         cfg.seed = int(self.seed) & (2**64 - 1)
         return cfg

@@ -480,3 +480,65 @@ def test_step_records_batch_consistently(orc):
             for k in range(3):
                 if k != n:
                     np.testing.assert_array_equal(Ac[k], before[k])
+
+
+# ------------------------------------------------------------------ #
+# Nonnegative variant (Table 5 / Fig. 2): projected steps             #
+# ------------------------------------------------------------------ #
+
+def test_nonneg_projected_steps_reach_nnls(orc):
+    """With the exact mode-n gradient (formed here from a library Khatri-Rao
+    product), repeated projected fixed steps through the oracle's update
+    converge to the row-wise nonnegative least-squares solution that
+    scipy.optimize.nnls computes: min_{A >= 0} ||X_(n) - A Z^T||."""
+    from scipy.optimize import nnls
+    rng = np.random.default_rng(31)
+    dims, R, n = (6, 5, 4), 3, 0
+    A = [np.abs(rng.standard_normal((d, R))) for d in dims]
+    X = np.asfortranarray(rng.standard_normal(dims))      # mixed signs: constraints bind
+    Z = explicit_Z(A, n)
+    Xn = unfold(X, n)
+    Jn = Z.shape[0]
+    L = np.linalg.eigvalsh(Z.T @ Z).max() / Jn            # Lipschitz constant of the gradient
+    cfg = orc.Config(dims=dims, R=R, B=1, step="fixed", alpha=1.0 / L, constraint="nonneg")
+    An = np.ascontiguousarray(A[n].copy())
+    for t in range(4000):
+        G = np.ascontiguousarray((An @ (Z.T @ Z) - Xn @ Z) / Jn)
+        orc.update(cfg, t, An, None, G)
+    ref = np.stack([nnls(Z, Xn[i])[0] for i in range(dims[n])])
+    assert (ref == 0).any()                               # some constraints are active
+    assert (An >= 0).all()
+    np.testing.assert_allclose(An, ref, rtol=0, atol=1e-9)
+
+
+def test_nonneg_adagrad_step_projects_each_entry(orc):
+    """Projected AdaGrad step on hand-picked values: entries that the step
+    drives below zero land on 0; the others move as without the constraint;
+    the accumulator is the same either way."""
+    cfg = orc.Config(dims=(2, 2, 2), R=2, B=1, step="adagrad", eta=0.5, b=0.0, constraint="nonneg")
+    An = np.array([[1.0, 0.1], [0.2, 3.0]])
+    G = np.array([[1.0, 2.0], [-4.0, 8.0]])
+    S = np.zeros((2, 2))
+    orc.update(cfg, 0, An, S, G)
+    # S = G^2; step = 0.5 * G / |G| = 0.5 * sign(G)
+    np.testing.assert_array_equal(S, G * G)
+    np.testing.assert_array_equal(An, [[0.5, 0.0], [0.7, 2.5]])
+
+
+def test_nonneg_recovery_keeps_factors_nonnegative(orc):
+    """Noiseless nonnegative rank-R data from a nonnegative perturbed start:
+    the projected run keeps every factor entry >= 0 and recovers X."""
+    dims, R = (8, 9, 10), 2
+    rng = np.random.default_rng(41)
+    A = [np.abs(rng.standard_normal((d, R))) + 0.1 for d in dims]
+    X = np.asfortranarray(np.einsum("ir,jr,kr->ijk", *A))
+    A0 = [np.maximum(a + 0.05 * rng.standard_normal(a.shape), 0.0) for a in A]
+    cfg = orc.Config(dims=dims, R=R, B=16, sampling="euclidean", step="fixed", alpha=0.2, seed=6,
+                     constraint="nonneg")
+    tol0, _ = orc.tol(X, A0)
+    for chunk in range(30):
+        assert orc.run(cfg, 200 * chunk, 200, X, A0) == orc.OK
+        assert all((a >= 0).all() for a in A0)
+    tol1, _ = orc.tol(X, A0)
+    assert tol0 > 1e-4
+    assert tol1 < 1e-20, tol1
