@@ -75,6 +75,14 @@ enum {
 /* Storage type of the tensor entries. */
 enum { CPD_F64 = 0, CPD_F32 = 1, CPD_BF16 = 2 };
 
+/* Constraint on the factors (Sec. 5, Table 5 / Fig. 2: the nonnegative
+ * variant, generalised as in Fu et al.'s BrasCPD): after every step the
+ * updated entries are projected onto the constraint set. */
+enum {
+    CPD_CONSTRAINT_NONE = 0,
+    CPD_CONSTRAINT_NONNEG = 1   /* a <- max(0, a) after the step (NaN kept)  */
+};
+
 typedef struct {
     int32_t N;          /* number of modes, 3 <= N <= CPD_MAX_MODES                 */
     int32_t R;          /* CP rank, 1 <= R <= 256                                   */
@@ -99,6 +107,8 @@ typedef struct {
                            decompositions share the GPU. Part of the arithmetic:
                            the grouping of the batch fixes the summation order of
                            the gradient partials.                                */
+    int32_t constraint; /* CPD_CONSTRAINT_*                                     */
+    int32_t reserved;   /* must be 0                                            */
 } cpd_config;
 
 typedef struct cpd_ctx cpd_ctx;

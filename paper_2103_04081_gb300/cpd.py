@@ -22,6 +22,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EDEGENERATE, EAGAIN, EBUSY = ra
 HOST, DEVICE = 0, 1
 SAMPLE = {"euclidean": 0, "leverage": 1, "uniform": 2}
 STEP = {"fixed": 0, "adagrad": 1, "decay": 2}
+CONSTRAINT = {"none": 0, "nonneg": 1}
 XDT = {"f64": 0, "f32": 1, "bf16": 2}
 ENGINE = {"auto": 0, "simt": 1, "tensor": 2, "cluster": 3}
 MAX_MODES = 8
@@ -41,6 +42,7 @@ class cpd_config(ctypes.Structure):
         ("alpha", ctypes.c_double), ("eta", ctypes.c_double), ("b", ctypes.c_double),
         ("beta", ctypes.c_double), ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("engine", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
+        ("constraint", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -119,7 +121,7 @@ def _check(st: int) -> None:
 
 def make_config(dims, R, B, sampling="euclidean", step="adagrad", x_dtype="bf16", alpha=0.1,
                 eta=0.1, b=1e-12, beta=1.0, gamma=1.0, seed=0, engine="auto",
-                max_ctas=0) -> cpd_config:
+                max_ctas=0, constraint="none") -> cpd_config:
     c = cpd_config()
     c.N, c.R, c.B = len(dims), int(R), int(B)
     c.sampling, c.step, c.x_dtype = SAMPLE[sampling], STEP[step], XDT[x_dtype]
@@ -129,6 +131,8 @@ def make_config(dims, R, B, sampling="euclidean", step="adagrad", x_dtype="bf16"
     c.seed = int(seed) & (2**64 - 1)
     c.engine = ENGINE[engine]
     c.max_ctas = int(max_ctas)
+    c.constraint = CONSTRAINT[constraint]
+    c.reserved = 0
     return c
 
 

@@ -118,6 +118,9 @@ static cpd_status validate(const cpd_config *cfg)
     if (cfg->step < 0 || cfg->step > 2) return fail(CPD_EINVAL, "unknown step");
     if (cfg->x_dtype < 0 || cfg->x_dtype > 2) return fail(CPD_EINVAL, "unknown x_dtype");
     if (cfg->max_ctas < 0) return fail(CPD_EINVAL, "max_ctas must be >= 0");
+    if (cfg->constraint != CPD_CONSTRAINT_NONE && cfg->constraint != CPD_CONSTRAINT_NONNEG)
+        return fail(CPD_EINVAL, "unknown constraint");
+    if (cfg->reserved != 0) return fail(CPD_EINVAL, "reserved must be 0");
     if (cfg->engine < 0 || cfg->engine > 3) return fail(CPD_EINVAL, "unknown engine");
     double total = 1.0;
     for (int k = 0; k < cfg->N; ++k) {
@@ -221,6 +224,7 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     const cpd_config &g = c->cfg;
     Problem<T> &P = problem<T>(c);
     P.N = g.N; P.R = g.R; P.B = g.B; P.sampling = g.sampling; P.step = g.step; P.x_dtype = g.x_dtype;
+    P.constraint = g.constraint;
     P.alpha = g.alpha; P.eta = g.eta; P.b = g.b; P.beta = g.beta; P.gamma = g.gamma;
     P.seed = g.seed;
     for (int k = 0; k < g.N; ++k) {

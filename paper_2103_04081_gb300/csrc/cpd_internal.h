@@ -39,6 +39,7 @@ struct ModeTile {
 template <class T>
 struct Problem {
     int N, R, B, sampling, step, x_dtype;
+    int constraint;           // CPD_CONSTRAINT_*
     int rb, fb, pf;           // rows per CTA, fibers per CTA, fiber groups
     int cs;                   // CTAs per cluster (clustered tensor-core engine)
     int64_t dims[kMaxModes];

@@ -244,6 +244,7 @@ __device__ __forceinline__ void update_body(const Problem<T> &P, int bid, unsign
             const T alpha = (T)((P.step == CPD_STEP_DECAY) ? P.beta / ((double)t + P.gamma) : P.alpha);
             an = An[i * R + r] - alpha * g;
         }
+        if (P.constraint == CPD_CONSTRAINT_NONNEG && an < (T)0) an = (T)0;   // projection; NaN kept
         if (!isfinite((double)an) || !isfinite((double)g)) atomicOr(P.status, kStNonFinite);
         An[i * R + r] = an;
         s_new[threadIdx.x] = an;

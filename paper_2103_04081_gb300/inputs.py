@@ -40,12 +40,16 @@ def _gen(seed: int, device) -> torch.Generator:
 
 
 def factors(dims, R: int, seed: int, *, congruence: float = 0.0,
-            lognormal_rows: bool = False, device="cpu") -> list[torch.Tensor]:
-    """Ground-truth factor matrices (float64, shape (I_k, R)) on ``device``."""
+            lognormal_rows: bool = False, nonneg: bool = False, device="cpu") -> list[torch.Tensor]:
+    """Ground-truth factor matrices (float64, shape (I_k, R)) on ``device``;
+    ``nonneg``: absolute values of the N(0,1) entries (the nonnegative case of
+    Table 5 / Fig. 2)."""
     g = _gen(seed, "cpu")
     out = []
     for I in dims:
         A = torch.randn(int(I), R, generator=g, dtype=torch.float64)
+        if nonneg:
+            A = A.abs()
         if congruence:
             C = (1.0 - congruence) * torch.eye(R, dtype=torch.float64) + congruence
             A = A @ torch.linalg.cholesky(C).T
@@ -55,11 +59,12 @@ def factors(dims, R: int, seed: int, *, congruence: float = 0.0,
     return out
 
 
-def init_factors(dims, R: int, seed: int, dtype=torch.float32) -> list[torch.Tensor]:
-    """Initial factors A_0^(k), i.i.d. N(0,1), seeded apart from the data."""
+def init_factors(dims, R: int, seed: int, dtype=torch.float32, nonneg: bool = False) -> list[torch.Tensor]:
+    """Initial factors A_0^(k), i.i.d. N(0,1) (absolute values if ``nonneg``),
+    seeded apart from the data."""
     g = _gen(seed ^ _INIT_SALT, "cpu")
-    return [torch.randn(int(I), R, generator=g, dtype=torch.float64).to(dtype)
-            for I in dims]
+    out = [torch.randn(int(I), R, generator=g, dtype=torch.float64) for I in dims]
+    return [(a.abs() if nonneg else a).to(dtype) for a in out]
 
 
 def _krp_rows(A: list[torch.Tensor], j0: int, j1: int) -> torch.Tensor:

@@ -14,12 +14,12 @@ TOL = {"f64": dict(G=1e-11, A=1e-13), "f32": dict(G=1e-5, A=1e-6),
 
 
 def make_problem(dims, R, noise=1e-2, x_dtype="f32", seed=0, init_seed=1, device="cpu",
-                 lognormal_rows=False, congruence=0.0):
+                 lognormal_rows=False, congruence=0.0, nonneg=False):
     A = IN.factors(dims, R, seed, congruence=congruence, lognormal_rows=lognormal_rows,
-                   device=device)
+                   nonneg=nonneg, device=device)
     X = IN.cp_tensor(A, noise, seed, x_dtype)
     A0 = IN.init_factors(dims, R, init_seed,
-                         dtype=torch.float64 if x_dtype == "f64" else torch.float32)
+                         dtype=torch.float64 if x_dtype == "f64" else torch.float32, nonneg=nonneg)
     return A, X, A0
 
 

@@ -60,6 +60,22 @@ def test_invalid_configs_rejected_on_host(cpd, kw, msg):
     assert msg in err
 
 
+def test_unknown_constraint_and_reserved_rejected(cpd):
+    import torch
+    for field, value, msg in (("constraint", 7, "constraint"), ("reserved", 1, "reserved"),
+                              ("max_ctas", -1, "max_ctas")):
+        cfg = cpd.make_config(dims=(2, 2, 2), R=1, B=1)
+        setattr(cfg, field, value)
+        X = torch.zeros(8)
+        A0 = [torch.zeros(2, 1) for _ in range(3)]
+        ctx = ctypes.c_void_p()
+        st = cpd.lib().cpd_init(ctypes.byref(cfg), X.data_ptr(), cpd.HOST,
+                                (ctypes.c_void_p * 3)(*[a.data_ptr() for a in A0]),
+                                cpd.HOST, None, ctypes.byref(ctx))
+        assert st == cpd.EINVAL
+        assert msg in cpd.lib().cpd_last_error().decode()
+
+
 def test_no_cpu_fallback(cpd):
     import torch
     if torch.cuda.is_available():

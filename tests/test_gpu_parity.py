@@ -32,7 +32,7 @@ def _ocfg(orc, dims, R, B, x_dtype, sampling, step, seed, **kw):
     return orc.Config(dims=tuple(dims), R=R, B=B, sampling=sampling, step=step,
                       x_dtype=x_dtype, seed=seed, alpha=kw.get("alpha", 0.1),
                       eta=kw.get("eta", 0.1), b=kw.get("b", 1e-12), beta=kw.get("beta", 1.0),
-                      gamma=kw.get("gamma", 1.0))
+                      gamma=kw.get("gamma", 1.0), constraint=kw.get("constraint", "none"))
 
 
 SMALL = [
@@ -111,6 +111,33 @@ def test_max_ctas_bounds_grid_and_keeps_parity(cpd, orc, engine, xdt, dims, R, B
     tol = TOL["bf16_tensor"] if engine != "simt" else TOL[xdt]
     worst = teacher_forced(dec, orc, ocfg, oracle_xbuf(X), 6, tol["G"], tol["A"])
     print(engine, dims, max_ctas, worst, d)
+    dec.close()
+
+
+@pytest.mark.parametrize("engine,xdt,dims,R,B,sampling,step,kw", [
+    ("simt", "f64", (50, 40, 30), 6, 40, "euclidean", "fixed", dict(alpha=0.1)),
+    ("simt", "f32", (150, 70, 33), 10, 100, "euclidean", "adagrad", {}),
+    ("simt", "f32", (90, 130, 40), 7, 64, "leverage", "adagrad", {}),
+    ("simt", "bf16", (40, 36, 30, 28), 12, 200, "uniform", "decay", dict(beta=0.05, gamma=2.0)),
+    ("tensor", "bf16", (200, 150, 100), 50, 300, "euclidean", "adagrad", {}),
+    ("cluster", "bf16", (300, 64, 90), 20, 1024, "euclidean", "adagrad", {}),
+])
+def test_teacher_forced_nonnegative(cpd, orc, engine, xdt, dims, R, B, sampling, step, kw):
+    """The nonnegative variant (projected step, Table 5 / Fig. 2) against the
+    oracle; the factors stay nonnegative on a free run."""
+    A, X, A0 = make_problem(dims, R, x_dtype=xdt, nonneg=True, noise=5e-2)
+    kw = dict(kw, constraint="nonneg")
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype=xdt,
+                            sampling=sampling, step=step, seed=99, engine=engine, **kw)
+    assert dec.describe()["engine"] == engine
+    ocfg = _ocfg(orc, dims, R, B, xdt, sampling, step, 99, **kw)
+    tol = TOL["bf16_tensor"] if engine != "simt" else TOL[xdt]
+    worst = teacher_forced(dec, orc, ocfg, oracle_xbuf(X), 8, tol["G"], tol["A"])
+    dec.sgd_iters(500)
+    assert all(bool((a >= 0).all()) for a in dec.factors())
+    fit, _ = dec.fit()
+    assert np.isfinite(fit)
+    print(engine, dims, worst, fit)
     dec.close()
 
 
