@@ -197,6 +197,23 @@ cpd_status cpd_last_sample(cpd_ctx *ctx, int32_t *n, int32_t *idx, double *p, vo
 cpd_status cpd_last_gradient(cpd_ctx *ctx, void *G, void *stream);
 
 /*
+ * cpd_grad_variance -- the exact conditional variance of the mini-batch
+ * gradient of mode n at the current factors under the context's own
+ * sampling distribution (Thm 10, Table 1; the quantity Fig. 3 follows along
+ * a run):
+ *   var        = E || G - E[G] ||_F^2 = (S1 - ||M||_F^2) / (B J_n^2),
+ *   mean_norm2 = || E[G] ||_F^2        = ||M||_F^2 / J_n^2   (may be NULL),
+ * with S1 = sum_j ||r_j||^2 ||z_j||^2 / p_j and M = sum_j r_j z_j^T over all
+ * J_n fibers j of the mode-n unfolding with p_j > 0, r_j = A^(n) z_j - x_j
+ * (Eq. gradient1's normalisation: the paper's Table 1 is J_n^2 times var).
+ * One pass over the mode-n replica: residuals in FP32, sums in FP64. A
+ * deferred CDF rebuild is completed first. Synchronises `stream`.
+ * Errors: CPD_EINVAL (NULL, n out of range, R > 64), CPD_EDEGENERATE,
+ * CPD_ENOMEM, CPD_ECUDA.
+ */
+cpd_status cpd_grad_variance(cpd_ctx *ctx, int32_t n, double *var, double *mean_norm2, void *stream);
+
+/*
  * cpd_sync -- synchronise `stream` and return a pending device fault, if any
  * (CPD_ENONFINITE, CPD_EDEGENERATE, CPD_ETIMEOUT), clearing it.
  */

@@ -92,6 +92,7 @@ def _load():
         "cpd_poll": [P, ctypes.c_uint64, ctypes.POINTER(cpd_result), P],
         "cpd_server_wait": [P, ctypes.c_double],
         "cpd_server_destroy": [P],
+        "cpd_grad_variance": [P, I32, P, P, P],
         "cpd_group_create": [P, I32, P, ctypes.POINTER(P)],
         "cpd_group_iters": [P, I64, P],
         "cpd_group_destroy": [P],
@@ -310,6 +311,13 @@ def cpd_server_destroy(srv) -> None:
     _check(_lib.cpd_server_destroy(srv))
 
 
+def cpd_grad_variance(ctx, n: int, stream=None) -> tuple[float, float]:
+    """(E||G - E[G]||^2, ||E[G]||^2) of the mode-n mini-batch gradient (Thm 10)."""
+    v, m = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.cpd_grad_variance(ctx, int(n), ctypes.byref(v), ctypes.byref(m), _stream(stream)))
+    return v.value, m.value
+
+
 def cpd_group_create(ctxs: list, stream=None):
     """One grouped launch per iteration for all of `ctxs` (borrowed handles)."""
     arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
@@ -383,6 +391,9 @@ class Decomposition:
 
     def sync(self) -> None:
         cpd_sync(self.ctx)
+
+    def grad_variance(self, n: int, stream=None) -> tuple[float, float]:
+        return cpd_grad_variance(self.ctx, n, stream)
 
     def describe(self) -> dict:
         return cpd_describe(self.ctx)

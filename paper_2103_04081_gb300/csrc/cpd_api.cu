@@ -904,3 +904,39 @@ extern "C" cpd_status cpd_group_destroy(cpd_group *g)
     delete g;
     return CPD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Gradient-variance diagnostic (Thm 10, Table 1, Fig. 3).
+// ---------------------------------------------------------------------------
+template <class T>
+static cpd_status variance_typed(cpd_ctx *c, int n, double *var, double *mean_norm2, cudaStream_t s)
+{
+    Problem<T> &P = problem<T>(c);
+    double *d2 = nullptr;
+    CK(cudaMallocAsync((void **)&d2, 2 * sizeof(double), s));
+    cudaError_t e = launch_flush_dirty(P, s);
+    if (e == cudaSuccess) e = launch_variance(P, n, d2, s);
+    double h2[2] = {0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h2, d2, sizeof h2, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d2, s);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return cuda_fail(e, "cpd_grad_variance");
+    int st = 0;
+    CK(cudaMemcpy(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & kStDegenerate) return fail(CPD_EDEGENERATE, "a sampling distribution has no mass");
+    const double J = P.Jn[n];
+    *var = (h2[0] - h2[1]) / ((double)c->cfg.B * J * J);
+    if (mean_norm2) *mean_norm2 = h2[1] / (J * J);
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_grad_variance(cpd_ctx *c, int32_t n, double *var, double *mean_norm2, void *stream)
+{
+    if (!c || !var) return fail(CPD_EINVAL, "NULL argument");
+    if (n < 0 || n >= c->cfg.N) return fail(CPD_EINVAL, "mode out of range");
+    if (c->cfg.R > 64) return fail(CPD_EINVAL, "the variance diagnostic takes R <= 64");
+    cudaStream_t s = (cudaStream_t)stream;
+    return c->fbytes == 8 ? variance_typed<double>(c, n, var, mean_norm2, s)
+                          : variance_typed<float>(c, n, var, mean_norm2, s);
+}

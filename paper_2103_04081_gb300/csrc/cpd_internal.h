@@ -96,6 +96,12 @@ cudaError_t launch_refresh_mode(const Problem<T> &P, int k, cudaStream_t stream)
 template <class T>
 cudaError_t launch_sample_probs(const Problem<T> &P, cudaStream_t stream);
 template <class T>
+cudaError_t launch_flush_dirty(const Problem<T> &P, cudaStream_t stream);
+// Gradient-variance diagnostic (cpd_variance.cu): writes {S1, M2} (see there)
+// to out2 on the device; scratch from the stream-ordered allocator.
+template <class T>
+cudaError_t launch_variance(const Problem<T> &P, int n, double *out2, cudaStream_t stream);
+template <class T>
 cudaError_t launch_fit(const Problem<T> &P, double *partials, int nblocks,
                        double *out2, cudaStream_t stream, int want_xnorm);
 cudaError_t launch_build_replica(const void *X, void *rep, int esize, int N,

@@ -411,6 +411,21 @@ __global__ void __launch_bounds__(kThreads) k_weights_euclid(const Problem<T> P,
     if (threadIdx.x == 0) P.counters[3] = 0;
 }
 
+// Bring a deferred CDF up to date: rebuild the dirty mode's distribution from
+// its row weights (the same exact fixed-point CDF the next gradient kernel
+// would build) and clear the flag. One CTA.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_flush_dirty(const Problem<T> P)
+{
+    __shared__ unsigned long long s_dist[2 * kThreads];
+    __shared__ __align__(16) double s_w[kWStage];
+    const int d = *P.dirty;
+    if (d < 0) return;
+    finish_distribution(P, d, s_dist, s_w);
+    __syncthreads();
+    if (threadIdx.x == 0) *P.dirty = -1;
+}
+
 // p_f of the last batch (Eq. block_lev_prob, FP64) for its record; the
 // distributions of the modes k != n it used have not changed since.
 template <class T>
@@ -664,6 +679,14 @@ cudaError_t launch_sample_probs(const Problem<T> &P, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t launch_flush_dirty(const Problem<T> &P, cudaStream_t s)
+{
+    if (!P.defer_cdf) return cudaSuccess;
+    k_flush_dirty<T><<<1, kThreads, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
 int fit_blocks() { return 4 * 152; }
 
 template <class T>
@@ -722,6 +745,8 @@ template cudaError_t launch_group_iteration<float>(const GroupLaunch<float> &, c
 template cudaError_t launch_group_iteration<double>(const GroupLaunch<double> &, cudaStream_t);
 template cudaError_t launch_refresh_mode<float>(const Problem<float> &, int, cudaStream_t);
 template cudaError_t launch_refresh_mode<double>(const Problem<double> &, int, cudaStream_t);
+template cudaError_t launch_flush_dirty<float>(const Problem<float> &, cudaStream_t);
+template cudaError_t launch_flush_dirty<double>(const Problem<double> &, cudaStream_t);
 template cudaError_t launch_sample_probs<float>(const Problem<float> &, cudaStream_t);
 template cudaError_t launch_sample_probs<double>(const Problem<double> &, cudaStream_t);
 template cudaError_t launch_fit<float>(const Problem<float> &, double *, int, double *, cudaStream_t, int);

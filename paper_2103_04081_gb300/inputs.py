@@ -191,3 +191,21 @@ def serve_requests(n: int, rate: float = 200.0, seed: int = 0) -> list[dict]:
         out.append(dict(i=i, arrival=float(arrive[i]), N=N, dims=dims, R=R, noise=1e-2,
                         data_seed=i, init_seed=i, sample_seed=i))
     return out
+
+
+def variance_study_factors(which: str, I: int = 300, R: int = 10, seed: int = 0,
+                           device="cpu") -> list[torch.Tensor]:
+    """Factors of the variance study (Sec. 5, Fig. 3), three modes of size I:
+
+    * ``"data2"``: i.i.d. N(0,1) entries (Data II);
+    * ``"data3"``: Data II with one entry of each factor, chosen uniformly,
+      set to 20 (Data III: coherent factors, a few large leverage scores).
+    """
+    A = factors((I, I, I), R, seed, device="cpu")
+    if which == "data3":
+        rng = np.random.default_rng(seed + 7919)
+        for a in A:
+            a[int(rng.integers(I)), int(rng.integers(R))] = 20.0
+    elif which != "data2":
+        raise ValueError(which)
+    return [a.to(device) for a in A]
