@@ -17,6 +17,11 @@
 // The A^(n) rows of the tile arrive by one global -> shared bulk copy. One
 // cluster barrier after all receptions guarantees that no source buffer is
 // reused while a copy could still read it.
+//
+// The tensor cores form G_g itself: the accumulator receives X (-Z') (the
+// B operands are built negated) and then A H_g, with A^(n)'s rows (MN-major,
+// like X) and H_g (K-major, like Z') split into bf16 hi/lo pairs
+// (hi*hi + hi*lo + lo*hi); the epilogue only reads TMEM and stores.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -35,7 +40,7 @@ constexpr int kK = 16;    // MMA K for 16-bit operands
 constexpr int kCols = 64; // TMEM columns
 
 struct TccSmem {
-    size_t a, bhi, blo, zo, zso, hp, hrecv, arow, h, rows, jcol, s, idx, bar, tmem, total;
+    size_t a, bhi, blo, zo, zso, hp, hrecv, arow, h, hb, rows, jcol, s, idx, bar, tmem, total;
     int fpc, hr;
     __host__ __device__ TccSmem(int N, int R, int fb, int cs)
     {
@@ -50,8 +55,10 @@ struct TccSmem {
         hp = o;   o += (size_t)kN * kN * 4;                 // H over own fibers
         hrecv = o; o += up((size_t)cs * hr * kN * 4);       // owned rows of every CTA's partial
         if (o - a < (size_t)kM * R * 4) o = a + up((size_t)kM * R * 4);   // epilogue tile staging
-        arow = o; o += up((size_t)kM * R * 4 + 16);         // A^(n) rows of the tile (bulk copy)
+        arow = o; o += up(aop_bytes(R));                    // A^(n) rows of the tile (bulk copy), then
+                                                            // their bf16 hi/lo operands in place
         h = o;    o += (size_t)kN * kN * 4;                 // H_g
+        hb = o;   o += (size_t)kN * kN * 2 * 2;             // H_g hi / lo (B operands of A H_g)
         rows = o; o += up((size_t)fpc * (N - 1) * R * 4);   // own fibers' factor rows
         jcol = o; o += up((size_t)fb * 8);
         s = o;    o += up((size_t)fb * 4);
@@ -61,6 +68,11 @@ struct TccSmem {
         total = o;
     }
     __host__ __device__ static size_t up(size_t v) { return (v + 127) / 128 * 128; }
+    __host__ __device__ static size_t aop_bytes(int R)
+    {
+        const size_t rows = (size_t)kM * R * 4 + 16, ops = (size_t)kM * kN * 2 * 2;
+        return rows > ops ? rows : ops;
+    }
 };
 
 // Fiber slots [c fpc, c fpc + nslot(c)) of CTA c (zero-padded past nf).
@@ -214,11 +226,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
             const float zs = v * ss[fo0 + fl];
             sZo[fl * kN + r] = v;
             sZso[fl * kN + r] = zs;
-            hi[u] = __float2bfloat16_rn(zs);
-            lo[u] = __float2bfloat16_rn(zs - __bfloat162float(hi[u]));
+            hi[u] = __float2bfloat16_rn(-zs);           // -Z': the accumulator gets -M_g
+            lo[u] = __float2bfloat16_rn(-zs - __bfloat162float(hi[u]));
         }
+        // K-major, fiber-block-major: core matrix (r/8, f/8) at ((f/8)*8 + r/8)*128 B,
+        // so every CTA's slice of fibers is one contiguous range
         const int f = fo0 + 8 * b;
-        const int off = (((r >> 3) * (fb >> 3) + (f >> 3)) << 6) + ((r & 7) << 3);
+        const int off = (((f >> 3) * (kN >> 3) + (r >> 3)) << 6) + ((r & 7) << 3);
         *reinterpret_cast<uint4 *>(sBhi + off) = *reinterpret_cast<uint4 *>(hi);
         *reinterpret_cast<uint4 *>(sBlo + off) = *reinterpret_cast<uint4 *>(lo);
     }
@@ -226,28 +240,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
     __syncthreads();
     trace_stamp(P.trace, 11, tr0);
     cluster_wait();     // every CTA's mbarriers exist: sends may start
+    trace_stamp(P.trace, 22, tr0);
     if (warp == 0 && cs > 1) {
-        // own slice -> every other CTA: 8 row groups x (hi, lo), columns, weights
+        // own slice -> every other CTA: B hi, B lo (one contiguous range each),
+        // columns, weights
         const uint32_t bhi_l = smem_u32(sBhi), blo_l = smem_u32(sBlo);
         const uint32_t j_l = smem_u32(jcol), s_l = smem_u32(ss);
-        const int per = 18;
+        const int per = 4;
         for (int task = lane; task < (cs - 1) * per; task += 32) {
             const int di = task / per, q = task % per;
             const int d = di + (di >= rank ? 1 : 0);
             const uint32_t mb = map_shared(bar_x, d);
             if (nb8 == 0) continue;
-            if (q < 16) {
-                const int rg = q & 7;
-                const uint32_t base = (q < 8) ? bhi_l : blo_l;
-                const uint32_t off = (uint32_t)((rg * (fb >> 3) + (fo0 >> 3)) * 128);
-                bulk_s2s(map_shared(base + off, d), base + off, (uint32_t)nb8 * 128u, mb);
-            } else if (q == 16) {
+            if (q < 2) {
+                const uint32_t base = q == 0 ? bhi_l : blo_l;
+                const uint32_t off = (uint32_t)(fo0 >> 3) * (uint32_t)(kN >> 3) * 128u;
+                bulk_s2s(map_shared(base + off, d), base + off, (uint32_t)nb8 * (uint32_t)(kN >> 3) * 128u, mb);
+            } else if (q == 2) {
                 bulk_s2s(map_shared(j_l + fo0 * 8, d), j_l + fo0 * 8, (uint32_t)myslots * 8u, mb);
             } else {
                 bulk_s2s(map_shared(s_l + fo0 * 4, d), s_l + fo0 * 4, (uint32_t)myslots * 4u, mb);
             }
         }
     }
+    trace_stamp(P.trace, 23, tr0);
     // H over the own fibers (all 64 x 64): one row, 16 columns per thread
     {
         const int r = threadIdx.x >> 2, c0 = 16 * (threadIdx.x & 3);
@@ -269,8 +285,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
             *reinterpret_cast<float4 *>(sHp + r * kN + c0 + 4 * q4) =
                 make_float4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]);
     }
+    trace_stamp(P.trace, 24, tr0);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
+    trace_stamp(P.trace, 25, tr0);
     if (warp == 1 && cs > 1) {
         // rows [d hr, d hr + hrows(d)) of the partial -> owner d, slot `rank`
         const uint32_t hp_l = smem_u32(sHp), hr_l = smem_u32(sHr);
@@ -301,6 +319,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
+    // A^(n) rows of the tile -> bf16 hi/lo, MN-major like X (K = R padded to
+    // kN), in place through registers: operands of the A H_g products
+    ok = mbar_wait_bounded(bar_a, 0) && ok;
+    __nv_bfloat16 *aHi = reinterpret_cast<__nv_bfloat16 *>(sArow);
+    __nv_bfloat16 *aLo = aHi + kM * kN;
+    if (has_rows) {
+        constexpr int kJobs = kN * (kM / 8) / kThreads;   // 4
+        float av[kJobs][8];
+#pragma unroll
+        for (int jj = 0; jj < kJobs; ++jj) {
+            const int job = threadIdx.x + jj * kThreads;
+            const int r = job % kN, ig = job / kN;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = 8 * ig + u;
+                av[jj][u] = (ok && i < nrows && r < R) ? sArow[i * R + r] : 0.f;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int jj = 0; jj < kJobs; ++jj) {
+            const int job = threadIdx.x + jj * kThreads;
+            const int r = job % kN, ig = job / kN;
+            __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                hi[u] = __float2bfloat16_rn(av[jj][u]);
+                lo[u] = __float2bfloat16_rn(av[jj][u] - __bfloat162float(hi[u]));
+            }
+            const int off = (((r >> 3) * (kM >> 3) + ig) << 6) + ((r & 7) << 3);
+            *reinterpret_cast<uint4 *>(aHi + off) = *reinterpret_cast<uint4 *>(hi);
+            *reinterpret_cast<uint4 *>(aLo + off) = *reinterpret_cast<uint4 *>(lo);
+        }
+    }
     // owned rows of H_g: partials of every CTA summed in ascending rank
     ok = mbar_wait_bounded(bar_hp, 0) && ok;
     {
@@ -324,20 +376,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
     }
     trace_stamp(P.trace, 5, tr0);
     uint32_t tmem = 0;
+    __shared__ int s_issued;
+    if (threadIdx.x == 0) s_issued = 0;
     if (has_rows) {
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         tmem = *tmem_holder;
         if (threadIdx.x == 0 && ok) {
+            s_issued = 1;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint32_t bhi = smem_u32(sBhi), blo = smem_u32(sBlo);
             const uint32_t idesc = idesc_bf16(kM, kN);
-            const uint32_t sboB = (uint32_t)(fb >> 3) * 128u;
+            const uint32_t kstepB = 2u * (uint32_t)(kN >> 3) * 128u;   // 16 fibers = 2 core matrices along K
             for (int ks = 0; ks < fb / kK; ++ks) {
                 const uint64_t da = smem_desc(aBase + ks * 4096u, (kM / 8) * 128u, 128u);
-                const uint64_t dh = smem_desc(bhi + ks * 256u, 128u, sboB);
-                const uint64_t dl = smem_desc(blo + ks * 256u, 128u, sboB);
+                const uint64_t dh = smem_desc(bhi + ks * kstepB, (uint32_t)(kN >> 3) * 128u, 128u);
+                const uint64_t dl = smem_desc(blo + ks * kstepB, (uint32_t)(kN >> 3) * 128u, 128u);
                 const uint32_t acc = ks > 0 ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -350,49 +405,81 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
                     "l"(da), "l"(dl), "r"(idesc), "r"(1u)
                     : "memory");
             }
+        }
+    }
+    ok = mbar_wait_bounded(bar_h, 0) && ok;
+    if (!ok && threadIdx.x == 0) atomicOr(P.status, kStTimeout);
+    cluster_arrive();   // this CTA has received everything; the barrier completes meanwhile
+    trace_stamp(P.trace, 14, tr0);
+
+    // 4. + A H_g on the tensor cores: H_g -> hi/lo, K-major like Z', in its own
+    //    buffer; K = R padded to 16.
+    __nv_bfloat16 *hHi = reinterpret_cast<__nv_bfloat16 *>(smem + L.hb);
+    __nv_bfloat16 *hLo = hHi + kN * kN;
+    if (has_rows) {
+        for (int job = threadIdx.x; job < kN * (kN / 8); job += blockDim.x) {
+            const int c = job % kN, rg = job / kN;  // column c of H, rows 8 rg .. 8 rg + 7 (the K index)
+            __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float h = sH[(8 * rg + u) * kN + c];
+                hi[u] = __float2bfloat16_rn(h);
+                lo[u] = __float2bfloat16_rn(h - __bfloat162float(hi[u]));
+            }
+            const int off = (((c >> 3) * (kN >> 3) + rg) << 6) + ((c & 7) << 3);
+            *reinterpret_cast<uint4 *>(hHi + off) = *reinterpret_cast<uint4 *>(hi);
+            *reinterpret_cast<uint4 *>(hLo + off) = *reinterpret_cast<uint4 *>(lo);
+        }
+    }
+    cluster_wait();     // no copy reads our buffers any more
+    trace_stamp(P.trace, 15, tr0);
+    if (has_rows) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0 && s_issued) {
+            if (ok) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t idesc = idesc_bf16(kM, kN);
+                const uint32_t ah = smem_u32(aHi), al = smem_u32(aLo), bh = smem_u32(hHi), bl = smem_u32(hLo);
+                for (int ks = 0; ks < (R + kK - 1) / kK; ++ks) {
+                    const uint64_t dah = smem_desc(ah + ks * 4096u, (kM / 8) * 128u, 128u);
+                    const uint64_t dal = smem_desc(al + ks * 4096u, (kM / 8) * 128u, 128u);
+                    const uint64_t dbh = smem_desc(bh + ks * 256u, 128u, (kN / 8) * 128u);
+                    const uint64_t dbl = smem_desc(bl + ks * 256u, 128u, (kN / 8) * 128u);
+                    const uint64_t pa[3] = {dah, dah, dal}, pb[3] = {dbh, dbl, dbh};
+#pragma unroll
+                    for (int u = 0; u < 3; ++u)
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                            "l"(pa[u]), "l"(pb[u]), "r"(idesc), "r"(1u)
+                            : "memory");
+                }
+            }
+            // completes when every product issued above (the M products included) has
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                              bar_mma)
                          : "memory");
         }
     }
-    ok = mbar_wait_bounded(bar_h, 0) && ok;
-    ok = mbar_wait_bounded(bar_a, 0) && ok;
-    if (!ok && threadIdx.x == 0) atomicOr(P.status, kStTimeout);
-    cluster_arrive();   // every CTA has received everything: no copy reads our buffers any more
-    cluster_wait();
     trace_stamp(P.trace, 6, tr0);
 
-    // 4. G_g = A H_g - M_g for this tile's rows
+    // 5. G_g = A H_g - M_g from TMEM for this tile's rows
     if (has_rows) {
-        bool done = ok && mbar_wait_bounded(bar_mma, 0);
-        if (!done && ok) {
+        bool done = s_issued && mbar_wait_bounded(bar_mma, 0);
+        if (!done && s_issued) {
             if (threadIdx.x == 0) atomicOr(P.status, kStTimeout);
             done = mbar_wait_bounded(bar_mma, 0);
         }
+        done = done && ok;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         trace_stamp(P.trace, 7, tr0);
         float *tile = reinterpret_cast<float *>(sA);
+        const int q = warp & 3, hh = warp >> 2;
+        const int il = 32 * q + lane;
         if (done) {
-            const int q = warp & 3, hh = warp >> 2;
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * hh), v);
-            const int il = 32 * q + lane;
-            trace_stamp(P.trace, 14, tr0);
-#pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] = -v[c];
-            for (int s2 = 0; s2 < R; ++s2) {
-                const float a = sArow[il * R + s2];
-                const float4 *hrow = reinterpret_cast<const float4 *>(sH + s2 * kN + 32 * hh);
-#pragma unroll
-                for (int c4 = 0; c4 < 8; ++c4) {
-                    const float4 hv = hrow[c4];
-                    v[4 * c4 + 0] += a * hv.x;
-                    v[4 * c4 + 1] += a * hv.y;
-                    v[4 * c4 + 2] += a * hv.z;
-                    v[4 * c4 + 3] += a * hv.w;
-                }
-            }
-            trace_stamp(P.trace, 15, tr0);
             // the staging region holds only dead operands (the MMAs are complete)
 #pragma unroll
             for (int c = 0; c < 32; ++c)
