@@ -37,6 +37,8 @@ constexpr int kTcM = 128;        // rows per CTA (MMA M)
 constexpr int kTcN = 64;         // R padded (MMA N)
 constexpr int kTcK = 16;         // K of one MMA for 16-bit operands
 constexpr int kTcCols = 64;      // TMEM columns allocated (FP32 accumulator, N = 64)
+constexpr size_t kAopBytes = (size_t)kTcM * kTcN * 2 * 2;   // A^(n) rows, bf16 hi + lo
+constexpr size_t kOpBytes = kAopBytes + (size_t)kTcN * kTcN * 2 * 2;   // + H_g hi + lo
 
 // Shared memory of one CTA (byte offsets; operand tiles 128-byte aligned).
 struct TcSmem {
@@ -51,6 +53,9 @@ struct TcSmem {
         blo = o;  o += (size_t)fb * kTcN * 2;               // Z' lo, K-major bf16
         zs = o;   o += (size_t)fb * kTcN * 4;               // s_f z_f, fp32, 64 wide
         z = o;    o += (size_t)fb * kTcN * 4;               // z_f, fp32, 64 wide
+        // [zs, zs + 48 KB) holds the A H_g operands once H_g is formed:
+        // A^(n) rows hi / lo (MN-major) then H_g hi / lo (K-major)
+        if (o - zs < kOpBytes) o = zs + kOpBytes;
         // [a, arow) is dead once the MMAs are done: it stages the 128 x R
         // G tile of the epilogue, so it must hold at least that much
         if (o - a < (size_t)kTcM * R * 4) o = a + up((size_t)kTcM * R * 4);
@@ -211,8 +216,8 @@ __device__ __forceinline__ void grad_tc_body(const Problem<float> &P, int bid)
         const float zp = z * ss[f];
         sz[f * kTcN + r] = z;
         szs[f * kTcN + r] = zp;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(zp);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(zp - __bfloat162float(hi));
+        const __nv_bfloat16 hi = __float2bfloat16_rn(-zp);     // -Z': the accumulator gets -M_g
+        const __nv_bfloat16 lo = __float2bfloat16_rn(-zp - __bfloat162float(hi));
         const int off = (((r >> 3) * (fb >> 3) + (f >> 3)) << 6) + ((r & 7) << 3) + (f & 7);
         sBhi[off] = hi;
         sBlo[off] = lo;
@@ -246,8 +251,6 @@ __device__ __forceinline__ void grad_tc_body(const Problem<float> &P, int bid)
                 "l"(da), "l"(dl), "r"(idesc), "r"(1u)
                 : "memory");
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
-                     : "memory");
     }
     {
         // H_g = sum_f (s_f z_f) z_f^T: a 4 x 4 block of the 64 x 64 result per thread
@@ -269,8 +272,69 @@ __device__ __forceinline__ void grad_tc_body(const Problem<float> &P, int bid)
     }
     __syncthreads();
 
+    // 5. + A H_g on the tensor cores: A^(n) rows -> bf16 hi/lo MN-major (like
+    //    X), H_g -> bf16 hi/lo K-major (like Z'), in the buffers H_g freed;
+    //    K = R padded to 16. One commit covers every product of this CTA.
+    {
+        __nv_bfloat16 *aHi = reinterpret_cast<__nv_bfloat16 *>(szs);
+        __nv_bfloat16 *aLo = aHi + kTcM * kTcN;
+        __nv_bfloat16 *hHi = aLo + kTcM * kTcN;
+        __nv_bfloat16 *hLo = hHi + kTcN * kTcN;
+        const int rowsA = (In - r0) < kTcM ? (int)(In - r0) : kTcM;
+        for (int job = threadIdx.x; job < kTcN * (kTcM / 8); job += blockDim.x) {
+            const int r = job % kTcN, ig = job / kTcN;   // K index r, rows 8 ig .. 8 ig + 7
+            __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = 8 * ig + u;
+                const float a = (i < rowsA && r < R) ? sArow[i * lda + r] : 0.f;
+                hi[u] = __float2bfloat16_rn(a);
+                lo[u] = __float2bfloat16_rn(a - __bfloat162float(hi[u]));
+            }
+            const int off = (((r >> 3) * (kTcM >> 3) + ig) << 6) + ((r & 7) << 3);
+            *reinterpret_cast<uint4 *>(aHi + off) = *reinterpret_cast<uint4 *>(hi);
+            *reinterpret_cast<uint4 *>(aLo + off) = *reinterpret_cast<uint4 *>(lo);
+        }
+        for (int job = threadIdx.x; job < kTcN * (kTcN / 8); job += blockDim.x) {
+            const int c = job % kTcN, rg = job / kTcN;   // column c of H_g, rows 8 rg .. 8 rg + 7
+            __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float h = sH[(8 * rg + u) * kTcN + c];
+                hi[u] = __float2bfloat16_rn(h);
+                lo[u] = __float2bfloat16_rn(h - __bfloat162float(hi[u]));
+            }
+            const int off = (((c >> 3) * (kTcN >> 3) + rg) << 6) + ((c & 7) << 3);
+            *reinterpret_cast<uint4 *>(hHi + off) = *reinterpret_cast<uint4 *>(hi);
+            *reinterpret_cast<uint4 *>(hLo + off) = *reinterpret_cast<uint4 *>(lo);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t idesc = idesc_bf16(kTcM, kTcN);
+            const uint32_t ah = smem_u32(aHi), al = smem_u32(aLo), bh = smem_u32(hHi), bl = smem_u32(hLo);
+            for (int ks = 0; ks < (R + kTcK - 1) / kTcK; ++ks) {
+                const uint64_t dah = smem_desc(ah + ks * 4096u, (kTcM / 8) * 128u, 128u);
+                const uint64_t dal = smem_desc(al + ks * 4096u, (kTcM / 8) * 128u, 128u);
+                const uint64_t dbh = smem_desc(bh + ks * 256u, 128u, (kTcN / 8) * 128u);
+                const uint64_t dbl = smem_desc(bl + ks * 256u, 128u, (kTcN / 8) * 128u);
+                const uint64_t pa[3] = {dah, dah, dal}, pb[3] = {dbh, dbl, dbh};
+#pragma unroll
+                for (int u = 0; u < 3; ++u)
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                        "l"(pa[u]), "l"(pb[u]), "r"(idesc), "r"(1u)
+                        : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                         : "memory");
+        }
+    }
+
     trace_stamp(P.trace, 6, tr0);
-    // 5. accumulator -> G_g = A H_g - M_g for row i, columns [32h, 32h+32)
+    // 6. accumulator -> G_g for row i, columns [32h, 32h+32)
     bool done = mbar_wait_bounded(bar, 0);
     if (!done) {
         if (threadIdx.x == 0) atomicOr(P.status, kStTimeout);
@@ -284,20 +348,6 @@ __device__ __forceinline__ void grad_tc_body(const Problem<float> &P, int bid)
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h), v);
         const int il = 32 * q + lane;
         trace_stamp(P.trace, 14, tr0);
-#pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] = -v[c];
-        for (int s2 = 0; s2 < R; ++s2) {
-            const float a = sArow[il * lda + s2];
-            const float4 *hrow = reinterpret_cast<const float4 *>(sH + s2 * kTcN + 32 * h);
-#pragma unroll
-            for (int c4 = 0; c4 < 8; ++c4) {
-                const float4 hv = hrow[c4];
-                v[4 * c4 + 0] += a * hv.x;
-                v[4 * c4 + 1] += a * hv.y;
-                v[4 * c4 + 2] += a * hv.z;
-                v[4 * c4 + 3] += a * hv.w;
-            }
-        }
         trace_stamp(P.trace, 15, tr0);
         float *tile = reinterpret_cast<float *>(sA);   // operands are dead: stage the 128 x R tile
 #pragma unroll
