@@ -264,26 +264,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
         }
     }
     trace_stamp(P.trace, 23, tr0);
-    // H over the own fibers (all 64 x 64): one row, 16 columns per thread
+    // H over the own fibers (all 64 x 64): a 4 x 4 block per thread; own slots
+    // past nown are zero (z_f = 0), so whole groups of 8 are summed
     {
-        const int r = threadIdx.x >> 2, c0 = 16 * (threadIdx.x & 3);
-        float acc[16] = {};
-        for (int fl = 0; fl < nown; ++fl) {
-            const float av = sZso[fl * kN + r];
-            const float4 *b4 = reinterpret_cast<const float4 *>(sZo + fl * kN + c0);
+        const int rb = threadIdx.x >> 4, cb = threadIdx.x & 15;
+        float acc[4][4] = {};
+#pragma unroll 4
+        for (int fl = 0; fl < 8 * nb8; ++fl) {
+            const float4 a = *reinterpret_cast<const float4 *>(sZso + fl * kN + 4 * rb);
+            const float4 b = *reinterpret_cast<const float4 *>(sZo + fl * kN + 4 * cb);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
-                const float4 y = b4[q4];
-                acc[4 * q4 + 0] += av * y.x;
-                acc[4 * q4 + 1] += av * y.y;
-                acc[4 * q4 + 2] += av * y.z;
-                acc[4 * q4 + 3] += av * y.w;
-            }
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
         }
 #pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4)
-            *reinterpret_cast<float4 *>(sHp + r * kN + c0 + 4 * q4) =
-                make_float4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]);
+        for (int u = 0; u < 4; ++u)
+            *reinterpret_cast<float4 *>(sHp + (4 * rb + u) * kN + 4 * cb) =
+                make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
     }
     trace_stamp(P.trace, 24, tr0);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
