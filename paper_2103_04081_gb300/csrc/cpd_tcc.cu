@@ -165,8 +165,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
     // 1. own fibers: draws (CDFs staged in the X-tile region), columns, weights
     unsigned long long *stage = reinterpret_cast<unsigned long long *>(sA);
     const long long cap = (long long)(fb * kM * 2) / 8;
+    // the grid's last CTA (the one with the fewest own fibers; no CTA of this
+    // kernel returns early) writes the rebuilt CDF back
     draw_indices(P, t, n, f0 + fo0, nown, sidx, stage, cap, reinterpret_cast<unsigned long long *>(sZo),
-                 blockIdx.x == 0);
+                 blockIdx.x == gridDim.x - 1);
     __syncthreads();
     trace_stamp(P.trace, 2, tr0);
     const bool staged = cdfs_staged(P, n, cap);
@@ -188,6 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
         jcol[fo0 + f] = j;
         ss[fo0 + f] = w;
     }
+    trace_stamp(P.trace, 26, tr0);
     {
         // own fibers' factor rows, one warp per (fiber, mode) row
         const uint32_t dst0 = smem_u32(sRows);
@@ -206,7 +209,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
+    trace_stamp(P.trace, 27, tr0);
     asm volatile("cp.async.wait_all;\n" ::: "memory");
+    trace_stamp(P.trace, 28, tr0);
     __syncthreads();
     trace_stamp(P.trace, 10, tr0);
 
