@@ -301,3 +301,28 @@ def test_full_c3_120pow4_bf16(cpd, orc):
 
 def test_full_c4_1000cube_bf16(cpd, orc):
     _full(cpd, orc, "c4_1000cube_bf16", "euclidean", steps=3, warm=50)
+
+
+EDGE = [
+    # dims, R, B, x_dtype, sampling: the extremes cpd_init accepts
+    ((3, 2, 4, 2, 3, 2, 2, 3), 2, 5, "f32", "euclidean"),     # N = 8 modes
+    ((300, 40, 30), 256, 32, "f32", "euclidean"),              # R = 256
+    ((1, 40, 30), 3, 16, "f32", "euclidean"),                  # a mode of size 1
+    ((50, 40, 30), 4, 65536, "f32", "uniform"),                # B = 65536
+    ((2, 3, 2), 1, 1, "f64", "euclidean"),                     # R = 1, B = 1
+]
+
+
+@pytest.mark.parametrize("dims,R,B,xdt,sampling", EDGE)
+def test_teacher_forced_edge_cases(cpd, orc, dims, R, B, xdt, sampling):
+    A, X, A0 = make_problem(dims, R, x_dtype=xdt, lognormal_rows=True)
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype=xdt,
+                            sampling=sampling, step="adagrad", seed=21, engine="simt")
+    ocfg = _ocfg(orc, dims, R, B, xdt, sampling, "adagrad", 21)
+    tol = TOL[xdt]
+    worst = teacher_forced(dec, orc, ocfg, oracle_xbuf(X), 6, tol["G"], tol["A"])
+    fit, t = dec.fit()
+    otol, _ = orc.tol(oracle_xbuf(X), [a.double().numpy() for a in dec.factors()], x_dtype=xdt, dims=dims)
+    assert t == pytest.approx(otol, rel=1e-9 if xdt == "f64" else 1e-4)
+    print(dims, R, B, worst, dec.describe())
+    dec.close()
