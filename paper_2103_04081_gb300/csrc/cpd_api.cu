@@ -189,7 +189,10 @@ static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
         if constexpr (sizeof(T) == 4)
             while (P.fb > 16 && tc_smem_bytes(P) > 220 * 1024) P.fb -= 16;
     } else {
-        P.rb = (int)std::min<int64_t>(64, round8(imax));
+        // Under a CTA cap (several decompositions share the GPU) a CTA takes
+        // whole modes of up to 512 rows, so a fiber group's draws and KRP rows
+        // are formed once instead of once per 64-row tile.
+        P.rb = (int)std::min<int64_t>(g.max_ctas > 0 ? 512 : 64, round8(imax));
         int64_t pr_max = (imax + P.rb - 1) / P.rb;
         int64_t target = g.max_ctas > 0 ? std::min<int64_t>(g.max_ctas, 2LL * sm_count) : 2LL * sm_count;
         int64_t pf = std::max<int64_t>(1, (target + pr_max - 1) / pr_max);

@@ -442,36 +442,56 @@ __global__ void k_sample_probs(const Problem<T> P)
 // x_hat(i, j) = A^(1)(i,:) . z_j, z_j the KRP row of mode-1 fiber j, read from
 // the mode-1 replica. FP64 accumulation, fixed-order reductions.
 // ---------------------------------------------------------------------------
-constexpr int kFitFibers = 16;
+constexpr int kFitFibers = 16;     // fibers per thread per chunk (reuse of each A^(1) entry)
+constexpr int kFitStage = 4096;    // staged KRP entries per chunk
 
+// One chunk = nblk blocks of kFitFibers fibers. Thread (row i, block b)
+// forms x_hat for its row and the block's fibers; when I_1 >= kThreads one
+// block spans the CTA and threads stride over the rows. Fixed order: rows
+// ascending within a thread, then the warp tree and the CTA's warps.
 template <class T, class XT>
 __global__ void __launch_bounds__(kThreads) k_fit(const Problem<T> P, double *partials, int want_xnorm)
 {
-    __shared__ T sz[kFitFibers * 256];
+    __shared__ T sz[kFitStage];
+    __shared__ int sidx[kThreads * (kMaxModes - 1)];   // the chunk's fibers' indices, modes 1..N-1
     __shared__ double red[kThreads / 32];
     const int N = P.N, R = P.R;
     const long long I0 = P.dims[0];
     long long J = 1;
     for (int k = 1; k < N; ++k) J *= P.dims[k];
+    int nblk = I0 >= kThreads ? 1 : (int)(kThreads / I0);
+    const int cap = kFitStage / (kFitFibers * R);
+    if (nblk > cap) nblk = cap;
+    if (nblk > kThreads / kFitFibers) nblk = kThreads / kFitFibers;   // one decoding thread per fiber
+    if (nblk < 1) nblk = 1;
+    const int F = kFitFibers * nblk;
+    const int b = nblk > 1 ? (int)(threadIdx.x / I0) : 0;
     const XT *rep = reinterpret_cast<const XT *>(P.rep[0]);
     const T *A0 = P.A[0];
     double acc = 0.0;
-    for (long long j0 = (long long)blockIdx.x * kFitFibers; j0 < J; j0 += (long long)gridDim.x * kFitFibers) {
-        const int nfib = (J - j0) < kFitFibers ? (int)(J - j0) : kFitFibers;
+    for (long long j0 = (long long)blockIdx.x * F; j0 < J; j0 += (long long)gridDim.x * F) {
+        const int nfib = (J - j0) < F ? (int)(J - j0) : F;
+        __syncthreads();
+        if (threadIdx.x < nfib) {               // Eq. map, inverted once per fiber
+            long long j = j0 + threadIdx.x;
+            for (int k = 1; k < N; ++k) {
+                sidx[threadIdx.x * (kMaxModes - 1) + k - 1] = (int)(j % P.dims[k]);
+                j /= P.dims[k];
+            }
+        }
         __syncthreads();
         for (int e = threadIdx.x; e < nfib * R; e += blockDim.x) {
             const int f = e / R, r = e % R;
-            long long j = j0 + f;
             T z = (T)1;
-            for (int k = 1; k < N; ++k) {
-                const long long ik = j % P.dims[k];
-                j /= P.dims[k];
-                z = z * P.A[k][ik * R + r];
-            }
+            for (int k = 1; k < N; ++k) z = z * P.A[k][(long long)sidx[f * (kMaxModes - 1) + k - 1] * R + r];
             sz[f * R + r] = want_xnorm ? (T)0 : z;
         }
         __syncthreads();
-        for (long long i = threadIdx.x; i < I0; i += blockDim.x) {
+        if (b >= nblk) continue;
+        const int f0 = b * kFitFibers;                       // this thread's fibers in the chunk
+        const long long i_begin = nblk > 1 ? (long long)(threadIdx.x % I0) : (long long)threadIdx.x;
+        const long long i_step = nblk > 1 ? I0 : (long long)blockDim.x;
+        for (long long i = i_begin; i < I0; i += i_step) {
             T xh[kFitFibers];
 #pragma unroll
             for (int f = 0; f < kFitFibers; ++f) xh[f] = (T)0;
@@ -479,16 +499,29 @@ __global__ void __launch_bounds__(kThreads) k_fit(const Problem<T> P, double *pa
                 for (int r = 0; r < R; ++r) {
                     const T a = A0[i * R + r];
 #pragma unroll
-                    for (int f = 0; f < kFitFibers; ++f) xh[f] += a * sz[f * R + r];
+                    for (int f = 0; f < kFitFibers; ++f) xh[f] += a * sz[(f0 + f) * R + r];   // in the stage; used if < nfib
                 }
             }
+            if constexpr (sizeof(T) == 8) {
 #pragma unroll
-            for (int f = 0; f < kFitFibers; ++f) {
-                if (f < nfib) {
-                    const T x = load_x<XT, T>(rep + (j0 + f) * P.ld[0] + i);
-                    const double d = (double)(x - xh[f]);
-                    acc = __fma_rn(d, d, acc);
+                for (int f = 0; f < kFitFibers; ++f) {
+                    if (f0 + f < nfib) {
+                        const double d = load_x<XT, T>(rep + (j0 + f0 + f) * P.ld[0] + i) - xh[f];
+                        acc = __fma_rn(d, d, acc);
+                    }
                 }
+            } else {
+                // this row's (at most 16) squared residuals summed in FP32, the
+                // running sum in FP64: one FP64 operation per 16 entries
+                float part = 0.f;
+#pragma unroll
+                for (int f = 0; f < kFitFibers; ++f) {
+                    if (f0 + f < nfib) {
+                        const float d = load_x<XT, T>(rep + (j0 + f0 + f) * P.ld[0] + i) - xh[f];
+                        part = fmaf(d, d, part);
+                    }
+                }
+                acc += (double)part;
             }
         }
     }
@@ -502,13 +535,19 @@ __global__ void __launch_bounds__(kThreads) k_fit(const Problem<T> P, double *pa
     }
 }
 
-__global__ void k_fold(const double *partials, int n, double *out)
+__global__ void __launch_bounds__(kThreads) k_fold(const double *partials, int n, double *out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < n; ++q) s += partials[q];
-        *out = s;
+    // fixed order: strided partial sums per thread, then a pairwise tree
+    __shared__ double red[kThreads];
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < n; q += kThreads) acc += partials[q];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *out = red[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -701,7 +740,7 @@ cudaError_t launch_fit(const Problem<T> &P, double *partials, int nblocks, doubl
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_fold<<<1, 32, 0, s>>>(partials, nblocks, out);
+    k_fold<<<1, kThreads, 0, s>>>(partials, nblocks, out);
     return cudaGetLastError();
 }
 

@@ -24,11 +24,15 @@ def cpd():
     return C
 
 
+# cpd_fit sums at most 16 squared residuals of a row in FP32 before adding
+# them to its FP64 running sum (float factors); the allocation-free pass
+# accumulates every entry in FP64. For float factors the two agree to the
+# FP32 rounding of those short sums.
 @pytest.mark.parametrize("xdt,dims,R,rtol", [
     ("f64", (30, 20, 25), 4, 1e-12),
-    ("f32", (64, 50, 40), 6, 1e-9),
-    ("bf16", (48, 40, 36, 20), 5, 1e-9),
-    ("bf16", (300, 1000, 1000), 32, 1e-9),
+    ("f32", (64, 50, 40), 6, 1e-6),
+    ("bf16", (48, 40, 36, 20), 5, 1e-6),
+    ("bf16", (300, 1000, 1000), 32, 1e-6),
 ])
 def test_noalloc_tol_matches_cpd_fit_twice(cpd, xdt, dims, R, rtol):
     _, X, A0 = make_problem(dims, R, noise=0.1, x_dtype=xdt)
@@ -51,7 +55,7 @@ def test_noalloc_tol_matches_cpd_fit_twice(cpd, xdt, dims, R, rtol):
     _, tol2 = d2.fit()
     cpd.cpd_tol_noalloc((17, 9, 33), 3, "f32", X2.cuda(), [a.cuda().float() for a in A2], out)
     torch.cuda.synchronize()
-    assert out.item() == pytest.approx(tol2, rel=1e-9)
+    assert out.item() == pytest.approx(tol2, rel=1e-6)
     cpd.cpd_tol_noalloc(dims, R, xdt, Xd, A, out)
     torch.cuda.synchronize()
     assert out.item() == pytest.approx(tol_ref, rel=rtol)
