@@ -442,71 +442,127 @@ __global__ void k_sample_probs(const Problem<T> P)
 // x_hat(i, j) = A^(1)(i,:) . z_j, z_j the KRP row of mode-1 fiber j, read from
 // the mode-1 replica. FP64 accumulation, fixed-order reductions.
 // ---------------------------------------------------------------------------
-constexpr int kFitFibers = 16;     // fibers per thread per chunk (reuse of each A^(1) entry)
-constexpr int kFitStage = 4096;    // staged KRP entries per chunk
+constexpr int kFitFibers = 16;        // fibers per thread per chunk (reuse of each A^(1) entry)
+constexpr int kFitStage = 4096;       // staged KRP entries per chunk
+constexpr int kFitAtBytes = 48 * 1024;   // A^(1) rows of a CTA's tile, transposed
 
-// One chunk = nblk blocks of kFitFibers fibers. Thread (row i, block b)
-// forms x_hat for its row and the block's fibers; when I_1 >= kThreads one
-// block spans the CTA and threads stride over the rows. Fixed order: rows
-// ascending within a thread, then the warp tree and the CTA's warps.
+// Work split of the fit pass. A CTA owns a tile of rt rows of A^(1) (staged
+// transposed in shared memory once) and walks its share of the mode-1
+// fibers in chunks of F = 16 nblk; thread (row il, block b) forms x_hat for
+// its row and 16 fibers. KRP rows are staged at a stride of R rounded up to
+// 4 for float factors (128-bit loads).
+struct FitTiling {
+    int rt, ntile, nblk, F, Rs;
+};
+
+__host__ __device__ inline FitTiling fit_tiling(long long I0, int R, int tsize)
+{
+    FitTiling t;
+    t.Rs = tsize == 4 ? (R + 3) / 4 * 4 : R;
+    int rmax = kThreads;
+    while (rmax > 16 && (long long)rmax * R * tsize > kFitAtBytes) rmax >>= 1;
+    t.rt = (int)(I0 < rmax ? I0 : rmax);
+    t.ntile = (int)((I0 + t.rt - 1) / t.rt);
+    int nblk = kThreads / t.rt;
+    const int cap = kFitStage / (kFitFibers * t.Rs);
+    if (nblk > cap) nblk = cap;
+    if (nblk > kThreads / kFitFibers) nblk = kThreads / kFitFibers;   // one decoding thread per fiber
+    if (nblk < 1) nblk = 1;
+    t.nblk = nblk;
+    t.F = kFitFibers * nblk;
+    return t;
+}
+
+// Fixed order: a thread's fibers and chunks in order, then the warp tree and
+// the CTA's warps; the CTAs' partials are folded by k_fold.
 template <class T, class XT>
 __global__ void __launch_bounds__(kThreads) k_fit(const Problem<T> P, double *partials, int want_xnorm)
 {
-    __shared__ T sz[kFitStage];
+    extern __shared__ __align__(16) unsigned char fit_dyn[];
+    __shared__ __align__(16) T sz[kFitStage];
     __shared__ int sidx[kThreads * (kMaxModes - 1)];   // the chunk's fibers' indices, modes 1..N-1
     __shared__ double red[kThreads / 32];
+    T *sAt = reinterpret_cast<T *>(fit_dyn);           // [R][rt]
     const int N = P.N, R = P.R;
     const long long I0 = P.dims[0];
     long long J = 1;
     for (int k = 1; k < N; ++k) J *= P.dims[k];
-    int nblk = I0 >= kThreads ? 1 : (int)(kThreads / I0);
-    const int cap = kFitStage / (kFitFibers * R);
-    if (nblk > cap) nblk = cap;
-    if (nblk > kThreads / kFitFibers) nblk = kThreads / kFitFibers;   // one decoding thread per fiber
-    if (nblk < 1) nblk = 1;
-    const int F = kFitFibers * nblk;
-    const int b = nblk > 1 ? (int)(threadIdx.x / I0) : 0;
+    const FitTiling L = fit_tiling(I0, R, (int)sizeof(T));
+    const int Rs = L.Rs, rt = L.rt, F = L.F;
+    // (tile, fiber group) pairs: one per CTA when the grid covers the tiles,
+    // otherwise each CTA walks several tiles with all fibers
+    const long long ngroups = (long long)gridDim.x >= L.ntile ? (long long)gridDim.x / L.ntile : 1;
+    const long long npairs = (long long)L.ntile * ngroups;
+    const int il = threadIdx.x % rt, b = threadIdx.x / rt;
+    const int f0 = b * kFitFibers;                     // this thread's fibers in a chunk
     const XT *rep = reinterpret_cast<const XT *>(P.rep[0]);
-    const T *A0 = P.A[0];
     double acc = 0.0;
-    for (long long j0 = (long long)blockIdx.x * F; j0 < J; j0 += (long long)gridDim.x * F) {
-        const int nfib = (J - j0) < F ? (int)(J - j0) : F;
-        __syncthreads();
-        if (threadIdx.x < nfib) {               // Eq. map, inverted once per fiber
-            long long j = j0 + threadIdx.x;
-            for (int k = 1; k < N; ++k) {
-                sidx[threadIdx.x * (kMaxModes - 1) + k - 1] = (int)(j % P.dims[k]);
-                j /= P.dims[k];
+    for (long long pair = blockIdx.x; pair < npairs; pair += gridDim.x) {
+        const long long tile = pair % L.ntile, group = pair / L.ntile;
+        const long long r0 = tile * rt;
+        const int rows = (int)((I0 - r0) < rt ? (I0 - r0) : rt);
+        const bool act = b < L.nblk && il < rows;
+        __syncthreads();                            // the previous pair's rows are no longer read
+        for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
+            const int i = e / R, r = e % R;
+            sAt[r * rt + i] = P.A[0][(r0 + i) * R + r];
+        }
+        for (long long j0 = group * F; j0 < J; j0 += ngroups * F) {
+            const int nfib = (J - j0) < F ? (int)(J - j0) : F;
+            __syncthreads();
+            if (threadIdx.x < nfib) {               // Eq. map, inverted once per fiber
+                long long j = j0 + threadIdx.x;
+                for (int k = 1; k < N; ++k) {
+                    sidx[threadIdx.x * (kMaxModes - 1) + k - 1] = (int)(j % P.dims[k]);
+                    j /= P.dims[k];
+                }
             }
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < nfib * R; e += blockDim.x) {
-            const int f = e / R, r = e % R;
-            T z = (T)1;
-            for (int k = 1; k < N; ++k) z = z * P.A[k][(long long)sidx[f * (kMaxModes - 1) + k - 1] * R + r];
-            sz[f * R + r] = want_xnorm ? (T)0 : z;
-        }
-        __syncthreads();
-        if (b >= nblk) continue;
-        const int f0 = b * kFitFibers;                       // this thread's fibers in the chunk
-        const long long i_begin = nblk > 1 ? (long long)(threadIdx.x % I0) : (long long)threadIdx.x;
-        const long long i_step = nblk > 1 ? I0 : (long long)blockDim.x;
-        for (long long i = i_begin; i < I0; i += i_step) {
+            __syncthreads();
+#pragma unroll 4
+            for (int e = threadIdx.x; e < F * Rs; e += blockDim.x) {   // unrolled: the L2 loads overlap
+                const int f = e / Rs, r = e % Rs;
+                T z = (T)0;
+                if (f < nfib && r < R && !want_xnorm) {
+                    z = (T)1;
+                    for (int k = 1; k < N; ++k) z = z * P.A[k][(long long)sidx[f * (kMaxModes - 1) + k - 1] * R + r];
+                }
+                sz[f * Rs + r] = z;
+            }
+            __syncthreads();
+            if (!act) continue;
             T xh[kFitFibers];
 #pragma unroll
             for (int f = 0; f < kFitFibers; ++f) xh[f] = (T)0;
             if (!want_xnorm) {
-                for (int r = 0; r < R; ++r) {
-                    const T a = A0[i * R + r];
+                if constexpr (sizeof(T) == 4) {
+                    for (int r = 0; r < Rs; r += 4) {   // staged KRP entries past R are 0
+                        const float a0 = sAt[r * rt + il];
+                        const float a1 = r + 1 < R ? sAt[(r + 1) * rt + il] : 0.f;
+                        const float a2 = r + 2 < R ? sAt[(r + 2) * rt + il] : 0.f;
+                        const float a3 = r + 3 < R ? sAt[(r + 3) * rt + il] : 0.f;
 #pragma unroll
-                    for (int f = 0; f < kFitFibers; ++f) xh[f] += a * sz[(f0 + f) * R + r];   // in the stage; used if < nfib
+                        for (int f = 0; f < kFitFibers; ++f) {   // in the stage; used if < nfib
+                            const float4 z = *reinterpret_cast<const float4 *>(sz + (f0 + f) * Rs + r);
+                            xh[f] += a0 * z.x;
+                            xh[f] += a1 * z.y;
+                            xh[f] += a2 * z.z;
+                            xh[f] += a3 * z.w;
+                        }
+                    }
+                } else {
+                    for (int r = 0; r < R; ++r) {
+                        const T a = sAt[r * rt + il];
+#pragma unroll
+                        for (int f = 0; f < kFitFibers; ++f) xh[f] += a * sz[(f0 + f) * Rs + r];
+                    }
                 }
             }
+            const XT *xr = rep + r0 + il;
             if constexpr (sizeof(T) == 8) {
 #pragma unroll
                 for (int f = 0; f < kFitFibers; ++f) {
                     if (f0 + f < nfib) {
-                        const double d = load_x<XT, T>(rep + (j0 + f0 + f) * P.ld[0] + i) - xh[f];
+                        const double d = load_x<XT, T>(xr + (j0 + f0 + f) * P.ld[0]) - xh[f];
                         acc = __fma_rn(d, d, acc);
                     }
                 }
@@ -517,7 +573,7 @@ __global__ void __launch_bounds__(kThreads) k_fit(const Problem<T> P, double *pa
 #pragma unroll
                 for (int f = 0; f < kFitFibers; ++f) {
                     if (f0 + f < nfib) {
-                        const float d = load_x<XT, T>(rep + (j0 + f0 + f) * P.ld[0] + i) - xh[f];
+                        const float d = load_x<XT, T>(xr + (j0 + f0 + f) * P.ld[0]) - xh[f];
                         part = fmaf(d, d, part);
                     }
                 }
@@ -728,17 +784,38 @@ cudaError_t launch_flush_dirty(const Problem<T> &P, cudaStream_t s)
 
 int fit_blocks() { return 4 * 152; }
 
+// Raise each fit kernel's dynamic shared-memory limit once to the tiling's maximum.
+template <class T, class XT>
+static cudaError_t launch_fit_kernel(int grid, size_t dyn, cudaStream_t s, const Problem<T> &P, double *partials,
+                                     int want_xnorm)
+{
+    static bool raised = false;   // one flag per kernel instantiation
+    void (*kernel)(const Problem<T>, double *, int) = k_fit<T, XT>;
+    if (!raised) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFitAtBytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        raised = true;
+    }
+    kernel<<<grid, kThreads, dyn, s>>>(P, partials, want_xnorm);
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_fit(const Problem<T> &P, double *partials, int nblocks, double *out, cudaStream_t s,
                        int want_xnorm)
 {
+    const FitTiling L = fit_tiling(P.dims[0], P.R, (int)sizeof(T));
+    const size_t dyn = (size_t)L.rt * P.R * sizeof(T);
+    cudaError_t e;
     if constexpr (sizeof(T) == 8) {
-        k_fit<T, double><<<nblocks, kThreads, 0, s>>>(P, partials, want_xnorm);
+        e = launch_fit_kernel<T, double>(nblocks, dyn, s, P, partials, want_xnorm);
     } else {
-        if (P.x_dtype == CPD_F32) k_fit<T, float><<<nblocks, kThreads, 0, s>>>(P, partials, want_xnorm);
-        else k_fit<T, __nv_bfloat16><<<nblocks, kThreads, 0, s>>>(P, partials, want_xnorm);
+        if (P.x_dtype == CPD_F32) e = launch_fit_kernel<T, float>(nblocks, dyn, s, P, partials, want_xnorm);
+        else e = launch_fit_kernel<T, __nv_bfloat16>(nblocks, dyn, s, P, partials, want_xnorm);
     }
-    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_fold<<<1, kThreads, 0, s>>>(partials, nblocks, out);
     return cudaGetLastError();
