@@ -82,3 +82,25 @@ def test_no_cpu_fallback(cpd):
         pytest.skip("a GPU is present")
     st, err = _init_status(cpd, dims=(2, 2, 2), R=1, B=1)
     assert st == cpd.ECUDA, err
+
+
+def test_server_group_and_variance_reject_bad_arguments_on_host(cpd):
+    """Argument checks that come before any device work."""
+    import ctypes as C
+    cfg = cpd.cpd_server_config()
+    cfg.reserved = 1
+    srv = C.c_void_p()
+    assert cpd.lib().cpd_server_create(C.byref(cfg), C.byref(srv)) == cpd.EINVAL
+    cfg = cpd.cpd_server_config()
+    cfg.no_grouping = 2
+    assert cpd.lib().cpd_server_create(C.byref(cfg), C.byref(srv)) == cpd.EINVAL
+    grp = C.c_void_p()
+    assert cpd.lib().cpd_group_create(None, 1, None, C.byref(grp)) == cpd.EINVAL
+    arr = (C.c_void_p * 1)(None)
+    assert cpd.lib().cpd_group_create(arr, 0, None, C.byref(grp)) == cpd.EINVAL
+    assert cpd.lib().cpd_group_create(arr, 1, None, C.byref(grp)) == cpd.EINVAL
+    assert cpd.lib().cpd_group_iters(None, 1, None) == cpd.EINVAL
+    assert cpd.lib().cpd_group_destroy(None) == cpd.OK
+    v = C.c_double()
+    assert cpd.lib().cpd_grad_variance(None, 0, C.byref(v), None, None) == cpd.EINVAL
+    assert cpd.lib().cpd_server_destroy(None) == cpd.OK
