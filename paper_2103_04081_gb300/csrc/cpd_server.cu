@@ -126,7 +126,6 @@ struct cpd_server {
 
 static void finish(cpd_server *srv, const std::shared_ptr<Request> &r, cpd_status st)
 {
-    r->res.status = st;
     if (r->ctx) {
         if (st == CPD_OK) {
             std::vector<void *> ptrs;
@@ -137,7 +136,7 @@ static void finish(cpd_server *srv, const std::shared_ptr<Request> &r, cpd_statu
                 ptrs.push_back(r->factors[k].data());
             }
             const cpd_status g = cpd_get_factors(r->ctx, ptrs.data(), CPD_HOST, r->stream);
-            if (g != CPD_OK) r->res.status = g;
+            if (g != CPD_OK) st = g;
         }
         destroy_on_home_stream(r->ctx);
         r->ctx = nullptr;
@@ -147,6 +146,7 @@ static void finish(cpd_server *srv, const std::shared_ptr<Request> &r, cpd_statu
         r->stream = nullptr;
     }
     std::lock_guard<std::mutex> lock(srv->mu);
+    r->res.status = st;
     r->res.t_done = now_s();
     r->res.done = 1;
     srv->used -= r->bytes;
@@ -155,10 +155,12 @@ static void finish(cpd_server *srv, const std::shared_ptr<Request> &r, cpd_statu
     srv->cv_done.notify_all();
 }
 
-// The outcome of a finished fit check: true if the request stops.
-static bool after_fit(const std::shared_ptr<Request> &r, cpd_status st, double fit, double tol,
+// The outcome of a finished fit check: true if the request stops. The
+// result fields change under the server's lock (cpd_poll reads them).
+static bool after_fit(cpd_server *srv, const std::shared_ptr<Request> &r, cpd_status st, double fit, double tol,
                       cpd_status *why)
 {
+    std::lock_guard<std::mutex> lock(srv->mu);
     r->res.fit = fit;
     r->res.tol = tol;
     *why = st;
@@ -168,6 +170,12 @@ static bool after_fit(const std::shared_ptr<Request> &r, cpd_status st, double f
         return true;
     }
     return r->res.iters >= r->max_iters;
+}
+
+static void add_iters(cpd_server *srv, const std::shared_ptr<Request> &r, int64_t n)
+{
+    std::lock_guard<std::mutex> lock(srv->mu);
+    r->res.iters += n;
 }
 
 static Lane *pick_lane(cpd_server *srv, const std::shared_ptr<Request> &r, int engine)
@@ -208,7 +216,7 @@ static bool step_lane(cpd_server *srv, Lane &l, int fit_every)
             double fit = 0.0, tol = 0.0;
             cpd_status st = cpd_fit_poll(m->ctx, &fit, &tol);
             cpd_status why = CPD_OK;
-            if (after_fit(m, st, fit, tol, &why)) {
+            if (after_fit(srv, m, st, fit, tol, &why)) {
                 finish(srv, m, why);
                 l.members.erase(l.members.begin() + q);
                 l.changed = true;
@@ -250,7 +258,7 @@ static bool step_lane(cpd_server *srv, Lane &l, int fit_every)
         l.members.clear();
         return true;
     }
-    for (auto &m : l.members) m->res.iters += chunk;
+    for (auto &m : l.members) add_iters(srv, m, chunk);
     l.busy = true;
     return true;
 }
@@ -281,7 +289,10 @@ static void worker_loop(cpd_server *srv)
             }
         }
         for (auto &r : admit) {
-            r->res.t_start = now_s();
+            {
+                std::lock_guard<std::mutex> lock(srv->mu);
+                r->res.t_start = now_s();
+            }
             cpd_status st = CPD_OK;
             if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess) st = CPD_ECUDA;
             if (st == CPD_OK) st = cpd_init(&r->cfg, r->X, r->x_loc, r->A0.data(), r->a0_loc, r->stream, &r->ctx);
@@ -317,7 +328,7 @@ static void worker_loop(cpd_server *srv)
                 }
                 progressed = true;
                 r->fit_pending = false;
-                retire = after_fit(r, ps, fit, tol, &st);
+                retire = after_fit(srv, r, ps, fit, tol, &st);
                 if (!retire) r->next_check = std::min<int64_t>(r->res.iters + fit_every, r->max_iters);
             }
             if (!retire && !r->fit_pending) {
@@ -327,7 +338,7 @@ static void worker_loop(cpd_server *srv)
                 if (st != CPD_OK) {
                     retire = true;
                 } else {
-                    r->res.iters += chunk;
+                    add_iters(srv, r, chunk);
                     r->fit_pending = true;
                     progressed = true;
                 }
