@@ -234,16 +234,20 @@ cpd_status cpd_profile_read(cpd_ctx *ctx, int64_t *launches, double *mean_grad_m
  * cpd_trace -- enable (1) or disable (0) device-side phase timestamps
  * (%globaltimer, ns) of the iterations that follow; cpd_trace_read copies the
  * 64 stamps of the most recent traced iteration to host memory `out`
- * (synchronising `stream`; 0 = phase not reached):
- *   [0..9]   gradient kernel, first CTA: entry, TMEM/mbarrier set-up done,
- *            draws done, weights and row copies issued, gather issued, KRP
- *            rows and operands built, MMAs issued and H formed, MMAs
- *            complete, epilogue done, exit;
- *   [10..15] gradient kernel detail: weights done, row copies issued, rows
- *            landed, operands built, accumulator read, A H_g formed;
- *   [16..19] update kernel, first CTA: entry, gradient reduced, step applied,
- *            row weights written;
- *   [20..21] update kernel, last CTA: distribution rebuild start / end.
+ * (synchronising `stream`; 0 = phase not reached). Gradient kernel, first
+ * CTA, in the cluster tensor-core engine's order:
+ *   0 entry; 1 mbarriers, TMEM and A^(n)-row copy set up; 2 draws done;
+ *   26 own fibers' columns and weights; 27 factor-row copies issued;
+ *   28 / 10 rows landed; 11 operands built; 22 cluster may exchange;
+ *   23 slices sent; 24 partial H formed; 25 / 3 partial-H rows sent;
+ *   4 all slices received; 5 gather issued, A^(n) operands converted, owned
+ *   H rows summed and sent; 14 all H rows received; 15 H operands converted,
+ *   cluster barrier passed; 6 A H_g products issued; 7 accumulator complete;
+ *   8 G_g stored; 9 exit.
+ * The other gradient engines use slots 0-15 for their own phases in the
+ * same spirit. Update kernel: 16 entry, 17 gradient reduced, 18 step
+ * applied, 19 row weights written (first CTA); 20 / 21 distribution
+ * rebuild start / end (last CTA).
  */
 cpd_status cpd_trace(cpd_ctx *ctx, int enable);
 cpd_status cpd_trace_read(cpd_ctx *ctx, uint64_t *out, void *stream);
