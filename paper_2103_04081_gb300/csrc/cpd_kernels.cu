@@ -187,6 +187,15 @@ __global__ void __launch_bounds__(kThreads) k_grad_simt_group(const Problem<T> *
 // Rebuild the fixed-point distribution of mode k from w[k] (one CTA); a
 // distribution without mass is flagged.
 constexpr int kWStage = 4096;  // doubles of shared staging for the row weights
+constexpr int kLevSmemR = 64;  // leverage: L staged in shared memory up to this rank
+// dynamic shared memory of the leverage kernels: L (R x R) and the inverse
+// pivots when staged, and at least the row-weight staging of a distribution rebuild
+inline size_t lev_smem_bytes(int R)
+{
+    const size_t l = R <= kLevSmemR ? (size_t)(R * R + R) * sizeof(double) : 0;
+    const size_t w = (size_t)kWStage * sizeof(double);
+    return l > w ? l : w;
+}
 
 template <class T>
 __device__ void finish_distribution(const Problem<T> &P, int k, unsigned long long *sm, double *wstage)
@@ -329,25 +338,42 @@ __global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mod
     double *Lm = P.lev_L, *inv = P.lev_L + R * R;
     __shared__ int s_bad;
     if (threadIdx.x == 0) s_bad = 0;
+    // Small R: factor in place in shared memory (the lower triangle of the
+    // staged Gram matrix becomes L; same operations in the same order), then
+    // store L and the inverse pivots. Large R: through global memory.
+    extern __shared__ __align__(16) double lev_dyn[];
+    const bool in_smem = R <= kLevSmemR;
+    double *W = in_smem ? lev_dyn : Lm;          // L, and the Gram entries not yet replaced
+    double *wi = in_smem ? lev_dyn + R * R : inv;
+    if (in_smem)
+        for (int e = threadIdx.x; e < R * R; e += blockDim.x) W[e] = __ldcg(g + e);
     __syncthreads();
     for (int j = 0; j < R; ++j) {
         if (threadIdx.x == 0) {
-            double d = __ldcg(g + j * R + j);
-            for (int q = 0; q < j; ++q) d = __fma_rn(-Lm[j * R + q], Lm[j * R + q], d);
-            if (!(d > 0x1.0p-40 * __ldcg(g + j * R + j))) {
+            const double gjj = in_smem ? W[j * R + j] : __ldcg(g + j * R + j);
+            double d = gjj;
+            for (int q = 0; q < j; ++q) d = __fma_rn(-W[j * R + q], W[j * R + q], d);
+            if (!(d > 0x1.0p-40 * gjj)) {
                 s_bad = 1;
                 d = 1.0;
             }
-            Lm[j * R + j] = __dsqrt_rn(d);
-            inv[j] = __ddiv_rn(1.0, Lm[j * R + j]);
+            W[j * R + j] = __dsqrt_rn(d);
+            wi[j] = __ddiv_rn(1.0, W[j * R + j]);
         }
         __syncthreads();
         for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) {
-            double v = __ldcg(g + i * R + j);
-            for (int q = 0; q < j; ++q) v = __fma_rn(-Lm[i * R + q], Lm[j * R + q], v);
-            Lm[i * R + j] = __dmul_rn(v, inv[j]);
+            double v = in_smem ? W[i * R + j] : __ldcg(g + i * R + j);
+            for (int q = 0; q < j; ++q) v = __fma_rn(-W[i * R + q], W[j * R + q], v);
+            W[i * R + j] = __dmul_rn(v, wi[j]);
         }
         __syncthreads();
+    }
+    if (in_smem) {
+        for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+            const int i = e / R, q = e % R;
+            if (q <= i) Lm[e] = W[e];
+        }
+        for (int j = threadIdx.x; j < R; j += blockDim.x) inv[j] = wi[j];
     }
     if (threadIdx.x == 0) {
         P.counters[1] = 0;
@@ -365,8 +391,16 @@ __global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k
     const int k = k_mode >= 0 ? k_mode : mode_draw(P.seed, t, P.N);
     const int R = P.R;
     const long long I = P.dims[k];
-    const double *Lm = P.lev_L, *inv = P.lev_L + R * R;
     const bool bad = __ldcg(P.lev_L + R * R + R + R * R) != 0.0;
+    // L and the inverse pivots in shared memory for small R (the dynamic
+    // buffer later serves as the last CTA's weight staging)
+    extern __shared__ __align__(16) double lev_dyn[];
+    const bool in_smem = R <= kLevSmemR;
+    if (in_smem) {
+        for (int e = threadIdx.x; e < R * R + R; e += blockDim.x) lev_dyn[e] = __ldcg(P.lev_L + e);
+        __syncthreads();
+    }
+    const double *Lm = in_smem ? lev_dyn : P.lev_L, *inv = Lm + R * R;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (!bad && i < I) {
         const T *a = P.A[k] + i * R;
@@ -374,16 +408,15 @@ __global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k
         double acc = 0.0;
         for (int j = 0; j < R; ++j) {
             double v = (double)a[j];
-            for (int q = 0; q < j; ++q) v = __fma_rn(-__ldcg(Lm + j * R + q), y[q], v);
-            y[j] = __dmul_rn(v, __ldcg(inv + j));
+            for (int q = 0; q < j; ++q) v = __fma_rn(-Lm[j * R + q], y[q], v);
+            y[j] = __dmul_rn(v, inv[j]);
             acc = __fma_rn(y[j], y[j], acc);
         }
         P.w[k][i] = acc;
     }
     if (!last_block(P.counters + 2)) return;
     __shared__ unsigned long long s_dist[2 * kThreads];
-    __shared__ double s_w[kWStage];
-    if (!bad) finish_distribution(P, k, s_dist, s_w);
+    if (!bad) finish_distribution(P, k, s_dist, lev_dyn);
     if (threadIdx.x == 0) {
         P.counters[2] = 0;
         if (advance) {
@@ -699,11 +732,11 @@ cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd, s
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (P.sampling == CPD_SAMPLE_LEVERAGE) {
         const int npairs = P.R * (P.R + 1) / 2;
-        k_gram<T><<<(npairs + 7) / 8, kThreads, 0, s>>>(P, -1);
+        k_gram<T><<<(npairs + 7) / 8, kThreads, lev_smem_bytes(P.R), s>>>(P, -1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         long long Imax = 0;
         for (int k = 0; k < P.N; ++k) Imax = P.dims[k] > Imax ? P.dims[k] : Imax;
-        k_lev_rows<T><<<(int)((Imax + kThreads - 1) / kThreads), kThreads, 0, s>>>(P, -1, 1);
+        k_lev_rows<T><<<(int)((Imax + kThreads - 1) / kThreads), kThreads, lev_smem_bytes(P.R), s>>>(P, -1, 1);
         e = cudaGetLastError();
     }
     if (ev2) cudaEventRecord(ev2, s);
@@ -757,10 +790,10 @@ cudaError_t launch_refresh_mode(const Problem<T> &P, int k, cudaStream_t s)
     const int grid_rows = (int)((I * 32 + kThreads - 1) / kThreads);
     if (P.sampling == CPD_SAMPLE_LEVERAGE) {
         const int npairs = P.R * (P.R + 1) / 2;
-        k_gram<T><<<(npairs + 7) / 8, kThreads, 0, s>>>(P, k);
+        k_gram<T><<<(npairs + 7) / 8, kThreads, lev_smem_bytes(P.R), s>>>(P, k);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_lev_rows<T><<<grid, kThreads, 0, s>>>(P, k, 0);
+        k_lev_rows<T><<<grid, kThreads, lev_smem_bytes(P.R), s>>>(P, k, 0);
     } else {
         k_weights_euclid<T><<<grid_rows, kThreads, 0, s>>>(P, k);
     }
