@@ -3,7 +3,8 @@
 A step is one SGD iteration of the whole path (mode draw, importance
 sampling, sampled KRP rows, fiber gather, weighted gradient, AdaGrad step,
 CDF refresh) on the 1000^3 BF16 tensor, R = 50, B = 2048, Euclidean
-sampling. Inputs are synthetic (lognormal-scaled N(0,1) factors, 1e-2
+sampling. Before the timed region the gradient engine and CTA cap are
+chosen by cpd_autotune (timing the applicable candidates). Inputs are synthetic (lognormal-scaled N(0,1) factors, 1e-2
 noise), generated on the device; the three mode replicas (6 GB) are far
 larger than L2, so no flush is needed between iterations.
 
@@ -349,6 +350,9 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip cpd_autotune (by default the applicable engines and CTA caps are timed first, "
+                         "outside the timed region, and the fastest is used)")
     ap.add_argument("--serve-requests", type=int, default=SERVE["requests"])
     ap.add_argument("--serve-plain", type=int, default=16)
     ap.add_argument("--serve-active", type=int, default=32)
@@ -370,6 +374,12 @@ def main() -> None:
     X, A0 = make_inputs(w, rank, dev)
     kw = cfg_kwargs(w, rank, args.engine)
     stream = torch.cuda.Stream()
+    tuned = None
+    if not args.no_autotune and args.engine == "auto":
+        best, rate = C.cpd_autotune(C.make_config(**kw), X, [a.to(dev) for a in A0], iters=300, stream=stream)
+        tuned = {"engine": {1: "simt", 2: "tensor", 3: "cluster"}[best.engine], "max_ctas": best.max_ctas,
+                 "tuning_iters_per_s": rate}
+        kw["engine"], kw["max_ctas"] = tuned["engine"], tuned["max_ctas"]
     with torch.cuda.stream(stream):
         dec = C.Decomposition(X, [a.to(dev) for a in A0], stream=stream, **kw)
     desc = dec.describe()
@@ -456,6 +466,8 @@ def main() -> None:
         "clocks": clocks, "gpu_launches": launches_per_iter * args.steps,
         "e2e": e2e, "final_tol": tol, "launch": desc,
     }
+    if tuned:
+        line["autotuned"] = tuned
     if not args.no_serving and world == 1:
         try:
             line["serving"] = serve_bench(dev, args.serve_requests, args.serve_plain, args.serve_active)

@@ -356,6 +356,27 @@ cpd_status cpd_server_destroy(cpd_server *srv);
 cpd_status cpd_destroy(cpd_ctx *ctx);
 
 /*
+ * cpd_autotune -- choose the gradient engine and CTA cap for a problem by
+ * timing. The paper has no counterpart: the launch shape is this library's
+ * choice, and it fixes the summation order of the gradient, so it is made
+ * once, explicitly, and handed back as a configuration. Runs built from
+ * `best` are reproducible; only the choice itself depends on timing.
+ *  cfg, X, x_loc, A0, a0_loc: as for cpd_init. If cfg->engine != 0 only
+ *    that engine and cfg->max_ctas are timed; otherwise every applicable
+ *    engine (CUDA cores; per-CTA and cluster tensor cores for BF16 tensors
+ *    with R <= 64) with a few CTA caps.
+ *  iters: timed iterations per candidate (after iters / 4 warm-up ones).
+ *  best: receives cfg with engine and max_ctas set to the fastest candidate;
+ *  best_iters_per_s (may be NULL): its measured rate.
+ * Creates and destroys one context per candidate on `stream` (device-wide
+ * synchronisation). Errors: those of cpd_init for cfg itself; CPD_ECUDA if
+ * no candidate ran.
+ */
+cpd_status cpd_autotune(const cpd_config *cfg, const void *X, int x_loc, const void *const *A0,
+                        int a0_loc, int64_t iters, cpd_config *best, double *best_iters_per_s,
+                        void *stream);
+
+/*
  * Groups -- advance many decompositions with one gradient launch and one
  * update launch per iteration (batched execution of Alg. 4 / Alg. 5 over
  * independent problems; the paper runs one problem at a time). Every member

@@ -93,6 +93,8 @@ def _load():
         "cpd_server_wait": [P, ctypes.c_double],
         "cpd_server_destroy": [P],
         "cpd_grad_variance": [P, I32, P, P, P],
+        "cpd_autotune": [ctypes.POINTER(cpd_config), P, I32, P, I32, I64, ctypes.POINTER(cpd_config),
+                         ctypes.POINTER(ctypes.c_double), P],
         "cpd_group_create": [P, I32, P, ctypes.POINTER(P)],
         "cpd_group_iters": [P, I64, P],
         "cpd_group_destroy": [P],
@@ -318,6 +320,15 @@ def cpd_grad_variance(ctx, n: int, stream=None) -> tuple[float, float]:
     return v.value, m.value
 
 
+def cpd_autotune(cfg: cpd_config, X: torch.Tensor, A0: list, iters: int = 500, stream=None):
+    """(configuration with the fastest engine and CTA cap, its iterations/s)."""
+    best = cpd_config()
+    rate = ctypes.c_double()
+    _check(_lib.cpd_autotune(ctypes.byref(cfg), X.data_ptr(), _loc(X), _ptrs(A0), _loc(A0[0]), int(iters),
+                             ctypes.byref(best), ctypes.byref(rate), _stream(stream)))
+    return best, rate.value
+
+
 def cpd_group_create(ctxs: list, stream=None):
     """One grouped launch per iteration for all of `ctxs` (borrowed handles)."""
     arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
@@ -339,12 +350,18 @@ def cpd_group_destroy(grp) -> None:
 class Decomposition:
     """One context: owns nothing on the Python side but the handle."""
 
-    def __init__(self, X: torch.Tensor, A0: list, stream=None, **cfg):
-        self.dims = tuple(int(d) for d in cfg["dims"])
-        self.R, self.B = int(cfg["R"]), int(cfg["B"])
-        self.x_dtype = cfg.get("x_dtype", "bf16")
+    def __init__(self, X: torch.Tensor, A0: list, stream=None, config: cpd_config | None = None, **cfg):
+        if config is not None:     # a ready configuration (e.g. from cpd_autotune)
+            self.dims = tuple(int(config.dims[k]) for k in range(config.N))
+            self.R, self.B = int(config.R), int(config.B)
+            self.x_dtype = {v: k for k, v in XDT.items()}[config.x_dtype]
+            self.cfg = config
+        else:
+            self.dims = tuple(int(d) for d in cfg["dims"])
+            self.R, self.B = int(cfg["R"]), int(cfg["B"])
+            self.x_dtype = cfg.get("x_dtype", "bf16")
+            self.cfg = make_config(**cfg)
         self.fdtype = torch.float64 if self.x_dtype == "f64" else torch.float32
-        self.cfg = make_config(**cfg)
         A0 = [a.to(self.fdtype).contiguous() for a in A0]
         self.ctx = cpd_init(self.cfg, X.contiguous(), A0, stream)
 

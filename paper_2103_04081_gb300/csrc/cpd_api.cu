@@ -943,3 +943,63 @@ extern "C" cpd_status cpd_grad_variance(cpd_ctx *c, int32_t n, double *var, doub
     return c->fbytes == 8 ? variance_typed<double>(c, n, var, mean_norm2, s)
                           : variance_typed<float>(c, n, var, mean_norm2, s);
 }
+
+// ---------------------------------------------------------------------------
+// Autotuner: time candidate gradient engines and CTA caps on the caller's
+// problem and return the fastest configuration.
+// ---------------------------------------------------------------------------
+extern "C" cpd_status cpd_autotune(const cpd_config *cfg, const void *X, int x_loc, const void *const *A0,
+                                   int a0_loc, int64_t iters, cpd_config *best, double *best_iters_per_s,
+                                   void *stream)
+{
+    cpd_status st = validate(cfg);
+    if (st != CPD_OK) return st;
+    if (!X || !A0 || !best || iters < 1) return fail(CPD_EINVAL, "NULL argument or iters < 1");
+    int64_t imax = 0;
+    for (int k = 0; k < cfg->N; ++k) imax = std::max<int64_t>(imax, cfg->dims[k]);
+    const bool tc_ok = cfg->x_dtype == CPD_BF16 && tc_supported(cfg->R, 128);
+    const int cs = (int)((imax + 127) / 128);
+    std::vector<std::pair<int, int>> cand;   // (engine, max_ctas)
+    if (cfg->engine != 0) {
+        cand.push_back({cfg->engine, cfg->max_ctas});
+    } else {
+        for (int mc : {0, 16, 64}) cand.push_back({kEngineSimt, mc});
+        if (tc_ok) {
+            for (int mc : {0, 16, 64}) cand.push_back({kEngineTensor, mc});
+            if (cs <= 8)
+                for (int m : {0, 4, 8, 12}) cand.push_back({kEngineTensorCluster, m * cs});
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best_rate = -1.0;
+    cpd_config chosen = *cfg;
+    for (const auto &c : cand) {
+        cpd_config trial = *cfg;
+        trial.engine = c.first;
+        trial.max_ctas = c.second;
+        cpd_ctx *ctx = nullptr;
+        if (cpd_init(&trial, X, x_loc, A0, a0_loc, stream, &ctx) != CPD_OK) continue;   // not applicable
+        float ms = 0.f;
+        bool ok = cpd_sgd_iters(ctx, std::max<int64_t>(1, iters / 4), stream) == CPD_OK &&
+                  cudaEventRecord(e0, s) == cudaSuccess && cpd_sgd_iters(ctx, iters, stream) == CPD_OK &&
+                  cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                  cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        if (ok) ok = read_status(ctx, s) == CPD_OK;
+        cpd_destroy(ctx);
+        if (!ok || !(ms > 0.f)) continue;
+        const double rate = (double)iters / (ms * 1e-3);
+        if (rate > best_rate) {
+            best_rate = rate;
+            chosen = trial;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_rate < 0.0) return fail(CPD_ECUDA, "no candidate configuration ran");
+    *best = chosen;
+    if (best_iters_per_s) *best_iters_per_s = best_rate;
+    return CPD_OK;
+}
