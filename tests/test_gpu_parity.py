@@ -268,16 +268,20 @@ def test_profile_events(cpd):
 # teacher-forced steps (the oracle gathers only the B sampled fibers).
 # --------------------------------------------------------------------------
 
-def _full(cpd, orc, name, sampling, steps, warm, engine="auto"):
+def _full(cpd, orc, name, sampling, steps, warm, engine="auto", max_ctas=0, autotune=False):
     w = IN.WORKLOADS[name]
     dims, R, B, xdt = w["dims"], w["R"], w["B"], w["x_dtype"]
     A = IN.factors(dims, R, w["data_seed"], congruence=w["congruence"],
                    lognormal_rows=w["lognormal_rows"], device="cuda")
     X = IN.cp_tensor(A, w["noise"], w["data_seed"], xdt)
     A0 = IN.init_factors(dims, R, w["init_seed"])
-    dec = cpd.Decomposition(X, [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype=xdt,
-                            sampling=sampling, step=w["step"], eta=w.get("eta", 0.1),
-                            b=w.get("b", 1e-12), seed=w["sample_seed"], engine=engine)
+    kw = dict(dims=dims, R=R, B=B, x_dtype=xdt, sampling=sampling, step=w["step"], eta=w.get("eta", 0.1),
+              b=w.get("b", 1e-12), seed=w["sample_seed"], engine=engine, max_ctas=max_ctas)
+    if autotune:   # the launch the bench times on this GPU
+        best, _ = cpd.cpd_autotune(cpd.make_config(**kw), X, [a.cuda() for a in A0], iters=200)
+        dec = cpd.Decomposition(X, [a.cuda() for a in A0], config=best)
+    else:
+        dec = cpd.Decomposition(X, [a.cuda() for a in A0], **kw)
     xb = oracle_xbuf(X)
     del X
     desc = dec.describe()
@@ -299,8 +303,15 @@ def test_full_c3_120pow4_bf16(cpd, orc):
     _full(cpd, orc, "c3_120pow4_bf16", "euclidean", steps=4, warm=100)
 
 
-def test_full_c4_1000cube_bf16(cpd, orc):
-    _full(cpd, orc, "c4_1000cube_bf16", "euclidean", steps=3, warm=50)
+@pytest.mark.parametrize("max_ctas", [0, 96])     # heuristic tiling; the autotuned one (12 groups)
+def test_full_c4_1000cube_bf16(cpd, orc, max_ctas):
+    _full(cpd, orc, "c4_1000cube_bf16", "euclidean", steps=3, warm=50, max_ctas=max_ctas)
+
+
+def test_full_c4_autotuned_launch(cpd, orc):
+    """Whatever engine and CTA cap cpd_autotune picks here (the bench's
+    launch), teacher-forced against the oracle at full size."""
+    _full(cpd, orc, "c4_1000cube_bf16", "euclidean", steps=2, warm=20, autotune=True)
 
 
 EDGE = [
