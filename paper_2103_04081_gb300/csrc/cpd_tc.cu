@@ -6,21 +6,25 @@
 // weight s_f folded into each sampled KRP row),
 //   M_g = X_S,g Z'_S,g      (I_n x R)  -- tensor cores
 //   H_g = Z_S,g^T Z'_S,g    (R x R)    -- CUDA cores, FP32
-//   G_g = A^(n) H_g - M_g               -- CUDA cores, FP32, in the epilogue
+//   G_g = A^(n) H_g - M_g               -- tensor cores, same accumulator
 // and k_update sums the G_g in fixed order. The gathered fibers are BF16
 // (exact copies of the stored tensor). Z' is split into a BF16 pair
-// hi = bf16(z'), lo = bf16(z' - hi); both products accumulate into the same
-// FP32 accumulator, which keeps ~16 significant bits of Z' instead of 8.
+// hi = bf16(z'), lo = bf16(z' - hi), built negated so that the accumulator
+// receives -M_g; A^(n)'s rows and H_g are split the same way and added as
+// hi*hi + hi*lo + lo*hi. Each operand keeps ~16 significant bits.
 //
 // Per CTA (rb = 128 rows of A^(n), fb fibers, fb a multiple of 16):
 //   1. draw the fibers (warp-cooperative inverse-CDF search), p_f, s_f;
 //   2. 16-byte cp.async copies of rows [r0, r0+128) of every fiber straight
 //      into the no-swizzle MN-major operand layout (zero fill past I_n), and
-//      the CTA's rows of A^(n) (transposed) into shared memory;
+//      the CTA's rows of A^(n) into shared memory;
 //   3. z_f and the hi/lo B operands (K-major), zero-padded to N = 64;
-//   4. one thread issues 2*fb/16 tcgen05.mma (M=128, N=64, K=16) and commits
-//      to an mbarrier; meanwhile the CTA computes H_g;
-//   5. tcgen05.ld of M_g, G_g = A H_g - M_g, stored as the group's partial.
+//   4. one thread issues 2*fb/16 tcgen05.mma (M=128, N=64, K=16); meanwhile
+//      the CTA computes H_g;
+//   5. A^(n) rows (MN-major) and H_g (K-major) become bf16 hi/lo operands in
+//      the buffers H_g's formation freed; one thread issues the A H_g
+//      products and commits every product to an mbarrier;
+//   6. tcgen05.ld of G_g, stored as the group's partial.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
