@@ -190,7 +190,7 @@ def oracle_baseline(w: dict, X_dev: torch.Tensor, A0: list, budget_s: float) -> 
         assert st == O.OK, st
         it += 1
     el = time.time() - t1
-    return {"value": it / el, "unit": "iters/s", "cores": 1, "kind": "oracle",
+    return {"value": it / el, "unit": "iters/s", "cores": 1, "kind": "oracle", "iterations": it,
             "sample": f"{it} consecutive oracle iterations of the {w['name']} workload "
                       f"({el:.1f} s single-threaded FP64 C; host copy {prep:.1f} s not timed)"}
 
@@ -204,7 +204,9 @@ def run_reference(args, w: dict) -> None:
     budget = max(10.0, min(60.0, 1.0 * args.steps))
     base = oracle_baseline(w, X, A0, budget)
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "iters/s",
-            "n_gpus": args.gpus, "steps": None, "warmup": 1, "ms_per_step": 1000.0 / base["value"],
+            # a step is one oracle iteration; the number timed is bounded by a time
+            # budget (10-60 s of single-core CPU work) rather than by --steps
+            "n_gpus": args.gpus, "steps": base["iterations"], "warmup": 1, "ms_per_step": 1000.0 / base["value"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_block(w, "oracle"),
             "cpu_baseline": base,
@@ -346,6 +348,7 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tensor", "cluster"])
+    ap.add_argument("--max-ctas", type=int, default=0, help="CTA cap of the gradient launch (0: none)")
     ap.add_argument("--sampling", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -373,9 +376,10 @@ def main() -> None:
     dev = f"cuda:{local}"
     X, A0 = make_inputs(w, rank, dev)
     kw = cfg_kwargs(w, rank, args.engine)
+    kw["max_ctas"] = args.max_ctas
     stream = torch.cuda.Stream()
     tuned = None
-    if not args.no_autotune and args.engine == "auto":
+    if not args.no_autotune and args.engine == "auto" and args.max_ctas == 0:
         best, rate = C.cpd_autotune(C.make_config(**kw), X, [a.to(dev) for a in A0], iters=300, stream=stream)
         tuned = {"engine": {1: "simt", 2: "tensor", 3: "cluster"}[best.engine], "max_ctas": best.max_ctas,
                  "tuning_iters_per_s": rate}
