@@ -358,7 +358,7 @@ def main() -> None:
                          "outside the timed region, and the fastest is used)")
     ap.add_argument("--serve-requests", type=int, default=SERVE["requests"])
     ap.add_argument("--serve-plain", type=int, default=16)
-    ap.add_argument("--serve-active", type=int, default=32)
+    ap.add_argument("--serve-active", type=int, default=64)
     args = ap.parse_args()
 
     from paper_2103_04081_gb300 import inputs as IN

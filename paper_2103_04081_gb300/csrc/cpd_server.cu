@@ -8,8 +8,8 @@
 //      leverage sampling) share a lane whose rounds advance all members with
 //      grouped launches (one gradient and one update launch per iteration
 //      for the whole lane), then start every member's fit; members leave and
-//      join between rounds. Two lanes per class overlap one lane's host work
-//      with the other's GPU work;
+//      join between rounds. Four lanes per class overlap one lane's fits and
+//      host work with the others' iterations;
 //   3. steps the requests that cannot be grouped, each on its own stream:
 //      iterations up to its next check and an asynchronous fit, so every
 //      stream has a bounded amount of queued work and the streams overlap;
@@ -105,7 +105,7 @@ struct Lane {
     bool busy = false, changed = false;
 };
 
-constexpr int kLanesPerClass = 2;
+constexpr int kLanesPerClass = 4;
 
 struct cpd_server {
     cpd_server_config cfg{};
