@@ -1,0 +1,54 @@
+"""The seeded input recipes: deterministic, and with the shapes, ranges and
+structure the measurement plan states."""
+import numpy as np
+import torch
+
+from paper_2103_04081_gb300 import inputs as IN
+
+
+def test_serve_requests_recipe():
+    a = IN.serve_requests(512, rate=200.0, seed=0)
+    b = IN.serve_requests(512, rate=200.0, seed=0)
+    assert a == b                                           # deterministic
+    assert a[0]["arrival"] == 0.0
+    arr = np.array([q["arrival"] for q in a])
+    assert (np.diff(arr) >= 0).all()
+    gaps = np.diff(arr)
+    assert abs(gaps.mean() - 1 / 200.0) < 0.15 / 200.0      # Poisson process at 200/s
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.15        # exponential gaps: CV ~ 1
+    n3 = sum(q["N"] == 3 for q in a)
+    assert 200 < n3 < 312                                   # 3- or 4-way with equal odds
+    for q in a:
+        lo, hi = (50, 400) if q["N"] == 3 else (50, 90)
+        assert len(q["dims"]) == q["N"] and all(lo <= d <= hi for d in q["dims"])
+        assert 5 <= q["R"] <= 32
+        assert q["data_seed"] == q["init_seed"] == q["sample_seed"] == q["i"]
+    assert {q["R"] for q in a} == set(range(5, 33))          # every rank occurs
+
+
+def test_variance_study_factors():
+    d2 = IN.variance_study_factors("data2", I=30, R=4, seed=1)
+    d3 = IN.variance_study_factors("data3", I=30, R=4, seed=1)
+    for a, b in zip(d2, d3):
+        diff = (a != b)
+        assert int(diff.sum()) <= 1                          # Data III: one entry per factor ...
+        assert (b == 20.0).sum() == 1                        # ... set to 20
+    assert all(a.shape == (30, 4) for a in d2)
+
+
+def test_cp_tensor_matches_explicit_outer_products():
+    A = IN.factors((5, 4, 3), 2, seed=3)
+    X = IN.cp_tensor(A, 0.0, seed=3, x_dtype="f64").reshape(3, 4, 5).permute(2, 1, 0)
+    ref = torch.einsum("ir,jr,kr->ijk", *A)
+    assert torch.allclose(X, ref, rtol=0, atol=1e-12)       # column-major, first index fastest
+
+
+def test_noise_level_and_nonnegative_factors():
+    A = IN.factors((20, 18, 16), 3, seed=5, nonneg=True)
+    assert all((a >= 0).all() for a in A)
+    X0 = IN.cp_tensor(A, 0.0, seed=5, x_dtype="f64")
+    X = IN.cp_tensor(A, 0.1, seed=5, x_dtype="f64")
+    rel = float((X - X0).norm() / X0.norm())
+    assert abs(rel - 0.1) < 1e-9                             # noise scaled to nu ||X_true||
+    A0 = IN.init_factors((20, 18, 16), 3, seed=5, nonneg=True)
+    assert all((a >= 0).all() for a in A0)
