@@ -305,7 +305,8 @@ __global__ void __launch_bounds__(kThreads) k_update_group(const Problem<T> *__r
 // ---------------------------------------------------------------------------
 // Leverage scores (Def. 3) in the canonical order: one warp per Gram entry
 // (32 strided partials, shuffle-down tree), the last CTA factors the Gram
-// matrix (left-looking Cholesky, k ascending) into P.lev_L.
+// matrix (Cholesky; every entry takes its updates with k ascending) into
+// P.lev_L.
 // k_mode < 0: the mode of the current iteration; else that mode.
 // ---------------------------------------------------------------------------
 template <class T>
@@ -337,34 +338,51 @@ __global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mod
     if (!last_block(P.counters + 1)) return;
     double *Lm = P.lev_L, *inv = P.lev_L + R * R;
     __shared__ int s_bad;
-    if (threadIdx.x == 0) s_bad = 0;
-    // Small R: factor in place in shared memory (the lower triangle of the
-    // staged Gram matrix becomes L; same operations in the same order), then
-    // store L and the inverse pivots. Large R: through global memory.
+    __shared__ double s_col[256];  // column q of L below the diagonal, contiguous
+    // Right-looking order: once column q of L is final, every entry (i, j)
+    // with q < j <= i takes its update -L_iq L_jq at once. Each entry still
+    // receives the fmas of q = 0, 1, ..., j-1 in ascending order, as in the
+    // left-looking form, so L and the inverse pivots are the same bits; the
+    // dependent depth per column is one update, one square root and one
+    // division instead of a chain of j fmas. Small R: in place in shared
+    // memory, then L and the inverse pivots are stored. Large R: in place in
+    // P.lev_L (its upper triangle keeps Gram entries nobody reads).
     extern __shared__ __align__(16) double lev_dyn[];
     const bool in_smem = R <= kLevSmemR;
-    double *W = in_smem ? lev_dyn : Lm;          // L, and the Gram entries not yet replaced
+    double *W = in_smem ? lev_dyn : Lm;
     double *wi = in_smem ? lev_dyn + R * R : inv;
-    if (in_smem)
-        for (int e = threadIdx.x; e < R * R; e += blockDim.x) W[e] = __ldcg(g + e);
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) W[e] = __ldcg(g + e);
+    // pivot j: W_jj holds g_jj minus all its updates
+    auto pivot = [&](int j) {
+        const double gjj = __ldcg(g + j * R + j);
+        double d = W[j * R + j];
+        if (!(d > 0x1.0p-40 * gjj)) {
+            s_bad = 1;
+            d = 1.0;
+        }
+        W[j * R + j] = __dsqrt_rn(d);
+        wi[j] = __ddiv_rn(1.0, W[j * R + j]);
+    };
     __syncthreads();
-    for (int j = 0; j < R; ++j) {
-        if (threadIdx.x == 0) {
-            const double gjj = in_smem ? W[j * R + j] : __ldcg(g + j * R + j);
-            double d = gjj;
-            for (int q = 0; q < j; ++q) d = __fma_rn(-W[j * R + q], W[j * R + q], d);
-            if (!(d > 0x1.0p-40 * gjj)) {
-                s_bad = 1;
-                d = 1.0;
-            }
-            W[j * R + j] = __dsqrt_rn(d);
-            wi[j] = __ddiv_rn(1.0, W[j * R + j]);
+    if (threadIdx.x == 0) {
+        s_bad = 0;
+        pivot(0);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int q = 0; q < R; ++q) {
+        for (int i = q + 1 + threadIdx.x; i < R; i += blockDim.x) {
+            const double l = __dmul_rn(W[i * R + q], wi[q]);
+            W[i * R + q] = l;
+            s_col[i] = l;
         }
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) {
-            double v = in_smem ? W[i * R + j] : __ldcg(g + i * R + j);
-            for (int q = 0; q < j; ++q) v = __fma_rn(-W[i * R + q], W[j * R + q], v);
-            W[i * R + j] = __dmul_rn(v, wi[j]);
+        // rows to warps; warp 0 starts with row q+1, whose only entry (q+1, q+1)
+        // is thread 0's, which then factors pivot q+1 at once
+        for (int i = q + 1 + warp; i < R; i += nwarp) {
+            const double li = s_col[i];
+            for (int j = q + 1 + lane; j <= i; j += 32) W[i * R + j] = __fma_rn(-li, s_col[j], W[i * R + j]);
+            if (i == q + 1 && threadIdx.x == 0) pivot(q + 1);
         }
         __syncthreads();
     }
@@ -382,8 +400,14 @@ __global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mod
     }
 }
 
-// l_i = ||L^{-1} a_i||^2 by forward substitution (k ascending), then the CDF
-// of the mode in the last CTA; advance = 1 closes the iteration (t += 1).
+// l_i = ||L^{-1} a_i||^2 by forward substitution, then the CDF of the mode in
+// the last CTA; advance = 1 closes the iteration (t += 1). One warp per row in
+// right-looking order: lane j % 32 holds the partial v_j (v_j = a_ij at the
+// start); at step q the owner of v_q forms y_q = v_q / L_qq (times the inverse
+// pivot), every lane adds y_q^2 to the row's sum, and every v_j with j > q
+// takes its fma -L_jq y_q. Each v_j receives the fmas of q = 0, ..., j-1 in
+// ascending order and the sum the squares in ascending order, as in the
+// sequential form, so l_i is the same bits.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k_mode, int advance)
 {
@@ -392,27 +416,49 @@ __global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k
     const int R = P.R;
     const long long I = P.dims[k];
     const bool bad = __ldcg(P.lev_L + R * R + R + R * R) != 0.0;
-    // L and the inverse pivots in shared memory for small R (the dynamic
-    // buffer later serves as the last CTA's weight staging)
+    // small R: L transposed (lt[q*R + j] = L_jq, j > q) and the inverse pivots
+    // in shared memory (the buffer later serves as the last CTA's weight staging)
     extern __shared__ __align__(16) double lev_dyn[];
     const bool in_smem = R <= kLevSmemR;
     if (in_smem) {
-        for (int e = threadIdx.x; e < R * R + R; e += blockDim.x) lev_dyn[e] = __ldcg(P.lev_L + e);
+        for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+            const int q = e / R, j = e % R;
+            lev_dyn[e] = j > q ? __ldcg(P.lev_L + j * R + q) : 0.0;
+        }
+        for (int j = threadIdx.x; j < R; j += blockDim.x) lev_dyn[R * R + j] = __ldcg(P.lev_L + R * R + j);
         __syncthreads();
     }
-    const double *Lm = in_smem ? lev_dyn : P.lev_L, *inv = Lm + R * R;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const double *inv = in_smem ? lev_dyn + R * R : P.lev_L + R * R;
+    const int lane = threadIdx.x & 31;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (!bad && i < I) {
+        constexpr int kSlots = 256 / 32;  // v_j of j = lane + 32 s
         const T *a = P.A[k] + i * R;
-        double y[256];
-        double acc = 0.0;
-        for (int j = 0; j < R; ++j) {
-            double v = (double)a[j];
-            for (int q = 0; q < j; ++q) v = __fma_rn(-Lm[j * R + q], y[q], v);
-            y[j] = __dmul_rn(v, inv[j]);
-            acc = __fma_rn(y[j], y[j], acc);
+        double v[kSlots];
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+            const int j = lane + 32 * s;
+            v[s] = j < R ? (double)a[j] : 0.0;
         }
-        P.w[k][i] = acc;
+        double acc = 0.0;
+        for (int q = 0; q < R; ++q) {
+            const int qs = q >> 5;
+            double vq = 0.0;
+#pragma unroll
+            for (int s = 0; s < kSlots; ++s)
+                if (s == qs) vq = v[s];
+            const double y = __shfl_sync(0xffffffffu, __dmul_rn(vq, inv[q]), q & 31);
+            acc = __fma_rn(y, y, acc);
+#pragma unroll
+            for (int s = 0; s < kSlots; ++s) {
+                const int j = lane + 32 * s;
+                if (s >= qs && j > q && j < R) {
+                    const double l = in_smem ? lev_dyn[q * R + j] : __ldg(P.lev_L + (long long)j * R + q);
+                    v[s] = __fma_rn(-l, y, v[s]);
+                }
+            }
+        }
+        if (lane == 0) P.w[k][i] = acc;
     }
     if (!last_block(P.counters + 2)) return;
     __shared__ unsigned long long s_dist[2 * kThreads];
@@ -736,7 +782,7 @@ cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd, s
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         long long Imax = 0;
         for (int k = 0; k < P.N; ++k) Imax = P.dims[k] > Imax ? P.dims[k] : Imax;
-        k_lev_rows<T><<<(int)((Imax + kThreads - 1) / kThreads), kThreads, lev_smem_bytes(P.R), s>>>(P, -1, 1);
+        k_lev_rows<T><<<(int)((Imax * 32 + kThreads - 1) / kThreads), kThreads, lev_smem_bytes(P.R), s>>>(P, -1, 1);
         e = cudaGetLastError();
     }
     if (ev2) cudaEventRecord(ev2, s);
@@ -786,14 +832,13 @@ template <class T>
 cudaError_t launch_refresh_mode(const Problem<T> &P, int k, cudaStream_t s)
 {
     const long long I = P.dims[k];
-    const int grid = (int)((I + kThreads - 1) / kThreads);
     const int grid_rows = (int)((I * 32 + kThreads - 1) / kThreads);
     if (P.sampling == CPD_SAMPLE_LEVERAGE) {
         const int npairs = P.R * (P.R + 1) / 2;
         k_gram<T><<<(npairs + 7) / 8, kThreads, lev_smem_bytes(P.R), s>>>(P, k);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_lev_rows<T><<<grid, kThreads, lev_smem_bytes(P.R), s>>>(P, k, 0);
+        k_lev_rows<T><<<grid_rows, kThreads, lev_smem_bytes(P.R), s>>>(P, k, 0);
     } else {
         k_weights_euclid<T><<<grid_rows, kThreads, 0, s>>>(P, k);
     }
