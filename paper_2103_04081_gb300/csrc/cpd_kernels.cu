@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mod
             d = 1.0;
         }
         W[j * R + j] = __dsqrt_rn(d);
-        wi[j] = __ddiv_rn(1.0, W[j * R + j]);
+        wi[j] = __drcp_rn(W[j * R + j]);  // 1/L_jj, correctly rounded
     };
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -369,6 +369,7 @@ __global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mod
         pivot(0);
     }
     __syncthreads();
+    static_assert(kThreads >= 64, "the factorisation needs a pivot warp and an update warp");
     const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int q = 0; q < R; ++q) {
         for (int i = q + 1 + threadIdx.x; i < R; i += blockDim.x) {
@@ -377,12 +378,19 @@ __global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mod
             s_col[i] = l;
         }
         __syncthreads();
-        // rows to warps; warp 0 starts with row q+1, whose only entry (q+1, q+1)
-        // is thread 0's, which then factors pivot q+1 at once
-        for (int i = q + 1 + warp; i < R; i += nwarp) {
-            const double li = s_col[i];
-            for (int j = q + 1 + lane; j <= i; j += 32) W[i * R + j] = __fma_rn(-li, s_col[j], W[i * R + j]);
-            if (i == q + 1 && threadIdx.x == 0) pivot(q + 1);
+        // row q+1 has one entry left, the diagonal: thread 0 updates it and
+        // factors pivot q+1 while warps 1, 2, ... update rows q+2, q+3, ...
+        if (warp == 0) {
+            if (lane == 0 && q + 1 < R) {
+                const int d = (q + 1) * (R + 1);
+                W[d] = __fma_rn(-s_col[q + 1], s_col[q + 1], W[d]);
+                pivot(q + 1);
+            }
+        } else {
+            for (int i = q + 2 + (warp - 1); i < R; i += nwarp - 1) {
+                const double li = s_col[i];
+                for (int j = q + 1 + lane; j <= i; j += 32) W[i * R + j] = __fma_rn(-li, s_col[j], W[i * R + j]);
+            }
         }
         __syncthreads();
     }
