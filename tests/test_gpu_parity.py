@@ -321,6 +321,8 @@ EDGE = [
     ((1, 40, 30), 3, 16, "f32", "euclidean"),                  # a mode of size 1
     ((50, 40, 30), 4, 65536, "f32", "uniform"),                # B = 65536
     ((2, 3, 2), 1, 1, "f64", "euclidean"),                     # R = 1, B = 1
+    ((150, 120, 110), 100, 64, "f32", "leverage"),             # leverage with L past shared memory (R > 64)
+    ((260, 258, 257), 256, 32, "f32", "leverage"),             # leverage at R = 256: every lane slot in use
 ]
 
 
