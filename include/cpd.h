@@ -4,20 +4,20 @@
  * decomposition (BrawsCPD, Alg. 4, and AdawsCPD, Alg. 5, of Yu & Li,
  * arXiv 2103.04081).
  *
- * The problem (Sec. 2, Eq. certain_criterion): given a dense N-way tensor X
+ * The problem (Sec. 2, Eq. (5)): given a dense N-way tensor X
  * of size I_1 x ... x I_N and a rank R, find factor matrices A^(k) (I_k x R)
  * minimising 1/2 ||X - [[A^(1), ..., A^(N)]]||_F^2. One iteration draws a
  * mode n, draws B mode-n fibers by Euclidean- or leverage-based importance
  * sampling (Alg. 3, Lemmas 2 and 4), forms the sampled Khatri-Rao rows and
- * fibers (Alg. 1), the weighted stochastic gradient (Eq. gradient1) and
- * updates A^(n) with a fixed (Eq. proposed), decreasing (Thm 9) or
- * AdaGrad-style step (Eq. etaada / Eq. Aada).
+ * fibers (Alg. 1), the weighted stochastic gradient (Eq. (11)) and
+ * updates A^(n) with a fixed (Eq. (12)), decreasing (Thm 9) or
+ * AdaGrad-style step (Eq. (13a) / (13b)).
  *
  * Conventions for every entry point:
  *  - Indices are 0-based; the paper's are 1-based.
  *  - X is dense and column-major (first index fastest): entry
  *    (i_1, ..., i_N) sits at element offset sum_k i_k * prod_{m<k} I_m,
- *    the order in which Eq. map numbers the columns of each unfolding.
+ *    the order in which Eq. (2) numbers the columns of each unfolding.
  *  - A factor matrix A^(k) is row-major I_k x R (row i contiguous).
  *    Factors are double when x_dtype is CPD_F64 and float otherwise.
  *  - "stream" is a cudaStream_t passed as void* (NULL = legacy stream).
@@ -67,8 +67,8 @@ enum {
 
 /* Step rule (Sec. 3.2). */
 enum {
-    CPD_STEP_FIXED = 0,   /* A -= alpha G                      (Eq. proposed)   */
-    CPD_STEP_ADAGRAD = 1, /* S += G.^2; A -= eta G ./ sqrt(b + S) (Eq. etaada/Aada) */
+    CPD_STEP_FIXED = 0,   /* A -= alpha G                      (Eq. (12))   */
+    CPD_STEP_ADAGRAD = 1, /* S += G.^2; A -= eta G ./ sqrt(b + S) (Eq. (13a)/(13b)) */
     CPD_STEP_DECAY = 2    /* A -= beta / (t + gamma) G            (Thm 9)        */
 };
 
@@ -133,7 +133,7 @@ cpd_status cpd_init(const cpd_config *cfg, const void *X, int x_loc,
 
 /*
  * cpd_sgd_iters -- run `iters` iterations t, t+1, ... of Alg. 4 / Alg. 5
- * (mode draw, SKRP-ST-I of Alg. 3, Eq. gradient1, the configured step).
+ * (mode draw, SKRP-ST-I of Alg. 3, Eq. (11), the configured step).
  * Asynchronous: enqueued on `stream`; t advances by `iters` on the host
  * immediately. Device-side faults (non-finite values, degenerate
  * distributions) are recorded and reported by the next synchronising call.
@@ -171,7 +171,7 @@ cpd_status cpd_set_factors(cpd_ctx *ctx, const void *const *A, int loc, void *st
 
 /*
  * cpd_get_adagrad / cpd_set_adagrad -- the FP64 accumulators S^(k)
- * (I_k x R row-major) of Eq. etaada, for checkpoint and resume.
+ * (I_k x R row-major) of Eq. (13a), for checkpoint and resume.
  */
 cpd_status cpd_get_adagrad(cpd_ctx *ctx, double *const *S, int loc, void *stream);
 cpd_status cpd_set_adagrad(cpd_ctx *ctx, const double *const *S, int loc, void *stream);
@@ -181,8 +181,8 @@ cpd_status cpd_get_iteration(cpd_ctx *ctx, int64_t *t);
 cpd_status cpd_set_iteration(cpd_ctx *ctx, int64_t t);
 
 /*
- * cpd_last_sample -- the mini-batch of the most recent iteration (Eq. idx,
- * Eq. block_lev_prob): its mode n, idx (B x N row-major int32, column n set
+ * cpd_last_sample -- the mini-batch of the most recent iteration (Eq. (4),
+ * Eq. (10)): its mode n, idx (B x N row-major int32, column n set
  * to -1) and the fiber probabilities p_f (B doubles). Host outputs; any may
  * be NULL. Synchronises `stream`. Returns CPD_EINVAL before the first
  * iteration.
@@ -190,7 +190,7 @@ cpd_status cpd_set_iteration(cpd_ctx *ctx, int64_t t);
 cpd_status cpd_last_sample(cpd_ctx *ctx, int32_t *n, int32_t *idx, double *p, void *stream);
 
 /*
- * cpd_last_gradient -- G^(n) of the most recent iteration (Eq. gradient1),
+ * cpd_last_gradient -- G^(n) of the most recent iteration (Eq. (11)),
  * I_n x R row-major in the factor type, copied to host memory `G`.
  * Synchronises `stream`.
  */
@@ -205,7 +205,7 @@ cpd_status cpd_last_gradient(cpd_ctx *ctx, void *G, void *stream);
  *   mean_norm2 = || E[G] ||_F^2        = ||M||_F^2 / J_n^2   (may be NULL),
  * with S1 = sum_j ||r_j||^2 ||z_j||^2 / p_j and M = sum_j r_j z_j^T over all
  * J_n fibers j of the mode-n unfolding with p_j > 0, r_j = A^(n) z_j - x_j
- * (Eq. gradient1's normalisation: the paper's Table 1 is J_n^2 times var).
+ * (Eq. (11)'s normalisation: the paper's Table 1 is J_n^2 times var).
  * One pass over the mode-n replica: residuals in FP32, sums in FP64. A
  * deferred CDF rebuild is completed first. Synchronises `stream`.
  * Errors: CPD_EINVAL (NULL, n out of range, R > 64), CPD_EDEGENERATE,

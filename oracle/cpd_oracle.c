@@ -9,23 +9,24 @@
  * includes the other.
  *
  * Plain loops in FP64, one function per step of the method, in the order of
- * Alg. 3 (SKRP-ST-I) -> Alg. 1 (SKRP-ST) -> Eq. gradient1 -> Eq. proposed /
- * Eq. etaada-Aada (Alg. 4 / Alg. 5). Built with -ffp-contract=off: the only
+ * Alg. 3 (SKRP-ST-I) -> Alg. 1 (SKRP-ST) -> Eq. (11) -> Eq. (12) /
+ * Eq. (13a)-(13b) (Alg. 4 / Alg. 5). Built with -ffp-contract=off: the only
  * fused multiply-adds are the explicit fma() calls below.
  *
  * Readings of the paper that this file implements (each also listed in the
  * design notes):
- *  - Gradient normalisation: Eq. gradient1 is used literally,
+ *  - Gradient normalisation: Eq. (11) is used literally,
  *    G = (1/(B*J_n)) (A Z_S^T D Z_S - X_S D Z_S), D = diag(1/p_f); with
  *    uniform p = 1/J_n this is exactly Alg. 2's BrasCPD gradient (Sec. 2).
- *  - The garbled operand order of Eq. gradient1 is read as A (Z_S^T D Z_S)
+ *  - The garbled operand order of Eq. (11) is read as A (Z_S^T D Z_S)
  *    and X_S D Z_S (the only conforming products).
- *  - Leverage probabilities (Eq. krp_lev_prob, Lemma 2) are normalised by
+ *  - Leverage probabilities (Eq. (7), Lemma 2) are normalised by
  *    the computed sum of leverage scores W_k (= R at full column rank).
  *  - Per-factor probabilities are recomputed from the current factors at
  *    every draw (Alg. 4/5 take {p_k} as inputs; they are functions of A^(k)).
- *  - Sampling is with replacement (Alg. 3, Randsample(..., true, ...)).
- *  - AdaGrad accumulator includes the current gradient (Eq. etaada).
+ *  - Sampling is with replacement (Alg. 3 draws each index independently,
+ *    repeats allowed).
+ *  - AdaGrad accumulator includes the current gradient (Eq. (13a)).
  *  - Random numbers: Philox4x64-10 (Salmon et al., SC'11); the paper uses
  *    MATLAB randsample, so bit-exact sampling is defined against this
  *    generator and the canonical sampling arithmetic below.
@@ -53,7 +54,7 @@
  * Conventions (0-based in code, the paper is 1-based):
  *  - X dense, column-major (first index fastest): entry (i_0..i_{N-1}) at
  *    offset sum_k i_k S_k with S_k = prod_{m<k} I_m.  This is the order in
- *    which Eq. map enumerates the columns j of the mode-n unfolding.
+ *    which Eq. (2) enumerates the columns j of the mode-n unfolding.
  *  - A^(k) row-major I_k x R (double).
  *  - idx is B x N row-major; column n (the drawn mode) is left as -1.
  */
@@ -78,9 +79,9 @@ typedef struct {
     int32_t step;
     int32_t x_dtype;
     int64_t dims[ORC_MAXN];
-    double alpha;  /* fixed step (Eq. proposed)                 */
-    double eta;    /* AdaGrad eta (Eq. etaada)                  */
-    double b;      /* AdaGrad b   (Eq. etaada)                  */
+    double alpha;  /* fixed step (Eq. (12))                 */
+    double eta;    /* AdaGrad eta (Eq. (13a))                  */
+    double b;      /* AdaGrad b   (Eq. (13a))                  */
     double beta;   /* decreasing step alpha_t = beta/(t+gamma)  */
     double gamma;  /*   (Thm 9)                                 */
     uint64_t seed;
@@ -131,7 +132,7 @@ uint64_t orc_fiber_word(uint64_t seed, int64_t t, int64_t f, int k)
     return out[k & 3];
 }
 
-/* Alg. 4/5: "uniformly sample n from {1..N}" (0-based here). */
+/* Alg. 4/5: the mode of the iteration is drawn uniformly among the N modes (0-based here). */
 int32_t orc_mode_draw(uint64_t seed, int64_t t, int32_t N)
 {
     uint64_t ctr[4] = {(uint64_t)t, ~0ULL, 0, 1};
@@ -303,7 +304,7 @@ int orc_weights(int32_t sampling, const double *A, int64_t I, int32_t R, double 
 }
 
 /* ------------------------------------------------------------------ */
-/* Tensor access (Eq. map) and the sampled KRP (Alg. 1).                */
+/* Tensor access (Eq. (2)) and the sampled KRP (Alg. 1).                */
 /* ------------------------------------------------------------------ */
 
 static double x_at(const void *X, int32_t dtype, int64_t off)
@@ -318,7 +319,7 @@ static double x_at(const void *X, int32_t dtype, int64_t off)
     return (double)f;
 }
 
-/* Eq. map: column j of X_(n) for the multi-index idx (idx[n] ignored). */
+/* Eq. (2): column j of X_(n) for the multi-index idx (idx[n] ignored). */
 int64_t orc_unfold_col(int32_t N, const int64_t *dims, int32_t n, const int64_t *idx)
 {
     int64_t j = 0, Jp = 1;
@@ -331,7 +332,7 @@ int64_t orc_unfold_col(int32_t N, const int64_t *dims, int32_t n, const int64_t 
     return j;
 }
 
-/* Alg. 1 line "X^F = X(idx(:,1),..,:,..,idx(:,N))" for one fiber. */
+/* Alg. 1: the sampled fiber of X through the multi-index idx (mode n free), i.e. one column of X_(n). */
 void orc_gather_fiber(const void *X, int32_t dtype, int32_t N, const int64_t *dims,
                       int32_t n, const int64_t *idx, double *x)
 {
@@ -347,7 +348,7 @@ void orc_gather_fiber(const void *X, int32_t dtype, int32_t N, const int64_t *di
         x[i] = x_at(X, dtype, base + i * Sn);
 }
 
-/* Eq. index_map: Z^(n)(j,:) = Hadamard product of A^(k)(i_k,:), k != n. */
+/* Eq. (3): Z^(n)(j,:) = Hadamard product of A^(k)(i_k,:), k != n. */
 void orc_krp_row(int32_t N, int32_t R, int32_t n, const double *const *A,
                  const int64_t *idx, double *z)
 {
@@ -394,7 +395,7 @@ static int build_distributions(const orc_cfg *c, int32_t n, const double *const 
     return ORC_OK;
 }
 
-/* Eq. block_lev_prob: p_f as the product of the per-factor probabilities. */
+/* Eq. (10): p_f as the product of the per-factor probabilities. */
 static double fiber_probability(const orc_cfg *c, int32_t n, const int64_t *idx,
                                 uint64_t *const *cdf)
 {
@@ -408,7 +409,7 @@ static double fiber_probability(const orc_cfg *c, int32_t n, const int64_t *idx,
 }
 
 /*
- * Eq. gradient1 for a given mini-batch:
+ * Eq. (11) for a given mini-batch:
  *   H = Z_S^T D Z_S (R x R),  M = X_S D Z_S (I_n x R),
  *   G = (A H - M) / (B J_n),  D = diag(1/p_f).
  * Z_S is B x R row-major, X_S is I_n x B with fiber f contiguous (x_S + f*I_n).
@@ -440,8 +441,8 @@ void orc_gradient(int64_t In, int32_t R, int32_t B, int64_t Jn, const double *An
 }
 
 /*
- * Eq. proposed (fixed alpha, or the decreasing alpha_t = beta/(t+gamma) of
- * Thm 9) and Eq. etaada / Eq. Aada (AdaGrad-style step, accumulator S
+ * Eq. (12) (fixed alpha, or the decreasing alpha_t = beta/(t+gamma) of
+ * Thm 9) and Eq. (13a) / (13b) (AdaGrad-style step, accumulator S
  * including the current gradient).
  *
  * Nonnegative variant (Sec. 5, Table 5 / Fig. 2, generalised "as in" Fu et
@@ -513,7 +514,7 @@ int orc_gradient_for_batch(const orc_cfg *c, int32_t n, const int64_t *idx,
 
 /*
  * One iteration of BrawsCPD (Alg. 4) / AdawsCPD (Alg. 5) at iteration t:
- * draw n, draw the mini-batch (Alg. 3), form G (Eq. gradient1), update
+ * draw n, draw the mini-batch (Alg. 3), form G (Eq. (11)), update
  * A^(n). A and S (AdaGrad accumulators, may be NULL for the other steps)
  * are arrays of N pointers, updated in place. Optional outputs (NULL to
  * skip): n_out; idx_out (B x N, column n = -1); p_out (B); G_out (I_n x R).

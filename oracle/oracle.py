@@ -8,7 +8,7 @@ Every function marshals numpy arrays into the C oracle; the arithmetic lives
 in the C file, which cites the paper's sections step by step.
 
 Conventions: X is a dense tensor in column-major order (first index fastest,
-the order of Eq. map), passed as a numpy array in Fortran order or as a flat
+the order of Eq. (2)), passed as a numpy array in Fortran order or as a flat
 buffer together with ``dims``. Factors are float64 arrays of shape (I_k, R).
 Indices are 0-based.
 """
@@ -234,7 +234,7 @@ def krp_row(A: list, n: int, idx) -> np.ndarray:
 
 
 def gradient(An, Zs, Xs, p, Jn: int) -> np.ndarray:
-    """Eq. gradient1 with Xs given as (B, I_n) rows = fibers."""
+    """Eq. (11) with Xs given as (B, I_n) rows = fibers."""
     An, Zs, Xs, p = _f64(An), _f64(Zs), _f64(Xs), _f64(p)
     In, R = An.shape
     B = Zs.shape[0]
@@ -244,7 +244,7 @@ def gradient(An, Zs, Xs, p, Jn: int) -> np.ndarray:
 
 
 def update(cfg: Config, t: int, An: np.ndarray, Sn, G) -> None:
-    """In-place Eq. proposed / Eq. etaada-Aada on float64 arrays."""
+    """In-place Eq. (12) / Eq. (13a)-(13b) on float64 arrays."""
     G = _f64(G)
     c = cfg.c()
     S_ptr = _ptr(Sn) if Sn is not None else None

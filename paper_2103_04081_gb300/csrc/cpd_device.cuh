@@ -346,8 +346,8 @@ __device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 x)
 // ---------------------------------------------------------------------------
 // Sampling steps shared by both gradient engines.
 // ---------------------------------------------------------------------------
-// Draw the (N-1) x nf indices of this CTA's fibers (Alg. 3 "Randsample(I_k,
-// |F_n|, true, p_k)"). When the CDFs of the modes k != n fit the shared
+// Draw the (N-1) x nf indices of this CTA's fibers (Alg. 3: for every mode
+// k != n, |F_n| independent draws from p_k, with replacement). When the CDFs of the modes k != n fit the shared
 // buffer `stage` (cap entries) they are copied there first (one coalesced
 // pass) and searched there; otherwise the warp-cooperative multi-level
 // search runs on the global copies. Warps take 32-fiber chunks per mode.
@@ -416,7 +416,7 @@ __device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int
     }
 }
 
-// p_f = prod_{k != n, ascending} q_k(i_k) / Q_k in FP64 (Eq. block_lev_prob),
+// p_f = prod_{k != n, ascending} q_k(i_k) / Q_k in FP64 (Eq. (10)),
 // for the record of the last batch; uniform: q = 1, Q = I_k.
 template <class T>
 __device__ __forceinline__ double fiber_prob(const Problem<T> &P, int n, const int *row)
@@ -453,7 +453,7 @@ __device__ __forceinline__ double fiber_prob_staged(const Problem<T> &P, int n, 
     return p;
 }
 
-// The fiber's weight in Eq. gradient1, s_f = 1 / (B J_n p_f), in FP32 (the
+// The fiber's weight in Eq. (11), s_f = 1 / (B J_n p_f), in FP32 (the
 // gradient's own precision): (1/(B J_n)) prod_k Q_k / q_k(i_k).
 template <class T>
 __device__ __forceinline__ float fiber_weight(const Problem<T> &P, int n, const int *row)

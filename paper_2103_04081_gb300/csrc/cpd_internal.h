@@ -3,10 +3,10 @@
 // Device-resident state of one decomposition (all of it lives in HBM for the
 // whole run; the host only launches work):
 //   rep[k]   mode-k-major replica of X: fiber j of the mode-k unfolding
-//            (Eq. map numbering) is contiguous at rep[k] + j * ld[k], so
+//            (Eq. (2) numbering) is contiguous at rep[k] + j * ld[k], so
 //            every sampled fiber is one contiguous, 16-byte-aligned run.
 //   A[k]     factor A^(k), row-major I_k x R, in the factor type T.
-//   S[k]     AdaGrad accumulators (FP64), Eq. etaada.
+//   S[k]     AdaGrad accumulators (FP64), Eq. (13a).
 //   w[k]     FP64 row weights (squared row norms or leverage scores).
 //   cdf[k]   FP64 inclusive prefix sums of w[k] in the canonical order.
 //   t_dev    the iteration counter; every kernel derives the mode n and the

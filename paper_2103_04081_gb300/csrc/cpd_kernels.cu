@@ -2,11 +2,11 @@
 // full-tensor relative error of Sec. 5.2.
 //
 // Per iteration (the mode n and all draws follow from (seed, *t_dev)):
-//   k_grad_simt   sampling (Alg. 3) + sampled KRP rows (Alg. 1, Eq. index_map)
-//                 + fiber gather (Alg. 1, Eq. map) + weighted gradient partials
-//                 (Eq. gradient1), split over (row tile, fiber group) CTAs;
+//   k_grad_simt   sampling (Alg. 3) + sampled KRP rows (Alg. 1, Eq. (3))
+//                 + fiber gather (Alg. 1, Eq. (2)) + weighted gradient partials
+//                 (Eq. (11)), split over (row tile, fiber group) CTAs;
 //   k_update      fixed-order reduction of the partials, the step
-//                 (Eq. proposed / Thm 9 / Eq. etaada-Aada), new Euclidean row
+//                 (Eq. (12) / Thm 9 / Eq. (13a)-(13b)), new Euclidean row
 //                 weights, and -- in the last CTA to finish -- the canonical
 //                 CDF rebuild of mode n and t += 1;
 //   k_gram, k_lev_rows   (leverage sampling only) Gram + Cholesky and the new
@@ -71,7 +71,7 @@ __device__ __forceinline__ void gather_rows(const XT *__restrict__ rep, long lon
 //   res_if = s_f * (A^(n)(i,:) . z_f - x_f(i))          (one row of A Zs^T - Xs, weighted)
 //   part[gf][i][r] = sum_f res_if * z_f(r)
 // so that sum over fiber groups gives (A Zs^T D Zs - Xs D Zs) / (B J_n),
-// Eq. gradient1, without the cancellation of forming the two products apart.
+// Eq. (11), without the cancellation of forming the two products apart.
 // ---------------------------------------------------------------------------
 // `bid` is the CTA's index among the CTAs of this problem.
 template <class T, class XT>
@@ -111,7 +111,7 @@ __device__ __forceinline__ void grad_simt_body(const Problem<T> &P, int bid)
     }
     __syncthreads();
 
-    // 2. fiber column j (Eq. map), probability p_f and weight s_f
+    // 2. fiber column j (Eq. (2)), probability p_f and weight s_f
     for (int f = threadIdx.x; f < nf; f += blockDim.x) {
         const int *row = sidx + f * N;
         long long j = 0, Jp = 1;
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(kThreads) k_flush_dirty(const Problem<T> P)
     if (threadIdx.x == 0) *P.dirty = -1;
 }
 
-// p_f of the last batch (Eq. block_lev_prob, FP64) for its record; the
+// p_f of the last batch (Eq. (10), FP64) for its record; the
 // distributions of the modes k != n it used have not changed since.
 template <class T>
 __global__ void k_sample_probs(const Problem<T> P)
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(kThreads) k_fit(const Problem<T> P, double *pa
         for (long long j0 = group * F; j0 < J; j0 += ngroups * F) {
             const int nfib = (J - j0) < F ? (int)(J - j0) : F;
             __syncthreads();
-            if (threadIdx.x < nfib) {               // Eq. map, inverted once per fiber
+            if (threadIdx.x < nfib) {               // Eq. (2), inverted once per fiber
                 long long j = j0 + threadIdx.x;
                 for (int k = 1; k < N; ++k) {
                     sidx[threadIdx.x * (kMaxModes - 1) + k - 1] = (int)(j % P.dims[k]);
@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(kThreads) k_fold(const double *partials, int n
 // ---------------------------------------------------------------------------
 // Mode-n-major replica: X viewed as [I_post][I_n][I_pre] (column-major, i_pre
 // fastest) becomes [I_post][I_pre][ld] with i_n fastest, so fiber
-// j = i_pre + I_pre * i_post of the mode-n unfolding (Eq. map) is contiguous.
+// j = i_pre + I_pre * i_post of the mode-n unfolding (Eq. (2)) is contiguous.
 // 32 x 32 tiles through shared memory keep both sides coalesced.
 // ---------------------------------------------------------------------------
 template <class E>

@@ -1,7 +1,7 @@
 // Tensor-core gradient engine for BF16 tensors (sm_103a: tcgen05.mma with the
 // accumulator in tensor memory).
 //
-// Eq. gradient1 split over fiber groups g (the batch is cut into groups of fb
+// Eq. (11) split over fiber groups g (the batch is cut into groups of fb
 // fibers, one CTA per (row tile, group)): with Z'_S = D Z_S / (B J_n) (the
 // weight s_f folded into each sampled KRP row),
 //   M_g = X_S,g Z'_S,g      (I_n x R)  -- tensor cores
@@ -136,7 +136,7 @@ __device__ __forceinline__ void grad_tc_body(const Problem<float> &P, int bid)
     }
 
     trace_stamp(P.trace, 1, tr0);
-    // 1. draws (Alg. 3), fiber columns (Eq. map) and weights s_f; the CDFs are
+    // 1. draws (Alg. 3), fiber columns (Eq. (2)) and weights s_f; the CDFs are
     //    staged over the operand tiles, which are not written before the gather
     const long long cap = (long long)(L.zs - L.a) / 8;
     draw_indices(P, t, n, f0, nf, sidx, reinterpret_cast<unsigned long long *>(sA), cap,

@@ -1,6 +1,6 @@
 // Tensor-core gradient engine with thread-block clusters (sm_103a).
 //
-// Same arithmetic as the per-CTA engine (Eq. gradient1 as G_g = A H_g - M_g
+// Same arithmetic as the per-CTA engine (Eq. (11) as G_g = A H_g - M_g
 // per fiber group g, M_g = X_S,g Z'_S,g on tcgen05, Z' as a bf16 hi/lo pair),
 // but one cluster of cs CTAs handles one fiber group: CTA `rank` owns the
 // row tile [128 rank, 128 rank + 128) of A^(n) and a slice of fpc of the
@@ -8,7 +8,7 @@
 // once, in slices, and moved between the CTAs' shared memories by bulk async
 // copies (cp.async.bulk shared::cta -> shared::cluster) that complete on the
 // receiving CTA's mbarrier:
-//   - each CTA draws its fibers (Alg. 3), forms their columns (Eq. map),
+//   - each CTA draws its fibers (Alg. 3), forms their columns (Eq. (2)),
 //     weights and sampled KRP rows (Alg. 1), and the B operands of its slice,
 //     and sends the slice (B hi/lo, columns, weights) to every other CTA;
 //   - each CTA forms H over its own fibers; CTA d owns rows [d hr, d hr + hr)

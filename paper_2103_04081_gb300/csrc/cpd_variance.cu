@@ -2,11 +2,11 @@
 //
 // For mode n and the current factors, the mini-batch gradient of Eq.
 // gradient1 is G = (1/(B J_n)) sum_f (1/p_f) r_f z_f^T with r_f = A z_f - x_f
-// (the residual column of fiber f, Eq. map) and B draws i.i.d. from p. Its
+// (the residual column of fiber f, Eq. (2)) and B draws i.i.d. from p. Its
 // conditional moments are exact sums over all J_n fibers j:
 //   S1 = sum_j ||r_j||^2 ||z_j||^2 / p_j,   M = sum_j r_j z_j^T,
 //   E[G] = M / J_n,   E||G - E[G]||_F^2 = (S1 - ||M||_F^2) / (B J_n^2),
-// Thm 10 in the normalisation of Eq. gradient1 (the paper's form is J_n^2
+// Thm 10 in the normalisation of Eq. (11) (the paper's form is J_n^2
 // times this). Fibers with p_j = 0 are never drawn and are left out of both
 // sums.
 //
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) k_variance(const Problem<T> P, int n
         const int nf = (int)((j1 - jb) < kVarFib ? (j1 - jb) : kVarFib);
         __syncthreads();
         for (int f = warp; f < nf; f += kThreads / 32) {
-            // indices of fiber j (Eq. map: first mode fastest, mode n skipped)
+            // indices of fiber j (Eq. (2): first mode fastest, mode n skipped)
             int idx[kMaxModes];
             long long rest = jb + f;
             for (int k = 0; k < N; ++k) {

@@ -21,7 +21,7 @@ Recipe (the paper's own generator in Sec. 5.2 uses an unspecified
   seed (Sec. 5.2 "random initialization").
 
 Tensors are returned flat in column-major order (first index fastest), the
-order in which Eq. map enumerates the columns of every unfolding.
+order in which Eq. (2) enumerates the columns of every unfolding.
 """
 from __future__ import annotations
 

@@ -30,7 +30,7 @@ def oracle_variance(orc, dims, R, B, sampling, x_dtype, xbuf, A, n):
     for j in range(int(np.prod([dims[k] for k in others]))):
         idx = np.full((1, len(dims)), -1, dtype=np.int64)
         rest = j
-        for k in others:                        # Eq. map: first mode fastest
+        for k in others:                        # Eq. (2): first mode fastest
             idx[0, k] = rest % dims[k]
             rest //= dims[k]
         st, p, G = orc.gradient_for_batch(cfg1, n, idx, xbuf, A)

@@ -19,7 +19,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def explicit_Z(A, n):
-    """Z^(n) = A^(N) kr ... kr A^(n+1) kr A^(n-1) kr ... kr A^(1) (Eq. lsq_krp)."""
+    """Z^(n) = A^(N) kr ... kr A^(n+1) kr A^(n-1) kr ... kr A^(1) (Eq. (1))."""
     order = [k for k in reversed(range(len(A))) if k != n]
     Z = A[order[0]]
     for k in order[1:]:
@@ -71,7 +71,7 @@ def test_mode_draw_uniform(orc):
 
 
 # ------------------------------------------------------------------ #
-# Eq. map / Eq. index_map: unfolding and KRP rows                      #
+# Eq. (2) / Eq. (3): unfolding and KRP rows                      #
 # ------------------------------------------------------------------ #
 
 @pytest.mark.parametrize("dims", [(3, 4, 5), (2, 3, 4, 5)])
@@ -111,7 +111,7 @@ def test_krp_row_and_cp_unfolding(orc, dims):
 # ------------------------------------------------------------------ #
 
 def enumerate_batches(orc, cfg, n, X, A):
-    """(p_j, G_j) for every single-fiber batch (B = 1), column j of Eq. map."""
+    """(p_j, G_j) for every single-fiber batch (B = 1), column j of Eq. (2)."""
     dims = cfg.dims
     others = [range(d) if k != n else [-1] for k, d in enumerate(dims)]
     out = {}
@@ -137,7 +137,7 @@ def test_euclidean_probabilities(orc):
             j = orc.unfold_col(dims, n, tup)
             rows = [np.linalg.norm(A[k][tup[k]]) ** 2 for k in range(3) if k != n]
             fro = [np.linalg.norm(A[k]) ** 2 for k in range(3) if k != n]
-            # Eq. krp_euc_prob (up to the 2^-50 resolution of the fixed-point weights)
+            # Eq. (8) (up to the 2^-50 resolution of the fixed-point weights)
             assert ps[j][0] == pytest.approx(np.prod(rows) / np.prod(fro), rel=1e-12)
             # Lemma 3
             assert np.linalg.norm(Z[j]) ** 2 <= np.prod(rows) * (1 + 1e-14)
@@ -177,7 +177,7 @@ def test_leverage_probabilities_and_lemma1(orc):
         for tup in itertools.product(*others):
             j = orc.unfold_col(dims, n, tup)
             prod = np.prod([lev[k][tup[k]] for k in lev])
-            # Eq. krp_lev_prob with K = N-1 factors
+            # Eq. (7) with K = N-1 factors
             assert ps[j][0] == pytest.approx(prod / R ** 2, rel=1e-9)
             # Lemma 1
             assert lev_z[j] <= prod * (1 + 1e-9)
@@ -299,7 +299,7 @@ def test_unbiased_gradient_thm5(orc, dims, R, sampling):
         Jn = Z.shape[0]
         ps = enumerate_batches(orc, cfg, n, X, A)
         EG = sum(p * G for p, G in ps.values())
-        # Eq. gradient1 taken literally: E[G] = (A Z^T Z - X_(n) Z) / J_n.
+        # Eq. (11) taken literally: E[G] = (A Z^T Z - X_(n) Z) / J_n.
         np.testing.assert_allclose(EG, grad / Jn, rtol=1e-11, atol=1e-13 * np.abs(grad).max())
 
 
@@ -315,7 +315,7 @@ def test_variance_thm10_table1(orc, dims, R, sampling):
         var1 = sum(p * np.sum((G - EG) ** 2) for p, G in ps.values())
         rz = (Res ** 2).sum(0) * (Z ** 2).sum(1)         # ||R(:,j)||^2 ||Z(j,:)||^2
         pj = np.array([ps[j][0] for j in range(Jn)])
-        # Thm 10, rescaled by 1/J_n^2 for the literal Eq. gradient1.
+        # Thm 10, rescaled by 1/J_n^2 for the literal Eq. (11).
         thm10 = (np.sum(rz / pj) - np.sum(grad ** 2)) / Jn ** 2
         assert var1 == pytest.approx(thm10, rel=1e-10)
         # Table 1, per distribution, in closed form (B = 1).
@@ -353,7 +353,7 @@ def test_variance_thm10_table1(orc, dims, R, sampling):
 
 
 def test_uniform_reduces_to_brascpd(orc):
-    """p = 1/J_n turns Eq. gradient1 into Alg. 2's (1/B)(A Zs^T Zs - Xs Zs)."""
+    """p = 1/J_n turns Eq. (11) into Alg. 2's (1/B)(A Zs^T Zs - Xs Zs)."""
     dims, R, B = (4, 5, 6), 3, 7
     A, X = rand_problem(dims, R, 9)
     rng = np.random.default_rng(10)
@@ -392,7 +392,7 @@ def test_hand_worked_2x2x2(orc):
 
 
 def test_adagrad_closed_form(orc):
-    """Eq. etaada with b=0: step 1 moves by eta*sign(G); step 2 by eta*G2/sqrt(G1^2+G2^2)."""
+    """Eq. (13a) with b=0: step 1 moves by eta*sign(G); step 2 by eta*G2/sqrt(G1^2+G2^2)."""
     rng = np.random.default_rng(12)
     A0 = rng.standard_normal((6, 3))
     G1, G2 = rng.standard_normal((6, 3)), rng.standard_normal((6, 3))
@@ -429,7 +429,7 @@ def test_tol_against_planted_residual(orc):
 
 
 def test_zero_gradient_at_exact_solution(orc):
-    """Interpolation: with X = [[A]] every sampled gradient vanishes (Eq. gradient1)."""
+    """Interpolation: with X = [[A]] every sampled gradient vanishes (Eq. (11))."""
     dims, R = (6, 7, 8), 3
     A, _ = rand_problem(dims, R, 16, noise=0.0)
     X = np.asfortranarray(np.einsum("ir,jr,kr->ijk", *A))
