@@ -166,9 +166,27 @@ def cfg_kwargs(w: dict, rank: int, engine: str) -> dict:
                 seed=w["sample_seed"] + rank, engine=engine)
 
 
-def oracle_baseline(w: dict, X_dev: torch.Tensor, A0: list, budget_s: float) -> dict:
+def _oracle_rate(O, ocfg, xb, A0: list, budget_s: float, omp: bool) -> tuple[float, int, float]:
+    """Consecutive oracle iterations from A0 for about budget_s seconds."""
+    import numpy as np
+    A = [a.double().numpy().copy() for a in A0]
+    S = [np.zeros_like(a) for a in A]
+    O.run(ocfg, 0, 1, None, A, S, xbuf=xb, omp=omp)          # warm-up iteration
+    it, t1 = 0, time.time()
+    while time.time() - t1 < budget_s or it < 2:
+        st = O.run(ocfg, 1 + it, 1, None, A, S, xbuf=xb, omp=omp)
+        assert st == O.OK, st
+        it += 1
+    el = time.time() - t1
+    return it / el, it, el
+
+
+def oracle_baseline(w: dict, X_dev: torch.Tensor, A0: list, budget_s: float, all_cores: bool = True) -> dict:
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
-    consecutive iterations from the same initial factors for about budget_s seconds."""
+    consecutive iterations from the same initial factors for about budget_s
+    seconds, single-threaded (the checker build); then the timing-only build
+    of the same source that spreads the fiber gather and the contraction rows
+    over every host core."""
     import numpy as np
 
     from oracle import oracle as O
@@ -180,19 +198,102 @@ def oracle_baseline(w: dict, X_dev: torch.Tensor, A0: list, budget_s: float) -> 
     ocfg = O.Config(dims=tuple(w["dims"]), R=w["R"], B=w["B"], sampling=w["sampling"], step=w["step"],
                     x_dtype=w["x_dtype"], alpha=w.get("alpha", 0.1), eta=w.get("eta", 0.1),
                     b=w.get("b", 1e-12), seed=w["sample_seed"])
-    A = [a.double().numpy().copy() for a in A0]
-    S = [np.zeros_like(a) for a in A]
     prep = time.time() - t0
-    O.run(ocfg, 0, 1, None, A, S, xbuf=xb)          # warm-up iteration
-    it, t1 = 0, time.time()
-    while time.time() - t1 < budget_s or it < 2:
-        st = O.run(ocfg, 1 + it, 1, None, A, S, xbuf=xb)
-        assert st == O.OK, st
-        it += 1
-    el = time.time() - t1
-    return {"value": it / el, "unit": "iters/s", "cores": 1, "kind": "oracle", "iterations": it,
-            "sample": f"{it} consecutive oracle iterations of the {w['name']} workload "
-                      f"({el:.1f} s single-threaded FP64 C; host copy {prep:.1f} s not timed)"}
+    rate, it, el = _oracle_rate(O, ocfg, xb, A0, budget_s, omp=False)
+    ncores = os.cpu_count() or 1
+    out = {"value": rate, "unit": "iters/s", "cores": 1, "cores_used": 1, "cores_on_box": ncores,
+           "kind": "oracle", "iterations": it,
+           "sample": f"{it} consecutive oracle iterations of the {w['name']} workload "
+                     f"({el:.1f} s single-threaded FP64 C; host copy {prep:.1f} s not timed)"}
+    if all_cores:
+        os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
+        r2, it2, el2 = _oracle_rate(O, ocfg, xb, A0, budget_s / 2, omp=True)
+        out["all_cores"] = {"value": r2, "unit": "iters/s", "cores_used": int(os.environ["OMP_NUM_THREADS"]),
+                            "iterations": it2,
+                            "sample": f"{it2} consecutive iterations, {el2:.1f} s, the OpenMP build of the "
+                                      "same oracle source (fiber gather and contraction rows over the cores)"}
+    return out
+
+
+def error_vs_oracle(C, dev: str, stream, kw: dict, steps_tf: int = 3, free_iters: int = 500) -> dict:
+    """Error of the GPU path against the FP64 oracle, stated beside the numbers:
+    (1) at the bench workload, teacher-forced iterations in the bench's launch
+    configuration (the oracle starts from the GPU's state at t): indices and
+    probabilities bit-exact, the gradient's relative Frobenius error and its
+    largest row error against the row's componentwise scale, the updated
+    factor's largest relative row error; (2) on the 120^4 BF16 workload (the
+    tensor-core path), free runs of both from the same start for free_iters
+    iterations, compared by the oracle's Tol routine."""
+    import math
+
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2103_04081_gb300 import inputs as IN
+    res = {}
+    w = dict(IN.WORKLOADS[DEFAULT_WORKLOAD])
+    X, A0 = make_inputs(w, 0, dev)
+    with torch.cuda.stream(stream):
+        dec = C.Decomposition(X, [a.to(dev) for a in A0], stream=stream, **kw)
+    xb = X.cpu().view(torch.int16).numpy().view(np.uint16) if X.dtype == torch.bfloat16 else X.cpu().numpy()
+    del X
+    dec.sgd_iters(50, stream)
+    ocfg = O.Config(dims=tuple(w["dims"]), R=w["R"], B=w["B"], sampling=w["sampling"], step=w["step"],
+                    x_dtype=w["x_dtype"], eta=w["eta"], b=w["b"], seed=w["sample_seed"])
+    worst = {"G_frobenius": 0.0, "G_row_scaled": 0.0, "A_row": 0.0}
+    exact = True
+    for _ in range(steps_tf):
+        t = dec.t
+        A = [a.double().numpy().copy() for a in dec.factors("cpu", stream)]
+        Ap = [a.copy() for a in A]
+        S = [s.numpy().copy() for s in dec.adagrad()]
+        out = O.step(ocfg, t, None, A, S, xbuf=xb)
+        dec.sgd_iters(1, stream)
+        n, idx, p = dec.last_sample()
+        _, G = dec.last_gradient()
+        exact = exact and n == out["n"] and bool(np.array_equal(idx.numpy().astype(np.int64), out["idx"])) \
+            and bool(np.array_equal(p.numpy(), out["p"]))
+        Gg = G.numpy().astype(np.float64)
+        sc = O.grad_row_scale(w["dims"], n, out["idx"], out["p"], Ap, xb, w["x_dtype"], w["B"])
+        An = dec.factors("cpu", stream)[n].double().numpy()
+        worst["G_frobenius"] = max(worst["G_frobenius"],
+                                   float(np.linalg.norm(Gg - out["G"]) / np.linalg.norm(out["G"])))
+        worst["G_row_scaled"] = max(worst["G_row_scaled"],
+                                    float(np.max(np.linalg.norm(Gg - out["G"], axis=1) / sc)))
+        den = np.maximum(np.linalg.norm(A[n], axis=1), np.linalg.norm(Ap[n], axis=1))
+        worst["A_row"] = max(worst["A_row"], float(np.max(np.linalg.norm(An - A[n], axis=1) / den)))
+    res["teacher_forced"] = {"workload": DEFAULT_WORKLOAD, "engine": dec.describe()["engine"],
+                             "iterations": steps_tf, "indices_and_probabilities_bit_exact": exact, **worst}
+    dec.close()
+    del xb
+    # free runs on the 120^4 BF16 workload
+    w3 = dict(IN.WORKLOADS["c3_120pow4_bf16"])
+    A3 = IN.factors(w3["dims"], w3["R"], w3["data_seed"], device=dev)
+    X3 = IN.cp_tensor(A3, w3["noise"], w3["data_seed"], "bf16")
+    A30 = IN.init_factors(w3["dims"], w3["R"], w3["init_seed"])
+    with torch.cuda.stream(stream):
+        d3 = C.Decomposition(X3, [a.to(dev) for a in A30], stream=stream, dims=w3["dims"], R=w3["R"],
+                             B=w3["B"], x_dtype="bf16", sampling=w3["sampling"], step=w3["step"],
+                             eta=w3["eta"], b=w3["b"], seed=w3["sample_seed"])
+    xb3 = X3.cpu().view(torch.int16).numpy().view(np.uint16)
+    del X3
+    d3.sgd_iters(free_iters, stream)
+    Ag = [a.double().numpy() for a in d3.factors("cpu", stream)]
+    eng3 = d3.describe()["engine"]
+    d3.close()
+    oc3 = O.Config(dims=tuple(w3["dims"]), R=w3["R"], B=w3["B"], sampling=w3["sampling"], step=w3["step"],
+                   x_dtype="bf16", eta=w3["eta"], b=w3["b"], seed=w3["sample_seed"])
+    Ao = [a.double().numpy().copy() for a in A30]
+    So = [np.zeros_like(a) for a in Ao]
+    assert O.run(oc3, 0, free_iters, None, Ao, So, xbuf=xb3, omp=True) == O.OK
+    tg, _ = O.tol_blas(xb3, w3["dims"], Ag, "bf16")
+    to, _ = O.tol_blas(xb3, w3["dims"], Ao, "bf16")
+    res["free_run"] = {"workload": "c3_120pow4_bf16", "engine": eng3, "iterations": free_iters,
+                       "fit_gpu": 1 - math.sqrt(tg), "fit_oracle": 1 - math.sqrt(to),
+                       "fit_diff": (1 - math.sqrt(tg)) - (1 - math.sqrt(to)),
+                       "factor_drift": max(float(np.linalg.norm(a - b) / np.linalg.norm(b))
+                                           for a, b in zip(Ag, Ao))}
+    return res
 
 
 def run_reference(args, w: dict) -> None:
@@ -202,7 +303,7 @@ def run_reference(args, w: dict) -> None:
     dev = f"cuda:{local}" if torch.cuda.is_available() else "cpu"
     X, A0 = make_inputs(w, 0, dev)
     budget = max(10.0, min(60.0, 1.0 * args.steps))
-    base = oracle_baseline(w, X, A0, budget)
+    base = oracle_baseline(w, X, A0, budget, all_cores=False)
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "iters/s",
             # a step is one oracle iteration; the number timed is bounded by a time
             # budget (10-60 s of single-core CPU work) rather than by --steps
@@ -390,8 +491,10 @@ def main() -> None:
     engine = desc["engine"]
     launches_per_iter = 2 + (2 if w["sampling"] == "leverage" else 0)
 
-    # warm-up (W iterations), then exactly K timed iterations
+    # warm-up (W iterations), the graphs a K-iteration call replays captured
+    # ahead (nothing runs), then exactly K timed iterations
     dec.sgd_iters(args.warmup, stream)
+    C.cpd_prepare(dec.ctx, args.steps, stream)
     C.cpd_sync(dec.ctx, stream)
     if dist:
         dist.barrier()
@@ -481,6 +584,12 @@ def main() -> None:
         Xc, A0c = make_inputs(w, 0, dev)
         line["cpu_baseline"] = oracle_baseline(w, Xc, A0c, args.cpu_budget)
         del Xc
+        torch.cuda.empty_cache()
+        if w["name"] == DEFAULT_WORKLOAD:
+            try:
+                line["error_vs_oracle"] = error_vs_oracle(C, dev, stream, kw)
+            except Exception as exc:  # reported, not hidden
+                line["error_vs_oracle"] = {"error": repr(exc)}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

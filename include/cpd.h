@@ -143,6 +143,16 @@ cpd_status cpd_init(const cpd_config *cfg, const void *X, int x_loc,
 cpd_status cpd_sgd_iters(cpd_ctx *ctx, int64_t iters, void *stream);
 
 /*
+ * cpd_prepare -- capture ahead of time the CUDA graphs that a later
+ * cpd_sgd_iters(ctx, iters, stream) replays (chunks of 32 iterations and one
+ * chunk per set bit of iters mod 32), so that call pays no capture. Runs no
+ * iteration and leaves t unchanged. The paper has no counterpart: graph
+ * capture is how this library keeps launch overhead off the iteration loop.
+ * Errors: CPD_EINVAL (NULL context, iters < 0), CPD_ECUDA.
+ */
+cpd_status cpd_prepare(cpd_ctx *ctx, int64_t iters, void *stream);
+
+/*
  * cpd_fit -- relative error of Sec. 5.2, Tol = ||[[A]] - X||_F^2 / ||X||_F^2,
  * by one pass over the whole tensor with FP64 accumulation; fit = 1 - sqrt(Tol).
  * Either output pointer may be NULL. Synchronises `stream`; returns a
@@ -274,11 +284,13 @@ cpd_status cpd_describe(cpd_ctx *ctx, char *buf, size_t len);
  * Limit: at most 1,048,576 mode-1 fibers (I_2 * ... * I_N <= 2^20); larger
  * tensors return CPD_EINVAL (use cpd_fit). Scratch: a 1 MiB array that the
  * library image places in the memory of every GPU that loads it, held until
- * the process exits. The first call on each device looks up that array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture on the device. Every call reuses the same array, so calls
- * that overlap on the GPU (e.g. on two streams at once) race: serialise
- * them. Each call overwrites every scratch slot it reads.
+ * the process exits. Every call looks up that array's device address on the
+ * calling device (cudaGetSymbolAddress); the first call on a device may load
+ * the library's device code, so make it before any stream capture on the
+ * device. Every call reuses the same array, so calls that overlap on the GPU
+ * (e.g. on two streams at once) race: serialise them. Each call overwrites
+ * every scratch slot it reads. A tensor with ||X|| = 0 has no relative
+ * error: tol_out then receives NaN (cpd_init rejects such a tensor).
  */
 cpd_status cpd_tol_noalloc(int32_t N, const int64_t *dims, int32_t R, int32_t x_dtype,
                            const void *X, const void *const *A, double *tol_out, void *stream);

@@ -8,6 +8,12 @@
  * path shares no code, header, table or helper with it, and neither side
  * includes the other.
  *
+ * A second build of this same file with -DORC_OMP -fopenmp (liboracle_omp.so)
+ * spreads the fiber gather and the rows of the contraction over the host's
+ * cores, for CPU-baseline timing only. Its pragmas split independent loop
+ * iterations and leave every sum in the order below, so both builds give the
+ * same bits; the single-threaded build is the checker.
+ *
  * Plain loops in FP64, one function per step of the method, in the order of
  * Alg. 3 (SKRP-ST-I) -> Alg. 1 (SKRP-ST) -> Eq. (11) -> Eq. (12) /
  * Eq. (13a)-(13b) (Alg. 4 / Alg. 5). Built with -ffp-contract=off: the only
@@ -419,16 +425,26 @@ void orc_gradient(int64_t In, int32_t R, int32_t B, int64_t Jn, const double *An
 {
     double *H = (double *)calloc((size_t)R * R, sizeof(double));
     double *M = (double *)calloc((size_t)In * R, sizeof(double));
+    /* every entry of H and M sums its terms over f = 0, 1, ..., B-1 in order */
     for (int32_t f = 0; f < B; ++f) {
         double d = 1.0 / p[f];
         for (int32_t r = 0; r < R; ++r)
             for (int32_t s = 0; s < R; ++s)
                 H[r * R + s] += Zs[f * R + r] * d * Zs[f * R + s];
-        for (int64_t i = 0; i < In; ++i)
+    }
+#ifdef ORC_OMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i = 0; i < In; ++i)
+        for (int32_t f = 0; f < B; ++f) {
+            double d = 1.0 / p[f];
             for (int32_t r = 0; r < R; ++r)
                 M[i * R + r] += Xs[f * In + i] * d * Zs[f * R + r];
-    }
+        }
     double scale = 1.0 / ((double)B * (double)Jn);
+#ifdef ORC_OMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t i = 0; i < In; ++i)
         for (int32_t r = 0; r < R; ++r) {
             double ah = 0.0;
@@ -551,6 +567,9 @@ int orc_step(const orc_cfg *c, int64_t t, const void *X, double *const *A,
         }
         double *Zs = (double *)malloc((size_t)B * R * sizeof(double));
         double *Xs = (double *)malloc((size_t)B * In * sizeof(double));
+#ifdef ORC_OMP
+#pragma omp parallel for schedule(static)
+#endif
         for (int32_t f = 0; f < B; ++f) {
             const int64_t *row = idx + (int64_t)f * N;
             p[f] = fiber_probability(c, n, row, cdf);

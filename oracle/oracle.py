@@ -33,23 +33,34 @@ CONSTRAINT = {"none": 0, "nonneg": 1}
 OK, EINVAL, EDEGENERATE = 0, 1, 6
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-ffp-contract=off: no implicit FMA)."""
-    if force or not os.path.exists(LIB_PATH) or (
-            os.path.getmtime(LIB_PATH) < os.path.getmtime(_SRC)):
-        tmp = LIB_PATH + f".tmp{os.getpid()}"
+OMP_LIB_PATH = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc (-ffp-contract=off: no implicit FMA). With
+    omp, the timing-only all-cores build of the same source."""
+    path = OMP_LIB_PATH if omp else LIB_PATH
+    if force or not os.path.exists(path) or (os.path.getmtime(path) < os.path.getmtime(_SRC)):
+        tmp = path + f".tmp{os.getpid()}"
+        extra = ["-DORC_OMP", "-fopenmp"] if omp else []
         subprocess.check_call([
-            "gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fPIC",
+            "gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fPIC", *extra,
             "-shared", _SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+        os.replace(tmp, path)
+    return path
 
 
 _lib = None
+_lib_omp = None
 
 
-def lib() -> ctypes.CDLL:
-    global _lib
+def lib(omp: bool = False) -> ctypes.CDLL:
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            _lib_omp = ctypes.CDLL(build(omp=True))
+            _declare(_lib_omp)
+        return _lib_omp
     if _lib is None:
         _lib = ctypes.CDLL(build())
         _declare(_lib)
@@ -282,13 +293,15 @@ def step(cfg: Config, t: int, X, A: list, S: list | None = None, xbuf=None) -> d
             "G": G[: cfg.dims[n.value]].copy()}
 
 
-def run(cfg: Config, t0: int, T: int, X, A: list, S: list | None = None, xbuf=None) -> int:
+def run(cfg: Config, t0: int, T: int, X, A: list, S: list | None = None, xbuf=None,
+        omp: bool = False) -> int:
+    """T iterations from t0 (A, S updated in place); omp: the all-cores build."""
     for a in A:
         assert a.dtype == np.float64 and a.flags.c_contiguous
     c = cfg.c()
     buf = x_buffer(X, cfg.x_dtype) if xbuf is None else xbuf
     S_arr = _ptr_array(S) if S is not None else None
-    return lib().orc_run(ctypes.byref(c), t0, T, _ptr(buf), _ptr_array(A), S_arr)
+    return lib(omp).orc_run(ctypes.byref(c), t0, T, _ptr(buf), _ptr_array(A), S_arr)
 
 
 def tol(X, A: list, x_dtype: str = "f64", dims=None) -> tuple[float, float]:
@@ -304,3 +317,67 @@ def tol(X, A: list, x_dtype: str = "f64", dims=None) -> tuple[float, float]:
     v = lib().orc_tol(len(d), _ptr(d), A[0].shape[1], _ptr(buf), XDT[x_dtype],
                       _ptr_array(A), ctypes.byref(xx))
     return v, xx.value
+
+
+def stored_values(xbuf: np.ndarray, x_dtype: str) -> np.ndarray:
+    """Exact float64 values of a flat buffer of stored tensor entries: bf16 bit
+    patterns are the upper half of an IEEE binary32 word, f32 and f64 widen
+    exactly."""
+    if x_dtype == "bf16":
+        return (np.asarray(xbuf, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    return np.asarray(xbuf).astype(np.float64)
+
+
+def tol_blas(xbuf: np.ndarray, dims, A: list, x_dtype: str = "f64",
+             chunk_cols: int = 1 << 15) -> tuple[float, float]:
+    """(Tol, ||X||^2) of Sec. 5.2, the same definition as ``tol`` (a direct
+    residual sum over every entry, FP64), taken over the columns of the mode-1
+    unfolding in chunks so that large tensors finish in seconds:
+    X_(1)(:, j) - A^(1) z_j with z_j = the Hadamard product of the rows
+    A^(k)(i_k, :), k >= 2 (Eq. (3)), j numbered by Eq. (2). The product
+    A^(1) z_j is a library matrix multiply."""
+    A = [_f64(a) for a in A]
+    dims = [int(d) for d in dims]
+    I0 = dims[0]
+    J = int(np.prod(dims[1:]))
+    res = xx = 0.0
+    for j0 in range(0, J, chunk_cols):
+        j1 = min(J, j0 + chunk_cols)
+        j = np.arange(j0, j1, dtype=np.int64)
+        Z = np.ones((j1 - j0, A[0].shape[1]))
+        for k in range(1, len(dims)):
+            Z *= A[k][j % dims[k]]
+            j //= dims[k]
+        x = stored_values(xbuf[j0 * I0: j1 * I0], x_dtype).reshape(j1 - j0, I0)
+        d = x - Z @ A[0].T
+        res += float(np.einsum("ij,ij->", d, d))
+        xx += float(np.einsum("ij,ij->", x, x))
+    return res / xx, xx
+
+
+def grad_row_scale(dims, n: int, idx, p, A: list, xbuf: np.ndarray, x_dtype: str, B: int) -> np.ndarray:
+    """Componentwise size of each row of the mini-batch gradient of Eq. (11):
+        scale_i = || |A^(n)_i| |H| ||  +  || sum_f s_f |x_f(i)| |z_f| ||,
+    |H| = sum_f s_f |z_f| |z_f|^T, s_f = 1 / (B J_n p_f), z_f the sampled KRP
+    row (Eq. (3)) and x_f the sampled fiber (Eq. (2)) of batch entry f. These
+    are the sizes of the two products whose difference is G_i, against which
+    the rounding error of any evaluation of G_i is measured. idx is B x N
+    (column n ignored), A the factors the batch was drawn from."""
+    N = len(dims)
+    strides = np.cumprod([1] + [int(d) for d in dims[:-1]])
+    Jn = float(np.prod([float(d) for k, d in enumerate(dims) if k != n]))
+    s = 1.0 / (B * Jn * np.asarray(p, dtype=np.float64))
+    Z = np.ones((B, A[0].shape[1]))
+    base = np.zeros(B, dtype=np.int64)
+    for k in range(N):
+        if k == n:
+            continue
+        ik = np.asarray(idx[:, k], dtype=np.int64)
+        Z *= np.abs(A[k][ik])
+        base += ik * strides[k]
+    off = base[None, :] + np.arange(int(dims[n]), dtype=np.int64)[:, None] * strides[n]
+    Xs = np.abs(stored_values(xbuf[off.ravel()], x_dtype).reshape(int(dims[n]), B))
+    H = (Z * s[:, None]).T @ Z
+    t1 = np.linalg.norm(np.abs(A[n]) @ H, axis=1)
+    t2 = np.linalg.norm(Xs @ (Z * s[:, None]), axis=1)
+    return t1 + t2

@@ -68,6 +68,7 @@ def _load():
     sig = {
         "cpd_init": [ctypes.POINTER(cpd_config), P, I32, P, I32, P, ctypes.POINTER(P)],
         "cpd_sgd_iters": [P, I64, P],
+        "cpd_prepare": [P, I64, P],
         "cpd_fit": [P, P, P, P],
         "cpd_fit_start": [P, P],
         "cpd_fit_poll": [P, P, P],
@@ -164,6 +165,10 @@ def cpd_init(cfg: cpd_config, X: torch.Tensor, A0: list, stream=None) -> ctypes.
 
 def cpd_sgd_iters(ctx, iters: int, stream=None) -> None:
     _check(_lib.cpd_sgd_iters(ctx, int(iters), _stream(stream)))
+
+
+def cpd_prepare(ctx, iters: int, stream=None) -> None:
+    _check(_lib.cpd_prepare(ctx, int(iters), _stream(stream)))
 
 
 def cpd_fit(ctx, stream=None) -> tuple[float, float]:

@@ -1,9 +1,10 @@
 // C ABI of libcpd (declared and documented in include/cpd.h).
 //
 // The context owns every device buffer of one decomposition. Iterations are
-// device-driven (mode and draws follow from the device counter t), so a
-// fixed chunk of iterations is captured once into a CUDA graph and replayed;
-// a remainder runs as plain launches.
+// device-driven (mode and draws follow from the device counter t), so chunks
+// of 32, 16, 8, 4, 2 and 1 iterations are each captured once into a CUDA
+// graph and replayed: any iteration count runs as at most one replay per
+// chunk size beyond the whole 32-iteration chunks.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,6 +40,7 @@ static cpd_status cuda_fail(cudaError_t e, const char *what)
     } while (0)
 
 static constexpr int kGraphChunk = 32;
+static constexpr int kGraphSizes = 6;   // chunks of 32, 16, 8, 4, 2, 1 iterations
 static constexpr int kProfSlots = 8192;
 
 struct cpd_ctx {
@@ -56,8 +58,8 @@ struct cpd_ctx {
     double *fit_partials = nullptr, *fit_out = nullptr;
     double xnorm2 = 0.0;
     int64_t imax = 0;
-    // graph replay of kGraphChunk iterations
-    cudaGraphExec_t graph = nullptr;
+    // graph replay: graph[q] runs kGraphChunk >> q iterations
+    cudaGraphExec_t graph[kGraphSizes] = {};
     cudaStream_t graph_stream = nullptr;
     // profiling
     bool profiling = false;
@@ -95,9 +97,18 @@ static cudaError_t dmalloc(cpd_ctx *c, void **p, size_t bytes)
     return e;
 }
 
+static void drop_graphs(cudaGraphExec_t *g, int n)
+{
+    for (int q = 0; q < n; ++q)
+        if (g[q]) {
+            cudaGraphExecDestroy(g[q]);
+            g[q] = nullptr;
+        }
+}
+
 static void free_all(cpd_ctx *c)
 {
-    if (c->graph) cudaGraphExecDestroy(c->graph);
+    drop_graphs(c->graph, kGraphSizes);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->fit_event) cudaEventDestroy(c->fit_event);
     if (c->fit_host) cudaFreeHost(c->fit_host);
@@ -396,40 +407,76 @@ static cudaError_t run_plain(cpd_ctx *c, int64_t iters, cudaStream_t s)
     return cudaSuccess;
 }
 
-template <class T>
-static cudaError_t run_graph(cpd_ctx *c, int64_t chunks, cudaStream_t s)
+// Capture `len` launches of `launch(stream)` into an executable graph.
+template <class F>
+static cudaError_t capture_graph(cudaGraphExec_t *out, int len, F &&launch)
 {
-    if (!c->graph || c->graph_stream != s) {
-        if (c->graph) {
-            cudaGraphExecDestroy(c->graph);
-            c->graph = nullptr;
-        }
-        cudaStream_t cap;
-        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-        if (e != cudaSuccess) return e;
-        cudaGraph_t g;
-        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    cudaStream_t cap;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int q = 0; q < len && e == cudaSuccess; ++q) e = launch(cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) {
-            Problem<T> &P = problem<T>(c);
-            for (int q = 0; q < kGraphChunk && e == cudaSuccess; ++q)
-                e = launch_iteration(P, c->grid_grad, c->grid_upd, c->smem_grad, cap, c->engine, nullptr,
-                                     nullptr, nullptr);
-            cudaError_t e2 = cudaStreamEndCapture(cap, &g);
-            if (e == cudaSuccess) e = e2;
-        }
-        if (e == cudaSuccess) {
-            e = cudaGraphInstantiate(&c->graph, g, 0);
+            e = cudaGraphInstantiate(out, g, 0);
             cudaGraphDestroy(g);
         }
-        cudaStreamDestroy(cap);
-        if (e != cudaSuccess) return e;
-        c->graph_stream = s;
     }
-    for (int64_t q = 0; q < chunks; ++q) {
-        cudaError_t e = cudaGraphLaunch(c->graph, s);
-        if (e != cudaSuccess) return e;
+    cudaStreamDestroy(cap);
+    return e;
+}
+
+// `iters` iterations as replays: whole 32-iteration chunks, then one replay
+// per set bit of the remainder (16, 8, 4, 2, 1). Graphs are captured on
+// first use and kept while the caller's stream stays the same.
+// With run = false only the missing graphs are captured (nothing executes).
+template <class F>
+static cudaError_t replay(cudaGraphExec_t *graphs, cudaStream_t &graph_stream, int64_t iters, cudaStream_t s,
+                          F &&launch, bool run = true)
+{
+    if (graph_stream != s) {
+        drop_graphs(graphs, kGraphSizes);
+        graph_stream = s;
+    }
+    for (int q = 0; q < kGraphSizes; ++q) {
+        const int len = kGraphChunk >> q;
+        const int64_t reps = q == 0 ? iters / kGraphChunk : ((iters & len) ? 1 : 0);
+        if (!reps) continue;
+        if (!graphs[q]) {
+            const cudaError_t e = capture_graph(&graphs[q], len, launch);
+            if (e != cudaSuccess) return e;
+        }
+        for (int64_t r = 0; r < reps && run; ++r) {
+            const cudaError_t e = cudaGraphLaunch(graphs[q], s);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
+}
+
+template <class T>
+static cudaError_t run_graph(cpd_ctx *c, int64_t iters, cudaStream_t s, bool run = true)
+{
+    Problem<T> &P = problem<T>(c);
+    return replay(
+        c->graph, c->graph_stream, iters, s,
+        [&](cudaStream_t cap) {
+            return launch_iteration(P, c->grid_grad, c->grid_upd, c->smem_grad, cap, c->engine, nullptr, nullptr,
+                                    nullptr);
+        },
+        run);
+}
+
+extern "C" cpd_status cpd_prepare(cpd_ctx *c, int64_t iters, void *stream)
+{
+    if (!c || iters < 0) return fail(CPD_EINVAL, "bad context or iteration count");
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaError_t e = c->fbytes == 8 ? run_graph<double>(c, iters, s, false) : run_graph<float>(c, iters, s, false);
+    if (e != cudaSuccess) return cuda_fail(e, "cpd_prepare capture");
+    return CPD_OK;
 }
 
 extern "C" cpd_status cpd_sgd_iters(cpd_ctx *c, int64_t iters, void *stream)
@@ -441,11 +488,7 @@ extern "C" cpd_status cpd_sgd_iters(cpd_ctx *c, int64_t iters, void *stream)
     if (c->profiling) {
         e = c->fbytes == 8 ? run_plain<double>(c, iters, s) : run_plain<float>(c, iters, s);
     } else {
-        const int64_t chunks = iters / kGraphChunk, rem = iters % kGraphChunk;
-        e = cudaSuccess;
-        if (chunks) e = c->fbytes == 8 ? run_graph<double>(c, chunks, s) : run_graph<float>(c, chunks, s);
-        if (e == cudaSuccess && rem)
-            e = c->fbytes == 8 ? run_plain<double>(c, rem, s) : run_plain<float>(c, rem, s);
+        e = c->fbytes == 8 ? run_graph<double>(c, iters, s) : run_graph<float>(c, iters, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "cpd_sgd_iters launch");
     c->t_host += iters;
@@ -683,10 +726,7 @@ extern "C" cpd_status cpd_trace(cpd_ctx *c, int enable)
         c->trace_buf = (unsigned long long *)p;
     }
     tr = enable ? c->trace_buf : nullptr;
-    if (c->graph) {  // captured launches carry the old pointer
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-    }
+    drop_graphs(c->graph, kGraphSizes);   // captured launches carry the old pointer
     return CPD_OK;
 }
 
@@ -757,7 +797,7 @@ struct cpd_group {
     GroupLaunch<float> Lf{};
     GroupLaunch<double> Ld{};
     cudaStream_t home = nullptr;          // stream of creation: allocation and free
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph[kGraphSizes] = {};
     cudaStream_t graph_stream = nullptr;
     cudaStream_t last = nullptr;          // last stream work was enqueued on
 };
@@ -844,41 +884,7 @@ template <class T>
 static cudaError_t group_run(cpd_group *g, int64_t iters, cudaStream_t s)
 {
     const GroupLaunch<T> &L = group_launch<T>(g);
-    const int64_t chunks = iters / kGraphChunk, rem = iters % kGraphChunk;
-    if (chunks) {
-        if (!g->graph || g->graph_stream != s) {
-            if (g->graph) {
-                cudaGraphExecDestroy(g->graph);
-                g->graph = nullptr;
-            }
-            cudaStream_t cap;
-            cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-            if (e != cudaSuccess) return e;
-            cudaGraph_t gr;
-            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                for (int q = 0; q < kGraphChunk && e == cudaSuccess; ++q) e = launch_group_iteration(L, cap);
-                cudaError_t e2 = cudaStreamEndCapture(cap, &gr);
-                if (e == cudaSuccess) e = e2;
-            }
-            if (e == cudaSuccess) {
-                e = cudaGraphInstantiate(&g->graph, gr, 0);
-                cudaGraphDestroy(gr);
-            }
-            cudaStreamDestroy(cap);
-            if (e != cudaSuccess) return e;
-            g->graph_stream = s;
-        }
-        for (int64_t q = 0; q < chunks; ++q) {
-            cudaError_t e = cudaGraphLaunch(g->graph, s);
-            if (e != cudaSuccess) return e;
-        }
-    }
-    for (int64_t q = 0; q < rem; ++q) {
-        cudaError_t e = launch_group_iteration(L, s);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return replay(g->graph, g->graph_stream, iters, s, [&](cudaStream_t cap) { return launch_group_iteration(L, cap); });
 }
 
 extern "C" cpd_status cpd_group_iters(cpd_group *g, int64_t iters, void *stream)
@@ -900,7 +906,7 @@ extern "C" cpd_status cpd_group_destroy(cpd_group *g)
 {
     if (!g) return CPD_OK;
     cudaStreamSynchronize(g->last);
-    if (g->graph) cudaGraphExecDestroy(g->graph);
+    drop_graphs(g->graph, kGraphSizes);
     cudaFreeAsync(g->dP, g->home);
     cudaFreeAsync(g->dcta, g->home);
     cudaStreamSynchronize(g->home);

@@ -16,7 +16,6 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "cpd.h"
@@ -33,16 +32,12 @@ namespace {
 
 constexpr int kTolFibers = 16;                      // mode-1 fibers per chunk
 constexpr long long kTolMaxChunks = 65536;          // => at most 1,048,576 fibers
-constexpr int kMaxDevices = 64;
 
 // Scratch: residual partials [0, nchunks) and ||X||^2 partials
 // [kTolMaxChunks, kTolMaxChunks + nchunks), one slot per chunk (1 MiB). Every
 // GPU that loads the library holds it until the process exits. Each call
 // writes every slot it later reads, so nothing has to start at zero.
 static __device__ __align__(256) double g_tol_scratch[2 * kTolMaxChunks];
-
-static double *g_scratch_addr[kMaxDevices];
-static std::mutex g_scratch_mu;
 
 struct TolArgs {
     int N, R;
@@ -121,43 +116,44 @@ __global__ void __launch_bounds__(kThreads) k_tol_chunks(const TolArgs a, const 
     }
 }
 
-__global__ void k_tol_fold(const double *scratch, long long nchunks, double *out)
+// Fixed-order fold of the chunk partials: thread q sums chunks q, q + 256,
+// ... in ascending order, then a pairwise tree over the 256 threads. A tensor
+// with ||X|| = 0 has no relative error: the result is then NaN.
+__global__ void __launch_bounds__(kThreads) k_tol_fold(const double *scratch, long long nchunks, double *out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double r = 0.0, x = 0.0;
-        for (long long c = 0; c < nchunks; ++c) {
-            r += scratch[c];
-            x += scratch[kTolMaxChunks + c];
-        }
-        *out = r / x;
+    __shared__ double red[2][kThreads];
+    double r = 0.0, x = 0.0;
+    for (long long c = threadIdx.x; c < nchunks; c += kThreads) {
+        r += scratch[c];
+        x += scratch[kTolMaxChunks + c];
     }
+    red[0][threadIdx.x] = r;
+    red[1][threadIdx.x] = x;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + w];
+            red[1][threadIdx.x] += red[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[1][0] > 0.0 ? red[0][0] / red[1][0] : __longlong_as_double(0x7ff8000000000000LL);
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress with that device current).
+// Device address of the scratch array on the current device. Looked up on
+// every call (cudaGetSymbolAddress with the calling device current), so the
+// address stays right if the device's context is reset and the library's
+// device code is loaded again; the first lookup on a device may load that
+// code, which is why the first call should precede any stream capture.
 static cpd_status scratch_address(double **out)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_tol_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
         return CPD_ECUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("cpd_tol_noalloc: device ordinal out of range");
-        return CPD_EINVAL;
-    }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_tol_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-            return CPD_ECUDA;
-        }
-        g_scratch_addr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<double *>(p);
     return CPD_OK;
 }
 
@@ -182,18 +178,24 @@ extern "C" cpd_status cpd_tol_noalloc(int32_t N, const int64_t *dims, int32_t R,
         }
         a.dims[k] = dims[k];
         a.A[k] = A[k];
+        // the product of the sizes of modes 2..N is bounded before it is formed
         if (k > 0) {
-            if (J > (long long)1 << 40) {
-                set_error("cpd_tol_noalloc: tensor too large");
-                return CPD_EINVAL;
+            if (dims[k] > kTolMaxChunks * kTolFibers / J) {
+                J = kTolMaxChunks * kTolFibers + 1;   // over the limit; reported below
+                break;
             }
             J *= dims[k];
         }
     }
+    for (int k = 0; k < N; ++k) {
+        if (dims[k] < 1 || !A[k]) {
+            set_error("cpd_tol_noalloc: every dim must be >= 1 and every factor non-NULL");
+            return CPD_EINVAL;
+        }
+    }
     const long long nchunks = (J + kTolFibers - 1) / kTolFibers;
     if (nchunks > kTolMaxChunks) {
-        set_error("cpd_tol_noalloc: the tensor has " + std::to_string(J) +
-                  " mode-1 fibers; the fixed scratch serves at most " +
+        set_error("cpd_tol_noalloc: the tensor has more mode-1 fibers than the fixed scratch serves, at most " +
                   std::to_string(kTolMaxChunks * kTolFibers) + " (use cpd_fit)");
         return CPD_EINVAL;
     }
@@ -201,7 +203,15 @@ extern "C" cpd_status cpd_tol_noalloc(int32_t N, const int64_t *dims, int32_t R,
     cpd_status st = scratch_address(&scratch);
     if (st != CPD_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int grid = (int)(nchunks < 8 * 152 ? nchunks : 8 * 152);
+    int dev = 0, sms = 0;
+    cudaError_t ea = cudaGetDevice(&dev);
+    if (ea == cudaSuccess) ea = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ea != cudaSuccess || sms < 1) {
+        set_error(std::string("cpd_tol_noalloc: device attributes: ") + cudaGetErrorString(ea));
+        return CPD_ECUDA;
+    }
+    const long long cap = 8LL * sms;   // eight CTAs per SM, each walking chunks
+    const int grid = (int)(nchunks < cap ? nchunks : cap);
     if (x_dtype == CPD_F64)
         k_tol_chunks<double, double><<<grid, kThreads, 0, s>>>(a, (const double *)X, J, nchunks, scratch);
     else if (x_dtype == CPD_F32)
@@ -211,7 +221,7 @@ extern "C" cpd_status cpd_tol_noalloc(int32_t N, const int64_t *dims, int32_t R,
                                                                      scratch);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
-        k_tol_fold<<<1, 32, 0, s>>>(scratch, nchunks, tol_out);
+        k_tol_fold<<<1, kThreads, 0, s>>>(scratch, nchunks, tol_out);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

@@ -542,3 +542,108 @@ def test_nonneg_recovery_keeps_factors_nonnegative(orc):
     tol1, _ = orc.tol(X, A0)
     assert tol0 > 1e-4
     assert tol1 < 1e-20, tol1
+
+
+# ------------------------------------------------------------------ #
+# Decoding of stored tensor entries (the oracle reads BF16 / FP32 X)   #
+# ------------------------------------------------------------------ #
+
+def _bf16_ieee(bits: int) -> float:
+    """Value of a bf16 bit pattern from the IEEE field definitions (1 sign, 8
+    exponent bits with bias 127, 7 fraction bits)."""
+    s = -1.0 if bits >> 15 else 1.0
+    e, m = (bits >> 7) & 0xFF, bits & 0x7F
+    if e == 0xFF:
+        return s * math.inf if m == 0 else math.nan
+    if e == 0:
+        return s * math.ldexp(m, -133)            # subnormal: m * 2^(1 - 127 - 7)
+    return s * math.ldexp(128 + m, e - 134)       # (1 + m/128) * 2^(e - 127)
+
+
+def test_bf16_decode_matches_ieee_fields(orc):
+    """x_at on bf16 bit patterns: printed values, both signs of zero, the
+    subnormal range, the largest finite value, infinities and NaN."""
+    golden = {0x3F80: 1.0, 0xC000: -2.0, 0x3F00: 0.5, 0x4049: 3.140625, 0x0001: 2.0 ** -133,
+              0x8001: -(2.0 ** -133), 0x007F: 127 * 2.0 ** -133, 0x0080: 2.0 ** -126,
+              0x7F7F: (2 - 2 ** -7) * 2.0 ** 127, 0x0000: 0.0, 0x8000: -0.0}
+    rng = np.random.default_rng(3)
+    pats = list(golden) + [0x7F80, 0xFF80, 0x7FC0, 0xFFC1] + [int(v) for v in rng.integers(0, 2**16, 4000)]
+    X = np.array(pats, dtype=np.uint16).reshape(len(pats), 1, 1, order="F")
+    got = orc.gather_fiber(X, 0, (0, 0, 0), "bf16")
+    for b, v in zip(pats, got):
+        want = golden.get(b, _bf16_ieee(b))
+        if math.isnan(want):
+            assert math.isnan(v), hex(b)
+        else:
+            assert v == want and math.copysign(1.0, v) == math.copysign(1.0, want), (hex(b), v, want)
+    # every pattern decodes to exactly one value: the map is injective on non-NaN
+    fin = [b for b in range(0, 2**16, 7) if not math.isnan(_bf16_ieee(b))]
+    Xf = np.array(fin, dtype=np.uint16).reshape(len(fin), 1, 1, order="F")
+    vals = orc.gather_fiber(Xf, 0, (0, 0, 0), "bf16")
+    np.testing.assert_array_equal(vals, [_bf16_ieee(b) for b in fin])
+
+
+def test_f32_decode_matches_numpy(orc):
+    """x_at on FP32 entries widens exactly: against numpy's conversion, with
+    subnormals, extremes and signed zero, along every mode."""
+    rng = np.random.default_rng(4)
+    dims = (7, 5, 6)
+    X = rng.standard_normal(dims).astype(np.float32) * np.float32(3.0)
+    X.flat[:6] = np.array([np.finfo(np.float32).tiny / 8, -np.finfo(np.float32).max, 0.0, -0.0,
+                           np.finfo(np.float32).eps, 1e-45], dtype=np.float32)
+    X = np.asfortranarray(X)
+    for n in range(3):
+        others = [range(d) if k != n else [0] for k, d in enumerate(dims)]
+        for tup in itertools.product(*others):
+            sl = list(tup)
+            sl[n] = slice(None)
+            got = orc.gather_fiber(X, n, tup, "f32")
+            want = X[tuple(sl)].astype(np.float64)
+            np.testing.assert_array_equal(got, want)
+            np.testing.assert_array_equal(np.signbit(got), np.signbit(want))
+
+
+@pytest.mark.parametrize("x_dtype,dims,R", [("f64", (9, 7, 8), 3), ("f32", (6, 5, 4, 3), 2),
+                                            ("bf16", (11, 4, 13), 4)])
+def test_tol_blas_equals_direct_sum(orc, x_dtype, dims, R):
+    """The chunked, matrix-multiply form of Tol equals the entry-by-entry sum."""
+    A, X = rand_problem(dims, R, 22, noise=0.4)
+    if x_dtype == "bf16":
+        xb = (np.asfortranarray(X).ravel(order="F").astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+    else:
+        xb = np.asfortranarray(X).ravel(order="F").astype(np.float64 if x_dtype == "f64" else np.float32)
+    t_direct, xx_direct = orc.tol(xb, A, x_dtype, dims=dims)
+    t_blas, xx_blas = orc.tol_blas(xb, dims, A, x_dtype, chunk_cols=5)
+    assert t_blas == pytest.approx(t_direct, rel=1e-12)
+    assert xx_blas == pytest.approx(xx_direct, rel=1e-13)
+
+
+def test_all_cores_build_gives_the_same_bits(orc):
+    """The timing-only OpenMP build runs the same arithmetic in the same order."""
+    dims, R, B = (23, 17, 19), 4, 64
+    A, X = rand_problem(dims, R, 31, noise=0.2)
+    for sampling in ("euclidean", "leverage"):
+        cfg = orc.Config(dims=dims, R=R, B=B, sampling=sampling, step="adagrad", seed=8)
+        A1 = [a.copy() for a in A]
+        A2 = [a.copy() for a in A]
+        S1 = [np.zeros_like(a) for a in A]
+        S2 = [np.zeros_like(a) for a in A]
+        assert orc.run(cfg, 0, 40, X, A1, S1) == orc.OK
+        assert orc.run(cfg, 0, 40, X, A2, S2, omp=True) == orc.OK
+        for a, b in zip(A1, A2):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_grad_row_scale_bounds_every_row(orc):
+    """|G_i| <= scale_i for every row (triangle inequality on Eq. (11)), with
+    equality-order size: the scale is not vacuous."""
+    dims, R, B = (9, 8, 7), 3, 25
+    A, X = rand_problem(dims, R, 33, noise=0.5)
+    xb = np.asfortranarray(X).ravel(order="F")
+    cfg = orc.Config(dims=dims, R=R, B=B, sampling="euclidean", step="fixed", seed=2)
+    out = orc.step(cfg, 0, X, [a.copy() for a in A])
+    n = out["n"]
+    scale = orc.grad_row_scale(dims, n, out["idx"], out["p"], A, xb, "f64", B)
+    g = np.linalg.norm(out["G"], axis=1)
+    assert np.all(g <= scale * (1 + 1e-12))
+    assert np.all(scale <= 100 * g.max() + 1e-300) and scale.min() > 0

@@ -6,10 +6,11 @@ their loop) use this entry point. It must agree with cpd_fit, the context-based
 entry point that computes the same Tol, on two calls in a row -- the second
 call runs on scratch left over from the first.
 """
+import numpy as np
 import pytest
 import torch
 
-from helpers import make_problem
+from helpers import make_problem, oracle_xbuf
 
 pytestmark = pytest.mark.gpu
 
@@ -72,3 +73,29 @@ def test_noalloc_rejects_oversize(cpd):
         cpd.cpd_tol_noalloc(dims, 2, "f32", X, A, out)
     assert e.value.status == cpd.EINVAL
     assert "at most 1048576" in str(e.value)
+    # sizes whose product overflows 64 bits are refused the same way
+    with pytest.raises(cpd.CpdError) as e:
+        cpd.cpd_tol_noalloc((4, 2**31, 2**31, 2**31), 2, "f32", X, A + [A[0]], out)
+    assert e.value.status == cpd.EINVAL
+
+
+@pytest.mark.parametrize("xdt,dims,R", [("f64", (13, 9, 11), 3), ("f32", (40, 33, 17), 5),
+                                        ("bf16", (21, 12, 10, 7), 4)])
+def test_noalloc_tol_matches_oracle(cpd, orc, xdt, dims, R):
+    """Directly against the oracle's entry-by-entry residual sum (Sec. 5.2)."""
+    _, X, A0 = make_problem(dims, R, noise=0.2, x_dtype=xdt)
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    cpd.cpd_tol_noalloc(dims, R, xdt, X.cuda(), [a.cuda() for a in A0], out)
+    torch.cuda.synchronize()
+    want, _ = orc.tol(oracle_xbuf(X), [a.double().numpy() for a in A0], xdt, dims=dims)
+    assert out.item() == pytest.approx(want, rel=1e-12 if xdt == "f64" else 1e-6)
+
+
+def test_noalloc_zero_tensor_gives_nan(cpd):
+    dims = (5, 6, 7)
+    X = torch.zeros(int(np.prod(dims)), device="cuda")
+    A = [torch.ones(d, 2, device="cuda") for d in dims]
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    cpd.cpd_tol_noalloc(dims, 2, "f32", X, A, out)
+    torch.cuda.synchronize()
+    assert np.isnan(out.item())
