@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "SGD iters/s & fiber-gather GB/s vs HBM peak; batched solves/s, p99 @ equal fit"
 DEFAULT_WORKLOAD = "c4_1000cube_bf16"
 KERNEL_SOURCES = ["paper_2103_04081_gb300/csrc/cpd_kernels.cu", "paper_2103_04081_gb300/csrc/cpd_tc.cu",
+                  "paper_2103_04081_gb300/csrc/cpd_pers.cu",
                   "paper_2103_04081_gb300/csrc/cpd_tcc.cu", "paper_2103_04081_gb300/csrc/cpd_tcgen05.cuh",
                   "paper_2103_04081_gb300/csrc/cpd_device.cuh"]
 
@@ -238,6 +239,7 @@ def error_vs_oracle(C, dev: str, stream, kw: dict, steps_tf: int = 3, free_iters
     xb = X.cpu().view(torch.int16).numpy().view(np.uint16) if X.dtype == torch.bfloat16 else X.cpu().numpy()
     del X
     dec.sgd_iters(50, stream)
+    torch.cuda.synchronize()
     ocfg = O.Config(dims=tuple(w["dims"]), R=w["R"], B=w["B"], sampling=w["sampling"], step=w["step"],
                     x_dtype=w["x_dtype"], eta=w["eta"], b=w["b"], seed=w["sample_seed"])
     worst = {"G_frobenius": 0.0, "G_row_scaled": 0.0, "A_row": 0.0}
@@ -249,6 +251,7 @@ def error_vs_oracle(C, dev: str, stream, kw: dict, steps_tf: int = 3, free_iters
         S = [s.numpy().copy() for s in dec.adagrad()]
         out = O.step(ocfg, t, None, A, S, xbuf=xb)
         dec.sgd_iters(1, stream)
+        torch.cuda.synchronize()    # the reads below use the default stream
         n, idx, p = dec.last_sample()
         _, G = dec.last_gradient()
         exact = exact and n == out["n"] and bool(np.array_equal(idx.numpy().astype(np.int64), out["idx"])) \
@@ -448,7 +451,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=500)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tensor", "cluster"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tensor", "cluster", "persistent"])
     ap.add_argument("--max-ctas", type=int, default=0, help="CTA cap of the gradient launch (0: none)")
     ap.add_argument("--sampling", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -482,7 +485,7 @@ def main() -> None:
     tuned = None
     if not args.no_autotune and args.engine == "auto" and args.max_ctas == 0:
         best, rate = C.cpd_autotune(C.make_config(**kw), X, [a.to(dev) for a in A0], iters=300, stream=stream)
-        tuned = {"engine": {1: "simt", 2: "tensor", 3: "cluster"}[best.engine], "max_ctas": best.max_ctas,
+        tuned = {"engine": {1: "simt", 2: "tensor", 3: "cluster", 4: "persistent"}[best.engine], "max_ctas": best.max_ctas,
                  "tuning_iters_per_s": rate}
         kw["engine"], kw["max_ctas"] = tuned["engine"], tuned["max_ctas"]
     with torch.cuda.stream(stream):
@@ -490,6 +493,8 @@ def main() -> None:
     desc = dec.describe()
     engine = desc["engine"]
     launches_per_iter = 2 + (2 if w["sampling"] == "leverage" else 0)
+    if engine == "persistent":   # one launch per call of cpd_sgd_iters (up to 2^20 iterations)
+        launches_per_iter = 1.0 / args.steps
 
     # warm-up (W iterations), the graphs a K-iteration call replays captured
     # ahead (nothing runs), then exactly K timed iterations
@@ -561,16 +566,16 @@ def main() -> None:
         "metric": METRIC, "value": iters_per_s, "unit": "iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if engine in ("tensor", "cluster") else ("f64" if w["x_dtype"] == "f64" else "f32"),
+        "dtype": "bf16" if engine in ("tensor", "cluster", "persistent") else ("f64" if w["x_dtype"] == "f64" else "f32"),
         "data": "synthetic", "config": config_block(w, engine),
         "gather_gbs_in_loop": gather_bytes * args.steps / (ms / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "kernel": {"tensor": "k_grad_tc", "cluster": "k_grad_tcc"}.get(engine, "k_grad_simt"),
+                     "kernel": {"tensor": "k_grad_tc", "cluster": "k_grad_tcc", "persistent": "k_pers"}.get(engine, "k_grad_simt"),
                      "algorithmic_bytes_per_launch": gather_bytes, "mean_launch_ms": grad_ms,
                      "timed_launches": nlaunch, "peak_source": src + " (hbm_gbs, of " + src + ")",
                      "update_mean_ms": upd_ms},
-        "clocks": clocks, "gpu_launches": launches_per_iter * args.steps,
+        "clocks": clocks, "gpu_launches": int(round(launches_per_iter * args.steps)),
         "e2e": e2e, "final_tol": tol, "launch": desc,
     }
     if tuned:

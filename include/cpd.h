@@ -100,13 +100,20 @@ typedef struct {
     int32_t engine;     /* 0 = automatic, 1 = CUDA-core gradient, 2 = tensor-core
                            gradient, one CTA per tile, 3 = tensor-core gradient,
                            one thread-block cluster per fiber group (2 and 3:
-                           BF16 tensors, R <= 64; 3: every I_k <= 1024)         */
+                           BF16 tensors, R <= 64; 3: every I_k <= 1024),
+                           4 = persistent cluster: one thread-block cluster runs
+                           whole calls of cpd_sgd_iters in one launch (BF16
+                           tensors, R <= 64, Euclidean or uniform sampling,
+                           sum of the I_k <= 4096, ceil(I_max/128) accumulator
+                           tiles of <= 64 columns within 512)                   */
     int32_t max_ctas;   /* 0: size the gradient grid for the whole GPU; > 0: use at
                            most about this many CTAs per gradient launch (fewer
                            fiber groups, more fibers per CTA), so that several
-                           decompositions share the GPU. Part of the arithmetic:
-                           the grouping of the batch fixes the summation order of
-                           the gradient partials.                                */
+                           decompositions share the GPU. Engine 4: the cluster
+                           size (1..16; 0 = 8, or less if the device cannot
+                           co-schedule 8). Part of the arithmetic: the grouping
+                           of the batch fixes the summation order of the
+                           gradient partials.                                   */
     int32_t constraint; /* CPD_CONSTRAINT_*                                     */
     int32_t reserved;   /* must be 0                                            */
 } cpd_config;

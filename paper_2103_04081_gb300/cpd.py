@@ -24,7 +24,7 @@ SAMPLE = {"euclidean": 0, "leverage": 1, "uniform": 2}
 STEP = {"fixed": 0, "adagrad": 1, "decay": 2}
 CONSTRAINT = {"none": 0, "nonneg": 1}
 XDT = {"f64": 0, "f32": 1, "bf16": 2}
-ENGINE = {"auto": 0, "simt": 1, "tensor": 2, "cluster": 3}
+ENGINE = {"auto": 0, "simt": 1, "tensor": 2, "cluster": 3, "persistent": 4}
 MAX_MODES = 8
 
 

@@ -72,6 +72,8 @@ struct cpd_ctx {
     cudaEvent_t fit_event = nullptr; // cpd_fit_start / cpd_fit_poll
     double *fit_host = nullptr;      // pinned copy of the residual sum
     bool fit_started = false;
+    PersArgs pers{};                 // persistent engine: launch arguments (P refreshed per launch)
+    int64_t prof_iters = 0;          // iterations covered by the profiled launches
 
     template <class F>
     cudaError_t with_problem(F &&f)
@@ -132,7 +134,12 @@ static cpd_status validate(const cpd_config *cfg)
     if (cfg->constraint != CPD_CONSTRAINT_NONE && cfg->constraint != CPD_CONSTRAINT_NONNEG)
         return fail(CPD_EINVAL, "unknown constraint");
     if (cfg->reserved != 0) return fail(CPD_EINVAL, "reserved must be 0");
-    if (cfg->engine < 0 || cfg->engine > 3) return fail(CPD_EINVAL, "unknown engine");
+    if (cfg->engine < 0 || cfg->engine > 4) return fail(CPD_EINVAL, "unknown engine");
+    if (cfg->engine == kEnginePersistent && !pers_supported(*cfg))
+        return fail(CPD_EINVAL, "persistent engine needs BF16 tensors, R <= 64, Euclidean or uniform "
+                                "sampling, sum of the I_k <= 4096 and ceil(I_max / 128) row tiles in tensor memory");
+    if (cfg->engine == kEnginePersistent && cfg->max_ctas > 16)
+        return fail(CPD_EINVAL, "persistent engine: max_ctas is the cluster size, at most 16");
     double total = 1.0;
     for (int k = 0; k < cfg->N; ++k) {
         if (cfg->dims[k] < 1 || cfg->dims[k] > (int64_t)1 << 31)
@@ -166,6 +173,30 @@ static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
     for (int k = 0; k < g.N; ++k) imax = std::max<int64_t>(imax, g.dims[k]);
     c->imax = imax;
     P.cs = 1;
+    if (c->engine == kEnginePersistent) {
+        if constexpr (sizeof(T) == 4) {
+            // one cluster; its size is max_ctas when given, else the largest
+            // of 8, 4, 2, 1 that the device can co-schedule with the layout
+            PersArgs &pa = c->pers;
+            pa.P = P;
+            int cs = g.max_ctas > 0 ? g.max_ctas : 8;
+            pers_fill(pa, cs);
+            while (g.max_ctas == 0 && cs > 1 && pers_max_clusters(pa) < 1) {
+                cs >>= 1;
+                pers_fill(pa, cs);
+            }
+            P.rb = 128;
+            P.cs = cs;
+            P.fb = pa.fpc;
+            P.pf = 1;
+            for (int k = 0; k < g.N; ++k) P.tile[k].pr = (int)((g.dims[k] + 127) / 128);
+            c->grid_grad = cs;
+            c->grid_upd = 0;
+            c->smem_grad = pers_smem_bytes(pa);
+            c->max_clusters = pers_max_clusters(pa);
+        }
+        return;
+    }
     if (c->engine == kEngineTensorCluster) {
         if constexpr (sizeof(T) == 4) {
             // one cluster of ceil(I_max / 128) CTAs per fiber group; as many
@@ -332,6 +363,21 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
         }
         P.defer_cdf = (g.sampling == CPD_SAMPLE_EUCLIDEAN && need <= cap) ? 1 : 0;
     }
+    if constexpr (sizeof(T) == 4) {
+        if (c->engine == kEnginePersistent) {
+            PersArgs &pa = c->pers;
+            if (c->max_clusters < 1) return fail(CPD_ECUDA, "persistent engine: the cluster cannot be scheduled");
+            for (int k = 0; k < g.N; ++k) {
+                CK(dmalloc(c, &p, (size_t)g.dims[k] * pa.R4 * sizeof(float)));
+                pa.Ap[k] = (float *)p;
+            }
+            CK(dmalloc(c, &p, (size_t)pa.cs * pa.ntile * 128 * pa.cst * sizeof(float)));
+            pa.part = (float *)p;
+            CK(dmalloc(c, &p, (size_t)pa.cs * 64 * 64 * sizeof(float)));
+            pa.hpart = (float *)p;
+            P.defer_cdf = 0;
+        }
+    }
     CK(dmalloc(c, &p, 16 * sizeof(unsigned)));  P.counters = (unsigned *)p;
     CK(dmalloc(c, &p, (size_t)fit_blocks() * sizeof(double)));  c->fit_partials = (double *)p;
     CK(dmalloc(c, &p, sizeof(double)));  c->fit_out = (double *)p;
@@ -400,6 +446,7 @@ static cudaError_t run_plain(cpd_ctx *c, int64_t iters, cudaStream_t s)
             e1 = c->ev[3 * c->prof_used + 1];
             e2 = c->ev[3 * c->prof_used + 2];
             ++c->prof_used;
+            ++c->prof_iters;
         }
         cudaError_t e = launch_iteration(P, c->grid_grad, c->grid_upd, c->smem_grad, s, c->engine, e0, e1, e2);
         if (e != cudaSuccess) return e;
@@ -474,9 +521,37 @@ extern "C" cpd_status cpd_prepare(cpd_ctx *c, int64_t iters, void *stream)
 {
     if (!c || iters < 0) return fail(CPD_EINVAL, "bad context or iteration count");
     cudaStream_t s = (cudaStream_t)stream;
+    if (c->engine == kEnginePersistent) return CPD_OK;   // one launch per call, no graph
     const cudaError_t e = c->fbytes == 8 ? run_graph<double>(c, iters, s, false) : run_graph<float>(c, iters, s, false);
     if (e != cudaSuccess) return cuda_fail(e, "cpd_prepare capture");
     return CPD_OK;
+}
+
+// Persistent engine: launches of at most 2^20 iterations each (one cluster
+// runs them back to back); profiled launches are bracketed by events.
+static cudaError_t run_pers(cpd_ctx *c, int64_t iters, cudaStream_t s)
+{
+    constexpr int64_t kMaxPerLaunch = (int64_t)1 << 20;
+    for (int64_t done = 0; done < iters;) {
+        const int64_t T = std::min(kMaxPerLaunch, iters - done);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c->profiling && c->prof_used < kProfSlots) {
+            e0 = c->ev[3 * c->prof_used];
+            e1 = c->ev[3 * c->prof_used + 1];
+            ++c->prof_used;
+            c->prof_iters += T;
+        }
+        c->pers.P = c->Pf;   // current pointers (trace buffer, ...)
+        if (e0) cudaEventRecord(e0, s);
+        cudaError_t e = launch_pers(c->pers, T, s);
+        if (e1) {
+            cudaEventRecord(e1, s);
+            cudaEventRecord(c->ev[3 * (c->prof_used - 1) + 2], s);
+        }
+        if (e != cudaSuccess) return e;
+        done += T;
+    }
+    return cudaSuccess;
 }
 
 extern "C" cpd_status cpd_sgd_iters(cpd_ctx *c, int64_t iters, void *stream)
@@ -485,7 +560,9 @@ extern "C" cpd_status cpd_sgd_iters(cpd_ctx *c, int64_t iters, void *stream)
     if (iters == 0) return CPD_OK;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
-    if (c->profiling) {
+    if (c->engine == kEnginePersistent) {
+        e = run_pers(c, iters, s);
+    } else if (c->profiling) {
         e = c->fbytes == 8 ? run_plain<double>(c, iters, s) : run_plain<float>(c, iters, s);
     } else {
         e = c->fbytes == 8 ? run_graph<double>(c, iters, s) : run_graph<float>(c, iters, s);
@@ -693,6 +770,7 @@ extern "C" cpd_status cpd_profile(cpd_ctx *c, int enable)
     }
     c->profiling = enable != 0;
     c->prof_used = 0;
+    c->prof_iters = 0;
     return CPD_OK;
 }
 
@@ -709,9 +787,11 @@ extern "C" cpd_status cpd_profile_read(cpd_ctx *c, int64_t *launches, double *me
         CK(cudaEventElapsedTime(&ms, c->ev[3 * q + 1], c->ev[3 * q + 2]));
         tu += ms;
     }
-    if (launches) *launches = c->prof_used;
-    if (mean_grad_ms) *mean_grad_ms = c->prof_used ? tg / c->prof_used : 0.0;
-    if (mean_update_ms) *mean_update_ms = c->prof_used ? tu / c->prof_used : 0.0;
+    // per iteration: a persistent launch covers many iterations (its whole
+    // time counts as the gradient part)
+    if (launches) *launches = c->prof_iters;
+    if (mean_grad_ms) *mean_grad_ms = c->prof_iters ? tg / c->prof_iters : 0.0;
+    if (mean_update_ms) *mean_update_ms = c->prof_iters ? tu / c->prof_iters : 0.0;
     return CPD_OK;
 }
 
@@ -750,7 +830,10 @@ extern "C" cpd_status cpd_describe(cpd_ctx *c, char *buf, size_t len)
                   "\"grad_grid\": %d, \"update_grid\": %d, \"grad_smem\": %zu, \"graph_chunk\": %d, "
                   "\"cluster\": %d, \"max_clusters\": %d, \"deferred_cdf\": %d, "
                   "\"xnorm2\": %.17g}",
-                  c->engine == kEngineTensorCluster ? "cluster" : c->engine == kEngineTensor ? "tensor" : "simt",
+                  c->engine == kEnginePersistent       ? "persistent"
+                  : c->engine == kEngineTensorCluster ? "cluster"
+                  : c->engine == kEngineTensor        ? "tensor"
+                                                      : "simt",
                   rb, fb, pf, c->grid_grad, c->grid_upd,
                   c->smem_grad, kGraphChunk, c->fbytes == 8 ? 1 : c->Pf.cs, c->max_clusters,
                   c->fbytes == 8 ? c->Pd.defer_cdf : c->Pf.defer_cdf, c->xnorm2);
@@ -975,6 +1058,8 @@ extern "C" cpd_status cpd_autotune(const cpd_config *cfg, const void *X, int x_l
             if (cs <= 8)
                 for (int m : {0, 4, 8, 12}) cand.push_back({kEngineTensorCluster, m * cs});
         }
+        if (pers_supported(*cfg))   // persistent cluster engine: the cluster size is the tile choice
+            for (int mc : {2, 4, 8, 16}) cand.push_back({kEnginePersistent, mc});
     }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;

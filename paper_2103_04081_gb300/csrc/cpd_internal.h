@@ -28,7 +28,7 @@ constexpr int kThreads = 256;
 enum : int { kStNonFinite = 1, kStDegenerate = 2, kStTimeout = 4 };
 
 // Gradient engines.
-enum : int { kEngineSimt = 1, kEngineTensor = 2, kEngineTensorCluster = 3 };
+enum : int { kEngineSimt = 1, kEngineTensor = 2, kEngineTensorCluster = 3, kEnginePersistent = 4 };
 
 // Launch tiling of the gradient kernel for one mode n: CTA (gr, gf) handles
 // rows [gr*rb, gr*rb+rb) of A^(n) and fibers [gf*fb, gf*fb+fb) of the batch.
@@ -83,6 +83,21 @@ struct GroupLaunch {
     size_t smem_grad;         // largest member's dynamic shared memory
 };
 
+// Persistent cluster engine (cpd_pers.cu): one thread-block cluster of cs
+// CTAs runs T consecutive iterations of one decomposition in one launch.
+// CTA c of the cluster owns fibers [c fpc, c fpc + fpc) of every batch for
+// the gather and the tensor-core contraction (all rows of A^(n)), and a
+// contiguous range of rows of A^(n) for the reduction and the step.
+struct PersArgs {
+    Problem<float> P;
+    float *Ap[kMaxModes];     // private copies of the factors, row stride R4
+    float *part;              // partial M per CTA: [cs][ntile * 128][cst] fp32
+    float *hpart;             // partial H per CTA: [cs][64][64] fp32
+    long long off[kMaxModes]; // offset of mode k's CDF in the shared staging
+    long long sumI;           // sum of the I_k (staging entries)
+    int cs, fpc, R4, Npad, cst, ntile;
+};
+
 // Launchers (cpd_kernels.cu). Every launcher enqueues on `stream` and
 // returns the launch error, if any.
 template <class T>
@@ -123,5 +138,13 @@ int tcc_max_clusters(const Problem<float> &P);
 long long tc_stage_cap(const Problem<float> &P);
 long long tcc_stage_cap(const Problem<float> &P);
 constexpr long long kSimtStageCap = 2048;
+
+// Persistent cluster engine (cpd_pers.cu).
+bool pers_supported(const cpd_config &cfg);
+void pers_fill(PersArgs &a, int cs);        // fpc, R4, Npad, cst, ntile, off, sumI
+size_t pers_smem_bytes(const PersArgs &a);
+int pers_max_clusters(const PersArgs &a);
+cudaError_t launch_pers(const PersArgs &a, long long T, cudaStream_t stream);
+cudaError_t launch_pers_group(const PersArgs *dargs, int G, int cs, size_t smem, long long T, cudaStream_t stream);
 
 }  // namespace cpd

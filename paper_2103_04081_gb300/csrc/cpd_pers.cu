@@ -1,0 +1,677 @@
+// Persistent cluster engine (sm_103a): one thread-block cluster runs T
+// consecutive iterations of Alg. 4 / Alg. 5 for one decomposition inside a
+// single launch, with no grid-wide synchronisation and no launch between
+// iterations.
+//
+// Work split inside the cluster (cs CTAs, CTA `rank`):
+//   * fibers: CTA rank owns fibers [rank fpc, rank fpc + fpc) of every batch.
+//     It draws them (Alg. 3), forms their columns (Eq. (2)), weights
+//     s_f = 1/(B J_n p_f) and sampled KRP rows z_f (Eq. (3)), gathers the
+//     whole fibers from the mode-n replica and contracts them on the tensor
+//     cores against Z' = s_f z_f (bf16 hi/lo pair, K-major) into a partial
+//     M_rank = X_S,rank Z'_S,rank held in tensor memory for every row of
+//     A^(n) (one 128-row accumulator tile per 128 rows). The CUDA cores form
+//     the partial H_rank = sum_f s_f z_f z_f^T meanwhile.
+//   * rows: CTA rank owns a contiguous range of rows of A^(n) (whole groups
+//     of 32). The partials of every CTA go to an L2-resident scratch; the
+//     owner sums its rows in ascending CTA order, forms G = A H - M
+//     (Eq. (11)) and the step (Eq. (12), Thm 9 or Eq. (13a)-(13b)), writes
+//     the rows back and sends their new Euclidean weights (Def. 5) to every
+//     CTA of the cluster through distributed shared memory.
+//   * every CTA keeps the fixed-point CDFs of all modes in shared memory and
+//     rebuilds mode n's in place from the gathered weights (the same exact
+//     integer CDF as the other engines), so the next iteration draws from
+//     the updated factor (Alg. 4 / Alg. 5 take p_k from the current factors).
+// Three cluster barriers per iteration order the phases: partials written,
+// H rows sent, weights sent. The gather of a CTA streams its fibers in
+// chunks of 16 (the MMA K) through a ring of stages filled by 16-byte
+// cp.async copies; a chunk's tensor-core products are issued by one thread
+// and complete on the stage's mbarrier, which releases the stage.
+//
+// The factors are mirrored, for the launch, in private copies whose rows
+// are padded to a multiple of 4 floats (16-byte aligned rows for the async
+// copies); the context's factors are read at the start and written at the
+// end, together with the CDFs, t and the last batch.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cpd_device.cuh"
+#include "cpd_internal.h"
+#include "cpd_tcgen05.cuh"
+
+namespace cpd {
+
+namespace {
+
+constexpr int kPM = 128;          // rows per accumulator tile (MMA M)
+constexpr int kPK = 16;           // fibers per chunk (MMA K for 16-bit operands)
+constexpr int kPS = 3;            // stages of the gather ring
+constexpr int kPHd = 64;          // H is formed 64 x 64 (4 x 4 blocks of 256 threads)
+constexpr int kPOwnBlock = 128;   // owned rows handled per pass of the step phase
+constexpr long long kPMaxStage = 4096;   // CDF staging entries (sum of all I_k)
+constexpr int kPMaxFpc = 1024;    // fibers per CTA
+
+__host__ __device__ inline size_t up128(size_t v) { return (v + 127) / 128 * 128; }
+
+// Shared-memory carve-up (byte offsets).
+struct PersLayout {
+    size_t cdf, dsm, idx, jcol, sw, stage, x, fr, bhi, blo, stage_bytes, zf, h, bar, total;
+    int nstage;
+    __host__ __device__ PersLayout(const PersArgs &a)
+    {
+        const int N = a.P.N;
+        size_t o = 0;
+        cdf = o;  o += up128((size_t)a.sumI * 8);
+        dsm = o;  o += 2 * kThreads * 8;
+        idx = o;  o += up128((size_t)a.fpc * N * 4);
+        jcol = o; o += up128((size_t)a.fpc * 8);
+        sw = o;   o += up128((size_t)a.fpc * 4);
+        x = 0;
+        fr = up128((size_t)kPK * a.ntile * kPM * 2);
+        bhi = fr + up128((size_t)kPK * (N - 1) * a.R4 * 4);
+        blo = bhi + (size_t)kPK * a.Npad * 2;
+        stage_bytes = up128(blo + (size_t)kPK * a.Npad * 2);
+        nstage = kPS;
+        stage = o;
+        size_t ring = stage_bytes * kPS;
+        // the step phase reuses the ring for A rows, M rows and new rows
+        const size_t own = 3 * up128((size_t)kPOwnBlock * a.R4 * 4);
+        o += ring > own ? ring : own;
+        zf = o;   o += 2 * (size_t)kPK * kPHd * 4;
+        h = o;    o += (size_t)kPHd * kPHd * 4;
+        bar = o;  o += 8 * (kPS + 2);
+        total = o;
+        // at least half of the SM's shared memory, so one CTA per SM (the
+        // tensor-memory allocation assumes it)
+        if (total < 120 * 1024) total = 120 * 1024;
+    }
+};
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int Nw>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(Nw) : "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t cluster_nctas()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;\n" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    cluster_arrive();
+    cluster_wait();
+}
+
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;\n" ::"r"(addr), "f"(v) : "memory");
+}
+
+// One MMA: D(tmem) (+)= A(desc) B(desc), kind::f16 (bf16 in, f32 accumulate).
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+
+// s_f = (1/(B J_n)) prod_{k != n, ascending} Q_k / q_k(i_k) in FP32 (the same
+// arithmetic as the other engines' fiber_weight), from the staged CDFs.
+__device__ __forceinline__ float pers_weight(const PersArgs &a, int n, const int *row,
+                                             const unsigned long long *stage)
+{
+    const Problem<float> &P = a.P;
+    float s = P.inv_bj[n];
+    for (int k = 0; k < P.N; ++k) {
+        if (k == n) continue;
+        if (P.sampling == CPD_SAMPLE_UNIFORM) {
+            s *= (float)P.dims[k];
+        } else {
+            const unsigned long long *c = stage + a.off[k];
+            const unsigned long long q = c[row[k]] - (row[k] > 0 ? c[row[k] - 1] : 0ULL);
+            s *= __ull2float_rn(c[P.dims[k] - 1]) / __ull2float_rn(q);
+        }
+    }
+    return s;
+}
+
+}  // namespace
+
+// One cluster per problem. `one` is used when `many` is null (single
+// decomposition); otherwise cluster g runs many[g].
+__global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const PersArgs *__restrict__ many,
+                                                      long long T)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(16) PersArgs sa;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort, s_flags;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int cs = (int)cluster_nctas();
+    const int rank = (int)cluster_rank();
+    const int g = blockIdx.x / cs;
+    {
+        static_assert(sizeof(PersArgs) % 8 == 0, "PersArgs is copied in 8-byte words");
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(many ? many + g : &one);
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sa);
+        for (int q = tid; q < (int)(sizeof(PersArgs) / 8); q += blockDim.x) dst[q] = src[q];
+    }
+    if (tid == 0) {
+        s_abort = 0;
+        s_flags = 0;
+    }
+    __syncthreads();
+    const PersArgs &a = sa;
+    const Problem<float> &P = a.P;
+    const int N = P.N, R = P.R, R4 = a.R4, Npad = a.Npad, cst = a.cst, fpc = a.fpc;
+    const PersLayout L(a);
+    unsigned long long *stage = reinterpret_cast<unsigned long long *>(smem + L.cdf);
+    unsigned long long *dsm = reinterpret_cast<unsigned long long *>(smem + L.dsm);
+    int *sidx = reinterpret_cast<int *>(smem + L.idx);
+    long long *jcol = reinterpret_cast<long long *>(smem + L.jcol);
+    float *sw = reinterpret_cast<float *>(smem + L.sw);
+    unsigned char *ring = smem + L.stage;
+    float *zf = reinterpret_cast<float *>(smem + L.zf);
+    float *sH = reinterpret_cast<float *>(smem + L.h);
+    const uint32_t bar0 = smem_u32(smem + L.bar);   // empty[0..kPS), mma done
+    const uint32_t bar_mma = bar0 + 8 * kPS;
+    const bool tr = (g == 0 && rank == 0);
+
+    // ---- set-up -------------------------------------------------------------
+    int tcols = 32;
+    while (tcols < a.ntile * cst) tcols <<= 1;
+    if (tid == 0) {
+        for (int q = 0; q <= kPS; ++q) mbar_init(bar0 + 8 * q, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    // CDFs of every mode (current at launch start: this engine never defers)
+    if (P.sampling != CPD_SAMPLE_UNIFORM)
+        for (int k = 0; k < N; ++k)
+            for (long long i = tid; i < P.dims[k]; i += blockDim.x) stage[a.off[k] + i] = __ldcg(P.cdf[k] + i);
+    for (int e = tid; e < 2 * kPK * kPHd; e += blockDim.x) zf[e] = 0.f;
+    // factors -> padded private copies, split over the cluster
+    for (int k = 0; k < N; ++k) {
+        const long long tot = P.dims[k] * R4;
+        for (long long e = (long long)rank * blockDim.x + tid; e < tot; e += (long long)cs * blockDim.x) {
+            const long long i = e / R4;
+            const int r = (int)(e % R4);
+            a.Ap[k][e] = r < R ? __ldcg(P.A[k] + i * R + r) : 0.f;
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    cluster_sync_all();
+
+    long long t = __ldcg(P.t_dev);
+    int n_prev = -1;
+    unsigned commits[kPS] = {0, 0, 0}, waited[kPS] = {0, 0, 0};
+    unsigned mma_iters = 0;
+    const int f0 = rank * fpc;
+    const int nf = (P.B - f0) < fpc ? ((P.B - f0) > 0 ? P.B - f0 : 0) : fpc;
+    const int nchunks = (nf + kPK - 1) / kPK;
+    int flags = 0;
+
+    for (long long it = 0; it < T; ++it, ++t) {
+        const bool last = it == T - 1;
+        const int n = mode_draw(P.seed, t, N);
+        const long long In = P.dims[n], ld = P.ld[n];
+        const int ntile = (int)((In + kPM - 1) / kPM);
+        const float *An = a.Ap[n];
+        trace_stamp(P.trace, 0, tr);
+
+        // 1. draws of the own fibers (Alg. 3), from the staged CDFs
+        {
+            const int ch = (nf + 31) / 32;
+            for (int job = warp; job < ch * N; job += kThreads / 32) {
+                const int k = job / ch, c = job % ch;
+                const int fl = 32 * c + lane;
+                const bool act = fl < nf;
+                if (k == n) {
+                    if (act) sidx[fl * N + k] = -1;
+                    continue;
+                }
+                const long long Ik = P.dims[k];
+                const unsigned long long x = act ? fiber_word(P.seed, t, (long long)(f0 + fl), k) : 0ULL;
+                long long i;
+                if (P.sampling == CPD_SAMPLE_UNIFORM) {
+                    i = (long long)__umul64hi(x, (unsigned long long)Ik);
+                } else {
+                    const unsigned long long *c0 = stage + a.off[k];
+                    i = warp_search_staged(c0, Ik, __umul64hi(x, c0[Ik - 1]), act);
+                }
+                if (act) sidx[fl * N + k] = (int)i;
+            }
+        }
+        __syncthreads();
+        // columns (Eq. (2)) and weights s_f of the own fibers; padding slots get 0
+        for (int fl = tid; fl < nchunks * kPK; fl += blockDim.x) {
+            long long j = 0;
+            float w = 0.f;
+            if (fl < nf) {
+                const int *row = sidx + fl * N;
+                long long Jp = 1;
+                for (int k = 0; k < N; ++k) {
+                    if (k == n) continue;
+                    j += (long long)row[k] * Jp;
+                    Jp *= P.dims[k];
+                }
+                w = pers_weight(a, n, row, stage);
+                if (last)
+                    for (int k = 0; k < N; ++k) P.idx[(long long)(f0 + fl) * N + k] = row[k];
+            }
+            jcol[fl] = j;
+            sw[fl] = w;
+        }
+        __syncthreads();
+        trace_stamp(P.trace, 2, tr);
+
+        // 2. gather + tensor-core contraction, streamed in chunks of 16 fibers
+        const uint32_t idesc = idesc_bf16(kPM, Npad);
+        const __nv_bfloat16 *rep = reinterpret_cast<const __nv_bfloat16 *>(P.rep[n]);
+        const int g8 = ntile * (kPM / 8);              // 16-byte row pieces per fiber (incl. zero fill)
+        const int pr = R4 / 4;                          // 16-byte pieces per factor row
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        const int hrb = tid >> 4, hcb = tid & 15;
+        for (int q = 0; q < nchunks + kPS - 1; ++q) {
+            if (q < nchunks) {
+                const int s = q % kPS;
+                if (commits[s] > waited[s]) {
+                    if (!s_abort && !mbar_wait_bounded(bar0 + 8 * s, waited[s] & 1)) s_abort = 1;
+                    ++waited[s];
+                }
+                unsigned char *st = ring + (size_t)s * L.stage_bytes;
+                const uint32_t xs = smem_u32(st + L.x), frs = smem_u32(st + L.fr);
+                for (int e = tid; e < kPK * g8; e += blockDim.x) {
+                    const int f = e / g8, ig = e % g8;
+                    const int fl = q * kPK + f;
+                    const bool v = fl < nf && 8LL * ig < ld;
+                    const __nv_bfloat16 *src = v ? rep + jcol[fl] * ld + 8LL * ig : rep;
+                    cp_async16(xs + (uint32_t)((((f >> 3) * g8 + ig) << 7) + ((f & 7) << 4)), src, v ? 16u : 0u);
+                }
+                for (int e = tid; e < kPK * (N - 1) * pr; e += blockDim.x) {
+                    const int f = e / ((N - 1) * pr), rem = e % ((N - 1) * pr);
+                    const int kk = rem / pr, pc = rem % pr;
+                    const int k = kk + (kk >= n ? 1 : 0);
+                    const int fl = q * kPK + f;
+                    const bool v = fl < nf;
+                    const float *src = v ? a.Ap[k] + (long long)sidx[fl * N + k] * R4 + 4 * pc : a.Ap[k];
+                    cp_async16(frs + (uint32_t)(((f * (N - 1) + kk) * R4 + 4 * pc) * 4), src, v ? 16u : 0u);
+                }
+            }
+            cp_async_commit();
+            const int c2 = q - (kPS - 1);
+            if (c2 < 0) continue;
+            cp_async_wait<kPS - 1>();
+            fence_async_smem();
+            __syncthreads();
+            // build z_f (fp32, for H) and the B operands Z' = s_f z_f as a bf16
+            // hi/lo pair, K-major: core matrix (f/8, r/8), 8 fibers per 16 bytes
+            const int s2 = c2 % kPS;
+            unsigned char *st2 = ring + (size_t)s2 * L.stage_bytes;
+            const float *fr = reinterpret_cast<const float *>(st2 + L.fr);
+            __nv_bfloat16 *bh = reinterpret_cast<__nv_bfloat16 *>(st2 + L.bhi);
+            __nv_bfloat16 *bl = reinterpret_cast<__nv_bfloat16 *>(st2 + L.blo);
+            float *z2 = zf + (c2 & 1) * kPK * kPHd;
+            for (int job = tid; job < Npad * 2; job += blockDim.x) {
+                const int r = job % Npad, fb8 = job / Npad;
+                __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int f = 8 * fb8 + u;
+                    const int fl = c2 * kPK + f;
+                    float z = 0.f;
+                    if (r < R && fl < nf) {
+                        const float *row = fr + (size_t)f * (N - 1) * R4 + r;
+                        z = 1.f;
+                        for (int kk = 0; kk < N - 1; ++kk) z = z * row[kk * R4];
+                    }
+                    z2[f * kPHd + r] = z;
+                    const float zs = z * sw[fl];
+                    hi[u] = __float2bfloat16_rn(zs);
+                    lo[u] = __float2bfloat16_rn(zs - __bfloat162float(hi[u]));
+                }
+                const int off = ((fb8 * (Npad >> 3) + (r >> 3)) << 6) + ((r & 7) << 3);
+                *reinterpret_cast<uint4 *>(bh + off) = *reinterpret_cast<uint4 *>(hi);
+                *reinterpret_cast<uint4 *>(bl + off) = *reinterpret_cast<uint4 *>(lo);
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0 && !s_abort) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t xs = smem_u32(st2 + L.x);
+                const uint64_t dh = smem_desc(smem_u32(bh), (uint32_t)(Npad >> 3) * 128u, 128u);
+                const uint64_t dl = smem_desc(smem_u32(bl), (uint32_t)(Npad >> 3) * 128u, 128u);
+                for (int m = 0; m < ntile; ++m) {
+                    const uint64_t da = smem_desc(xs + (uint32_t)m * 2048u, (uint32_t)g8 * 128u, 128u);
+                    const uint32_t d = tmem + (uint32_t)(m * cst);
+                    mma_bf16(d, da, dh, idesc, c2 > 0 ? 1u : 0u);
+                    mma_bf16(d, da, dl, idesc, 1u);
+                }
+                mma_commit(bar0 + 8 * s2);
+            }
+            ++commits[s2];
+            // H over this chunk's fibers, a 4 x 4 block per thread
+            for (int f = 0; f < kPK; ++f) {
+                const int fl = c2 * kPK + f;
+                const float s = fl < nf ? sw[fl] : 0.f;
+                const float4 zr = *reinterpret_cast<const float4 *>(z2 + f * kPHd + 4 * hrb);
+                const float4 zc = *reinterpret_cast<const float4 *>(z2 + f * kPHd + 4 * hcb);
+                const float ar[4] = {zr.x * s, zr.y * s, zr.z * s, zr.w * s}, ac[4] = {zc.x, zc.y, zc.z, zc.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] += ar[u] * ac[v];
+            }
+        }
+        // every product of the iteration has completed
+        if (nchunks > 0) {
+            if (tid == 0 && !s_abort) mma_commit(bar_mma);
+            __syncthreads();
+            if (!s_abort && !mbar_wait_bounded(bar_mma, mma_iters & 1)) s_abort = 1;
+            ++mma_iters;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        trace_stamp(P.trace, 7, tr);
+
+        // 3. partials to the scratch: M rows of every tile, H
+        {
+            float *pm = a.part + (size_t)rank * a.ntile * kPM * cst;
+            const int qd = warp & 3, hh = warp >> 2;
+            for (int m = 0; m < ntile; ++m) {
+                if (32 * hh >= Npad) break;
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(m * cst + 32 * hh), v);
+                const long long row = (long long)m * kPM + 32 * qd + lane;
+                if (row < In) {
+                    float4 *dst = reinterpret_cast<float4 *>(pm + row * cst + 32 * hh);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const bool z0 = nchunks == 0 || s_abort;
+                        dst[c] = z0 ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                    : make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                    }
+                }
+            }
+            float *ph = a.hpart + (size_t)rank * kPHd * kPHd;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                *reinterpret_cast<float4 *>(ph + (4 * hrb + u) * kPHd + 4 * hcb) =
+                    make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        trace_stamp(P.trace, 8, tr);
+        cluster_sync_all();   // B1: every partial is in the scratch
+        trace_stamp(P.trace, 14, tr);
+
+        // 4. owned rows of H: summed in ascending CTA order, sent to every CTA
+        {
+            const int hpc = (R + cs - 1) / cs;
+            const int h0 = rank * hpc, h1 = (h0 + hpc) < R ? h0 + hpc : R;
+            const uint32_t hbase = smem_u32(sH);
+            for (int e = tid; e < (h1 > h0 ? (h1 - h0) * R : 0); e += blockDim.x) {
+                const int i = h0 + e / R, c = e % R;
+                float v = 0.f;
+                for (int src = 0; src < cs; ++src) v += __ldcg(a.hpart + (size_t)src * kPHd * kPHd + i * kPHd + c);
+                const uint32_t addr = hbase + (uint32_t)((i * kPHd + c) * 4);
+                for (int d = 0; d < cs; ++d) st_cluster_f32(map_shared(addr, (uint32_t)d), v);
+            }
+        }
+        cluster_sync_all();   // B2: H complete in every CTA
+        trace_stamp(P.trace, 15, tr);
+
+        // 5. owned rows of A^(n): M, G = A H - M, the step, the new weights
+        const long long ngroups = (In + 31) / 32;
+        const long long gpc = (ngroups + cs - 1) / cs;
+        const long long row0 = 32 * gpc * rank;
+        const long long row1 = (row0 + 32 * gpc) < In ? row0 + 32 * gpc : In;
+        float *sA = reinterpret_cast<float *>(ring);
+        float *sM = sA + up128((size_t)kPOwnBlock * R4 * 4) / 4;
+        float *sN = sM + up128((size_t)kPOwnBlock * R4 * 4) / 4;
+        const uint32_t wslot = smem_u32(stage + a.off[n]);
+        const double alpha = P.step == CPD_STEP_DECAY ? P.beta / ((double)t + P.gamma) : P.alpha;
+        for (long long b0 = row0; b0 < row1; b0 += kPOwnBlock) {
+            const int nr = (int)((row1 - b0) < kPOwnBlock ? row1 - b0 : kPOwnBlock);
+            for (int e = tid; e < nr * (R4 / 4); e += blockDim.x) {
+                const int i = e / (R4 / 4), c4 = e % (R4 / 4);
+                const long long row = b0 + i;
+                const float4 av = __ldcg(reinterpret_cast<const float4 *>(An + row * R4) + c4);
+                float4 mv = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int src = 0; src < cs; ++src) {
+                    const float4 p = __ldcg(reinterpret_cast<const float4 *>(a.part + ((size_t)src * a.ntile * kPM + row) * cst) + c4);
+                    mv.x += p.x;
+                    mv.y += p.y;
+                    mv.z += p.z;
+                    mv.w += p.w;
+                }
+                reinterpret_cast<float4 *>(sA + i * R4)[c4] = av;
+                reinterpret_cast<float4 *>(sM + i * R4)[c4] = mv;
+            }
+            __syncthreads();
+            for (int e = tid; e < nr * R; e += blockDim.x) {
+                const int i = e / R, r = e % R;
+                const long long row = b0 + i;
+                float ah = 0.f;
+                for (int s = 0; s < R; ++s) ah += sA[i * R4 + s] * sH[s * kPHd + r];
+                const float gr = ah - sM[i * R4 + r];
+                const float aold = sA[i * R4 + r];
+                float an;
+                if (P.step == CPD_STEP_ADAGRAD) {
+                    double *Sp = P.S[n] + row * R + r;
+                    const double S = __fma_rn((double)gr, (double)gr, *Sp);
+                    *Sp = S;
+                    an = aold - (float)P.eta * gr * rsqrtf((float)S + (float)P.b);
+                } else {
+                    an = aold - (float)alpha * gr;
+                }
+                if (P.constraint == CPD_CONSTRAINT_NONNEG && an < 0.f) an = 0.f;   // projection; NaN kept
+                if (!isfinite(an) || !isfinite(gr)) flags |= kStNonFinite;
+                a.Ap[n][row * R4 + r] = an;
+                sN[i * R + r] = an;
+                if (last) P.G[row * R + r] = gr;
+            }
+            __syncthreads();
+            if (P.sampling == CPD_SAMPLE_EUCLIDEAN) {
+                for (int lr = warp; lr < nr; lr += kThreads / 32) {
+                    // the canonical tree leaves the row's weight in lane 0
+                    const double wv = __shfl_sync(0xffffffffu, warp_row_weight(sN + lr * R, R), 0);
+                    if (lane < cs) {
+                        const uint32_t addr = wslot + (uint32_t)((b0 + lr) * 8);
+                        st_cluster_u64(map_shared(addr, (uint32_t)lane), (unsigned long long)__double_as_longlong(wv));
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        trace_stamp(P.trace, 18, tr);
+        cluster_sync_all();   // B3: new rows in the private factor, weights in every CTA
+        trace_stamp(P.trace, 20, tr);
+
+        // 6. mode n's CDF from its new weights, in place (exact fixed point)
+        if (P.sampling == CPD_SAMPLE_EUCLIDEAN) {
+            if (!block_distribution_inplace(stage + a.off[n], In, dsm)) flags |= kStDegenerate;
+        }
+        __syncthreads();
+        n_prev = n;
+        trace_stamp(P.trace, 21, tr);
+    }
+
+    // ---- results back to the context ----------------------------------------
+    for (int k = 0; k < N; ++k) {
+        const long long tot = P.dims[k] * R;
+        for (long long e = (long long)rank * blockDim.x + tid; e < tot; e += (long long)cs * blockDim.x) {
+            const long long i = e / R;
+            const int r = (int)(e % R);
+            P.A[k][e] = __ldcg(a.Ap[k] + i * R4 + r);
+        }
+    }
+    if (rank == 0) {
+        if (P.sampling != CPD_SAMPLE_UNIFORM)
+            for (int k = 0; k < N; ++k)
+                for (long long i = tid; i < P.dims[k]; i += blockDim.x) P.cdf[k][i] = stage[a.off[k] + i];
+        if (tid == 0) {
+            *P.t_dev = t;
+            if (n_prev >= 0) *P.n_last = n_prev;
+            *P.dirty = -1;
+        }
+    }
+    if (flags) atomicOr(&s_flags, flags);
+    __syncthreads();
+    if (tid == 0) {
+        if (s_flags) atomicOr(P.status, s_flags);
+        if (s_abort) atomicOr(P.status, kStTimeout);
+    }
+    // products still in flight after a timed-out wait must finish before the
+    // accumulator is freed
+    if (s_abort && tid == 0) mbar_wait_bounded(bar_mma, mma_iters & 1);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tcols) : "memory");
+    cluster_sync_all();   // no CTA leaves while another may still address its shared memory
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+bool pers_supported(const cpd_config &c)
+{
+    if (c.x_dtype != CPD_BF16 || c.R > 64 || c.sampling == CPD_SAMPLE_LEVERAGE) return false;
+    long long sumI = 0, imax = 0;
+    for (int k = 0; k < c.N; ++k) {
+        sumI += c.dims[k];
+        imax = c.dims[k] > imax ? c.dims[k] : imax;
+    }
+    const int Npad = (c.R + 15) / 16 * 16;
+    const int cst = Npad <= 32 ? 32 : 64;
+    return sumI <= kPMaxStage && ((imax + kPM - 1) / kPM) * cst <= 512;
+}
+
+void pers_fill(PersArgs &a, int cs)
+{
+    const Problem<float> &P = a.P;
+    a.cs = cs;
+    a.fpc = (P.B + cs - 1) / cs;
+    a.fpc = (a.fpc + kPK - 1) / kPK * kPK;
+    a.R4 = (P.R + 3) / 4 * 4;
+    a.Npad = (P.R + 15) / 16 * 16;
+    a.cst = a.Npad <= 32 ? 32 : 64;
+    long long imax = 0, o = 0;
+    for (int k = 0; k < P.N; ++k) {
+        a.off[k] = o;
+        o += P.dims[k];
+        imax = P.dims[k] > imax ? P.dims[k] : imax;
+    }
+    a.sumI = o;
+    a.ntile = (int)((imax + kPM - 1) / kPM);
+}
+
+size_t pers_smem_bytes(const PersArgs &a)
+{
+    if (a.fpc > kPMaxFpc) return (size_t)1 << 30;   // refused by the caller (over the limit)
+    return PersLayout(a).total;
+}
+
+static cudaError_t pers_attrs(int cs, size_t smem)
+{
+    static size_t attr_bytes = 0;
+    static bool nonportable = false;
+    cudaError_t e = cudaSuccess;
+    if (smem > attr_bytes) {
+        e = cudaFuncSetAttribute(k_pers, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        attr_bytes = smem;
+    }
+    if (cs > 8 && !nonportable) {
+        e = cudaFuncSetAttribute(k_pers, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        nonportable = true;
+    }
+    return cudaSuccess;
+}
+
+static void pers_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr, int grid, int cs, size_t smem,
+                        cudaStream_t s)
+{
+    cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+}
+
+int pers_max_clusters(const PersArgs &a)
+{
+    const size_t smem = pers_smem_bytes(a);
+    if (smem > 227 * 1024 || a.cs < 1 || a.cs > 16) return 0;
+    if (pers_attrs(a.cs, smem) != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    pers_config(cfg, attr, a.cs, a.cs, smem, nullptr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_pers, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t launch_pers(const PersArgs &a, long long T, cudaStream_t s)
+{
+    const size_t smem = pers_smem_bytes(a);
+    if (cudaError_t e = pers_attrs(a.cs, smem); e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    pers_config(cfg, attr, a.cs, a.cs, smem, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_pers, a, (const PersArgs *)nullptr, T);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
+}
+
+cudaError_t launch_pers_group(const PersArgs *dargs, int G, int cs, size_t smem, long long T, cudaStream_t s)
+{
+    if (cudaError_t e = pers_attrs(cs, smem); e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    pers_config(cfg, attr, G * cs, cs, smem, s);
+    PersArgs dummy{};
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_pers, dummy, dargs, T);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
+}
+
+}  // namespace cpd

@@ -283,7 +283,7 @@ def _full(cpd, orc, name, sampling, steps, warm, engine="auto", max_ctas=0, auto
     del X
     desc = dec.describe()
     dec.sgd_iters(warm)
-    key = "bf16_tensor" if desc["engine"] in ("tensor", "cluster") else xdt
+    key = "bf16_tensor" if desc["engine"] in ("tensor", "cluster", "persistent") else xdt
     ocfg = _ocfg(orc, dims, R, B, xdt, sampling, w["step"], w["sample_seed"],
                  eta=w.get("eta", 0.1), b=w.get("b", 1e-12))
     worst = forced(dec, orc, ocfg, xb, steps, key)
@@ -335,3 +335,79 @@ def test_teacher_forced_edge_cases(cpd, orc, dims, R, B, xdt, sampling):
     assert t == pytest.approx(otol, rel=1e-9 if xdt == "f64" else 1e-4)
     print(dims, R, B, worst, dec.describe())
     dec.close()
+
+
+# --------------------------------------------------------------------------
+# Persistent cluster engine (engine 4): whole calls of cpd_sgd_iters in one
+# launch of one thread-block cluster. max_ctas is its cluster size.
+# --------------------------------------------------------------------------
+PERSISTENT = [
+    # dims, R, B, sampling, cluster size: ragged row tiles (200 = 128 + 72,
+    # 129 = 128 + 1), a ragged last chunk of fibers, R below 16, at 64 and
+    # between, one CTA without fibers (B = 77 over 8 CTAs of 16)
+    ((200, 150, 100), 50, 300, "euclidean", 4),
+    ((40, 36, 130, 28), 12, 77, "euclidean", 8),
+    ((129, 257, 70), 64, 512, "euclidean", 2),
+    ((300, 64, 90), 20, 1024, "uniform", 8),
+    ((90, 70, 60), 8, 100, "euclidean", 1),
+]
+
+
+@pytest.mark.parametrize("dims,R,B,sampling,cs", PERSISTENT)
+def test_teacher_forced_persistent(cpd, orc, dims, R, B, sampling, cs):
+    A, X, A0 = make_problem(dims, R, x_dtype="bf16", lognormal_rows=True)
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype="bf16",
+                            sampling=sampling, step="adagrad", seed=77, engine="persistent", max_ctas=cs)
+    d = dec.describe()
+    assert d["engine"] == "persistent" and d["cluster"] == cs, d
+    ocfg = _ocfg(orc, dims, R, B, "bf16", sampling, "adagrad", 77)
+    worst = forced(dec, orc, ocfg, oracle_xbuf(X), 8, "bf16_tensor")
+    print(dims, R, B, sampling, cs, worst, d)
+    dec.close()
+
+
+@pytest.mark.parametrize("step,kw", [("fixed", dict(alpha=0.05)), ("decay", dict(beta=0.05, gamma=2.0))])
+def test_persistent_other_steps_and_nonneg(cpd, orc, step, kw):
+    dims, R, B = (150, 120, 90), 24, 256
+    A, X, A0 = make_problem(dims, R, x_dtype="bf16", nonneg=True, noise=5e-2)
+    kw = dict(kw, constraint="nonneg")
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype="bf16",
+                            sampling="euclidean", step=step, seed=5, engine="persistent", max_ctas=4, **kw)
+    ocfg = _ocfg(orc, dims, R, B, "bf16", "euclidean", step, 5, **kw)
+    forced(dec, orc, ocfg, oracle_xbuf(X), 6, "bf16_tensor")
+    dec.sgd_iters(300)
+    assert all(bool((a >= 0).all()) for a in dec.factors())
+    dec.close()
+
+
+def test_persistent_chunking_is_bitwise(cpd):
+    """One launch of 100 iterations and launches of 1, 31, 32, 5, 31 give the same bits."""
+    dims, R, B = (120, 100, 80), 16, 256
+    _, X, A0 = make_problem(dims, R, x_dtype="bf16")
+    kw = dict(dims=dims, R=R, B=B, x_dtype="bf16", sampling="euclidean", step="adagrad", seed=9,
+              engine="persistent", max_ctas=4)
+    d1 = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], **kw)
+    d1.sgd_iters(100)
+    d2 = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], **kw)
+    for q in (1, 31, 32, 5, 31):
+        d2.sgd_iters(q)
+    assert d1.t == d2.t == 100
+    for a, b in zip(d1.factors(), d2.factors()):
+        assert torch.equal(a, b)
+    for a, b in zip(d1.adagrad(), d2.adagrad()):
+        assert torch.equal(a, b)
+    f1, t1 = d1.fit()
+    assert np.isfinite(f1) and t1 < 1.0
+    d1.close()
+    d2.close()
+
+
+@pytest.mark.parametrize("cs", [8, 16])
+def test_full_c4_persistent(cpd, orc, cs):
+    """The 1000^3 workload on the persistent engine, teacher-forced at full size."""
+    try:   # a 16-CTA cluster is a non-portable size: only where the device can schedule it
+        _full(cpd, orc, "c4_1000cube_bf16", "euclidean", steps=3, warm=50, engine="persistent", max_ctas=cs)
+    except cpd.CpdError as e:
+        if cs == 16 and e.status == cpd.ECUDA and "cannot be scheduled" in str(e):
+            pytest.skip("this device does not co-schedule 16-CTA clusters with this layout")
+        raise
