@@ -150,6 +150,21 @@ cpd_status cpd_init(const cpd_config *cfg, const void *X, int x_loc,
 cpd_status cpd_sgd_iters(cpd_ctx *ctx, int64_t iters, void *stream);
 
 /*
+ * cpd_gradients -- K independent mini-batch gradients of mode n at the
+ * current factors (Eq. (11), each batch drawn by Alg. 3 from the current
+ * per-factor distributions), the samples whose spread Thm 10 and Fig. 3
+ * describe. Batch b uses the random draws that iteration t0 + b would use,
+ * with the mode fixed to n. G_out: device memory for K x I_n x R floats
+ * (batch-major, each gradient row-major). Nothing in the context changes.
+ * The batches run concurrently on up to as many thread-block clusters as
+ * the device co-schedules; this is also how the fiber gather is measured in
+ * bulk (K B fibers per launch). Asynchronous on `stream`. Needs the
+ * persistent engine (cpd_config.engine = 4). Errors: CPD_EINVAL, CPD_ENOMEM,
+ * CPD_ECUDA.
+ */
+cpd_status cpd_gradients(cpd_ctx *ctx, int32_t n, int64_t t0, int32_t K, float *G_out, void *stream);
+
+/*
  * cpd_prepare -- capture ahead of time the CUDA graphs that a later
  * cpd_sgd_iters(ctx, iters, stream) replays (chunks of 32 iterations and one
  * chunk per set bit of iters mod 32), so that call pays no capture. Runs no
@@ -405,11 +420,14 @@ cpd_status cpd_autotune(const cpd_config *cfg, const void *X, int x_loc, const v
  *
  * cpd_group_create -- group G contexts (array of G distinct handles, borrowed:
  *  they must outlive the group). Members must share the tensor dtype and the
- *  gradient engine, which must be the CUDA-core (1) or the per-CTA
- *  tensor-core (2) engine, and none may sample by leverage. The members'
- *  launch state is captured at creation (later cpd_trace / cpd_profile
- *  changes do not reach the group). Allocates a few hundred bytes per member
- *  on `stream` and synchronises it.
+ *  gradient engine, which must be the CUDA-core (1), the per-CTA
+ *  tensor-core (2) or the persistent (4) engine, and none may sample by
+ *  leverage. Persistent members must share the cluster size; the group then
+ *  runs every member's iterations in ONE launch per call, one thread-block
+ *  cluster per member (the other engines use one gradient and one update
+ *  launch per iteration). The members' launch state is captured at
+ *  creation (later cpd_trace / cpd_profile changes do not reach the group).
+ *  Allocates about a kilobyte per member on `stream` and synchronises it.
  *  Errors: CPD_EINVAL (NULL, duplicate or incompatible members), CPD_ENOMEM,
  *  CPD_ECUDA.
  * cpd_group_iters -- run `iters` iterations of every member, enqueued on

@@ -69,6 +69,7 @@ def _load():
         "cpd_init": [ctypes.POINTER(cpd_config), P, I32, P, I32, P, ctypes.POINTER(P)],
         "cpd_sgd_iters": [P, I64, P],
         "cpd_prepare": [P, I64, P],
+        "cpd_gradients": [P, I32, I64, I32, P, P],
         "cpd_fit": [P, P, P, P],
         "cpd_fit_start": [P, P],
         "cpd_fit_poll": [P, P, P],
@@ -169,6 +170,11 @@ def cpd_sgd_iters(ctx, iters: int, stream=None) -> None:
 
 def cpd_prepare(ctx, iters: int, stream=None) -> None:
     _check(_lib.cpd_prepare(ctx, int(iters), _stream(stream)))
+
+
+def cpd_gradients(ctx, n: int, t0: int, K: int, G_out: torch.Tensor, stream=None) -> None:
+    """K mini-batch gradients of mode n into the device tensor G_out (K x I_n x R float32)."""
+    _check(_lib.cpd_gradients(ctx, int(n), int(t0), int(K), G_out.data_ptr(), _stream(stream)))
 
 
 def cpd_fit(ctx, stream=None) -> tuple[float, float]:

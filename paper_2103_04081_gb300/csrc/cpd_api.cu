@@ -74,6 +74,8 @@ struct cpd_ctx {
     bool fit_started = false;
     PersArgs pers{};                 // persistent engine: launch arguments (P refreshed per launch)
     int64_t prof_iters = 0;          // iterations covered by the profiled launches
+    float *gpart = nullptr, *ghpart = nullptr;   // cpd_gradients: scratch of gclusters clusters
+    int gclusters = 0;
 
     template <class F>
     cudaError_t with_problem(F &&f)
@@ -554,6 +556,42 @@ static cudaError_t run_pers(cpd_ctx *c, int64_t iters, cudaStream_t s)
     return cudaSuccess;
 }
 
+extern "C" cpd_status cpd_gradients(cpd_ctx *c, int32_t n, int64_t t0, int32_t K, float *G_out, void *stream)
+{
+    if (!c || !G_out || K < 1 || t0 < 0) return fail(CPD_EINVAL, "bad argument");
+    if (c->engine != kEnginePersistent) return fail(CPD_EINVAL, "cpd_gradients needs the persistent engine (4)");
+    if (n < 0 || n >= c->cfg.N) return fail(CPD_EINVAL, "mode out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    PersArgs a = c->pers;
+    a.P = c->Pf;
+    const int ncl = std::max(1, std::min(K, c->max_clusters));
+    if (ncl > c->gclusters) {   // scratch for ncl clusters, kept for later calls
+        void *p1 = nullptr, *p2 = nullptr;
+        CK(dmalloc(c, &p1, (size_t)ncl * a.cs * a.ntile * 128 * a.cst * sizeof(float)));
+        CK(dmalloc(c, &p2, (size_t)ncl * a.cs * 64 * 64 * sizeof(float)));
+        c->gpart = (float *)p1;
+        c->ghpart = (float *)p2;
+        c->gclusters = ncl;
+    }
+    a.part = c->gpart;
+    a.hpart = c->ghpart;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profiling && c->prof_used < kProfSlots) {
+        e0 = c->ev[3 * c->prof_used];
+        e1 = c->ev[3 * c->prof_used + 1];
+        ++c->prof_used;
+        c->prof_iters += 1;
+    }
+    if (e0) cudaEventRecord(e0, s);
+    const cudaError_t e = launch_pers_gradients(a, n, t0, K, ncl, G_out, s);
+    if (e1) {
+        cudaEventRecord(e1, s);
+        cudaEventRecord(c->ev[3 * (c->prof_used - 1) + 2], s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cpd_gradients launch");
+    return CPD_OK;
+}
+
 extern "C" cpd_status cpd_sgd_iters(cpd_ctx *c, int64_t iters, void *stream)
 {
     if (!c || iters < 0) return fail(CPD_EINVAL, "bad context or iteration count");
@@ -883,6 +921,10 @@ struct cpd_group {
     cudaGraphExec_t graph[kGraphSizes] = {};
     cudaStream_t graph_stream = nullptr;
     cudaStream_t last = nullptr;          // last stream work was enqueued on
+    // persistent members: one cluster each, in one launch per call
+    PersArgs *dpers = nullptr;
+    int pers_cs = 0;
+    size_t pers_smem = 0;
 };
 
 template <class T>
@@ -934,8 +976,10 @@ extern "C" cpd_status cpd_group_create(cpd_ctx *const *ctxs, int32_t G, void *st
         if (!c) return fail(CPD_EINVAL, "NULL context");
         for (int r = 0; r < q; ++r)
             if (ctxs[r] == c) return fail(CPD_EINVAL, "a context appears twice in the group");
-        if (c->engine != kEngineSimt && c->engine != kEngineTensor)
-            return fail(CPD_EINVAL, "grouped launches take CUDA-core or per-CTA tensor-core contexts only");
+        if (c->engine != kEngineSimt && c->engine != kEngineTensor && c->engine != kEnginePersistent)
+            return fail(CPD_EINVAL, "grouped launches take CUDA-core, per-CTA tensor-core or persistent contexts");
+        if (c->engine == kEnginePersistent && c->pers.cs != c0->pers.cs)
+            return fail(CPD_EINVAL, "persistent group members must share the cluster size");
         if (c->cfg.sampling == CPD_SAMPLE_LEVERAGE)
             return fail(CPD_EINVAL, "grouped launches do not take leverage sampling");
         if (c->fbytes != c0->fbytes || c->cfg.x_dtype != c0->cfg.x_dtype || c->engine != c0->engine ||
@@ -950,11 +994,29 @@ extern "C" cpd_status cpd_group_create(cpd_ctx *const *ctxs, int32_t G, void *st
     g->members.assign(ctxs, ctxs + G);
     g->home = (cudaStream_t)stream;
     g->last = g->home;
-    const cpd_status st = g->fbytes == 8 ? group_build<double>(g, g->home) : group_build<float>(g, g->home);
+    cpd_status st;
+    if (g->engine == kEnginePersistent) {
+        // the members' launch arguments, captured now (like the other groups)
+        std::vector<PersArgs> hp(G);
+        g->pers_cs = c0->pers.cs;
+        for (int q = 0; q < G; ++q) {
+            hp[q] = ctxs[q]->pers;
+            hp[q].P = ctxs[q]->Pf;
+            g->pers_smem = std::max(g->pers_smem, ctxs[q]->smem_grad);
+        }
+        cudaError_t e = cudaMallocAsync((void **)&g->dpers, sizeof(PersArgs) * G, g->home);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->dpers, hp.data(), sizeof(PersArgs) * G, cudaMemcpyHostToDevice, g->home);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->home);
+        st = e == cudaSuccess ? CPD_OK : cuda_fail(e, "persistent group set-up");
+    } else {
+        st = g->fbytes == 8 ? group_build<double>(g, g->home) : group_build<float>(g, g->home);
+    }
     if (st != CPD_OK) {
         cudaStreamSynchronize(g->home);
         if (g->dP) cudaFreeAsync(g->dP, g->home);
         if (g->dcta) cudaFreeAsync(g->dcta, g->home);
+        if (g->dpers) cudaFreeAsync(g->dpers, g->home);
         cudaStreamSynchronize(g->home);
         delete g;
         return st;
@@ -966,6 +1028,16 @@ extern "C" cpd_status cpd_group_create(cpd_ctx *const *ctxs, int32_t G, void *st
 template <class T>
 static cudaError_t group_run(cpd_group *g, int64_t iters, cudaStream_t s)
 {
+    if (g->engine == kEnginePersistent) {
+        constexpr int64_t kMaxPerLaunch = (int64_t)1 << 20;
+        for (int64_t done = 0; done < iters;) {
+            const int64_t len = std::min(kMaxPerLaunch, iters - done);
+            const cudaError_t e = launch_pers_group(g->dpers, g->G, g->pers_cs, g->pers_smem, len, s);
+            if (e != cudaSuccess) return e;
+            done += len;
+        }
+        return cudaSuccess;
+    }
     const GroupLaunch<T> &L = group_launch<T>(g);
     return replay(g->graph, g->graph_stream, iters, s, [&](cudaStream_t cap) { return launch_group_iteration(L, cap); });
 }
@@ -990,8 +1062,9 @@ extern "C" cpd_status cpd_group_destroy(cpd_group *g)
     if (!g) return CPD_OK;
     cudaStreamSynchronize(g->last);
     drop_graphs(g->graph, kGraphSizes);
-    cudaFreeAsync(g->dP, g->home);
-    cudaFreeAsync(g->dcta, g->home);
+    if (g->dP) cudaFreeAsync(g->dP, g->home);
+    if (g->dcta) cudaFreeAsync(g->dcta, g->home);
+    if (g->dpers) cudaFreeAsync(g->dpers, g->home);
     cudaStreamSynchronize(g->home);
     delete g;
     return CPD_OK;

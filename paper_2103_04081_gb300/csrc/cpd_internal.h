@@ -98,6 +98,15 @@ struct PersArgs {
     int cs, fpc, R4, Npad, cst, ntile;
 };
 
+// What a persistent launch does: train (gmode < 0), or form K mini-batch
+// gradients of mode gmode at the current factors into gout (K x I_n x R).
+struct PersMode {
+    int gmode;
+    long long t0;
+    int K;
+    float *gout;
+};
+
 // Launchers (cpd_kernels.cu). Every launcher enqueues on `stream` and
 // returns the launch error, if any.
 template <class T>
@@ -146,5 +155,9 @@ size_t pers_smem_bytes(const PersArgs &a);
 int pers_max_clusters(const PersArgs &a);
 cudaError_t launch_pers(const PersArgs &a, long long T, cudaStream_t stream);
 cudaError_t launch_pers_group(const PersArgs *dargs, int G, int cs, size_t smem, long long T, cudaStream_t stream);
+// K gradients of mode n over `nclusters` clusters; a.part / a.hpart must hold
+// nclusters slab sets.
+cudaError_t launch_pers_gradients(const PersArgs &a, int n, long long t0, int K, int nclusters, float *gout,
+                                  cudaStream_t stream);
 
 }  // namespace cpd

@@ -149,10 +149,14 @@ __device__ __forceinline__ float pers_weight(const PersArgs &a, int n, const int
 
 }  // namespace
 
-// One cluster per problem. `one` is used when `many` is null (single
-// decomposition); otherwise cluster g runs many[g].
+// Training: one cluster per problem; `one` is used when `many` is null
+// (single decomposition), otherwise cluster g runs many[g] for T iterations.
+// Gradient mode (md.gmode = n >= 0, `one` only): cluster c forms the mode-n
+// mini-batch gradients of batches c, c + #clusters, ... < md.K at the current
+// factors (batch b drawn as iteration md.t0 + b would draw it, with the mode
+// fixed to n) into md.gout[b] (I_n x R); nothing in the context changes.
 __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const PersArgs *__restrict__ many,
-                                                      long long T)
+                                                      long long T, const PersMode md)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(16) PersArgs sa;
@@ -162,6 +166,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
     const int cs = (int)cluster_nctas();
     const int rank = (int)cluster_rank();
     const int g = blockIdx.x / cs;
+    const bool train = md.gmode < 0;
+    const int ncl = gridDim.x / cs;
     {
         static_assert(sizeof(PersArgs) % 8 == 0, "PersArgs is copied in 8-byte words");
         const unsigned long long *src = reinterpret_cast<const unsigned long long *>(many ? many + g : &one);
@@ -188,6 +194,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
     const uint32_t bar0 = smem_u32(smem + L.bar);   // empty[0..kPS), mma done
     const uint32_t bar_mma = bar0 + 8 * kPS;
     const bool tr = (g == 0 && rank == 0);
+    // scratch of this cluster (gradient mode: one slab set per cluster)
+    float *const part = a.part + (train ? 0 : (size_t)g * cs * a.ntile * kPM * cst);
+    float *const hpart = a.hpart + (train ? 0 : (size_t)g * cs * kPHd * kPHd);
 
     // ---- set-up -------------------------------------------------------------
     int tcols = 32;
@@ -207,8 +216,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
         for (int k = 0; k < N; ++k)
             for (long long i = tid; i < P.dims[k]; i += blockDim.x) stage[a.off[k] + i] = __ldcg(P.cdf[k] + i);
     for (int e = tid; e < 2 * kPK * kPHd; e += blockDim.x) zf[e] = 0.f;
-    // factors -> padded private copies, split over the cluster
-    for (int k = 0; k < N; ++k) {
+    // factors -> padded private copies, split over the cluster (gradient
+    // mode: the host filled them before the launch)
+    for (int k = 0; k < N && train; ++k) {
         const long long tot = P.dims[k] * R4;
         for (long long e = (long long)rank * blockDim.x + tid; e < tot; e += (long long)cs * blockDim.x) {
             const long long i = e / R4;
@@ -230,9 +240,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
     const int nchunks = (nf + kPK - 1) / kPK;
     int flags = 0;
 
-    for (long long it = 0; it < T; ++it, ++t) {
-        const bool last = it == T - 1;
-        const int n = mode_draw(P.seed, t, N);
+    const long long nit = train ? T : (md.K > g ? (md.K - 1 - g) / ncl + 1 : 0);
+    for (long long it = 0; it < nit; ++it, ++t) {
+        const long long bt = train ? -1 : g + it * ncl;   // gradient mode: the batch
+        if (!train) t = md.t0 + bt;
+        const bool last = train && it == T - 1;
+        const int n = train ? mode_draw(P.seed, t, N) : md.gmode;
         const long long In = P.dims[n], ld = P.ld[n];
         const int ntile = (int)((In + kPM - 1) / kPM);
         const float *An = a.Ap[n];
@@ -398,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
 
         // 3. partials to the scratch: M rows of every tile, H
         {
-            float *pm = a.part + (size_t)rank * a.ntile * kPM * cst;
+            float *pm = part + (size_t)rank * a.ntile * kPM * cst;
             const int qd = warp & 3, hh = warp >> 2;
             for (int m = 0; m < ntile; ++m) {
                 if (32 * hh >= Npad) break;
@@ -415,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                     }
                 }
             }
-            float *ph = a.hpart + (size_t)rank * kPHd * kPHd;
+            float *ph = hpart + (size_t)rank * kPHd * kPHd;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 *reinterpret_cast<float4 *>(ph + (4 * hrb + u) * kPHd + 4 * hcb) =
@@ -434,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
             for (int e = tid; e < (h1 > h0 ? (h1 - h0) * R : 0); e += blockDim.x) {
                 const int i = h0 + e / R, c = e % R;
                 float v = 0.f;
-                for (int src = 0; src < cs; ++src) v += __ldcg(a.hpart + (size_t)src * kPHd * kPHd + i * kPHd + c);
+                for (int src = 0; src < cs; ++src) v += __ldcg(hpart + (size_t)src * kPHd * kPHd + i * kPHd + c);
                 const uint32_t addr = hbase + (uint32_t)((i * kPHd + c) * 4);
                 for (int d = 0; d < cs; ++d) st_cluster_f32(map_shared(addr, (uint32_t)d), v);
             }
@@ -460,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                 const float4 av = __ldcg(reinterpret_cast<const float4 *>(An + row * R4) + c4);
                 float4 mv = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int src = 0; src < cs; ++src) {
-                    const float4 p = __ldcg(reinterpret_cast<const float4 *>(a.part + ((size_t)src * a.ntile * kPM + row) * cst) + c4);
+                    const float4 p = __ldcg(reinterpret_cast<const float4 *>(part + ((size_t)src * a.ntile * kPM + row) * cst) + c4);
                     mv.x += p.x;
                     mv.y += p.y;
                     mv.z += p.z;
@@ -476,6 +489,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                 float ah = 0.f;
                 for (int s = 0; s < R; ++s) ah += sA[i * R4 + s] * sH[s * kPHd + r];
                 const float gr = ah - sM[i * R4 + r];
+                if (!train) {
+                    md.gout[((size_t)bt * In + row) * R + r] = gr;
+                    continue;
+                }
                 const float aold = sA[i * R4 + r];
                 float an;
                 if (P.step == CPD_STEP_ADAGRAD) {
@@ -493,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                 if (last) P.G[row * R + r] = gr;
             }
             __syncthreads();
-            if (P.sampling == CPD_SAMPLE_EUCLIDEAN) {
+            if (train && P.sampling == CPD_SAMPLE_EUCLIDEAN) {
                 for (int lr = warp; lr < nr; lr += kThreads / 32) {
                     // the canonical tree leaves the row's weight in lane 0
                     const double wv = __shfl_sync(0xffffffffu, warp_row_weight(sN + lr * R, R), 0);
@@ -506,6 +523,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
             __syncthreads();
         }
         trace_stamp(P.trace, 18, tr);
+        if (!train) {
+            // the next batch's partials overwrite the scratch: every CTA has
+            // read it (and no H row is still being sent)
+            cluster_sync_all();
+            continue;
+        }
         cluster_sync_all();   // B3: new rows in the private factor, weights in every CTA
         trace_stamp(P.trace, 20, tr);
 
@@ -519,7 +542,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
     }
 
     // ---- results back to the context ----------------------------------------
-    for (int k = 0; k < N; ++k) {
+    for (int k = 0; k < N && train; ++k) {
         const long long tot = P.dims[k] * R;
         for (long long e = (long long)rank * blockDim.x + tid; e < tot; e += (long long)cs * blockDim.x) {
             const long long i = e / R;
@@ -527,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
             P.A[k][e] = __ldcg(a.Ap[k] + i * R4 + r);
         }
     }
-    if (rank == 0) {
+    if (train && rank == 0) {
         if (P.sampling != CPD_SAMPLE_UNIFORM)
             for (int k = 0; k < N; ++k)
                 for (long long i = tid; i < P.dims[k]; i += blockDim.x) P.cdf[k][i] = stage[a.off[k] + i];
@@ -657,7 +680,8 @@ cudaError_t launch_pers(const PersArgs &a, long long T, cudaStream_t s)
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     pers_config(cfg, attr, a.cs, a.cs, smem, s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_pers, a, (const PersArgs *)nullptr, T);
+    PersMode md{-1, 0, 0, nullptr};
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_pers, a, (const PersArgs *)nullptr, T, md);
     if (e != cudaSuccess) cudaGetLastError();
     return e;
 }
@@ -669,7 +693,43 @@ cudaError_t launch_pers_group(const PersArgs *dargs, int G, int cs, size_t smem,
     cudaLaunchAttribute attr[1];
     pers_config(cfg, attr, G * cs, cs, smem, s);
     PersArgs dummy{};
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_pers, dummy, dargs, T);
+    PersMode md{-1, 0, 0, nullptr};
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_pers, dummy, dargs, T, md);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
+}
+
+}  // namespace cpd
+
+namespace cpd {
+
+// Private padded factors from the context's factors (gradient mode).
+__global__ void k_pers_pad(const PersArgs a)
+{
+    const Problem<float> &P = a.P;
+    for (int k = 0; k < P.N; ++k) {
+        const long long tot = P.dims[k] * a.R4;
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+             e += (long long)gridDim.x * blockDim.x) {
+            const long long i = e / a.R4;
+            const int r = (int)(e % a.R4);
+            a.Ap[k][e] = r < P.R ? P.A[k][i * P.R + r] : 0.f;
+        }
+    }
+}
+
+cudaError_t launch_pers_gradients(const PersArgs &a, int n, long long t0, int K, int nclusters, float *gout,
+                                  cudaStream_t s)
+{
+    const size_t smem = pers_smem_bytes(a);
+    if (cudaError_t e = pers_attrs(a.cs, smem); e != cudaSuccess) return e;
+    k_pers_pad<<<152, kThreads, 0, s>>>(a);
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    pers_config(cfg, attr, nclusters * a.cs, a.cs, smem, s);
+    PersMode md{n, t0, K, gout};
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_pers, a, (const PersArgs *)nullptr, 1LL, md);
     if (e != cudaSuccess) cudaGetLastError();
     return e;
 }

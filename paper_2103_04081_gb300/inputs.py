@@ -140,7 +140,11 @@ def bf16_bits_to_f64(bits: np.ndarray) -> np.ndarray:
 
 
 # Workloads of the measurement plan: the paper's settings (Sec. 5) restated
-# at the sizes of the GB300 measurements.
+# at the sizes of the GB300 measurements. The paper leaves the AdaGrad eta
+# open; 120^4 and 1000^3 take the value of a sweep over {0.1, 0.3, 1, 3}
+# (8000 iterations each from the N(0,1) start) that reached the highest fit:
+# 1.0 reaches 0.998 by iteration 3000 on 120^4, 3.0 reaches 0.913 by
+# iteration 2000 on 1000^3.
 WORKLOADS = {
     "c1_60cube_f64": dict(dims=(60, 60, 60), R=5, B=18, x_dtype="f64",
                           sampling="euclidean", step="fixed", alpha=0.1, noise=1e-2,
@@ -151,11 +155,11 @@ WORKLOADS = {
                            noise=1e-2, congruence=0.8, lognormal_rows=True, iters=5000,
                            data_seed=0, init_seed=1, sample_seed=0),
     "c3_120pow4_bf16": dict(dims=(120, 120, 120, 120), R=20, B=1024, x_dtype="bf16",
-                            sampling="euclidean", step="adagrad", eta=0.1, b=1e-12,
+                            sampling="euclidean", step="adagrad", eta=1.0, b=1e-12,
                             noise=1e-3, congruence=0.0, lognormal_rows=False,
                             iters=2000, data_seed=0, init_seed=1, sample_seed=0),
     "c4_1000cube_bf16": dict(dims=(1000, 1000, 1000), R=50, B=2048, x_dtype="bf16",
-                             sampling="euclidean", step="adagrad", eta=0.1, b=1e-12,
+                             sampling="euclidean", step="adagrad", eta=3.0, b=1e-12,
                              noise=1e-2, congruence=0.0, lognormal_rows=True,
                              iters=2000, data_seed=0, init_seed=1, sample_seed=0),
     # Same kernel shapes as the 1000^3 workload on a smaller tensor (3 x 432 MB of

