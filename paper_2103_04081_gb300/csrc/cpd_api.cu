@@ -329,7 +329,7 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
         const size_t fb = (size_t)g.dims[k] * g.R;
         void *a, *S, *w, *cdf;
         CK(dmalloc(c, &a, fb * sizeof(T) + 64));   // tail room for 16-byte bulk copies of row blocks
-        CK(dmalloc(c, &S, fb * sizeof(double)));
+        CK(dmalloc(c, &S, fb * sizeof(double) + 64));   // tail room for 16-byte bulk copies of row blocks
         CK(dmalloc(c, &w, g.dims[k] * sizeof(double)));
         CK(dmalloc(c, &cdf, g.dims[k] * sizeof(unsigned long long)));
         CK(cudaMemcpyAsync(a, A0[k], fb * sizeof(T),

@@ -46,24 +46,30 @@ namespace {
 
 constexpr int kPM = 128;          // rows per accumulator tile (MMA M)
 constexpr int kPK = 16;           // fibers per chunk (MMA K for 16-bit operands)
-constexpr int kPSMax = 4;         // stages of the gather ring (4 where shared memory allows, else 3)
-constexpr int kPHd = 64;          // H is formed 64 x 64 (4 x 4 blocks of 256 threads)
-constexpr int kPOwnBlock = 128;   // owned rows handled per pass of the step phase
+constexpr int kPLand = 3;         // landing stages: whole fibers by bulk copies
+constexpr int kPOp = 2;           // operand buffers in the MMA layout
+constexpr int kPTW = 6;           // transform warps (warps 2..7)
+constexpr int kPTT = kPTW * 32;   // transform threads
+constexpr int kPHd = 64;          // H is formed 64 x 64 (4 x 4 blocks, upper triangle)
+constexpr int kPOwnBlock = 64;    // owned rows handled per pass of the step phase
 constexpr long long kPMaxStage = 4096;   // CDF staging entries (sum of all I_k)
 constexpr int kPMaxFpc = 1024;    // fibers per CTA
 constexpr size_t kPSmemMax = 226 * 1024;  // dynamic shared memory per CTA (plus ~1 KB static)
 
 __host__ __device__ inline size_t up128(size_t v) { return (v + 127) / 128 * 128; }
 
-// Shared-memory carve-up (byte offsets). The ring of gather stages is reused,
-// once every product of an iteration has completed, by the step phase: H,
-// the owned rows of A^(n), of M and of the new factor, and the scratch of the
+// Shared-memory carve-up (byte offsets). The landing stages and operand
+// buffers form one region that the phases after the contraction reuse: the
+// staging of the partial tiles, then H, the owned rows (A, S, M, new rows),
+// the staging of the partial blocks being summed, and the scratch of the
 // CDF rebuild.
 struct PersLayout {
-    size_t cdf, idx, jcol, sw, stage, x, fr, bhi, blo, stage_bytes, zf, bar, total;
-    size_t h, own_a, own_m, own_n, dsm;   // inside the ring
-    int nstage;
-    __host__ __device__ size_t with_stages(const PersArgs &a, int S)
+    size_t cdf, idx, jcol, sw, land, land_bytes, lx, lfr, pitch, op, op_bytes, ox, obh, obl, zf, bar, total;
+    size_t region, region_bytes;
+    size_t h, own_a, own_m, own_s, own_n, dsm, red;   // inside the region (step phase)
+    int nland;                                        // landing stages (3, or 2 when memory is short)
+    int red_slots;                                    // partial blocks staged at once
+    __host__ __device__ PersLayout(const PersArgs &a)
     {
         const int N = a.P.N;
         size_t o = 0;
@@ -71,44 +77,57 @@ struct PersLayout {
         idx = o;  o += up128((size_t)a.fpc * N * 4);
         jcol = o; o += up128((size_t)a.fpc * 8);
         sw = o;   o += up128((size_t)a.fpc * 4);
-        x = 0;
-        fr = up128((size_t)kPK * a.ntile * kPM * 2);
-        bhi = fr + up128((size_t)kPK * (N - 1) * a.R4 * 4);
-        blo = bhi + (size_t)kPK * a.Npad * 2;
-        stage_bytes = up128(blo + (size_t)kPK * a.Npad * 2);
-        stage = o;
+        region = o;
+        const size_t fixed = o + 2 * (size_t)kPK * kPHd * 4 + 8 * 16;   // + zf, barriers
+        // landing pitch of one fiber: 16-byte multiple with pitch / 16 odd, so
+        // the 16-byte pieces of 8 consecutive fibers fall in distinct banks
+        long long ldmax = 0;
+        for (int k = 0; k < N; ++k) ldmax = a.P.ld[k] > ldmax ? a.P.ld[k] : ldmax;
+        pitch = (size_t)ldmax * 2;
+        if (((pitch / 16) & 1) == 0) pitch += 16;
+        lx = 0;
+        lfr = up128((size_t)kPK * pitch);
+        land_bytes = up128(lfr + (size_t)kPK * (N - 1) * a.R4 * 4);
+        ox = 0;
+        obh = up128((size_t)kPK * a.ntile * kPM * 2);
+        obl = obh + (size_t)kPK * a.Npad * 2;
+        op_bytes = up128(obl + (size_t)kPK * a.Npad * 2);
+        // step phase inside the region: H, owned rows (A, M, new, S), the
+        // CDF-rebuild scratch, then the staged partial blocks
+        const size_t blk = (size_t)kPOwnBlock * a.R4 * 4;
         h = 0;
         own_a = h + (size_t)kPHd * kPHd * 4;
-        own_m = own_a + up128((size_t)kPOwnBlock * a.R4 * 4);
-        own_n = own_m + up128((size_t)kPOwnBlock * a.R4 * 4);
-        dsm = own_n + up128((size_t)kPOwnBlock * a.R4 * 4);
-        const size_t own = dsm + 2 * kThreads * 8;
-        const size_t ring = stage_bytes * S;
-        o += ring > own ? ring : own;
-        zf = o;   o += 2 * (size_t)kPK * kPHd * 4;
-        bar = o;  o += 8 * (kPSMax + 2);
-        return o;
-    }
-    __host__ __device__ PersLayout(const PersArgs &a)
-    {
-        nstage = kPSMax;
-        total = with_stages(a, kPSMax);
-        if (total > kPSmemMax) {
-            nstage = kPSMax - 1;
-            total = with_stages(a, nstage);
+        own_m = own_a + up128(blk);
+        own_n = own_m + up128(blk);
+        own_s = own_n + up128(blk);
+        dsm = own_s + up128((size_t)kPOwnBlock * a.P.R * 8 + 16);
+        red = dsm + 2 * kThreads * 8;
+        const size_t tiles = 4 * up128((size_t)kPM * a.R4 * 4);   // staged partial tiles
+        nland = kPLand;
+        size_t base = land_bytes * nland + op_bytes * kPOp;
+        if (fixed + (base > red + blk ? base : red + blk) > kPSmemMax) {
+            nland = 2;
+            base = land_bytes * nland + op_bytes * kPOp;
         }
+        const size_t room = kPSmemMax > fixed + red ? kPSmemMax - fixed - red : 0;
+        red_slots = (int)(room / blk);
+        if (red_slots > a.cs) red_slots = a.cs;
+        if (red_slots < 1) red_slots = 1;
+        region_bytes = base;
+        if (region_bytes < red + blk * red_slots) region_bytes = red + blk * red_slots;
+        if (region_bytes < tiles) region_bytes = tiles;
+        land = region;
+        op = land + land_bytes * nland;
+        o += region_bytes;
+        zf = o;   o += 2 * (size_t)kPK * kPHd * 4;
+        bar = o;  o += 8 * 16;
+        total = o;
         // at least half of the SM's shared memory, so one CTA per SM (the
         // tensor-memory allocation assumes it)
         if (total < 120 * 1024) total = 120 * 1024;
     }
 };
 
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_stages(int S)
-{
-    if (S >= 4) asm volatile("cp.async.wait_group 3;\n" ::: "memory");
-    else asm volatile("cp.async.wait_group 2;\n" ::: "memory");
-}
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t cluster_nctas()
@@ -129,6 +148,23 @@ __device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v)
     asm volatile("st.shared::cluster.f32 [%0], %1;\n" ::"r"(addr), "f"(v) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+
+// Bulk store shared -> global (async proxy), tracked by a bulk group.
+__device__ __forceinline__ void bulk_s2g(void *dst, uint32_t src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
+// Named barrier of the transform warps.
+__device__ __forceinline__ void transform_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(kPTT) : "memory"); }
+
 // One MMA: D(tmem) (+)= A(desc) B(desc), kind::f16 (bf16 in, f32 accumulate).
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
 {
@@ -143,6 +179,13 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
                  : "memory");
+}
+
+// Wait for the phase of parity `par` unless the CTA gave up already.
+__device__ __forceinline__ void wait_or_abort(uint32_t mbar, uint32_t par, volatile int *abort)
+{
+    if (*abort) return;
+    if (!mbar_wait_bounded(mbar, par)) *abort = 1;
 }
 
 // s_f = (1/(B J_n)) prod_{k != n, ascending} Q_k / q_k(i_k) in FP32 (the same
@@ -198,6 +241,11 @@ __device__ __forceinline__ void warp_row_weights8(const float *rows, int stride,
 // mini-batch gradients of batches c, c + #clusters, ... < md.K at the current
 // factors (batch b drawn as iteration md.t0 + b would draw it, with the mode
 // fixed to n) into md.gout[b] (I_n x R); nothing in the context changes.
+//
+// Warp roles in the contraction phase: warp 0 lane 0 issues the bulk copies
+// of whole fibers (and their factor rows) into the landing stages; warp 1
+// lane 0 issues the tensor-core products; warps 2..7 move each landed chunk
+// into the MMA operand layout, build its B operands and accumulate H.
 __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const PersArgs *__restrict__ many,
                                                       long long T, const PersMode md)
 {
@@ -222,25 +270,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
         s_flags = 0;
     }
     __syncthreads();
+    volatile int *abort = &s_abort;
     const PersArgs &a = sa;
     const Problem<float> &P = a.P;
     const int N = P.N, R = P.R, R4 = a.R4, Npad = a.Npad, cst = a.cst, fpc = a.fpc;
     const PersLayout L(a);
-    const int S = L.nstage;
     const int rows_all = a.ntile * kPM;     // row extent of a partial slab
     unsigned long long *stage = reinterpret_cast<unsigned long long *>(smem + L.cdf);
     int *sidx = reinterpret_cast<int *>(smem + L.idx);
     long long *jcol = reinterpret_cast<long long *>(smem + L.jcol);
     float *sw = reinterpret_cast<float *>(smem + L.sw);
-    unsigned char *ring = smem + L.stage;
+    unsigned char *region = smem + L.region;
     float *zf = reinterpret_cast<float *>(smem + L.zf);
-    float *sH = reinterpret_cast<float *>(ring + L.h);
-    unsigned long long *dsm = reinterpret_cast<unsigned long long *>(ring + L.dsm);
-    const uint32_t bar0 = smem_u32(smem + L.bar);   // empty[0..S), mma done
-    const uint32_t bar_mma = bar0 + 8 * kPSMax;
+    float *sH = reinterpret_cast<float *>(region + L.h);
+    unsigned long long *dsm = reinterpret_cast<unsigned long long *>(region + L.dsm);
+    // mbarriers: land_full[3], land_empty[3], op_full[2], op_empty[2], mma done, step
+    const uint32_t bar0 = smem_u32(smem + L.bar);
+    const uint32_t b_lfull = bar0, b_lempty = bar0 + 8 * kPLand, b_ofull = bar0 + 16 * kPLand;
+    const uint32_t b_oempty = b_ofull + 8 * kPOp, b_mma = b_oempty + 8 * kPOp, b_step = b_mma + 8;
     const bool tr = (g == 0 && rank == 0);
     // scratch of this cluster (gradient mode: one slab set per cluster);
-    // partial M is stored column-major per CTA: [cs][cst][rows_all]
+    // CTA c's partial M is slab c (rows_all * cst floats), row-major with
+    // row stride R4
     float *const part = a.part + (train ? 0 : (size_t)g * cs * rows_all * cst);
     float *const hpart = a.hpart + (train ? 0 : (size_t)g * cs * kPHd * kPHd);
 
@@ -248,7 +299,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
     int tcols = 32;
     while (tcols < a.ntile * cst) tcols <<= 1;
     if (tid == 0) {
-        for (int q = 0; q <= kPSMax; ++q) mbar_init(bar0 + 8 * q, 1);
+        for (int q = 0; q < kPLand; ++q) {
+            mbar_init(b_lfull + 8 * q, 1);
+            mbar_init(b_lempty + 8 * q, 1);
+        }
+        for (int q = 0; q < kPOp; ++q) {
+            mbar_init(b_ofull + 8 * q, 1);
+            mbar_init(b_oempty + 8 * q, 1);
+        }
+        mbar_init(b_mma, 1);
+        mbar_init(b_step, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -279,22 +339,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
 
     long long t = __ldcg(P.t_dev);
     int n_prev = -1;
-    unsigned commits[kPSMax] = {0, 0, 0, 0}, waited[kPSMax] = {0, 0, 0, 0};
-    unsigned mma_iters = 0;
+    unsigned mma_iters = 0, step_phase = 0;
+    long long gq0 = 0;                    // chunks of earlier iterations (barrier phases)
     const int f0 = rank * fpc;
     const int nf = (P.B - f0) < fpc ? ((P.B - f0) > 0 ? P.B - f0 : 0) : fpc;
     const int nchunks = (nf + kPK - 1) / kPK;
     int flags = 0;
+    // H: thread tt < 136 of the transform warps owns the 4 x 4 block (hbi, hbj),
+    // hbi <= hbj, of the upper triangle of the 64 x 64 grid of blocks
+    const int tt = tid - 64;
+    int hbi = 0, hbj = 0;
+    if (tt >= 0 && tt < 136) {
+        int rem = tt;
+        while (rem >= 16 - hbi) {
+            rem -= 16 - hbi;
+            ++hbi;
+        }
+        hbj = hbi + rem;
+    }
 
     const long long nit = train ? T : (md.K > g ? (md.K - 1 - g) / ncl + 1 : 0);
-    for (long long it = 0; it < nit; ++it, ++t) {
+    for (long long it = 0; it < nit; ++it, ++t, gq0 += nchunks) {
         const long long bt = train ? -1 : g + it * ncl;   // gradient mode: the batch
         if (!train) t = md.t0 + bt;
         const bool last = train && it == T - 1;
         const int n = train ? mode_draw(P.seed, t, N) : md.gmode;
         const long long In = P.dims[n], ld = P.ld[n];
         const int ntile = (int)((In + kPM - 1) / kPM);
-        const float *An = a.Ap[n];
         trace_stamp(P.trace, 0, tr);
 
         // 1. draws of the own fibers (Alg. 3), from the staged CDFs
@@ -343,154 +414,188 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
         __syncthreads();
         trace_stamp(P.trace, 2, tr);
 
-        // 2. gather + tensor-core contraction, streamed in chunks of 16 fibers
-        const uint32_t idesc = idesc_bf16(kPM, Npad);
-        const __nv_bfloat16 *rep = reinterpret_cast<const __nv_bfloat16 *>(P.rep[n]);
-        const int g8 = ntile * (kPM / 8);              // 16-byte row pieces per fiber (incl. zero fill)
-        const int pr = R4 / 4;                          // 16-byte pieces per factor row
+        // 2. gather + tensor-core contraction in chunks of 16 fibers
+        const int g8 = ntile * (kPM / 8);          // 16-byte row pieces per fiber in the operand
+        const int lpieces = (int)(ld / 8);         // 16-byte pieces of a landed fiber
         float acc[4][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-        const int hrb = tid >> 4, hcb = tid & 15;
-        for (int q = 0; q < nchunks + S - 1; ++q) {
-            const bool trq = tr && q == S + 1;
-            trace_stamp(P.trace, 30, trq);
-            if (q < nchunks) {
-                const int s = q % S;
-                if (commits[s] > waited[s]) {
-                    if (!s_abort && !mbar_wait_bounded(bar0 + 8 * s, waited[s] & 1)) s_abort = 1;
-                    ++waited[s];
-                }
-                trace_stamp(P.trace, 31, trq);
-                unsigned char *st = ring + (size_t)s * L.stage_bytes;
-                const uint32_t xs = smem_u32(st + L.x), frs = smem_u32(st + L.fr);
-                // piece (f, ig): rows [8 ig, 8 ig + 8) of fiber f. Thread pairs
-                // read 32 contiguous bytes of one fiber; the 8 fibers of a
-                // core matrix land in consecutive 16-byte slots (no bank
-                // conflicts on the shared-memory side).
-                for (int e = tid; e < kPK * g8; e += blockDim.x) {
-                    const int ig = ((e >> 5) << 1) | (e & 1), f = (e >> 1) & 15;
-                    const int fl = q * kPK + f;
-                    const bool v = fl < nf && 8LL * ig < ld;
-                    const __nv_bfloat16 *src = v ? rep + jcol[fl] * ld + 8LL * ig : rep;
-                    cp_async16(xs + (uint32_t)((((f >> 3) * g8 + ig) << 7) + ((f & 7) << 4)), src, v ? 16u : 0u);
-                }
-                for (int e = tid; e < kPK * (N - 1) * pr; e += blockDim.x) {
-                    const int f = e / ((N - 1) * pr), rem = e % ((N - 1) * pr);
-                    const int kk = rem / pr, pc = rem % pr;
-                    const int k = kk + (kk >= n ? 1 : 0);
-                    const int fl = q * kPK + f;
-                    const bool v = fl < nf;
-                    const float *src = v ? a.Ap[k] + (long long)sidx[fl * N + k] * R4 + 4 * pc : a.Ap[k];
-                    cp_async16(frs + (uint32_t)(((f * (N - 1) + kk) * R4 + 4 * pc) * 4), src, v ? 16u : 0u);
-                }
-            }
-            cp_async_commit();
-            trace_stamp(P.trace, 32, trq);
-            const int c2 = q - (S - 1);
-            if (c2 < 0) continue;
-            cp_async_wait_stages(S);
-            fence_async_smem();
-            __syncthreads();
-            trace_stamp(P.trace, 33, trq);
-            // build z_f (fp32, for H) and the B operands Z' = s_f z_f as a bf16
-            // hi/lo pair, K-major: core matrix (f/8, r/8), 8 fibers per 16 bytes
-            const int s2 = c2 % S;
-            unsigned char *st2 = ring + (size_t)s2 * L.stage_bytes;
-            const float *fr = reinterpret_cast<const float *>(st2 + L.fr);
-            __nv_bfloat16 *bh = reinterpret_cast<__nv_bfloat16 *>(st2 + L.bhi);
-            __nv_bfloat16 *bl = reinterpret_cast<__nv_bfloat16 *>(st2 + L.blo);
-            float *z2 = zf + (c2 & 1) * kPK * kPHd;
-            for (int job = tid; job < Npad * 2; job += blockDim.x) {
-                const int r = job % Npad, fb8 = job / Npad;
-                __nv_bfloat16 hi[8], lo[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int f = 8 * fb8 + u;
-                    const int fl = c2 * kPK + f;
-                    float z = 0.f;
-                    if (r < R && fl < nf) {
-                        const float *row = fr + (size_t)f * (N - 1) * R4 + r;
-                        z = 1.f;
-                        for (int kk = 0; kk < N - 1; ++kk) z = z * row[kk * R4];
+        if (warp == 0) {
+            // producer: whole fibers (ld elements) and their factor rows
+            if (lane == 0) {
+                const __nv_bfloat16 *rep = reinterpret_cast<const __nv_bfloat16 *>(P.rep[n]);
+                for (int c = 0; c < nchunks; ++c) {
+                    const long long gq = gq0 + c;
+                    const int s = (int)(gq % L.nland);
+                    if (gq >= L.nland) wait_or_abort(b_lempty + 8 * s, (uint32_t)((gq / L.nland - 1) & 1), abort);
+                    const uint32_t lb = smem_u32(smem + L.land + (size_t)s * L.land_bytes);
+                    int nv = nf - c * kPK;
+                    nv = nv < kPK ? nv : kPK;
+                    const uint32_t fbytes = (uint32_t)ld * 2, rbytes = (uint32_t)R4 * 4;
+                    mbar_expect_tx(b_lfull + 8 * s, (uint32_t)nv * (fbytes + (uint32_t)(N - 1) * rbytes));
+                    if (!*abort) {
+                        for (int f = 0; f < nv; ++f) {
+                            const int fl = c * kPK + f;
+                            bulk_g2s(lb + (uint32_t)(L.lx + f * L.pitch), rep + jcol[fl] * ld, fbytes, b_lfull + 8 * s);
+                            for (int kk = 0; kk < N - 1; ++kk) {
+                                const int k = kk + (kk >= n ? 1 : 0);
+                                bulk_g2s(lb + (uint32_t)(L.lfr + ((f * (N - 1) + kk) * R4) * 4),
+                                         a.Ap[k] + (long long)sidx[fl * N + k] * R4, rbytes, b_lfull + 8 * s);
+                            }
+                        }
                     }
-                    z2[f * kPHd + r] = z;
-                    const float zs = z * sw[fl];
-                    hi[u] = __float2bfloat16_rn(zs);
-                    lo[u] = __float2bfloat16_rn(zs - __bfloat162float(hi[u]));
                 }
-                const int off = ((fb8 * (Npad >> 3) + (r >> 3)) << 6) + ((r & 7) << 3);
-                *reinterpret_cast<uint4 *>(bh + off) = *reinterpret_cast<uint4 *>(hi);
-                *reinterpret_cast<uint4 *>(bl + off) = *reinterpret_cast<uint4 *>(lo);
             }
-            fence_async_smem();
-            __syncthreads();
-            trace_stamp(P.trace, 34, trq);
-            if (tid == 0 && !s_abort) {
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const uint32_t xs = smem_u32(st2 + L.x);
-                const uint64_t dh = smem_desc(smem_u32(bh), (uint32_t)(Npad >> 3) * 128u, 128u);
-                const uint64_t dl = smem_desc(smem_u32(bl), (uint32_t)(Npad >> 3) * 128u, 128u);
-                for (int m = 0; m < ntile; ++m) {
-                    const uint64_t da = smem_desc(xs + (uint32_t)m * 2048u, (uint32_t)g8 * 128u, 128u);
-                    const uint32_t d = tmem + (uint32_t)(m * cst);
-                    mma_bf16(d, da, dh, idesc, c2 > 0 ? 1u : 0u);
-                    mma_bf16(d, da, dl, idesc, 1u);
+        } else if (warp == 1) {
+            // tensor-core products
+            if (lane == 0) {
+                const uint32_t idesc = idesc_bf16(kPM, Npad);
+                for (int c = 0; c < nchunks; ++c) {
+                    const long long gq = gq0 + c;
+                    const int o = (int)(gq % kPOp);
+                    wait_or_abort(b_ofull + 8 * o, (uint32_t)((gq / kPOp) & 1), abort);
+                    if (*abort) continue;
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    unsigned char *ob = smem + L.op + (size_t)o * L.op_bytes;
+                    const uint32_t xs = smem_u32(ob + L.ox);
+                    const uint64_t dh = smem_desc(smem_u32(ob + L.obh), (uint32_t)(Npad >> 3) * 128u, 128u);
+                    const uint64_t dl = smem_desc(smem_u32(ob + L.obl), (uint32_t)(Npad >> 3) * 128u, 128u);
+                    for (int m = 0; m < ntile; ++m) {
+                        const uint64_t da = smem_desc(xs + (uint32_t)m * 2048u, (uint32_t)g8 * 128u, 128u);
+                        const uint32_t d = tmem + (uint32_t)(m * cst);
+                        mma_bf16(d, da, dh, idesc, c > 0 ? 1u : 0u);
+                        mma_bf16(d, da, dl, idesc, 1u);
+                    }
+                    mma_commit(b_oempty + 8 * o);
                 }
-                mma_commit(bar0 + 8 * s2);
+                if (nchunks > 0 && !*abort) mma_commit(b_mma);
             }
-            ++commits[s2];
-            trace_stamp(P.trace, 35, trq);
-            // H over this chunk's fibers, a 4 x 4 block per thread
-            for (int f = 0; f < kPK; ++f) {
-                const int fl = c2 * kPK + f;
-                const float s = fl < nf ? sw[fl] : 0.f;
-                const float4 zr = *reinterpret_cast<const float4 *>(z2 + f * kPHd + 4 * hrb);
-                const float4 zc = *reinterpret_cast<const float4 *>(z2 + f * kPHd + 4 * hcb);
-                const float ar[4] = {zr.x * s, zr.y * s, zr.z * s, zr.w * s}, ac[4] = {zc.x, zc.y, zc.z, zc.w};
+        } else {
+            // transform warps
+            for (int c = 0; c < nchunks; ++c) {
+                const long long gq = gq0 + c;
+                const int s = (int)(gq % L.nland), o = (int)(gq % kPOp);
+                wait_or_abort(b_lfull + 8 * s, (uint32_t)((gq / L.nland) & 1), abort);
+                if (gq >= kPOp) wait_or_abort(b_oempty + 8 * o, (uint32_t)((gq / kPOp - 1) & 1), abort);
+                const unsigned char *lb = smem + L.land + (size_t)s * L.land_bytes;
+                unsigned char *ob = smem + L.op + (size_t)o * L.op_bytes;
+                // fibers into the no-swizzle MN-major operand: piece (f, ig) =
+                // rows [8 ig, 8 ig + 8) of fiber f at core matrix (f/8, ig),
+                // slot f % 8; zero past the fiber and past the valid fibers
+                for (int e = tt; e < kPK * g8; e += kPTT) {
+                    const int f = (e & 7) | (((e >> 3) & 1) << 3), ig = e >> 4;
+                    const int fl = c * kPK + f;
+                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                    if (fl < nf && ig < lpieces)
+                        v = *reinterpret_cast<const uint4 *>(lb + L.lx + (size_t)f * L.pitch + (size_t)ig * 16);
+                    *reinterpret_cast<uint4 *>(ob + L.ox + ((size_t)((f >> 3) * g8 + ig) << 7) + ((f & 7) << 4)) = v;
+                }
+                // z_f (fp32, for H) and Z' = s_f z_f as a bf16 hi/lo pair, K-major:
+                // core matrix (f/8, r/8), 8 fibers per 16 bytes
+                const float *fr = reinterpret_cast<const float *>(lb + L.lfr);
+                __nv_bfloat16 *bh = reinterpret_cast<__nv_bfloat16 *>(ob + L.obh);
+                __nv_bfloat16 *bl = reinterpret_cast<__nv_bfloat16 *>(ob + L.obl);
+                float *z2 = zf + (gq & 1) * kPK * kPHd;
+                for (int job = tt; job < Npad * 2; job += kPTT) {
+                    const int r = job % Npad, fb8 = job / Npad;
+                    __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                    for (int u = 0; u < 8; ++u) {
+                        const int f = 8 * fb8 + u;
+                        const int fl = c * kPK + f;
+                        float z = 0.f;
+                        if (r < R && fl < nf) {
+                            const float *row = fr + (size_t)f * (N - 1) * R4 + r;
+                            z = 1.f;
+                            for (int kk = 0; kk < N - 1; ++kk) z = z * row[kk * R4];
+                        }
+                        z2[f * kPHd + r] = z;
+                        const float zs = z * sw[fl];
+                        hi[u] = __float2bfloat16_rn(zs);
+                        lo[u] = __float2bfloat16_rn(zs - __bfloat162float(hi[u]));
+                    }
+                    const int off = ((fb8 * (Npad >> 3) + (r >> 3)) << 6) + ((r & 7) << 3);
+                    *reinterpret_cast<uint4 *>(bh + off) = *reinterpret_cast<uint4 *>(hi);
+                    *reinterpret_cast<uint4 *>(bl + off) = *reinterpret_cast<uint4 *>(lo);
+                }
+                fence_async_smem();
+                transform_sync();   // the chunk's operands and z_f are complete; the landing stage is read
+                if (tt == 0) {
+                    mbar_arrive(b_ofull + 8 * o);
+                    mbar_arrive(b_lempty + 8 * s);
+                }
+                // H over this chunk's fibers: the thread's upper-triangle block
+                if (tt < 136) {
+                    for (int f = 0; f < kPK; ++f) {
+                        const int fl = c * kPK + f;
+                        const float sv = fl < nf ? sw[fl] : 0.f;
+                        const float4 zr = *reinterpret_cast<const float4 *>(z2 + f * kPHd + 4 * hbi);
+                        const float4 zc = *reinterpret_cast<const float4 *>(z2 + f * kPHd + 4 * hbj);
+                        const float ar[4] = {zr.x * sv, zr.y * sv, zr.z * sv, zr.w * sv};
+                        const float ac[4] = {zc.x, zc.y, zc.z, zc.w};
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] += ar[u] * ac[v];
+                        for (int u = 0; u < 4; ++u)
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) acc[u][v] += ar[u] * ac[v];
+                    }
+                }
             }
-            trace_stamp(P.trace, 36, trq);
         }
+        __syncthreads();
         trace_stamp(P.trace, 3, tr);
-        // every product of the iteration has completed
         if (nchunks > 0) {
-            if (tid == 0 && !s_abort) mma_commit(bar_mma);
-            __syncthreads();
-            if (!s_abort && !mbar_wait_bounded(bar_mma, mma_iters & 1)) s_abort = 1;
+            wait_or_abort(b_mma, mma_iters & 1, abort);
             ++mma_iters;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         trace_stamp(P.trace, 7, tr);
 
-        // 3. partials to the scratch: M (column-major, so a warp's 32 rows of
-        //    one column are one 128-byte store), H
+        // 3. partials to the scratch: M tiles staged row-major in shared memory
+        //    (four at a time) and stored by bulk copies; H blocks directly
         {
             float *pm = part + (size_t)rank * rows_all * cst;
             const int qd = warp & 3, hh = warp >> 2;
-            const bool z0 = nchunks == 0 || s_abort;
-            for (int m = 0; m < ntile; ++m) {
-                if (32 * hh >= Npad) break;
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(m * cst + 32 * hh), v);
-                const long long row = (long long)m * kPM + 32 * qd + lane;
-                if (row < In) {
+            const bool z0 = nchunks == 0 || *abort;
+            const size_t tb = up128((size_t)kPM * R4 * 4);
+            for (int m0 = 0; m0 < ntile; m0 += 4) {
+                for (int m = m0; m < ntile && m < m0 + 4; ++m) {
+                    if (32 * hh >= Npad) break;
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(m * cst + 32 * hh), v);
+                    float *tile = reinterpret_cast<float *>(region + (size_t)(m - m0) * tb);
+                    const int rl = 32 * qd + lane;
 #pragma unroll
                     for (int c = 0; c < 32; ++c)
-                        if (32 * hh + c < R4) pm[(size_t)(32 * hh + c) * rows_all + row] = z0 ? 0.f : v[c];
+                        if (32 * hh + c < R4) tile[rl * R4 + 32 * hh + c] = z0 ? 0.f : v[c];
+                }
+                fence_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    for (int m = m0; m < ntile && m < m0 + 4; ++m) {
+                        const long long r0 = (long long)m * kPM;
+                        const long long nr = (In - r0) < kPM ? In - r0 : kPM;
+                        bulk_s2g(pm + r0 * R4, smem_u32(region + (size_t)(m - m0) * tb), (uint32_t)(nr * R4 * 4));
+                    }
+                    bulk_commit();
+                    bulk_wait_all();   // written, and the staging may be reused
+                }
+                __syncthreads();
+            }
+            if (tt >= 0 && tt < 136) {
+                float *ph = hpart + (size_t)rank * kPHd * kPHd;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    *reinterpret_cast<float4 *>(ph + (4 * hbi + u) * kPHd + 4 * hbj) =
+                        make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+                    if (hbi != hbj)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) ph[(4 * hbj + v) * kPHd + 4 * hbi + u] = acc[u][v];
                 }
             }
-            float *ph = hpart + (size_t)rank * kPHd * kPHd;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                *reinterpret_cast<float4 *>(ph + (4 * hrb + u) * kPHd + 4 * hcb) =
-                    make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
         }
+        if (tid == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         trace_stamp(P.trace, 8, tr);
         cluster_sync_all();   // B1: every partial is in the scratch
@@ -519,38 +624,52 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
         cluster_sync_all();   // B2: H complete in every CTA
         trace_stamp(P.trace, 15, tr);
 
-        // 5. owned rows of A^(n): M, G = A H - M, the step, the new weights
+        // 5. owned rows of A^(n), in blocks: A and S rows and the partial
+        //    blocks by bulk copies; M summed in ascending CTA order; G = A H - M;
+        //    the step; rows and S back by bulk stores; the new weights
         const long long ngroups = (In + 31) / 32;
         const long long gpc = (ngroups + cs - 1) / cs;
         const long long row0 = 32 * gpc * rank;
         const long long row1 = (row0 + 32 * gpc) < In ? row0 + 32 * gpc : In;
-        float *sA = reinterpret_cast<float *>(ring + L.own_a);
-        float *sM = reinterpret_cast<float *>(ring + L.own_m);
-        float *sN = reinterpret_cast<float *>(ring + L.own_n);
+        float *sA = reinterpret_cast<float *>(region + L.own_a);
+        float *sM = reinterpret_cast<float *>(region + L.own_m);
+        float *sN = reinterpret_cast<float *>(region + L.own_n);
+        double *sS = reinterpret_cast<double *>(region + L.own_s);
+        const float *red = reinterpret_cast<const float *>(region + L.red);
         const uint32_t wslot = smem_u32(stage + a.off[n]);
         const double alpha = P.step == CPD_STEP_DECAY ? P.beta / ((double)t + P.gamma) : P.alpha;
+        const bool ada = train && P.step == CPD_STEP_ADAGRAD;
         for (long long b0 = row0; b0 < row1; b0 += kPOwnBlock) {
             const int nr = (int)((row1 - b0) < kPOwnBlock ? row1 - b0 : kPOwnBlock);
-            for (int e = tid; e < nr * (R4 / 4); e += blockDim.x) {
-                const int i = e / (R4 / 4), c4 = e % (R4 / 4);
-                reinterpret_cast<float4 *>(sA + i * R4)[c4] =
-                    __ldcg(reinterpret_cast<const float4 *>(An + (b0 + i) * R4) + c4);
+            const uint32_t blkb = (uint32_t)(nr * R4 * 4);
+            const size_t blks = (size_t)kPOwnBlock * R4 * 4;
+            for (int s0 = 0; s0 < cs; s0 += L.red_slots) {
+                const int ns = (cs - s0) < L.red_slots ? cs - s0 : L.red_slots;
+                if (tid == 0) {
+                    uint32_t bytes = (uint32_t)ns * blkb;
+                    if (s0 == 0) bytes += blkb + (ada ? (uint32_t)((nr * R * 8 + 15) / 16 * 16) : 0u);
+                    mbar_expect_tx(b_step, bytes);
+                    if (!*abort) {
+                        if (s0 == 0) {
+                            bulk_g2s(smem_u32(sA), a.Ap[n] + b0 * R4, blkb, b_step);
+                            if (ada) bulk_g2s(smem_u32(sS), P.S[n] + b0 * R, (uint32_t)((nr * R * 8 + 15) / 16 * 16), b_step);
+                        }
+                        for (int q = 0; q < ns; ++q)
+                            bulk_g2s(smem_u32(region + L.red + q * blks),
+                                     part + (size_t)(s0 + q) * rows_all * cst + (size_t)b0 * R4, blkb, b_step);
+                    }
+                }
+                wait_or_abort(b_step, step_phase & 1, abort);
+                ++step_phase;
+                for (int e = tid; e < nr * R; e += blockDim.x) {
+                    const int i = e / R, c = e % R;
+                    float v = s0 == 0 ? 0.f : sM[i * R4 + c];
+                    for (int q = 0; q < ns; ++q) v += red[q * (blks / 4) + i * R4 + c];
+                    sM[i * R4 + c] = v;
+                }
+                __syncthreads();   // the staged blocks are read
             }
-            // M rows: thread per (column, row), rows fastest (coalesced slabs)
-            for (int e = tid; e < nr * R; e += blockDim.x) {
-                const int c = e / nr, i = e % nr;
-                const float *src0 = part + (size_t)c * rows_all + b0 + i;
-                float pv[16];
-#pragma unroll
-                for (int src = 0; src < 16; ++src)
-                    pv[src] = src < cs ? __ldcg(src0 + (size_t)src * rows_all * cst) : 0.f;
-                float v = 0.f;
-#pragma unroll
-                for (int src = 0; src < 16; ++src)
-                    if (src < cs) v += pv[src];
-                sM[i * R4 + c] = v;
-            }
-            __syncthreads();
+            trace_stamp(P.trace, 40, tr && b0 == row0);
             for (int e = tid; e < nr * R; e += blockDim.x) {
                 const int i = e / R, r = e % R;
                 const long long row = b0 + i;
@@ -563,21 +682,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                 }
                 const float aold = sA[i * R4 + r];
                 float an;
-                if (P.step == CPD_STEP_ADAGRAD) {
-                    double *Sp = P.S[n] + row * R + r;
-                    const double S2 = __fma_rn((double)gr, (double)gr, *Sp);
-                    *Sp = S2;
+                if (ada) {
+                    const double S2 = __fma_rn((double)gr, (double)gr, sS[i * R + r]);
+                    sS[i * R + r] = S2;
                     an = aold - (float)P.eta * gr * rsqrtf((float)S2 + (float)P.b);
                 } else {
                     an = aold - (float)alpha * gr;
                 }
                 if (P.constraint == CPD_CONSTRAINT_NONNEG && an < 0.f) an = 0.f;   // projection; NaN kept
                 if (!isfinite(an) || !isfinite(gr)) flags |= kStNonFinite;
-                a.Ap[n][row * R4 + r] = an;
+                sA[i * R4 + r] = an;
                 sN[i * R + r] = an;
                 if (last) P.G[row * R + r] = gr;
             }
+            fence_async_smem();
             __syncthreads();
+            trace_stamp(P.trace, 41, tr && b0 == row0);
+            if (train && tid == 0) {
+                // rows and S back (the padding columns of the rows are unchanged)
+                bulk_s2g(a.Ap[n] + b0 * R4, smem_u32(sA), blkb);
+                if (ada) bulk_s2g(P.S[n] + b0 * R, smem_u32(sS), (uint32_t)(nr * R * 8 / 16 * 16));
+                bulk_commit();
+            }
+            if (ada && tid == 0 && ((nr * R) & 1)) P.S[n][(b0 + nr) * R - 1] = sS[nr * R - 1];   // odd tail
             if (train && P.sampling == CPD_SAMPLE_EUCLIDEAN) {
                 // eight rows per warp at a time; lanes < cs send the weights
                 for (int lr0 = 8 * warp; lr0 < nr; lr0 += 8 * (kThreads / 32)) {
@@ -594,8 +721,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                     }
                 }
             }
+            if (train && tid == 0) bulk_wait_all();   // the stores read the staging before it is reused
             __syncthreads();
+            trace_stamp(P.trace, 42, tr && b0 == row0);
         }
+        if (tid == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
         trace_stamp(P.trace, 18, tr);
         if (!train) {
             // the next batch's partials overwrite the scratch: every CTA has
@@ -638,11 +768,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
     __syncthreads();
     if (tid == 0) {
         if (s_flags) atomicOr(P.status, s_flags);
-        if (s_abort) atomicOr(P.status, kStTimeout);
+        if (*abort) {
+            atomicOr(P.status, kStTimeout);
+            // products and copies still in flight must finish before the
+            // accumulator and the shared memory are released
+            mbar_wait_bounded(b_mma, mma_iters & 1);
+            for (int q = 0; q < L.nland; ++q) {
+                const long long issued = (gq0 + L.nland - 1 - q) / L.nland;   // phases issued on stage q
+                if (issued > 0) mbar_wait_bounded(b_lfull + 8 * q, (uint32_t)((issued - 1) & 1));
+            }
+        }
     }
-    // products still in flight after a timed-out wait must finish before the
-    // accumulator is freed
-    if (s_abort && tid == 0) mbar_wait_bounded(bar_mma, mma_iters & 1);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0)
