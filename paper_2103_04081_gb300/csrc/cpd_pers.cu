@@ -332,6 +332,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
             a.Ap[k][e] = r < R ? __ldcg(P.A[k] + i * R + r) : 0.f;
         }
     }
+    // the private factors are read by bulk copies (the async proxy) from now on
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = s_tmem;
@@ -425,6 +427,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
         if (warp == 0) {
             // producer: whole fibers (ld elements) and their factor rows
             if (lane == 0) {
+                // rows other CTAs stored (bulk stores, then a cluster barrier)
+                // are read by bulk copies below
+                asm volatile("fence.proxy.async.global;\n" ::: "memory");
                 const __nv_bfloat16 *rep = reinterpret_cast<const __nv_bfloat16 *>(P.rep[n]);
                 for (int c = 0; c < nchunks; ++c) {
                     const long long gq = gq0 + c;
@@ -646,6 +651,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
             for (int s0 = 0; s0 < cs; s0 += L.red_slots) {
                 const int ns = (cs - s0) < L.red_slots ? cs - s0 : L.red_slots;
                 if (tid == 0) {
+                    asm volatile("fence.proxy.async.global;\n" ::: "memory");
                     uint32_t bytes = (uint32_t)ns * blkb;
                     if (s0 == 0) bytes += blkb + (ada ? (uint32_t)((nr * R * 8 + 15) / 16 * 16) : 0u);
                     mbar_expect_tx(b_step, bytes);
@@ -701,7 +707,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
             if (train && tid == 0) {
                 // rows and S back (the padding columns of the rows are unchanged)
                 bulk_s2g(a.Ap[n] + b0 * R4, smem_u32(sA), blkb);
-                if (ada) bulk_s2g(P.S[n] + b0 * R, smem_u32(sS), (uint32_t)(nr * R * 8 / 16 * 16));
+                if (ada && nr * R >= 2) bulk_s2g(P.S[n] + b0 * R, smem_u32(sS), (uint32_t)(nr * R * 8 / 16 * 16));
                 bulk_commit();
             }
             if (ada && tid == 0 && ((nr * R) & 1)) P.S[n][(b0 + nr) * R - 1] = sS[nr * R - 1];   // odd tail
