@@ -697,16 +697,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                 }
                 if (P.constraint == CPD_CONSTRAINT_NONNEG && an < 0.f) an = 0.f;   // projection; NaN kept
                 if (!isfinite(an) || !isfinite(gr)) flags |= kStNonFinite;
-                sA[i * R4 + r] = an;
+                sM[i * R4 + r] = an;   // M(i, r) is read by this thread only; sA stays intact for A H
                 sN[i * R + r] = an;
                 if (last) P.G[row * R + r] = gr;
             }
+            if (R4 > R)   // the stored rows keep their zero padding
+                for (int e = tid; e < nr * (R4 - R); e += blockDim.x) sM[(e / (R4 - R)) * R4 + R + e % (R4 - R)] = 0.f;
             fence_async_smem();
             __syncthreads();
             trace_stamp(P.trace, 41, tr && b0 == row0);
             if (train && tid == 0) {
                 // rows and S back (the padding columns of the rows are unchanged)
-                bulk_s2g(a.Ap[n] + b0 * R4, smem_u32(sA), blkb);
+                bulk_s2g(a.Ap[n] + b0 * R4, smem_u32(sM), blkb);
                 if (ada && nr * R >= 2) bulk_s2g(P.S[n] + b0 * R, smem_u32(sS), (uint32_t)(nr * R * 8 / 16 * 16));
                 bulk_commit();
             }
