@@ -66,7 +66,7 @@ __host__ __device__ inline size_t up128(size_t v) { return (v + 127) / 128 * 128
 struct PersLayout {
     size_t cdf, idx, jcol, sw, land, land_bytes, lx, lfr, pitch, op, op_bytes, ox, obh, obl, zf, bar, total;
     size_t region, region_bytes;
-    size_t h, own_a, own_m, own_s, own_n, dsm, red;   // inside the region (step phase)
+    size_t h, own_a, own_m, own_s, own_n, own_g, dsm, red;   // inside the region (step phase)
     int nland;                                        // landing stages (3, or 2 when memory is short)
     int red_slots;                                    // partial blocks staged at once
     __host__ __device__ PersLayout(const PersArgs &a)
@@ -100,7 +100,8 @@ struct PersLayout {
         own_m = own_a + up128(blk);
         own_n = own_m + up128(blk);
         own_s = own_n + up128(blk);
-        dsm = own_s + up128((size_t)kPOwnBlock * a.P.R * 8 + 16);
+        own_g = own_s + up128((size_t)kPOwnBlock * a.P.R * 8 + 16);
+        dsm = own_g + up128(blk);
         red = dsm + 2 * kThreads * 8;
         const size_t tiles = 4 * up128((size_t)kPM * a.R4 * 4);   // staged partial tiles
         nland = kPLand;
@@ -127,6 +128,16 @@ struct PersLayout {
         if (total < 120 * 1024) total = 120 * 1024;
     }
 };
+
+// Phase timestamp (%globaltimer, ns) from the calling thread, when tracing is on.
+__device__ __forceinline__ void stamp_here(unsigned long long *trace, int slot, bool cond)
+{
+    if (trace && cond) {
+        unsigned long long ns;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(ns));
+        trace[slot] = ns;
+    }
+}
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
@@ -425,33 +436,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
         if (warp == 0) {
-            // producer: whole fibers (ld elements) and their factor rows
-            if (lane == 0) {
-                // rows other CTAs stored (bulk stores, then a cluster barrier)
-                // are read by bulk copies below
-                asm volatile("fence.proxy.async.global;\n" ::: "memory");
-                const __nv_bfloat16 *rep = reinterpret_cast<const __nv_bfloat16 *>(P.rep[n]);
-                for (int c = 0; c < nchunks; ++c) {
-                    const long long gq = gq0 + c;
-                    const int s = (int)(gq % L.nland);
-                    if (gq >= L.nland) wait_or_abort(b_lempty + 8 * s, (uint32_t)((gq / L.nland - 1) & 1), abort);
-                    const uint32_t lb = smem_u32(smem + L.land + (size_t)s * L.land_bytes);
-                    int nv = nf - c * kPK;
-                    nv = nv < kPK ? nv : kPK;
-                    const uint32_t fbytes = (uint32_t)ld * 2, rbytes = (uint32_t)R4 * 4;
-                    mbar_expect_tx(b_lfull + 8 * s, (uint32_t)nv * (fbytes + (uint32_t)(N - 1) * rbytes));
-                    if (!*abort) {
-                        for (int f = 0; f < nv; ++f) {
-                            const int fl = c * kPK + f;
-                            bulk_g2s(lb + (uint32_t)(L.lx + f * L.pitch), rep + jcol[fl] * ld, fbytes, b_lfull + 8 * s);
-                            for (int kk = 0; kk < N - 1; ++kk) {
-                                const int k = kk + (kk >= n ? 1 : 0);
-                                bulk_g2s(lb + (uint32_t)(L.lfr + ((f * (N - 1) + kk) * R4) * 4),
-                                         a.Ap[k] + (long long)sidx[fl * N + k] * R4, rbytes, b_lfull + 8 * s);
-                            }
-                        }
+            // producer: whole fibers (ld elements) and their factor rows; lane 0
+            // announces the bytes, the warp's lanes issue the bulk copies
+            // (lane f < 16: fiber f; every lane: a share of the factor rows)
+            // rows other CTAs stored (bulk stores, then a cluster barrier) are
+            // read by bulk copies below
+            asm volatile("fence.proxy.async.global;\n" ::: "memory");
+            const __nv_bfloat16 *rep = reinterpret_cast<const __nv_bfloat16 *>(P.rep[n]);
+            const uint32_t fbytes = (uint32_t)ld * 2, rbytes = (uint32_t)R4 * 4;
+            for (int c = 0; c < nchunks; ++c) {
+                const long long gq = gq0 + c;
+                const int s = (int)(gq % L.nland);
+                const bool trc = tr && c == 3;
+                stamp_here(P.trace, 30, trc && lane == 0);
+                if (gq >= L.nland) wait_or_abort(b_lempty + 8 * s, (uint32_t)((gq / L.nland - 1) & 1), abort);
+                stamp_here(P.trace, 31, trc && lane == 0);
+                const uint32_t lb = smem_u32(smem + L.land + (size_t)s * L.land_bytes);
+                int nv = nf - c * kPK;
+                nv = nv < kPK ? nv : kPK;
+                if (lane == 0) mbar_expect_tx(b_lfull + 8 * s, (uint32_t)nv * (fbytes + (uint32_t)(N - 1) * rbytes));
+                __syncwarp();
+                if (!*abort) {
+                    if (lane < nv) {
+                        const int fl = c * kPK + lane;
+                        bulk_g2s(lb + (uint32_t)(L.lx + lane * L.pitch), rep + jcol[fl] * ld, fbytes, b_lfull + 8 * s);
+                    }
+                    for (int q = lane; q < nv * (N - 1); q += 32) {
+                        const int f = q / (N - 1), kk = q % (N - 1);
+                        const int k = kk + (kk >= n ? 1 : 0);
+                        const int fl = c * kPK + f;
+                        bulk_g2s(lb + (uint32_t)(L.lfr + ((f * (N - 1) + kk) * R4) * 4),
+                                 a.Ap[k] + (long long)sidx[fl * N + k] * R4, rbytes, b_lfull + 8 * s);
                     }
                 }
+                stamp_here(P.trace, 32, trc && lane == 0);
             }
         } else if (warp == 1) {
             // tensor-core products
@@ -461,6 +479,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                     const long long gq = gq0 + c;
                     const int o = (int)(gq % kPOp);
                     wait_or_abort(b_ofull + 8 * o, (uint32_t)((gq / kPOp) & 1), abort);
+                    stamp_here(P.trace, 39, tr && c == 3);
                     if (*abort) continue;
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     unsigned char *ob = smem + L.op + (size_t)o * L.op_bytes;
@@ -474,6 +493,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                         mma_bf16(d, da, dl, idesc, 1u);
                     }
                     mma_commit(b_oempty + 8 * o);
+                    stamp_here(P.trace, 43, tr && c == 3);
                 }
                 if (nchunks > 0 && !*abort) mma_commit(b_mma);
             }
@@ -482,8 +502,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
             for (int c = 0; c < nchunks; ++c) {
                 const long long gq = gq0 + c;
                 const int s = (int)(gq % L.nland), o = (int)(gq % kPOp);
+                const bool trc = tr && c == 3 && tt == 0;
+                stamp_here(P.trace, 33, trc);
                 wait_or_abort(b_lfull + 8 * s, (uint32_t)((gq / L.nland) & 1), abort);
+                stamp_here(P.trace, 34, trc);
                 if (gq >= kPOp) wait_or_abort(b_oempty + 8 * o, (uint32_t)((gq / kPOp - 1) & 1), abort);
+                stamp_here(P.trace, 35, trc);
                 const unsigned char *lb = smem + L.land + (size_t)s * L.land_bytes;
                 unsigned char *ob = smem + L.op + (size_t)o * L.op_bytes;
                 // fibers into the no-swizzle MN-major operand: piece (f, ig) =
@@ -497,6 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                         v = *reinterpret_cast<const uint4 *>(lb + L.lx + (size_t)f * L.pitch + (size_t)ig * 16);
                     *reinterpret_cast<uint4 *>(ob + L.ox + ((size_t)((f >> 3) * g8 + ig) << 7) + ((f & 7) << 4)) = v;
                 }
+                stamp_here(P.trace, 36, trc);
                 // z_f (fp32, for H) and Z' = s_f z_f as a bf16 hi/lo pair, K-major:
                 // core matrix (f/8, r/8), 8 fibers per 16 bytes
                 const float *fr = reinterpret_cast<const float *>(lb + L.lfr);
@@ -527,6 +552,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                 }
                 fence_async_smem();
                 transform_sync();   // the chunk's operands and z_f are complete; the landing stage is read
+                stamp_here(P.trace, 37, trc);
                 if (tt == 0) {
                     mbar_arrive(b_ofull + 8 * o);
                     mbar_arrive(b_lempty + 8 * s);
@@ -546,6 +572,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                             for (int v = 0; v < 4; ++v) acc[u][v] += ar[u] * ac[v];
                     }
                 }
+                stamp_here(P.trace, 38, trc);
             }
         }
         __syncthreads();
@@ -639,6 +666,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
         float *sA = reinterpret_cast<float *>(region + L.own_a);
         float *sM = reinterpret_cast<float *>(region + L.own_m);
         float *sN = reinterpret_cast<float *>(region + L.own_n);
+        float *sG = reinterpret_cast<float *>(region + L.own_g);
         double *sS = reinterpret_cast<double *>(region + L.own_s);
         const float *red = reinterpret_cast<const float *>(region + L.red);
         const uint32_t wslot = smem_u32(stage + a.off[n]);
@@ -676,12 +704,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_pers(const PersArgs one, const 
                 __syncthreads();   // the staged blocks are read
             }
             trace_stamp(P.trace, 40, tr && b0 == row0);
+            // A H for a row and 4 consecutive columns per thread (4 independent
+            // chains; one broadcast A load and one float4 H load per step)
+            const int r4n = R4 / 4;
+            for (int e = tid; e < nr * r4n; e += blockDim.x) {
+                const int i = e / r4n, r0c = 4 * (e % r4n);
+                float ah4[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int s = 0; s < R; ++s) {
+                    const float av = sA[i * R4 + s];
+                    const float4 hv = *reinterpret_cast<const float4 *>(sH + s * kPHd + r0c);
+                    ah4[0] += av * hv.x;
+                    ah4[1] += av * hv.y;
+                    ah4[2] += av * hv.z;
+                    ah4[3] += av * hv.w;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) sG[i * R4 + r0c + u] = ah4[u];
+            }
+            __syncthreads();
             for (int e = tid; e < nr * R; e += blockDim.x) {
                 const int i = e / R, r = e % R;
                 const long long row = b0 + i;
-                float ah = 0.f;
-                for (int s = 0; s < R; ++s) ah += sA[i * R4 + s] * sH[s * kPHd + r];
-                const float gr = ah - sM[i * R4 + r];
+                const float gr = sG[i * R4 + r] - sM[i * R4 + r];
                 if (!train) {
                     md.gout[((size_t)bt * In + row) * R + r] = gr;
                     continue;
