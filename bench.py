@@ -310,28 +310,39 @@ def _event_ms(stream, fn) -> float:
     return e0.elapsed_time(e1)
 
 
-def gather_per_mode(C, X, A0: list, w: dict, dev: str, stream, peak: float, K: int = 32, cs: int = 4,
-                    reps: int = 10) -> dict:
-    """The fiber gather in bulk, per mode: cpd_gradients forms K = 32 mini-batch
-    gradients of one mode (K B fibers, each a whole mode-n fiber of the replica,
-    contracted on the tensor cores) in one launch of one cluster per batch.
-    Useful bytes per launch K B I_n elem; GB/s from CUDA events over `reps`
-    launches with fresh draws each (batches t0 + b), on the launching stream."""
-    kw = cfg_kwargs(w, 0, "persistent")
-    kw["max_ctas"] = cs
+def gather_per_mode(C, X, A0: list, w: dict, dev: str, stream, peak: float, K: int = 32, reps: int = 10) -> dict:
+    """The fiber gather in bulk, per mode: cpd_skrp materialises K = 32
+    mini-batches of one mode (Alg. 3 + Alg. 1: the draws, p_f, the sampled KRP
+    rows and the K B sampled fibers) in one launch over every SM, the fibers
+    moving by bulk copies. Bytes per launch: the K B I_n elem fiber bytes read
+    (the useful gather) and as many written; the copy-equivalent rate (read +
+    write) is the one comparable with the measured copy peak. CUDA events over
+    `reps` launches with fresh draws each (batches t0 + b), on the launching
+    stream; the replicas (6 GB) are far larger than L2."""
+    kw = cfg_kwargs(w, 0, "auto")
     with torch.cuda.stream(stream):
         dec = C.Decomposition(X, [a.to(dev) for a in A0], stream=stream, **kw)
     esize = {"bf16": 2, "f32": 4, "f64": 8}[w["x_dtype"]]
-    out = {"K": K, "B": w["B"], "cluster": cs, "launches_timed": reps, "modes": []}
+    tdt = {"bf16": torch.bfloat16, "f32": torch.float32}[w["x_dtype"]]
+    N, B, R = len(w["dims"]), w["B"], w["R"]
+    out = {"K": K, "B": B, "launches_timed": reps, "kernel": "k_skrp", "modes": []}
+    idx = torch.empty(K * B, N, dtype=torch.int32, device=dev)
+    p = torch.empty(K * B, dtype=torch.float64, device=dev)
+    Z = torch.empty(K * B, R, dtype=torch.float32, device=dev)
     for n, In in enumerate(w["dims"]):
-        G = torch.empty(K, In, w["R"], device=dev)
-        C.cpd_gradients(dec.ctx, n, 0, K, G, stream)
-        ms = _event_ms(stream, lambda: [C.cpd_gradients(dec.ctx, n, K * (1 + r), K, G, stream)
+        ld = (In + 7) // 8 * 8
+        Xs = torch.empty(K * B * ld, dtype=tdt, device=dev)
+        C.cpd_skrp(dec.ctx, n, 0, K, idx, p, Z, Xs, stream)
+        ms = _event_ms(stream, lambda: [C.cpd_skrp(dec.ctx, n, K * (1 + r), K, idx, p, Z, Xs, stream)
                                         for r in range(reps)]) / reps
-        useful = K * w["B"] * In * esize
-        gbs = useful / (ms * 1e-3) / 1e9
+        useful = K * B * In * esize
+        moved = 2 * K * B * ld * esize
         out["modes"].append({"mode": n, "I_n": In, "useful_bytes_per_launch": useful, "ms_per_launch": ms,
-                             "gbs": gbs, "frac": gbs / peak})
+                             "gather_gbs": useful / (ms * 1e-3) / 1e9,
+                             "gather_frac": useful / (ms * 1e-3) / 1e9 / peak,
+                             "copy_equivalent_gbs": moved / (ms * 1e-3) / 1e9,
+                             "copy_equivalent_frac": moved / (ms * 1e-3) / 1e9 / peak})
+        del Xs
     dec.close()
     return out
 

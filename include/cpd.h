@@ -150,6 +150,25 @@ cpd_status cpd_init(const cpd_config *cfg, const void *X, int x_loc,
 cpd_status cpd_sgd_iters(cpd_ctx *ctx, int64_t iters, void *stream);
 
 /*
+ * cpd_skrp -- Alg. 3 (SKRP-ST-I) followed by Alg. 1 (SKRP-ST), materialised
+ * for K mini-batches of mode n: batch b takes the random draws of iteration
+ * t0 + b with the mode fixed to n, from the context's current per-factor
+ * distributions. Outputs (device memory, each may be NULL):
+ *  idx : K*B x N int32, the multi-indices (Eq. (4)), column n = -1;
+ *  p   : K*B doubles, p_f of Eq. (10) (FP64, the same bits as the oracle);
+ *  Z   : K*B x R floats, the sampled Khatri-Rao rows (Eq. (3)), unweighted;
+ *  X   : K*B fibers of the mode-n unfolding (Eq. (2)), fiber f of batch b at
+ *        element (b*B + f) * ld_n, ld_n = I_n rounded up to 8 (the padding
+ *        entries are 0), in the tensor's storage type.
+ * The fibers move by bulk copies over every SM: this is the sampled gather
+ * on its own, the bandwidth measure of the access pattern. Float factors
+ * only (F32 or BF16 tensors); I_n times the element size at most about 5 KB.
+ * Asynchronous on `stream`. Errors: CPD_EINVAL, CPD_ECUDA.
+ */
+cpd_status cpd_skrp(cpd_ctx *ctx, int32_t n, int64_t t0, int32_t K, int32_t *idx, double *p, float *Z, void *X,
+                    void *stream);
+
+/*
  * cpd_gradients -- K independent mini-batch gradients of mode n at the
  * current factors (Eq. (11), each batch drawn by Alg. 3 from the current
  * per-factor distributions), the samples whose spread Thm 10 and Fig. 3

@@ -529,6 +529,57 @@ int orc_gradient_for_batch(const orc_cfg *c, int32_t n, const int64_t *idx,
 }
 
 /*
+ * Alg. 3 (SKRP-ST-I) followed by Alg. 1 (SKRP-ST) for mode n with the random
+ * words of iteration t: the per-factor distributions of the current factors,
+ * the B x (N-1) draws, the fiber probabilities p_f (Eq. (10)), the sampled
+ * KRP rows Z_S (B x R, Eq. (3)) and the sampled fibers X_S (B x I_n, fiber f
+ * contiguous, Eq. (2)). idx is B x N with column n = -1. Z and X may be NULL.
+ */
+int orc_sample_batch(const orc_cfg *c, int32_t n, int64_t t, const void *X, const double *const *A,
+                     int64_t *idx, double *p, double *Zs, double *Xs)
+{
+    int32_t N = c->N, R = c->R, B = c->B;
+    if (N < 2 || N > ORC_MAXN || R < 1 || B < 1 || n < 0 || n >= N)
+        return ORC_EINVAL;
+    int64_t In = c->dims[n];
+    double *w[ORC_MAXN] = {0};
+    uint64_t *cdf[ORC_MAXN] = {0};
+    for (int32_t k = 0; k < N; ++k) {
+        w[k] = (double *)malloc((size_t)c->dims[k] * sizeof(double));
+        cdf[k] = (uint64_t *)malloc((size_t)c->dims[k] * sizeof(uint64_t));
+    }
+    int st = build_distributions(c, n, A, w, cdf);
+    if (st == ORC_OK) {
+        for (int32_t f = 0; f < B; ++f) {
+            for (int32_t k = 0; k < N; ++k) {
+                if (k == n) {
+                    idx[(int64_t)f * N + k] = -1;
+                    continue;
+                }
+                const uint64_t x = orc_fiber_word(c->seed, t, f, k);
+                idx[(int64_t)f * N + k] = orc_draw(cdf[k], c->dims[k], x);
+            }
+        }
+#ifdef ORC_OMP
+#pragma omp parallel for schedule(static)
+#endif
+        for (int32_t f = 0; f < B; ++f) {
+            const int64_t *row = idx + (int64_t)f * N;
+            p[f] = fiber_probability(c, n, row, cdf);
+            if (Zs)
+                orc_krp_row(N, R, n, A, row, Zs + (int64_t)f * R);
+            if (Xs)
+                orc_gather_fiber(X, c->x_dtype, N, c->dims, n, row, Xs + (int64_t)f * In);
+        }
+    }
+    for (int32_t k = 0; k < N; ++k) {
+        free(w[k]);
+        free(cdf[k]);
+    }
+    return st;
+}
+
+/*
  * One iteration of BrawsCPD (Alg. 4) / AdawsCPD (Alg. 5) at iteration t:
  * draw n, draw the mini-batch (Alg. 3), form G (Eq. (11)), update
  * A^(n). A and S (AdaGrad accumulators, may be NULL for the other steps)
@@ -544,42 +595,15 @@ int orc_step(const orc_cfg *c, int64_t t, const void *X, double *const *A,
         return ORC_EINVAL;
     int32_t n = orc_mode_draw(c->seed, t, N);
     int64_t In = c->dims[n];
-    double *w[ORC_MAXN] = {0};
-    uint64_t *cdf[ORC_MAXN] = {0};
-    for (int32_t k = 0; k < N; ++k) {
-        w[k] = (double *)malloc((size_t)c->dims[k] * sizeof(double));
-        cdf[k] = (uint64_t *)malloc((size_t)c->dims[k] * sizeof(uint64_t));
-    }
     int64_t *idx = (int64_t *)malloc((size_t)B * N * sizeof(int64_t));
     double *p = (double *)malloc((size_t)B * sizeof(double));
     double *G = (double *)malloc((size_t)In * R * sizeof(double));
-    int st = build_distributions(c, n, (const double *const *)A, w, cdf);
+    double *Zs = (double *)malloc((size_t)B * R * sizeof(double));
+    double *Xs = (double *)malloc((size_t)B * In * sizeof(double));
+    int st = orc_sample_batch(c, n, t, X, (const double *const *)A, idx, p, Zs, Xs);
     if (st == ORC_OK) {
-        for (int32_t f = 0; f < B; ++f) {
-            for (int32_t k = 0; k < N; ++k) {
-                if (k == n) {
-                    idx[(int64_t)f * N + k] = -1;
-                    continue;
-                }
-                const uint64_t x = orc_fiber_word(c->seed, t, f, k);
-                idx[(int64_t)f * N + k] = orc_draw(cdf[k], c->dims[k], x);
-            }
-        }
-        double *Zs = (double *)malloc((size_t)B * R * sizeof(double));
-        double *Xs = (double *)malloc((size_t)B * In * sizeof(double));
-#ifdef ORC_OMP
-#pragma omp parallel for schedule(static)
-#endif
-        for (int32_t f = 0; f < B; ++f) {
-            const int64_t *row = idx + (int64_t)f * N;
-            p[f] = fiber_probability(c, n, row, cdf);
-            orc_krp_row(N, R, n, (const double *const *)A, row, Zs + (int64_t)f * R);
-            orc_gather_fiber(X, c->x_dtype, N, c->dims, n, row, Xs + (int64_t)f * In);
-        }
         orc_gradient(In, R, B, j_count(c, n), A[n], Zs, Xs, p, G);
         orc_update(c, t, In, A[n], S ? S[n] : NULL, G);
-        free(Zs);
-        free(Xs);
         if (n_out)
             *n_out = n;
         if (idx_out)
@@ -589,10 +613,8 @@ int orc_step(const orc_cfg *c, int64_t t, const void *X, double *const *A,
         if (G_out)
             memcpy(G_out, G, (size_t)In * R * sizeof(double));
     }
-    for (int32_t k = 0; k < N; ++k) {
-        free(w[k]);
-        free(cdf[k]);
-    }
+    free(Zs);
+    free(Xs);
     free(idx);
     free(p);
     free(G);

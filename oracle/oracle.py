@@ -146,6 +146,8 @@ def _declare(L):
     L.orc_gradient_for_batch.argtypes = [ctypes.POINTER(_Cfg), _i32, _p, _p, _p, _p, _p]
     L.orc_gradient_for_batch.restype = ctypes.c_int
     L.orc_step.argtypes = [ctypes.POINTER(_Cfg), _i64, _p, _p, _p, _p, _p, _p, _p]
+    L.orc_sample_batch.argtypes = [ctypes.POINTER(_Cfg), _i32, _i64, _p, _p, _p, _p, _p, _p]
+    L.orc_sample_batch.restype = ctypes.c_int
     L.orc_step.restype = ctypes.c_int
     L.orc_run.argtypes = [ctypes.POINTER(_Cfg), _i64, _i64, _p, _p, _p]
     L.orc_run.restype = ctypes.c_int
@@ -291,6 +293,22 @@ def step(cfg: Config, t: int, X, A: list, S: list | None = None, xbuf=None) -> d
                         ctypes.byref(n), _ptr(idx), _ptr(p), _ptr(G))
     return {"status": st, "n": n.value, "idx": idx, "p": p,
             "G": G[: cfg.dims[n.value]].copy()}
+
+
+def sample_batch(cfg: Config, n: int, t: int, A: list, xbuf=None, X=None, want_fibers: bool = True) -> dict:
+    """Alg. 3 + Alg. 1 for mode n with the draws of iteration t: idx (B x N,
+    column n = -1), p (B), Z (B x R) and, if wanted, the fibers X_S (B x I_n)."""
+    A = [_f64(a) for a in A]
+    c = cfg.c()
+    buf = x_buffer(X, cfg.x_dtype) if xbuf is None else xbuf
+    B, N, R = cfg.B, len(cfg.dims), cfg.R
+    idx = np.empty((B, N), dtype=np.int64)
+    p = np.empty(B)
+    Z = np.empty((B, R))
+    Xs = np.empty((B, int(cfg.dims[n]))) if want_fibers else None
+    st = lib().orc_sample_batch(ctypes.byref(c), n, t, _ptr(buf), _ptr_array(A), _ptr(idx), _ptr(p), _ptr(Z),
+                                _ptr(Xs) if Xs is not None else None)
+    return {"status": st, "idx": idx, "p": p, "Z": Z, "X": Xs}
 
 
 def run(cfg: Config, t0: int, T: int, X, A: list, S: list | None = None, xbuf=None,

@@ -70,6 +70,7 @@ def _load():
         "cpd_sgd_iters": [P, I64, P],
         "cpd_prepare": [P, I64, P],
         "cpd_gradients": [P, I32, I64, I32, P, P],
+        "cpd_skrp": [P, I32, I64, I32, P, P, P, P, P],
         "cpd_fit": [P, P, P, P],
         "cpd_fit_start": [P, P],
         "cpd_fit_poll": [P, P, P],
@@ -175,6 +176,13 @@ def cpd_prepare(ctx, iters: int, stream=None) -> None:
 def cpd_gradients(ctx, n: int, t0: int, K: int, G_out: torch.Tensor, stream=None) -> None:
     """K mini-batch gradients of mode n into the device tensor G_out (K x I_n x R float32)."""
     _check(_lib.cpd_gradients(ctx, int(n), int(t0), int(K), G_out.data_ptr(), _stream(stream)))
+
+
+def cpd_skrp(ctx, n: int, t0: int, K: int, idx=None, p=None, Z=None, X=None, stream=None) -> None:
+    """Alg. 3 + Alg. 1 materialised for K batches of mode n into device tensors
+    (idx K*B x N int32, p K*B float64, Z K*B x R float32, X K*B x ld_n)."""
+    ptr = (lambda t: t.data_ptr() if t is not None else None)
+    _check(_lib.cpd_skrp(ctx, int(n), int(t0), int(K), ptr(idx), ptr(p), ptr(Z), ptr(X), _stream(stream)))
 
 
 def cpd_fit(ctx, stream=None) -> tuple[float, float]:

@@ -592,6 +592,36 @@ extern "C" cpd_status cpd_gradients(cpd_ctx *c, int32_t n, int64_t t0, int32_t K
     return CPD_OK;
 }
 
+extern "C" cpd_status cpd_skrp(cpd_ctx *c, int32_t n, int64_t t0, int32_t K, int32_t *idx, double *p, float *Z,
+                               void *X, void *stream)
+{
+    if (!c || K < 1 || t0 < 0) return fail(CPD_EINVAL, "bad argument");
+    if (c->fbytes != 4) return fail(CPD_EINVAL, "cpd_skrp takes float factors (F32 or BF16 tensors)");
+    if (n < 0 || n >= c->cfg.N) return fail(CPD_EINVAL, "mode out of range");
+    if ((double)K * c->cfg.B > 2.0e9) return fail(CPD_EINVAL, "K B too large");
+    if (skrp_smem_bytes(c->Pf, n, c->xbytes) > 200 * 1024)
+        return fail(CPD_EINVAL, "mode too long for the fiber staging (I_n * element size above about 5 KB)");
+    cudaStream_t s = (cudaStream_t)stream;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    cudaError_t e = launch_flush_dirty(c->Pf, s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profiling && c->prof_used < kProfSlots) {
+        e0 = c->ev[3 * c->prof_used];
+        e1 = c->ev[3 * c->prof_used + 1];
+        ++c->prof_used;
+        c->prof_iters += 1;
+    }
+    if (e == cudaSuccess && e0) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = launch_skrp(c->Pf, n, t0, K, idx, p, Z, X, c->xbytes, sms, s);
+    if (e == cudaSuccess && e1) {
+        e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev[3 * (c->prof_used - 1) + 2], s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cpd_skrp launch");
+    return CPD_OK;
+}
+
 extern "C" cpd_status cpd_sgd_iters(cpd_ctx *c, int64_t iters, void *stream)
 {
     if (!c || iters < 0) return fail(CPD_EINVAL, "bad context or iteration count");

@@ -148,6 +148,11 @@ long long tc_stage_cap(const Problem<float> &P);
 long long tcc_stage_cap(const Problem<float> &P);
 constexpr long long kSimtStageCap = 2048;
 
+// SKRP-ST-I materialised (cpd_skrp.cu).
+cudaError_t launch_skrp(const Problem<float> &P, int n, long long t0, int K, int *idx, double *p, float *Z, void *X,
+                        int esize, int sm_count, cudaStream_t stream);
+size_t skrp_smem_bytes(const Problem<float> &P, int n, int esize);
+
 // Persistent cluster engine (cpd_pers.cu).
 bool pers_supported(const cpd_config &cfg);
 void pers_fill(PersArgs &a, int cs);        // fpc, R4, Npad, cst, ntile, off, sumI

@@ -1,0 +1,84 @@
+"""cpd_skrp (Alg. 3 + Alg. 1 materialised) against the oracle's batch draw.
+
+The GPU draws K batches of one mode from the context's current per-factor
+distributions; the oracle draws the same batches (same Philox words, the
+same exact fixed-point CDFs) from the GPU's factors. Multi-indices and p_f
+must agree bit for bit, the fibers are the stored tensor values (exact), and
+the sampled Khatri-Rao rows -- products of at most N-1 FP32 factor entries
+on the GPU, in FP64 in the oracle -- within 1e-6 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+from helpers import make_problem, oracle_xbuf
+from paper_2103_04081_gb300 import inputs as IN
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cpd():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2103_04081_gb300 import build
+    build.build()
+    from paper_2103_04081_gb300 import cpd as C
+    return C
+
+
+def check_batches(cpd, orc, dec, xb, x_dtype, dims, R, B, sampling, modes, K=3, t0=1000):
+    N = len(dims)
+    A = [a.double().numpy() for a in dec.factors()]
+    ocfg = orc.Config(dims=tuple(dims), R=R, B=B, sampling=sampling, step="adagrad", x_dtype=x_dtype,
+                      seed=int(dec.cfg.seed))
+    tdt = {"bf16": torch.bfloat16, "f32": torch.float32}[x_dtype]
+    for n in modes:
+        ld = (dims[n] + 7) // 8 * 8
+        idx = torch.empty(K * B, N, dtype=torch.int32, device="cuda")
+        p = torch.empty(K * B, dtype=torch.float64, device="cuda")
+        Z = torch.empty(K * B, R, dtype=torch.float32, device="cuda")
+        X = torch.empty(K * B * ld, dtype=tdt, device="cuda")
+        cpd.cpd_skrp(dec.ctx, n, t0, K, idx, p, Z, X)
+        torch.cuda.synchronize()
+        idx, p, Z = idx.cpu().numpy(), p.cpu().numpy(), Z.cpu().double().numpy()
+        Xg = oracle_xbuf(X).reshape(K * B, ld)
+        for b in range(K):
+            o = orc.sample_batch(ocfg, n, t0 + b, A, xbuf=xb)
+            sl = slice(b * B, (b + 1) * B)
+            np.testing.assert_array_equal(idx[sl].astype(np.int64), o["idx"])
+            np.testing.assert_array_equal(p[sl], o["p"])
+            np.testing.assert_allclose(Z[sl], o["Z"], rtol=1e-6, atol=1e-30)
+            got = orc.stored_values(Xg[sl].ravel(), x_dtype).reshape(B, ld)
+            np.testing.assert_array_equal(got[:, :dims[n]], o["X"])
+            assert not got[:, dims[n]:].any()
+
+
+@pytest.mark.parametrize("dims,R,B,xdt,sampling,engine", [
+    ((200, 150, 100), 12, 300, "bf16", "euclidean", "auto"),       # deferred CDF flushed first
+    ((90, 80, 70), 6, 100, "f32", "leverage", "simt"),
+    ((40, 36, 30, 28), 8, 77, "bf16", "uniform", "auto"),
+    ((120, 100, 80), 16, 256, "bf16", "euclidean", "persistent"),
+])
+def test_skrp_matches_oracle(cpd, orc, dims, R, B, xdt, sampling, engine):
+    _, X, A0 = make_problem(dims, R, x_dtype=xdt, lognormal_rows=True)
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype=xdt,
+                            sampling=sampling, step="adagrad", seed=31, engine=engine)
+    dec.sgd_iters(20)
+    check_batches(cpd, orc, dec, oracle_xbuf(X), xdt, dims, R, B, sampling, range(len(dims)))
+    dec.close()
+
+
+def test_skrp_full_size_c4(cpd, orc):
+    """The 1000^3 workload, one sampled batch per mode at full size."""
+    w = IN.WORKLOADS["c4_1000cube_bf16"]
+    A = IN.factors(w["dims"], w["R"], w["data_seed"], lognormal_rows=True, device="cuda")
+    X = IN.cp_tensor(A, w["noise"], w["data_seed"], "bf16")
+    A0 = IN.init_factors(w["dims"], w["R"], w["init_seed"])
+    dec = cpd.Decomposition(X, [a.cuda() for a in A0], dims=w["dims"], R=w["R"], B=w["B"], x_dtype="bf16",
+                            sampling="euclidean", step="adagrad", eta=w["eta"], seed=0)
+    xb = oracle_xbuf(X)
+    del X
+    dec.sgd_iters(30)
+    check_batches(cpd, orc, dec, xb, "bf16", w["dims"], w["R"], w["B"], "euclidean", range(3), K=1)
+    dec.close()

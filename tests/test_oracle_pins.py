@@ -647,3 +647,25 @@ def test_grad_row_scale_bounds_every_row(orc):
     g = np.linalg.norm(out["G"], axis=1)
     assert np.all(g <= scale * (1 + 1e-12))
     assert np.all(scale <= 100 * g.max() + 1e-300) and scale.min() > 0
+
+
+def test_sample_batch_is_the_step_batch(orc):
+    """orc_sample_batch with the mode of iteration t draws exactly the batch
+    orc_step records, and its Z and X rows are the KRP rows and fibers of
+    that batch (Eq. (3), Eq. (2) through the explicit unfolding)."""
+    dims, R, B = (7, 6, 5), 3, 9
+    A, X = rand_problem(dims, R, 41, noise=0.2)
+    cfg = orc.Config(dims=dims, R=R, B=B, sampling="euclidean", step="fixed", seed=4)
+    for t in range(5):
+        out = orc.step(cfg, t, X, [a.copy() for a in A])
+        n = out["n"]
+        sb = orc.sample_batch(cfg, n, t, A, X=X)
+        np.testing.assert_array_equal(sb["idx"], out["idx"])
+        np.testing.assert_array_equal(sb["p"], out["p"])
+        Z = explicit_Z(A, n)
+        Xn = unfold(X, n)
+        for f in range(B):
+            tup = [int(v) for v in sb["idx"][f]]
+            j = orc.unfold_col(dims, n, tup)
+            np.testing.assert_allclose(sb["Z"][f], Z[j], rtol=1e-15)
+            np.testing.assert_array_equal(sb["X"][f], Xn[:, j])
