@@ -934,6 +934,7 @@ extern "C" const char *cpd_last_error(void) { return g_err.c_str(); }
 namespace cpd {
 void set_error(const std::string &msg) { g_err = msg; }
 int ctx_engine(const cpd_ctx *c) { return c->engine; }
+int ctx_cluster(const cpd_ctx *c) { return c->engine == kEnginePersistent ? c->pers.cs : 0; }
 }  // namespace cpd
 
 // ---------------------------------------------------------------------------

@@ -5,10 +5,11 @@
 //   1. admits queued requests first-fit while the memory budget and the
 //      concurrency limit allow (cpd_init on a fresh non-blocking stream);
 //   2. steps the lanes: requests of one class (tensor dtype and engine, no
-//      leverage sampling) share a lane whose rounds advance all members with
-//      grouped launches (one gradient and one update launch per iteration
-//      for the whole lane), then start every member's fit; members leave and
-//      join between rounds. Four lanes per class overlap one lane's fits and
+//      leverage sampling; for the persistent engine also the cluster size)
+//      share a lane whose rounds advance all members with grouped launches
+//      (one gradient and one update launch per iteration for the whole
+//      lane, or one launch per round for persistent members), then start
+//      every member's fit; members leave and join between rounds. Four lanes per class overlap one lane's fits and
 //      host work with the others' iterations;
 //   3. steps the requests that cannot be grouped, each on its own stream:
 //      iterations up to its next check and an asynchronous fit, so every
@@ -35,6 +36,7 @@ namespace cpd {
 void set_error(const std::string &msg);
 void destroy_on_home_stream(cpd_ctx *c);
 int ctx_engine(const cpd_ctx *c);
+int ctx_cluster(const cpd_ctx *c);
 }  // namespace cpd
 
 using namespace cpd;
@@ -97,7 +99,7 @@ struct Request {
 // iterations of every member, then every member's asynchronous fit, then an
 // event. Members join and leave between rounds.
 struct Lane {
-    int fbytes = 4, x_dtype = 0, engine = 0;
+    int fbytes = 4, x_dtype = 0, engine = 0, cluster = 0;
     std::vector<std::shared_ptr<Request>> members, joining;
     cpd_group *grp = nullptr;
     cudaStream_t stream = nullptr;
@@ -181,10 +183,12 @@ static void add_iters(cpd_server *srv, const std::shared_ptr<Request> &r, int64_
 static Lane *pick_lane(cpd_server *srv, const std::shared_ptr<Request> &r, int engine)
 {
     const int fbytes = r->cfg.x_dtype == CPD_F64 ? 8 : 4;
+    const int cluster = engine == kEnginePersistent ? ctx_cluster(r->ctx) : 0;
     Lane *best = nullptr;
     int found = 0;
     for (auto &l : srv->lanes) {
-        if (l->fbytes != fbytes || l->x_dtype != r->cfg.x_dtype || l->engine != engine) continue;
+        if (l->fbytes != fbytes || l->x_dtype != r->cfg.x_dtype || l->engine != engine || l->cluster != cluster)
+            continue;
         ++found;
         if (!best || l->members.size() + l->joining.size() < best->members.size() + best->joining.size())
             best = l.get();
@@ -194,6 +198,7 @@ static Lane *pick_lane(cpd_server *srv, const std::shared_ptr<Request> &r, int e
         l->fbytes = fbytes;
         l->x_dtype = r->cfg.x_dtype;
         l->engine = engine;
+        l->cluster = cluster;
         if (cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
         if (cudaEventCreateWithFlags(&l->done, cudaEventDisableTiming) != cudaSuccess) {
             cudaStreamDestroy(l->stream);
@@ -302,7 +307,7 @@ static void worker_loop(cpd_server *srv)
             }
             const int engine = ctx_engine(r->ctx);
             const bool groupable = !srv->cfg.no_grouping && r->cfg.sampling != CPD_SAMPLE_LEVERAGE &&
-                                   (engine == kEngineSimt || engine == kEngineTensor);
+                                   (engine == kEngineSimt || engine == kEngineTensor || engine == kEnginePersistent);
             Lane *lane = groupable ? pick_lane(srv, r, engine) : nullptr;
             if (lane) {
                 lane->joining.push_back(r);
