@@ -158,6 +158,10 @@ def make_inputs(w: dict, rank: int, device: str):
     X = IN.cp_tensor(A, w["noise"], w["data_seed"] + rank, w["x_dtype"])
     A0 = IN.init_factors(w["dims"], w["R"], w["init_seed"] + rank,
                          dtype=torch.float64 if w["x_dtype"] == "f64" else torch.float32)
+    if X.is_cuda:
+        # X is written on torch's current stream; cpd_init reads it on the
+        # side stream the context is built on, which is not ordered after it
+        torch.cuda.synchronize()
     return X, A0
 
 
@@ -316,37 +320,43 @@ def _event_ms(stream, fn) -> float:
 
 
 def gather_per_mode(C, X, A0: list, w: dict, dev: str, stream, peak: float, K: int = 32, reps: int = 10) -> dict:
-    """The fiber gather in bulk, per mode: cpd_skrp materialises K = 32
-    mini-batches of one mode (Alg. 3 + Alg. 1: the draws, p_f, the sampled KRP
-    rows and the K B sampled fibers) in one launch over every SM, the fibers
-    moving by bulk copies. Bytes per launch: the K B I_n elem fiber bytes read
-    (the useful gather) and as many written; the copy-equivalent rate (read +
-    write) is the one comparable with the measured copy peak. CUDA events over
-    `reps` launches with fresh draws each (batches t0 + b), on the launching
-    stream; the replicas (6 GB) are far larger than L2."""
+    """The fiber gather in bulk, per mode: cpd_skrp draws K = 32 mini-batches
+    of one mode (Alg. 3) and gathers their K B fibers (Alg. 1) in one launch
+    over every SM, (a) writing the fibers only and (b) also p_f, the
+    multi-indices and the sampled KRP rows. The fibers are read once and
+    written once, like the measured copy peak, so `frac` = (bytes read +
+    bytes written) / time / peak; `gather_gbs` counts the useful fiber bytes
+    (K B I_n elem) alone. CUDA events over `reps` launches with fresh draws
+    each, on the launching stream; the replicas are far larger than L2."""
     kw = cfg_kwargs(w, 0, "auto")
     with torch.cuda.stream(stream):
         dec = C.Decomposition(X, [a.to(dev) for a in A0], stream=stream, **kw)
     esize = {"bf16": 2, "f32": 4, "f64": 8}[w["x_dtype"]]
     tdt = {"bf16": torch.bfloat16, "f32": torch.float32}[w["x_dtype"]]
     N, B, R = len(w["dims"]), w["B"], w["R"]
-    out = {"K": K, "B": B, "launches_timed": reps, "kernel": "k_skrp", "modes": []}
+    out = {"K": K, "B": B, "launches_timed": reps, "kernel": "k_skrp",
+           "peak": "hbm_gbs of MEASURED_PEAKS.json (a copy: bytes read + bytes written)", "modes": []}
     idx = torch.empty(K * B, N, dtype=torch.int32, device=dev)
     p = torch.empty(K * B, dtype=torch.float64, device=dev)
     Z = torch.empty(K * B, R, dtype=torch.float32, device=dev)
+    side = K * B * (N * 4 + 8 + R * 4)          # idx, p and Z written
+    t0 = K
     for n, In in enumerate(w["dims"]):
         ld = (In + 7) // 8 * 8
         Xs = torch.empty(K * B * ld, dtype=tdt, device=dev)
-        C.cpd_skrp(dec.ctx, n, 0, K, idx, p, Z, Xs, stream)
-        ms = _event_ms(stream, lambda: [C.cpd_skrp(dec.ctx, n, K * (1 + r), K, idx, p, Z, Xs, stream)
-                                        for r in range(reps)]) / reps
-        useful = K * B * In * esize
-        moved = 2 * K * B * ld * esize
-        out["modes"].append({"mode": n, "I_n": In, "useful_bytes_per_launch": useful, "ms_per_launch": ms,
-                             "gather_gbs": useful / (ms * 1e-3) / 1e9,
-                             "gather_frac": useful / (ms * 1e-3) / 1e9 / peak,
-                             "copy_equivalent_gbs": moved / (ms * 1e-3) / 1e9,
-                             "copy_equivalent_frac": moved / (ms * 1e-3) / 1e9 / peak})
+        fib = K * B * ld * esize                  # fiber bytes read (= written)
+        row = {"mode": n, "I_n": In, "useful_bytes_per_launch": K * B * In * esize}
+        # fibers only (the draws and the gather), then every output of Alg. 3 + Alg. 1
+        for name, outs, moved in (("fibers_only", (None, None, None), 2 * fib), ("all_outputs", (idx, p, Z), 2 * fib + side)):
+            C.cpd_skrp(dec.ctx, n, 0, K, *outs, Xs, stream)
+            ms = _event_ms(stream, lambda: [C.cpd_skrp(dec.ctx, n, t0 + K * r, K, *outs, Xs, stream)
+                                            for r in range(reps)]) / reps
+            t0 += K * reps
+            row[name] = {"ms_per_launch": ms, "bytes_moved_per_launch": moved,
+                         "gather_gbs": row["useful_bytes_per_launch"] / (ms * 1e-3) / 1e9,
+                         "copy_equivalent_gbs": moved / (ms * 1e-3) / 1e9,
+                         "frac": moved / (ms * 1e-3) / 1e9 / peak}
+        out["modes"].append(row)
         del Xs
     dec.close()
     return out

@@ -160,9 +160,11 @@ cpd_status cpd_sgd_iters(cpd_ctx *ctx, int64_t iters, void *stream);
  *  X   : K*B fibers of the mode-n unfolding (Eq. (2)), fiber f of batch b at
  *        element (b*B + f) * ld_n, ld_n = I_n rounded up to 8 (the padding
  *        entries are 0), in the tensor's storage type.
- * The fibers move by bulk copies over every SM: this is the sampled gather
- * on its own, the bandwidth measure of the access pattern. Float factors
- * only (F32 or BF16 tensors); I_n times the element size at most about 5 KB.
+ * Every SM takes warp blocks of 32 output fibers and streams them in the
+ * widest unit (16, 8, 4 or 2 bytes) that divides the fiber length and the
+ * addresses of X and the replica: this is the sampled gather on its own, the
+ * bandwidth measure of the access pattern. Float factors only (F32 or BF16
+ * tensors); X needs only the element alignment of its type.
  * Asynchronous on `stream`. Errors: CPD_EINVAL, CPD_ECUDA.
  */
 cpd_status cpd_skrp(cpd_ctx *ctx, int32_t n, int64_t t0, int32_t K, int32_t *idx, double *p, float *Z, void *X,

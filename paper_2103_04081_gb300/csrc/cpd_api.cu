@@ -599,8 +599,6 @@ extern "C" cpd_status cpd_skrp(cpd_ctx *c, int32_t n, int64_t t0, int32_t K, int
     if (c->fbytes != 4) return fail(CPD_EINVAL, "cpd_skrp takes float factors (F32 or BF16 tensors)");
     if (n < 0 || n >= c->cfg.N) return fail(CPD_EINVAL, "mode out of range");
     if ((double)K * c->cfg.B > 2.0e9) return fail(CPD_EINVAL, "K B too large");
-    if (skrp_smem_bytes(c->Pf, n, c->xbytes) > 200 * 1024)
-        return fail(CPD_EINVAL, "mode too long for the fiber staging (I_n * element size above about 5 KB)");
     cudaStream_t s = (cudaStream_t)stream;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);

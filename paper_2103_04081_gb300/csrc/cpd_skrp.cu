@@ -5,12 +5,18 @@
 // words of iteration t0 + b with the mode fixed to n, from the context's
 // current per-factor distributions.
 //
-// This is the gather on its own, spread over every SM: each CTA takes blocks
-// of up to 16 fibers; a warp per mode draws them (CDFs staged in shared
-// memory), one thread per fiber forms the column and p_f, the CTA forms the
-// KRP rows, and the fibers move global -> shared -> global by bulk copies
-// (the tensor memory accelerator), double-buffered so a block's stores drain
-// while the next block's fibers load.
+// This is the gather on its own, spread over every SM. The unit of work is a
+// warp block of 32 consecutive output fibers, owned by one warp from the
+// draws to the last store, so warps never wait on one another: the lanes
+// draw their fibers' indices (CDFs staged in shared memory once per CTA),
+// form the column and p_f, the warp writes the multi-indices and the KRP rows
+// (coalesced), then streams the 32 fibers global -> registers -> global in
+// the widest unit the alignment allows, kSkUnroll units per lane in flight.
+// With two CTAs (16 warps) per SM the SM holds 16 x 32 x 8 x 16 B = 64 KB of
+// loads in flight, about what an SM needs to draw its share of HBM bandwidth
+// at the loaded memory latency (the unrolled copy needs 124 registers, so a
+// third CTA would spill); a per-CTA staged pipeline with CTA-wide barriers
+// kept the loads in a serial chain behind the draws.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -19,14 +25,14 @@
 
 #include "cpd_device.cuh"
 #include "cpd_internal.h"
-#include "cpd_tcgen05.cuh"
 
 namespace cpd {
 
 namespace {
 
-constexpr int kSkFib = 16;               // fibers per block
+constexpr int kSkWarps = kThreads / 32;
 constexpr long long kSkStageCap = 4096;  // staged CDF entries (modes != n)
+constexpr int kSkUnroll = 8;             // copy units in flight per lane
 
 struct SkrpArgs {
     int n, K;
@@ -35,71 +41,103 @@ struct SkrpArgs {
     double *p;       // K B
     float *Z;        // K B x R
     void *X;         // K B x ld_n elements
-    size_t stage_bytes;   // one fiber stage: kSkFib * ld_n * esize
-    int esize;
+    long long units; // copy units per fiber (ld_n * esize / unit)
+    int unit;        // copy unit in bytes: 16, 8, 4 or 2
 };
 
-__device__ __forceinline__ void bulk_s2g_grp(void *dst, uint32_t src, uint32_t bytes)
+// The 32 fibers of one warp block: fiber u's units [0, units) start at
+// rep + jc[u] * units; the output is contiguous. Lane-strided over the flat
+// unit index, the (fiber, offset) pair carried along instead of divided out.
+// units < 2^26 (the fiber is under 1 GB), so a warp block's flat index fits
+// 32 bits.
+template <class U>
+__device__ __forceinline__ void copy_fibers(const U *__restrict__ rep, const long long *jc, int nf, int units,
+                                            U *__restrict__ dst, int lane)
 {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(src), "r"(bytes)
-                 : "memory");
-    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+    const int total = nf * units;
+    int u = 0, r = lane;
+    while (r >= units) {
+        r -= units;
+        ++u;
+    }
+    for (int base = 0; base < total; base += 32 * kSkUnroll) {
+        U v[kSkUnroll];
+#pragma unroll
+        for (int j = 0; j < kSkUnroll; ++j) {
+            if (base + j * 32 + lane < total) v[j] = __ldcs(rep + jc[u] * units + r);
+            r += 32;
+            while (r >= units) {
+                r -= units;
+                ++u;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kSkUnroll; ++j) {
+            const int c = base + j * 32 + lane;
+            if (c < total) __stcs(dst + c, v[j]);
+        }
+    }
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads) k_skrp(const Problem<float> P, const SkrpArgs s)
+// kGlobal: a mode's CDFs too long to stage are searched in global memory
+// (the warp-cooperative 32-way search, which needs its own 64 registers).
+template <bool kGlobal>
+__global__ void __launch_bounds__(kThreads, 2) k_skrp(const Problem<float> P, const SkrpArgs s)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ int sidx[kSkFib * kMaxModes];
-    __shared__ long long jcol[kSkFib];
-    __shared__ __align__(8) unsigned long long bars[2];
+    extern __shared__ __align__(16) unsigned long long cdfs[];
+    __shared__ int sidx_all[kSkWarps][32 * kMaxModes];
+    __shared__ long long jc_all[kSkWarps][32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = P.N, R = P.R, n = s.n;
     const long long B = P.B, total = (long long)s.K * B;
-    const long long ld = P.ld[n];
-    const uint32_t fbytes = (uint32_t)(ld * s.esize);
+    __shared__ long long off[kMaxModes];
+    __shared__ int ks[kMaxModes];   // the modes k != n, ascending
+    int *sidx = sidx_all[warp];
+    long long *jc = jc_all[warp];
     // staged CDFs of the modes k != n (ascending), when they fit
-    long long need = 0, off[kMaxModes];
+    long long need = 0;
     for (int k = 0; k < N; ++k) {
-        off[k] = need;
+        if (tid == 0) {
+            off[k] = need;
+            ks[k - (k > n)] = k;   // k == n writes slot n, which k = n + 1 overwrites
+        }
         if (k != n) need += P.dims[k];
     }
-    const bool staged = P.sampling != CPD_SAMPLE_UNIFORM && need <= kSkStageCap;
-    unsigned long long *cdfs = reinterpret_cast<unsigned long long *>(smem);
-    unsigned char *stage0 = smem + (staged ? (size_t)kSkStageCap * 8 : 0);
-    if (staged)
+    const bool staged = P.sampling != CPD_SAMPLE_UNIFORM && !kGlobal;
+    __syncthreads();
+    if (staged) {
         for (int k = 0; k < N; ++k)
             if (k != n)
                 for (long long i = tid; i < P.dims[k]; i += blockDim.x) cdfs[off[k] + i] = __ldcg(P.cdf[k] + i);
-    if (tid == 0) {
-        mbar_init(smem_u32(&bars[0]), 1);
-        mbar_init(smem_u32(&bars[1]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        __syncthreads();
     }
-    __syncthreads();
-    const char *rep = reinterpret_cast<const char *>(P.rep[n]);
-    unsigned uses[2] = {0u, 0u};
-    int local = 0;
-    const long long nblk = (total + kSkFib - 1) / kSkFib;
-    for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x, ++local) {
-        const long long fg0 = blk * kSkFib;
-        const int nfib = (int)((total - fg0) < kSkFib ? total - fg0 : kSkFib);
-        // draws: warp w takes modes w, w + 8, ...; lane = fiber of the block
-        for (int k = warp; k < N; k += kThreads / 32) {
-            const bool act = lane < nfib;
-            const long long fg = fg0 + (act ? lane : 0);
-            const long long b = fg / B, f = fg % B;
+    const long long nwb = (total + 31) / 32;
+    for (long long wb = (long long)blockIdx.x * kSkWarps + warp; wb < nwb; wb += (long long)gridDim.x * kSkWarps) {
+        const long long fg0 = wb * 32;
+        const int nf = (int)((total - fg0) < 32 ? total - fg0 : 32);
+        const bool act = lane < nf;
+        const long long fg = fg0 + (act ? lane : 0);
+        const long long b = fg / B, f = fg % B;
+        // draws (Alg. 3): one Philox block per group of four modes
+        U64x4 words{};
+        for (int k = 0; k < N; ++k) {
+            if ((k & 3) == 0)
+                words = philox4x64_10((unsigned long long)(s.t0 + b), (unsigned long long)f,
+                                      (unsigned long long)(k >> 2), 0ULL, P.seed, 0ULL);
             if (k == n) {
                 if (act) sidx[lane * N + k] = -1;
                 continue;
             }
             const long long Ik = P.dims[k];
-            const unsigned long long x = act ? fiber_word(P.seed, s.t0 + b, f, k) : 0ULL;
+            const int q = k & 3;
+            const unsigned long long w = q == 0 ? words.v[0] : q == 1 ? words.v[1] : q == 2 ? words.v[2] : words.v[3];
+            const unsigned long long x = act ? w : 0ULL;
             long long i;
             if (P.sampling == CPD_SAMPLE_UNIFORM) {
                 i = (long long)__umul64hi(x, (unsigned long long)Ik);
-            } else if (staged) {
+            } else if (!kGlobal) {
                 const unsigned long long *c = cdfs + off[k];
                 i = warp_search_staged(c, Ik, __umul64hi(x, c[Ik - 1]), act);
             } else {
@@ -108,67 +146,104 @@ __global__ void __launch_bounds__(kThreads) k_skrp(const Problem<float> P, const
             }
             if (act) sidx[lane * N + k] = (int)i;
         }
-        __syncthreads();
-        // column (Eq. (2)), p_f (Eq. (10), FP64), the multi-index
-        if (tid < nfib) {
-            const int *row = sidx + tid * N;
+        __syncwarp();
+        // column (Eq. (2)) and p_f (Eq. (10), FP64), one lane per fiber
+        if (act) {
+            const int *row = sidx + lane * N;
             long long j = 0, Jp = 1;
             for (int k = 0; k < N; ++k) {
                 if (k == n) continue;
                 j += (long long)row[k] * Jp;
                 Jp *= P.dims[k];
             }
-            jcol[tid] = j;
-            const long long fg = fg0 + tid;
-            if (s.p) s.p[fg] = fiber_prob(P, n, row);
-            if (s.idx)
-                for (int k = 0; k < N; ++k) s.idx[fg * N + k] = row[k];
+            jc[lane] = j;
+            if (s.p) s.p[fg] = fiber_prob_staged(P, n, row, staged ? cdfs : nullptr);
         }
-        // sampled KRP rows (Eq. (3)), factor rows ascending in k
+        __syncwarp();
+        // the multi-indices, contiguous for the warp block
+        if (s.idx)
+            for (int e = lane; e < nf * N; e += 32) s.idx[fg0 * N + e] = sidx[e];
+        // sampled KRP rows (Eq. (3)), factor rows multiplied in ascending k;
+        // lane-strided over the warp block's nf x R entries, kSkUnroll at a
+        // time, two factors at a time so that 2 kSkUnroll loads are in flight
         if (s.Z) {
-            for (int e = tid; e < nfib * R; e += blockDim.x) {
-                const int fl = e / R, r = e % R;
-                float z = 1.f;
-                for (int k = 0; k < N; ++k) {
-                    if (k == n) continue;
-                    z = z * P.A[k][(long long)sidx[fl * N + k] * R + r];
+            const int nk = N - 1;
+            const int tot = nf * R;
+            int fl = 0, r = lane;
+            while (r >= R) {
+                r -= R;
+                ++fl;
+            }
+            for (int base = 0; base < tot; base += 32 * kSkUnroll) {
+                float z[kSkUnroll];
+                int fe[kSkUnroll], re[kSkUnroll];
+#pragma unroll
+                for (int j = 0; j < kSkUnroll; ++j) {
+                    z[j] = 1.f;
+                    fe[j] = fl;
+                    re[j] = r;
+                    r += 32;
+                    while (r >= R) {
+                        r -= R;
+                        ++fl;
+                    }
                 }
-                s.Z[(fg0 + fl) * R + r] = z;
+                for (int q = 0; q < nk; q += 2) {
+                    const int ka = ks[q], kb = q + 1 < nk ? ks[q + 1] : -1;
+                    float va[kSkUnroll], vb[kSkUnroll];
+#pragma unroll
+                    for (int j = 0; j < kSkUnroll; ++j) {
+                        const bool in = base + j * 32 + lane < tot;
+                        va[j] = in ? __ldg(P.A[ka] + (long long)sidx[fe[j] * N + ka] * R + re[j]) : 1.f;
+                        vb[j] = (in && kb >= 0) ? __ldg(P.A[kb] + (long long)sidx[fe[j] * N + kb] * R + re[j]) : 1.f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < kSkUnroll; ++j) {
+                        z[j] = z[j] * va[j];
+                        if (kb >= 0) z[j] = z[j] * vb[j];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kSkUnroll; ++j) {
+                    const int c = base + j * 32 + lane;
+                    if (c < tot) s.Z[fg0 * R + c] = z[j];
+                }
             }
         }
-        __syncthreads();
-        // fibers: global -> shared (one bulk copy per fiber) -> global
-        if (s.X && warp == 0) {
-            const int st = local & 1;
-            unsigned char *sb = stage0 + (size_t)st * s.stage_bytes;
-            const uint32_t bar = smem_u32(&bars[st]);
-            // this lane's store from this stage two blocks ago has read its slot
-            asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
-            if (lane == 0) mbar_expect_tx(bar, (uint32_t)nfib * fbytes);
-            __syncwarp();
-            if (lane < nfib)
-                bulk_g2s(smem_u32(sb + (size_t)lane * fbytes), rep + jcol[lane] * ld * s.esize, fbytes, bar);
-            bool ok = mbar_wait_bounded(bar, uses[st] & 1);
-            ++uses[st];
-            if (!ok) {
-                if (lane == 0) atomicOr(P.status, kStTimeout);
-            } else if (lane < nfib) {
-                bulk_s2g_grp(static_cast<char *>(s.X) + (size_t)(fg0 + lane) * fbytes,
-                             smem_u32(sb + (size_t)lane * fbytes), fbytes);
+        // the sampled fibers
+        if (s.X) {
+            const int ub = (int)s.units;
+            char *out = static_cast<char *>(s.X) + (size_t)fg0 * ub * s.unit;
+            const char *rep = reinterpret_cast<const char *>(P.rep[n]);
+            switch (s.unit) {
+            case 16:
+                copy_fibers(reinterpret_cast<const uint4 *>(rep), jc, nf, ub, reinterpret_cast<uint4 *>(out), lane);
+                break;
+            case 8:
+                copy_fibers(reinterpret_cast<const uint2 *>(rep), jc, nf, ub, reinterpret_cast<uint2 *>(out), lane);
+                break;
+            case 4:
+                copy_fibers(reinterpret_cast<const unsigned *>(rep), jc, nf, ub, reinterpret_cast<unsigned *>(out),
+                            lane);
+                break;
+            default:
+                copy_fibers(reinterpret_cast<const unsigned short *>(rep), jc, nf, ub,
+                            reinterpret_cast<unsigned short *>(out), lane);
+                break;
             }
         }
+        __syncwarp();   // sidx / jc are rewritten by the next warp block
     }
-    // every store has completed before the CTA's shared memory goes away
-    if (warp == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
 }
 
 size_t skrp_smem_bytes(const Problem<float> &P, int n, int esize)
 {
+    (void)esize;
     long long need = 0;
     for (int k = 0; k < P.N; ++k)
         if (k != n) need += P.dims[k];
     const bool staged = P.sampling != CPD_SAMPLE_UNIFORM && need <= kSkStageCap;
-    return (staged ? (size_t)kSkStageCap * 8 : 0) + 2 * (size_t)kSkFib * P.ld[n] * esize;
+    return staged ? (size_t)need * 8 : 0;
 }
 
 cudaError_t launch_skrp(const Problem<float> &P, int n, long long t0, int K, int *idx, double *p, float *Z, void *X,
@@ -182,26 +257,28 @@ cudaError_t launch_skrp(const Problem<float> &P, int n, long long t0, int K, int
     a.p = p;
     a.Z = Z;
     a.X = X;
-    a.esize = esize;
-    a.stage_bytes = (size_t)kSkFib * P.ld[n] * esize;
+    // the widest unit dividing the fiber length and both base addresses
+    // (replica fibers start at multiples of ld_n * esize bytes)
+    const unsigned long long fb = (unsigned long long)P.ld[n] * esize;
+    const unsigned long long mix = fb | (unsigned long long)(uintptr_t)X | (unsigned long long)(uintptr_t)P.rep[n];
+    a.unit = (mix % 16 == 0) ? 16 : (mix % 8 == 0) ? 8 : (mix % 4 == 0) ? 4 : 2;
+    a.units = (long long)(fb / a.unit);
+    // staged CDFs take at most kSkStageCap * 8 = 32 KB: no opt-in needed
     const size_t smem = skrp_smem_bytes(P, n, esize);
-    static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_skrp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return e;
-        }
-        attr = smem;
-    }
+    const bool global = P.sampling != CPD_SAMPLE_UNIFORM && smem == 0;
+    const void *fn = global ? (const void *)k_skrp<true> : (const void *)k_skrp<false>;
     int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_skrp, kThreads, smem) != cudaSuccess || per_sm < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
-    const long long nblk = ((long long)K * P.B + kSkFib - 1) / kSkFib;
-    const int grid = (int)std::min<long long>(nblk, (long long)per_sm * sm_count);
-    k_skrp<<<grid, kThreads, smem, stream>>>(P, a);
+    const long long nwb = ((long long)K * P.B + 31) / 32;
+    const long long want = (nwb + kSkWarps - 1) / kSkWarps;
+    const int grid = (int)std::min<long long>(want, (long long)per_sm * sm_count);
+    if (global)
+        k_skrp<true><<<grid, kThreads, smem, stream>>>(P, a);
+    else
+        k_skrp<false><<<grid, kThreads, smem, stream>>>(P, a);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ def cpd():
     return C
 
 
-def check_batches(cpd, orc, dec, xb, x_dtype, dims, R, B, sampling, modes, K=3, t0=1000):
+def check_batches(cpd, orc, dec, xb, x_dtype, dims, R, B, sampling, modes, K=3, t0=1000, x_offset=0):
     N = len(dims)
     A = [a.double().numpy() for a in dec.factors()]
     ocfg = orc.Config(dims=tuple(dims), R=R, B=B, sampling=sampling, step="adagrad", x_dtype=x_dtype,
@@ -38,7 +38,9 @@ def check_batches(cpd, orc, dec, xb, x_dtype, dims, R, B, sampling, modes, K=3, 
         idx = torch.empty(K * B, N, dtype=torch.int32, device="cuda")
         p = torch.empty(K * B, dtype=torch.float64, device="cuda")
         Z = torch.empty(K * B, R, dtype=torch.float32, device="cuda")
-        X = torch.empty(K * B * ld, dtype=tdt, device="cuda")
+        # x_offset elements into the allocation: the copy falls back to a
+        # narrower unit when X is not 16-byte aligned
+        X = torch.empty(K * B * ld + x_offset, dtype=tdt, device="cuda")[x_offset:]
         cpd.cpd_skrp(dec.ctx, n, t0, K, idx, p, Z, X)
         torch.cuda.synchronize()
         idx, p, Z = idx.cpu().numpy(), p.cpu().numpy(), Z.cpu().double().numpy()
@@ -66,6 +68,33 @@ def test_skrp_matches_oracle(cpd, orc, dims, R, B, xdt, sampling, engine):
                             sampling=sampling, step="adagrad", seed=31, engine=engine)
     dec.sgd_iters(20)
     check_batches(cpd, orc, dec, oracle_xbuf(X), xdt, dims, R, B, sampling, range(len(dims)))
+    dec.close()
+
+
+@pytest.mark.parametrize("xdt,x_offset", [("bf16", 1), ("bf16", 2), ("bf16", 4), ("f32", 1), ("f32", 2)])
+def test_skrp_unaligned_output(cpd, orc, xdt, x_offset):
+    """X at 2, 4 or 8 bytes past a 16-byte boundary: 2-, 4- and 8-byte units."""
+    dims, R, B = (50, 43, 37), 5, 70
+    _, X, A0 = make_problem(dims, R, x_dtype=xdt, lognormal_rows=True)
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype=xdt,
+                            sampling="euclidean", step="adagrad", seed=5)
+    dec.sgd_iters(7)
+    check_batches(cpd, orc, dec, oracle_xbuf(X), xdt, dims, R, B, "euclidean", range(3), K=2,
+                  x_offset=x_offset)
+    dec.close()
+
+
+def test_skrp_long_modes_global_cdf(cpd, orc):
+    """Modes whose CDFs exceed the 4096-entry shared-memory stage: mode 0's
+    draws search the CDFs of modes 1 and 2 (4500 entries) in global memory."""
+    dims, R, B = (20, 2500, 2000), 4, 500
+    _, X, A0 = make_problem(dims, R, x_dtype="bf16", lognormal_rows=True, device="cuda")
+    dec = cpd.Decomposition(X, [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype="bf16",
+                            sampling="euclidean", step="adagrad", seed=9)
+    xb = oracle_xbuf(X)
+    del X
+    dec.sgd_iters(5)
+    check_batches(cpd, orc, dec, xb, "bf16", dims, R, B, "euclidean", (0, 1), K=2)
     dec.close()
 
 
