@@ -308,6 +308,30 @@ def error_vs_oracle(C, dev: str, stream, kw: dict, steps_tf: int = 3, free_iters
     return res
 
 
+def fit_pass(C, dec, w: dict, stream, reps: int = 5) -> dict:
+    """The stop check of Sec. 5.2 (one pass over the mode-1 replica): mean
+    device time of cpd_fit_start's launches (operand preparation, the pass,
+    the fold) over `reps` passes, CUDA events on the launching stream, and the
+    replica bytes it reads per pass against the measured copy peak."""
+    esize = {"bf16": 2, "f32": 4, "f64": 8}[w["x_dtype"]]
+    I0 = w["dims"][0]
+    J = 1
+    for d in w["dims"][1:]:
+        J *= d
+    rbytes = J * ((I0 + 7) // 8 * 8) * esize
+    C.cpd_fit_start(dec.ctx, stream)
+    while C.cpd_fit_poll(dec.ctx) is None:
+        time.sleep(1e-4)
+    ms = _event_ms(stream, lambda: [C.cpd_fit_start(dec.ctx, stream) for _ in range(reps)]) / reps
+    while C.cpd_fit_poll(dec.ctx) is None:
+        time.sleep(1e-4)
+    peaks, _ = measured_peaks()
+    gbs = rbytes / (ms * 1e-3) / 1e9
+    return {"kernel": "k_fit_tc" if dec.describe().get("fit_pass") == "tensor" else "k_fit",
+            "ms_per_pass": ms, "replica_bytes_read": rbytes, "gbs": gbs, "frac": gbs / peaks["hbm_gbs"],
+            "note": "read-only pass, against the copy peak (read + write)"}
+
+
 def _event_ms(stream, fn) -> float:
     """Device time of fn's work on `stream` (CUDA events on that stream)."""
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -559,6 +583,7 @@ def main() -> None:
                          "outside the timed region, and the fastest is used)")
     ap.add_argument("--no-gather-legs", action="store_true", help="skip the bulk gather and batched-form legs")
     ap.add_argument("--only-gather", action="store_true", help="run only the bulk gather leg (--steps launches per mode)")
+    ap.add_argument("--only-fit", action="store_true", help="run only the stop-check pass (--steps passes)")
     ap.add_argument("--batch-g", type=int, default=15, help="decompositions in the batched-form leg")
     ap.add_argument("--batch-cs", type=int, default=8, help="cluster size of the batched-form leg")
     ap.add_argument("--batch-iters", type=int, default=1000)
@@ -583,6 +608,14 @@ def main() -> None:
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     X, A0 = make_inputs(w, rank, dev)
+    if args.only_fit:      # the stop-check pass alone (e.g. for a counter capture)
+        kwf = cfg_kwargs(w, rank, "auto")
+        with torch.cuda.stream(stream0 := torch.cuda.Stream()):
+            decf = C.Decomposition(X, [a.to(dev) for a in A0], stream=stream0, **kwf)
+        decf.sgd_iters(20, stream0)
+        print(json.dumps({"fit_pass": fit_pass(C, decf, w, stream0, reps=args.steps)}), flush=True)
+        decf.close()
+        return
     if args.only_gather:   # the bulk gather leg alone (e.g. for a counter capture)
         peaks, _ = measured_peaks()
         print(json.dumps({"gather_per_mode": gather_per_mode(C, X, A0, w, dev, torch.cuda.Stream(),
@@ -635,6 +668,7 @@ def main() -> None:
     nlaunch, grad_ms, upd_ms = C.cpd_profile_read(dec.ctx, stream)
     C.cpd_profile(dec.ctx, False)
     fit, tol = dec.fit(stream)
+    fit_leg = fit_pass(C, dec, w, stream)
     dec.close()
 
     iters_per_s = whole_job_rate(world, args.steps, ms)
@@ -685,7 +719,7 @@ def main() -> None:
                      "timed_launches": nlaunch, "peak_source": src + " (hbm_gbs, of " + src + ")",
                      "update_mean_ms": upd_ms},
         "clocks": clocks, "gpu_launches": int(round(launches_per_iter * args.steps)),
-        "e2e": e2e, "final_tol": tol, "launch": desc,
+        "e2e": e2e, "final_tol": tol, "launch": desc, "fit_pass": fit_leg,
     }
     if tuned:
         line["autotuned"] = tuned

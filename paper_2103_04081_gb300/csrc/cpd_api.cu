@@ -56,6 +56,8 @@ struct cpd_ctx {
     int grid_grad = 0, grid_upd = 0;
     size_t smem_grad = 0;
     double *fit_partials = nullptr, *fit_out = nullptr;
+    void *fit_tc = nullptr;  // scratch of the tensor-core stop check (BF16 tensors), or null
+    int sm_count = 152;
     double xnorm2 = 0.0;
     int64_t imax = 0;
     // graph replay: graph[q] runs kGraphChunk >> q iterations
@@ -285,6 +287,7 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     }
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    c->sm_count = sm_count;
     if (g.engine == 0) {
         int64_t imax = 0;
         for (int k = 0; k < g.N; ++k) imax = std::max<int64_t>(imax, g.dims[k]);
@@ -383,6 +386,12 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     CK(dmalloc(c, &p, 16 * sizeof(unsigned)));  P.counters = (unsigned *)p;
     CK(dmalloc(c, &p, (size_t)fit_blocks() * sizeof(double)));  c->fit_partials = (double *)p;
     CK(dmalloc(c, &p, sizeof(double)));  c->fit_out = (double *)p;
+    if constexpr (sizeof(T) == 4) {
+        if (fit_tc_supported(P)) {
+            CK(dmalloc(c, &p, fit_tc_scratch_bytes(P)));
+            c->fit_tc = p;
+        }
+    }
     CK(cudaMemsetAsync(P.t_dev, 0, sizeof(long long), s));
     CK(cudaMemsetAsync(P.n_last, 0xff, sizeof(int), s));
     CK(cudaMemsetAsync(P.status, 0, sizeof(int), s));
@@ -659,13 +668,19 @@ extern "C" cpd_status cpd_sync(cpd_ctx *c, void *stream)
     return read_status(c, (cudaStream_t)stream);
 }
 
+// Tol's numerator into fit_out: on the tensor cores for BF16 tensors (float
+// factors, R <= 64), else on CUDA cores.
+static cudaError_t launch_tol(cpd_ctx *c, cudaStream_t s)
+{
+    if (c->fit_tc) return launch_fit_tc(c->Pf, c->fit_tc, c->fit_partials, c->sm_count, c->fit_out, s);
+    return c->with_problem([&](auto &P) { return launch_fit(P, c->fit_partials, fit_blocks(), c->fit_out, s, 0); });
+}
+
 extern "C" cpd_status cpd_fit(cpd_ctx *c, double *fit, double *tol, void *stream)
 {
     if (!c) return fail(CPD_EINVAL, "NULL context");
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = c->with_problem([&](auto &P) {
-        return launch_fit(P, c->fit_partials, fit_blocks(), c->fit_out, s, 0);
-    });
+    cudaError_t e = launch_tol(c, s);
     if (e != cudaSuccess) return cuda_fail(e, "fit launch");
     double res = 0.0;
     CK(cudaMemcpyAsync(&res, c->fit_out, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -684,9 +699,7 @@ extern "C" cpd_status cpd_fit_start(cpd_ctx *c, void *stream)
         CK(cudaEventCreateWithFlags(&c->fit_event, cudaEventDisableTiming));
         CK(cudaMallocHost((void **)&c->fit_host, 2 * sizeof(double)));   // residual, status word
     }
-    cudaError_t e = c->with_problem([&](auto &P) {
-        return launch_fit(P, c->fit_partials, fit_blocks(), c->fit_out, s, 0);
-    });
+    cudaError_t e = launch_tol(c, s);
     if (e != cudaSuccess) return cuda_fail(e, "fit launch");
     CK(cudaMemcpyAsync(c->fit_host, c->fit_out, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->fit_host + 1, c->fbytes == 8 ? c->Pd.status : c->Pf.status, sizeof(int),
@@ -895,14 +908,15 @@ extern "C" cpd_status cpd_describe(cpd_ctx *c, char *buf, size_t len)
                   "{\"engine\": \"%s\", \"rows_per_cta\": %d, \"fibers_per_cta\": %d, \"fiber_groups\": %d, "
                   "\"grad_grid\": %d, \"update_grid\": %d, \"grad_smem\": %zu, \"graph_chunk\": %d, "
                   "\"cluster\": %d, \"max_clusters\": %d, \"deferred_cdf\": %d, "
-                  "\"xnorm2\": %.17g}",
+                  "\"fit_pass\": \"%s\", \"xnorm2\": %.17g}",
                   c->engine == kEnginePersistent       ? "persistent"
                   : c->engine == kEngineTensorCluster ? "cluster"
                   : c->engine == kEngineTensor        ? "tensor"
                                                       : "simt",
                   rb, fb, pf, c->grid_grad, c->grid_upd,
                   c->smem_grad, kGraphChunk, c->fbytes == 8 ? 1 : c->Pf.cs, c->max_clusters,
-                  c->fbytes == 8 ? c->Pd.defer_cdf : c->Pf.defer_cdf, c->xnorm2);
+                  c->fbytes == 8 ? c->Pd.defer_cdf : c->Pf.defer_cdf, c->fit_tc ? "tensor" : "cuda_cores",
+                  c->xnorm2);
     return CPD_OK;
 }
 

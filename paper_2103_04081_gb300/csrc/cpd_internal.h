@@ -14,6 +14,7 @@
 //            launches replay correctly.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -147,6 +148,20 @@ int tcc_max_clusters(const Problem<float> &P);
 long long tc_stage_cap(const Problem<float> &P);
 long long tcc_stage_cap(const Problem<float> &P);
 constexpr long long kSimtStageCap = 2048;
+
+// Tensor-core stop check (cpd_fit_tc.cu): BF16 tensors, float factors, R <= 64.
+struct FitTcArgs {
+    __nv_bfloat16 *a0op;        // A^(1) hi/lo operand, chunks of 256 rows
+    float *apad[kMaxModes];     // factors k >= 1 with rows of Kp floats (apad[0] unused)
+    double *partials;           // one FP64 partial per CTA
+    long long J;                // mode-1 fibers
+    int Kp, nchunks;            // R rounded up to 16; chunks of A^(1)
+};
+bool fit_tc_supported(const Problem<float> &P);
+size_t fit_tc_scratch_bytes(const Problem<float> &P);
+cudaError_t launch_fit_tc(const Problem<float> &P, void *scratch, double *partials, int sm_count, double *out,
+                          cudaStream_t s);
+cudaError_t launch_fold(const double *partials, int n, double *out, cudaStream_t s);
 
 // SKRP-ST-I materialised (cpd_skrp.cu).
 cudaError_t launch_skrp(const Problem<float> &P, int n, long long t0, int K, int *idx, double *p, float *Z, void *X,

@@ -870,6 +870,12 @@ cudaError_t launch_flush_dirty(const Problem<T> &P, cudaStream_t s)
 
 int fit_blocks() { return 4 * 152; }
 
+cudaError_t launch_fold(const double *partials, int n, double *out, cudaStream_t s)
+{
+    k_fold<<<1, kThreads, 0, s>>>(partials, n, out);
+    return cudaGetLastError();
+}
+
 // Raise each fit kernel's dynamic shared-memory limit once to the tiling's maximum.
 template <class T, class XT>
 static cudaError_t launch_fit_kernel(int grid, size_t dyn, cudaStream_t s, const Problem<T> &P, double *partials,

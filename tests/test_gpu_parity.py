@@ -411,3 +411,46 @@ def test_full_c4_persistent(cpd, orc, cs):
         if cs == 16 and e.status == cpd.ECUDA and "cannot be scheduled" in str(e):
             pytest.skip("this device does not co-schedule 16-CTA clusters with this layout")
         raise
+
+
+def _krp_mode1(A: list) -> np.ndarray:
+    """Rows z_j of the mode-1 unfolding's Khatri-Rao product, j = i_2 + I_2 i_3 + ...
+    (Eq. (2)): the second factor varies fastest."""
+    Z = A[1]
+    for a in A[2:]:
+        Z = (a[:, None, :] * Z[None, :, :]).reshape(-1, a.shape[1])
+    return Z
+
+
+@pytest.mark.parametrize("dims,R", [
+    ((300, 70, 50), 50),          # 2 resident chunks of A^(1) (256 + 44 rows), 28 tiles, ragged last tile
+    ((600, 40, 30), 33),          # 3 chunks through the two-slot ring, K = 48
+    ((1000, 60, 40), 64),         # 4 chunks, K = 64, the largest operand
+    ((20, 30, 40, 5), 16),        # 4-way, one 32-column chunk for 20 rows
+    ((100, 50, 40), 1),           # rank 1, K = 16
+])
+def test_tensor_core_fit_within_split_bound(cpd, orc, dims, R):
+    """The tensor-core stop check (BF16 tensors) against the oracle's direct
+    residual sum. x_hat is formed from bf16 hi/lo pairs (hi*hi + hi*lo +
+    lo*hi), so each entry of x_hat is off by at most
+    eps sum_r |a_ir z_jr|, eps = 2^-15 + R 2^-23 (the dropped lo*lo term, the
+    two splitting errors, FP32 accumulation over K). With ||delta|| <= eps
+    || |A1| |Z|^T ||_F, Cauchy-Schwarz bounds the residual sum's error by
+    2 ||r|| ||delta|| + ||delta||^2."""
+    _, X, A0 = make_problem(dims, R, noise=0.05, x_dtype="bf16", lognormal_rows=True)
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=64, x_dtype="bf16",
+                            sampling="euclidean", step="adagrad", seed=12)
+    assert dec.describe()["fit_pass"] == "tensor"
+    dec.sgd_iters(30)
+    _, tol = dec.fit()
+    A = [a.double().numpy() for a in dec.factors()]
+    xb = oracle_xbuf(X)
+    tol_o, xx = orc.tol(xb, A, "bf16", dims=dims)
+    eps = 2.0 ** -15 + R * 2.0 ** -23
+    E = eps * np.linalg.norm(np.abs(A[0]) @ np.abs(_krp_mode1(A)).T)
+    bound = (2.0 * np.sqrt(tol_o * xx) * E + E * E) / xx
+    assert abs(tol - tol_o) <= bound + 1e-6 * tol_o, (tol, tol_o, bound)
+    # a second pass over unchanged factors gives the same bits (fixed order)
+    _, tol_again = dec.fit()
+    assert tol_again == tol
+    dec.close()

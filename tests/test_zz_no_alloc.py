@@ -25,15 +25,17 @@ def cpd():
     return C
 
 
-# cpd_fit sums at most 16 squared residuals of a row in FP32 before adding
-# them to its FP64 running sum (float factors); the allocation-free pass
-# accumulates every entry in FP64. For float factors the two agree to the
-# FP32 rounding of those short sums.
+# cpd_fit sums at most 16 (CUDA cores) or 32 (tensor cores) squared
+# residuals in FP32 before adding them to its FP64 running sum (float
+# factors); the allocation-free pass accumulates every entry in FP64. For a
+# BF16 tensor cpd_fit forms x_hat from bf16 hi/lo pairs on the tensor cores
+# (about 2^-15 relative per product). These runs are far from converged
+# (residual comparable to X), where both effects stay below the tolerances.
 @pytest.mark.parametrize("xdt,dims,R,rtol", [
     ("f64", (30, 20, 25), 4, 1e-12),
     ("f32", (64, 50, 40), 6, 1e-6),
-    ("bf16", (48, 40, 36, 20), 5, 1e-6),
-    ("bf16", (300, 1000, 1000), 32, 1e-6),
+    ("bf16", (48, 40, 36, 20), 5, 2e-5),
+    ("bf16", (300, 1000, 1000), 32, 2e-5),
 ])
 def test_noalloc_tol_matches_cpd_fit_twice(cpd, xdt, dims, R, rtol):
     _, X, A0 = make_problem(dims, R, noise=0.1, x_dtype=xdt)
