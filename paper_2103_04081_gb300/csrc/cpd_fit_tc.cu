@@ -13,33 +13,39 @@
 // sum_r |a_ir z_jr| per entry, a few hundred times finer than the stored
 // BF16 entries themselves.
 //
-// Layout. The pass tiles the fibers: tile t = fibers [128 t, 128 t + 128)
-// (MMA M = 128, one TMEM lane per fiber), the rows of A^(1) in chunks of 256
-// (MMA N <= 256), K = R rounded up to 16. A CTA per SM walks tiles t = b,
-// b + grid, ...; its warps take fixed roles:
-//   warps 0-7   epilogue: warp w reads TMEM lanes 32 (w % 4) .. (its fibers),
-//               warps 0-3 the even 32-row groups of a chunk, 4-7 the odd ones;
-//               each thread loads its fiber's 32 entries of a group from the
-//               replica (four 16-byte loads, issued for the whole chunk before
-//               the accumulator is ready), subtracts x_hat, squares, sums.
-//   warps 8-11  producer: the tile's KRP rows (FP32 products of the factor
-//               rows, from padded copies with 16-byte rows), split hi/lo into
-//               the K-major operand; two stages.
-//   warp 12     one thread issues the MMAs: 3 K/16 per (tile, chunk), into one
-//               of two 256-column TMEM accumulators.
-//   warp 13     one thread loads the A^(1) operand chunks (hi/lo, prepared by
-//               k_fit_tc_prep) with bulk copies into two slots; when all
-//               chunks fit the two slots they are loaded once.
+// Three launches. k_fit_tc_prep writes A^(1)'s hi/lo operand in chunks of 128
+// rows and copies of the other factors with 16-byte rows; k_fit_tc_z writes
+// the hi/lo KRP operand of every tile of 128 fibers (the operand layout of
+// the MMA, so one bulk copy moves a tile); k_fit_tc makes the pass.
+//
+// k_fit_tc: a CTA per SM walks tiles t = b, b + grid, ... (MMA M = 128, one
+// TMEM lane per fiber) and, per tile, the chunks of A^(1) (MMA N <= 128,
+// K = R rounded up to 16). Warp roles:
+//   warp 17     lane 0 loads a tile's KRP operand (bulk copy, two stages)
+//               and the A^(1) chunks (bulk copies, two slots, loaded once when
+//               all chunks fit); lane 1 loads each (tile, chunk) block of the
+//               replica, 128 fibers x 128 entries, by two 2-D tensor copies
+//               with the 128-byte swizzle into one of three stages; entries
+//               past the fibers or past I_1's padding arrive as zeros.
+//   warp 16     one thread issues the 3 K/16 MMAs of a (tile, chunk) into one
+//               of four 128-column TMEM accumulators.
+//   warps 0-15  epilogue: warp w reads TMEM lanes 32 (w % 4) .. (its fibers)
+//               and the 32-row group w / 4 of every chunk; x comes from the
+//               swizzled stage (conflict-free 16-byte reads), d = x - x_hat,
+//               d^2 summed.
 // Hand-offs are mbarriers; every wait is bounded and a timeout makes every
 // role leave its loop (status kStTimeout), so the kernel always returns.
 // Sums are in a fixed order: a thread's groups in order (32 squared residuals
-// in FP32, then one FP64 add), the warp tree, the CTA's warps, and k_fold over
-// the CTAs.
+// in four FP32 partial sums, then one FP64 add), the warp tree, the CTA's
+// warps, and k_fold over the CTAs.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "cpd_device.cuh"
 #include "cpd_internal.h"
@@ -50,12 +56,14 @@ namespace cpd {
 namespace {
 
 constexpr int kFtM = 128;           // fibers per tile (MMA M)
-constexpr int kFtN = 256;           // rows of A^(1) per chunk (MMA N, largest)
-constexpr int kFtThreads = 448;     // 14 warps
-constexpr int kFtEpiWarps = 8;
-constexpr int kFtProdWarp0 = 8, kFtProdThreads = 128;
-constexpr int kFtMmaWarp = 12;      // warp 13 loads the A^(1) chunks
-constexpr int kFtColumns = 512;     // TMEM: two 256-column accumulators
+constexpr int kFtN = 128;           // rows of A^(1) per chunk (MMA N, largest)
+constexpr int kFtThreads = 576;     // 18 warps
+constexpr int kFtEpiWarps = 16;
+constexpr int kFtMmaWarp = 16, kFtLoadWarp = 17;
+constexpr int kFtBufs = 4;          // TMEM accumulators of 128 columns
+constexpr int kFtXStages = 3;       // replica blocks in flight
+constexpr int kFtColumns = 512;
+constexpr uint32_t kFtXBytes = kFtM * kFtN * 2;   // one replica block: 128 fibers x 128 entries
 
 // Instruction descriptor of kind::f16, D = F32, A = B = BF16, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_kk(int M, int N)
@@ -71,25 +79,26 @@ __host__ __device__ inline int kmaj(int row, int k, int Kp)
     return (((row >> 3) * (Kp >> 3) + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7);
 }
 
+// Dynamic shared memory, from a 1024-byte aligned base (the swizzled stages).
 struct FitTcLayout {
-    size_t zst, aslot, z, a, fi, bar, misc, total;
+    size_t zst, aslot, x, z, a, bar, misc, total;
     __host__ __device__ FitTcLayout(int Kp)
     {
-        zst = (size_t)kFtM * Kp * 2 * 2;     // one stage: Z hi, Z lo
-        aslot = (size_t)kFtN * Kp * 2 * 2;   // one chunk: A hi, A lo
-        z = 0;
+        zst = (size_t)kFtM * Kp * 2 * 2;     // a tile's KRP operand: hi, lo
+        aslot = (size_t)kFtN * Kp * 2 * 2;   // a chunk of A^(1): hi, lo
+        x = 0;                               // kFtXStages replica blocks (1024-aligned)
+        z = x + (size_t)kFtXStages * kFtXBytes;
         a = z + 2 * zst;
-        fi = a + 2 * aslot;                  // the tile's fibers' indices, [128][kMaxModes]
-        bar = fi + (size_t)kFtM * kMaxModes * 4;
-        misc = bar + 128;                    // tmem holder, abort flag, warp sums
-        total = misc + 16 + (kFtThreads / 32) * 8;
-        // at least 120 KB: one CTA per SM, so the 512-column TMEM
-        // allocation never waits for another CTA's
-        if (total < 120 * 1024) total = 120 * 1024;
+        bar = a + 2 * aslot;
+        misc = bar + 256;                    // tmem holder, abort flag, warp sums
+        total = misc + 16 + (kFtThreads / 32) * 8 + 1024;   // + alignment slack
     }
 };
 
-enum { kBarZFull = 0, kBarZFree = 2, kBarAFull = 4, kBarAFree = 6, kBarMDone = 8, kBarTFree = 10, kBarDrain = 12 };
+enum {
+    kBarZFull = 0, kBarZFree = 2, kBarAFull = 4, kBarAFree = 6, kBarXFull = 8, kBarXFree = 11,
+    kBarMDone = 14, kBarTFree = 18, kBarDrain = 22
+};
 
 __device__ __forceinline__ unsigned long long ft_now()
 {
@@ -138,71 +147,23 @@ __device__ __forceinline__ void ft_mma(uint32_t d, uint64_t a, uint64_t b, uint3
         : "memory");
 }
 
-// Columns of chunk c: its rows of A^(1) rounded up to 16 (MMA N), at most 256.
+// 2-D tensor copy global -> shared completing on an mbarrier; x (the
+// contiguous coordinate) is a multiple of 64 entries, 128 bytes.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+// Columns of chunk c: its rows of A^(1) rounded up to 16 (MMA N), at most 128.
 __host__ __device__ inline int chunk_cols(long long I0, int c)
 {
     const long long rows = I0 - (long long)c * kFtN;
     const long long n = (rows + 15) / 16 * 16;
     return (int)(n < kFtN ? n : kFtN);
-}
-
-// A step of the epilogue: group g = h + 2 u of chunk c of tile t (the
-// warpgroup h's u-th group of that chunk), qi = the (tile, chunk) sequence
-// number of the CTA. next() skips chunks that hold no group for h (a tail
-// chunk of at most 32 rows has none for h = 1); qi still counts them.
-struct FtStep {
-    long long t, qi;
-    int c, u;
-    bool valid;
-    __device__ __forceinline__ static int groups(long long I0, int c) { return (chunk_cols(I0, c) + 31) / 32; }
-    __device__ __forceinline__ void settle(int grid, long long ntile, int nch, int h, long long I0)
-    {
-        while (valid && h + 2 * u >= groups(I0, c)) {
-            u = 0;
-            ++qi;
-            if (++c == nch) {
-                c = 0;
-                t += grid;
-                if (t >= ntile) valid = false;
-            }
-        }
-    }
-    __device__ __forceinline__ void start(long long t0, int grid, long long ntile, int nch, int h, long long I0)
-    {
-        t = t0;
-        qi = 0;
-        c = 0;
-        u = 0;
-        valid = t0 < ntile;
-        settle(grid, ntile, nch, h, I0);
-    }
-    __device__ __forceinline__ void next(int grid, long long ntile, int nch, int h, long long I0)
-    {
-        ++u;
-        settle(grid, ntile, nch, h, I0);
-    }
-    __device__ __forceinline__ bool last_in_chunk(int h, long long I0) const
-    {
-        return h + 2 * (u + 1) >= groups(I0, c);
-    }
-};
-
-// The 32 replica entries of a step for fiber m of its tile, warpgroup h
-// (zeros past the tensor's fibers; each 16-byte load lies inside the fiber's
-// ld0 entries, the padding past I_1 being zero).
-__device__ __forceinline__ void ft_load(uint4 (&x)[4], const FtStep &s, int h, const __nv_bfloat16 *rep, int m,
-                                        long long J, long long ld0)
-{
-#pragma unroll
-    for (int w = 0; w < 4; ++w) x[w] = make_uint4(0u, 0u, 0u, 0u);
-    if (!s.valid) return;
-    const long long j = s.t * kFtM + m;
-    if (j >= J) return;
-    const long long i0 = (long long)s.c * kFtN + 32 * (h + 2 * s.u);
-    const uint4 *p = reinterpret_cast<const uint4 *>(rep + j * ld0 + i0);
-#pragma unroll
-    for (int w = 0; w < 4; ++w)
-        if (i0 + 8 * w < ld0) x[w] = __ldcs(p + w);
 }
 
 // v = hi + lo with hi = bf16(v), lo = bf16(v - hi), four entries packed as
@@ -220,9 +181,9 @@ __device__ __forceinline__ void split4(float4 v, uint2 &hi, uint2 &lo)
 
 }  // namespace
 
-// A^(1)'s hi/lo operand in chunks of 256 rows (rows past I_1 zero), and the
-// factors k >= 2 (in the paper's 1-based numbering: every mode but the first)
-// copied with rows of Kp floats, zero-padded.
+// A^(1)'s hi/lo operand in chunks of 128 rows (rows past I_1 zero), and the
+// other factors (modes k >= 1 here; the paper's modes 2..N) copied with rows
+// of Kp floats, zero-padded.
 __global__ void __launch_bounds__(kThreads) k_fit_tc_prep(const Problem<float> P, FitTcArgs a)
 {
     const int R = P.R, Kp = a.Kp;
@@ -250,20 +211,66 @@ __global__ void __launch_bounds__(kThreads) k_fit_tc_prep(const Problem<float> P
     }
 }
 
-// 14 warps: four to a sub-partition, whose 16K registers cap a thread at 128
-__global__ void __launch_bounds__(kFtThreads, 1) k_fit_tc(const Problem<float> P, const FitTcArgs a)
+// The KRP operand of every tile: z_j = A^(2)(i_2,:) * ... * A^(N)(i_N,:) in
+// FP32 (factors in ascending order, Eq. (3)), j = t 128 + f, split hi/lo and
+// written in the tile's K-major layout; fibers past J are zero. A thread
+// forms one 16-byte row of a core matrix (8 entries of z_j), so the fiber's
+// indices are decoded once per 8 entries and 8 consecutive threads write a
+// core matrix's 128 contiguous bytes.
+__global__ void __launch_bounds__(kThreads) k_fit_tc_z(const Problem<float> P, FitTcArgs a)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int Kp = a.Kp, N = P.N, nch = a.nchunks;
+    const int Kp = a.Kp, N = P.N;
+    const int per_tile = kFtM * Kp / 8;   // 16-byte rows of a tile's hi (or lo) half
+    const long long ntile = (a.J + kFtM - 1) / kFtM;
+    const long long total = ntile * per_tile;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long t = e / per_tile;
+        const int o = (int)(e - t * per_tile);
+        const int cm = o >> 3, kb = cm % (Kp >> 3);
+        const int f = (cm / (Kp >> 3)) * 8 + (o & 7);
+        const long long j = t * kFtM + f;
+        float4 z0 = make_float4(0.f, 0.f, 0.f, 0.f), z1 = z0;
+        if (j < a.J) {
+            unsigned rest = (unsigned)j;   // Eq. (2) inverted, mode 2 fastest; J < 2^31
+            for (int k = 1; k < N; ++k) {
+                const unsigned Ik = (unsigned)P.dims[k];
+                const unsigned ik = rest % Ik;
+                rest /= Ik;
+                const float4 *src = reinterpret_cast<const float4 *>(a.apad[k] + (long long)ik * Kp + kb * 8);
+                const float4 v0 = __ldg(src), v1 = __ldg(src + 1);
+                if (k == 1) {
+                    z0 = v0;
+                    z1 = v1;
+                } else {
+                    z0.x *= v0.x; z0.y *= v0.y; z0.z *= v0.z; z0.w *= v0.w;
+                    z1.x *= v1.x; z1.y *= v1.y; z1.z *= v1.z; z1.w *= v1.w;
+                }
+            }
+        }
+        uint2 h0, l0, h1, l1;
+        split4(z0, h0, l0);
+        split4(z1, h1, l1);
+        uint4 *tile = reinterpret_cast<uint4 *>(a.ztiles + (size_t)t * (2 * kFtM * Kp));
+        tile[o] = make_uint4(h0.x, h0.y, h1.x, h1.y);
+        tile[per_tile + o] = make_uint4(l0.x, l0.y, l1.x, l1.y);
+    }
+}
+
+// 18 warps: at most five to a sub-partition, whose 16K registers allow 102 a thread
+__global__ void __launch_bounds__(kFtThreads, 1) k_fit_tc(const Problem<float> P, const FitTcArgs a,
+                                                          const __grid_constant__ CUtensorMap xmap)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int Kp = a.Kp, nch = a.nchunks;
     const FitTcLayout L(Kp);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long I0 = P.dims[0], J = a.J, ld0 = P.ld[0];
+    const long long I0 = P.dims[0], J = a.J;
     const long long ntile = (J + kFtM - 1) / kFtM;
-    int *sfi = reinterpret_cast<int *>(smem + L.fi);
     const uint32_t bar0 = smem_u32(smem + L.bar);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + L.misc);
     volatile int *abort = reinterpret_cast<volatile int *>(smem + L.misc + 4);
-    volatile int *pdec = reinterpret_cast<volatile int *>(smem + L.misc + 8);   // producers' verdict
     double *wsum = reinterpret_cast<double *>(smem + L.misc + 16);
     auto bar = [&](int which, int idx) { return bar0 + 8u * (uint32_t)(which + idx); };
     const bool resident = nch <= 2;
@@ -274,8 +281,14 @@ __global__ void __launch_bounds__(kFtThreads, 1) k_fit_tc(const Problem<float> P
             mbar_init(bar(kBarZFree, s), 1);
             mbar_init(bar(kBarAFull, s), 1);
             mbar_init(bar(kBarAFree, s), 1);
-            mbar_init(bar(kBarMDone, s), 1);
-            mbar_init(bar(kBarTFree, s), kFtEpiWarps);
+        }
+        for (int s = 0; s < kFtXStages; ++s) {
+            mbar_init(bar(kBarXFull, s), 1);
+            mbar_init(bar(kBarXFree, s), kFtEpiWarps);
+        }
+        for (int b = 0; b < kFtBufs; ++b) {
+            mbar_init(bar(kBarMDone, b), 1);
+            mbar_init(bar(kBarTFree, b), kFtEpiWarps);
         }
         mbar_init(bar(kBarDrain, 0), 1);
         *abort = 0;
@@ -301,156 +314,56 @@ __global__ void __launch_bounds__(kFtThreads, 1) k_fit_tc(const Problem<float> P
 
     if (warp < kFtEpiWarps) {
         // ---- epilogue ------------------------------------------------------
-        // The thread's work is a sequence of steps, one per 32-row group of a
-        // (tile, chunk) that its warpgroup owns; the replica entries of step
-        // n + 4 are loaded while step n is processed (a ring of four register
-        // slots, rotated by unrolling), so loads stay in flight across chunk
-        // and tile boundaries.
-        const int q = warp & 3, h = warp >> 2, m = 32 * q + lane;
-        const __nv_bfloat16 *rep = reinterpret_cast<const __nv_bfloat16 *>(P.rep[0]);
-        FtStep ld, pr;
-        ld.start(blockIdx.x, gridDim.x, ntile, nch, h, I0);
-        pr = ld;
-        uint4 xv[4][4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            ft_load(xv[k], ld, h, rep, m, J, ld0);
-            ld.next(gridDim.x, ntile, nch, h, I0);
-        }
-        long long waited = -1;   // chunks whose accumulator this warp has waited for
-        const long long nseq = ((ntile - 1 - blockIdx.x) / gridDim.x + 1) * nch;
-        while (pr.valid && !timed_out) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (!pr.valid || timed_out) break;
-                while (waited < pr.qi && !timed_out) {   // the step's chunk (and chunks empty for this warp)
-                    ++waited;
-                    const bool ok = ft_wait(bar(kBarMDone, (int)(waited & 1)), (uint32_t)((waited >> 1) & 1), abort,
-                                            timed, &w0);
-                    if (!__all_sync(0xffffffffu, ok)) {
-                        timed_out = true;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    if (waited < pr.qi) {
-                        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                        __syncwarp();
-                        if (lane == 0) ft_arrive(bar(kBarTFree, (int)(waited & 1)));
-                    }
+        const int q = warp & 3, g = warp >> 2, m = 32 * q + lane;
+        long long qi = 0;   // (tile, chunk) sequence number of the CTA
+        for (long long t = blockIdx.x; t < ntile && !timed_out; t += gridDim.x) {
+            for (int c = 0; c < nch; ++c, ++qi) {
+                const int b = (int)(qi & (kFtBufs - 1)), xs = (int)(qi % kFtXStages);
+                // every lane waits; the warp leaves together if any lane gave up
+                bool ok = ft_wait(bar(kBarMDone, b), (uint32_t)((qi / kFtBufs) & 1), abort, timed, &w0);
+                ok = ok && ft_wait(bar(kBarXFull, xs), (uint32_t)((qi / kFtXStages) & 1), abort, timed, &w1);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    timed_out = true;
+                    break;
                 }
-                if (timed_out) break;
-                const int b = (int)(pr.qi & 1), g = h + 2 * pr.u;
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kFtN + 32 * g), v);
-                // No per-entry mask: past I_1 and past the fibers both x (zero
-                // padding or skipped loads) and x_hat (zero operand rows) are 0.
-                // Only columns at or past the chunk's MMA width Nc hold stale
-                // accumulator values: Nc is a multiple of 16, so a group
-                // straddling it keeps its first 16 columns.
-                const bool half = 32 * g + 32 > chunk_cols(I0, pr.c);
-                float p4[4] = {0.f, 0.f, 0.f, 0.f};
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const int Nc = chunk_cols(I0, c);
+                const unsigned char *xst = smem + L.x + (size_t)xs * kFtXBytes;
+                if (32 * g < Nc) {   // warp-uniform
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kFtN + 32 * g), v);
+                    // No per-entry mask: past I_1 and past the fibers both x
+                    // (zero padding or the copies' zero fill) and x_hat (zero
+                    // operand rows) are 0. Columns at or past Nc (a multiple of
+                    // 16) hold stale accumulator values: a group straddling Nc
+                    // keeps its first 16 columns.
+                    const bool half = 32 * g + 32 > Nc;
+                    // box g / 2 holds rows [64 (g / 2), +64) of the 128 fibers; the
+                    // 16-byte chunk k of fiber m's 128-byte row sits at k ^ (m % 8)
+                    const unsigned char *row = xst + (size_t)(g >> 1) * (kFtXBytes / 2) + (size_t)m * 128;
+                    float p4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    if (w >= 2 && half) break;
-                    const uint32_t wd[4] = {xv[k][w].x, xv[k][w].y, xv[k][w].z, xv[k][w].w};
+                    for (int w = 0; w < 4; ++w) {
+                        if (w >= 2 && half) break;
+                        const int kc = ((g & 1) * 4 + w) ^ (m & 7);
+                        const uint4 xv = *reinterpret_cast<const uint4 *>(row + kc * 16);
+                        const uint32_t wd[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const uint32_t bits = (e & 1) ? (wd[e >> 1] & 0xffff0000u) : (wd[e >> 1] << 16);
-                        const float d = __uint_as_float(bits) - v[8 * w + e];
-                        p4[e & 3] = fmaf(d, d, p4[e & 3]);
-                    }
-                }
-                const float part = (p4[0] + p4[1]) + (p4[2] + p4[3]);
-                acc += (double)part;
-                if (pr.last_in_chunk(h, I0)) {
-                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) ft_arrive(bar(kBarTFree, b));
-                }
-                ft_load(xv[k], ld, h, rep, m, J, ld0);
-                ld.next(gridDim.x, ntile, nch, h, I0);
-                pr.next(gridDim.x, ntile, nch, h, I0);
-            }
-        }
-        while (!timed_out && waited + 1 < nseq) {   // trailing chunks empty for this warp
-            ++waited;
-            const bool ok = ft_wait(bar(kBarMDone, (int)(waited & 1)), (uint32_t)((waited >> 1) & 1), abort);
-            if (!__all_sync(0xffffffffu, ok)) {
-                timed_out = true;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            __syncwarp();
-            if (lane == 0) ft_arrive(bar(kBarTFree, (int)(waited & 1)));
-        }
-    } else if (warp < kFtMmaWarp) {
-        // ---- producer: KRP rows of the tile, hi/lo, K-major ----------------
-        const int pt = tid - kFtProdWarp0 * 32;
-        const int nq = Kp / 4, tot = kFtM * nq;
-        long long tl = 0;
-        for (long long t = blockIdx.x; t < ntile && !timed_out; t += gridDim.x, ++tl) {
-            const int s = (int)(tl & 1);
-            // one thread waits for the stage; its verdict, in shared memory,
-            // is read by all 128 after the barrier, so they leave together
-            if (pt == 0)
-                *pdec = (tl >= 2 && !ft_wait(bar(kBarZFree, s), (uint32_t)(((tl >> 1) + 1) & 1), abort, timed, &w0)) ? 1 : 0;
-            asm volatile("bar.sync 1, %0;\n" ::"r"(kFtProdThreads) : "memory");
-            if (*pdec) {
-                timed_out = true;
-                break;
-            }
-            {   // Eq. (2) inverted once per fiber: i_k = (j / prod_{1<=l<k} I_l) mod I_k
-                long long j = t * kFtM + pt;
-                int *row = sfi + pt * kMaxModes;
-                row[0] = j < J ? 1 : 0;
-                for (int k = 1; k < N; ++k) {
-                    row[k] = (int)(j % P.dims[k]);
-                    j /= P.dims[k];
-                }
-            }
-            asm volatile("bar.sync 1, %0;\n" ::"r"(kFtProdThreads) : "memory");
-            unsigned char *zs = smem + L.z + (size_t)s * L.zst;
-            uint2 *zhi = reinterpret_cast<uint2 *>(zs);
-            uint2 *zlo = reinterpret_cast<uint2 *>(zs + (size_t)kFtM * Kp * 2);
-            for (int base = 0; base < tot; base += kFtProdThreads * 8) {
-                float4 z[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e4 = base + u * kFtProdThreads + pt;
-                    const int f = e4 / nq, r4 = e4 - f * nq;
-                    const bool ok = e4 < tot && sfi[f * kMaxModes] != 0;
-                    z[u] = ok ? __ldg(reinterpret_cast<const float4 *>(a.apad[1] + (long long)sfi[f * kMaxModes + 1] * Kp) + r4)
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                for (int k = 2; k < N; ++k) {   // ascending k, as in Eq. (3)
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int e4 = base + u * kFtProdThreads + pt;
-                        const int f = e4 / nq, r4 = e4 - f * nq;
-                        if (e4 < tot && sfi[f * kMaxModes] != 0) {
-                            const float4 v = __ldg(
-                                reinterpret_cast<const float4 *>(a.apad[k] + (long long)sfi[f * kMaxModes + k] * Kp) + r4);
-                            z[u].x *= v.x;
-                            z[u].y *= v.y;
-                            z[u].z *= v.z;
-                            z[u].w *= v.w;
+                        for (int e = 0; e < 8; ++e) {
+                            const uint32_t bits = (e & 1) ? (wd[e >> 1] & 0xffff0000u) : (wd[e >> 1] << 16);
+                            const float d = __uint_as_float(bits) - v[8 * w + e];
+                            p4[e & 3] = fmaf(d, d, p4[e & 3]);
                         }
                     }
+                    acc += (double)((p4[0] + p4[1]) + (p4[2] + p4[3]));
                 }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e4 = base + u * kFtProdThreads + pt;
-                    if (e4 < tot) {
-                        const int f = e4 / nq, r4 = e4 - f * nq;
-                        const int o = kmaj(f, 4 * r4, Kp) >> 2;   // 4 bf16 = one uint2
-                        split4(z[u], zhi[o], zlo[o]);
-                    }
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    ft_arrive(bar(kBarTFree, b));
+                    ft_arrive(bar(kBarXFree, xs));
                 }
             }
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            asm volatile("bar.sync 1, %0;\n" ::"r"(kFtProdThreads) : "memory");
-            if (pt == 0) ft_arrive(bar(kBarZFull, s));
         }
     } else if (warp == kFtMmaWarp) {
         // ---- MMA issue -----------------------------------------------------
@@ -468,9 +381,10 @@ __global__ void __launch_bounds__(kFtThreads, 1) k_fit_tc(const Problem<float> P
                 for (int c = 0; c < nch; ++c, ++qi) {
                     const int slot = resident ? c : (int)(qi & 1);
                     const uint32_t apar = resident ? 0u : (uint32_t)((qi >> 1) & 1);
-                    const int b = (int)(qi & 1);
+                    const int b = (int)(qi & (kFtBufs - 1));
                     if (!ft_wait(bar(kBarAFull, slot), apar, abort, timed, &w1) ||
-                        (qi >= 2 && !ft_wait(bar(kBarTFree, b), (uint32_t)(((qi >> 1) + 1) & 1), abort, timed, &w2))) {
+                        (qi >= kFtBufs &&
+                         !ft_wait(bar(kBarTFree, b), (uint32_t)(((qi / kFtBufs) + 1) & 1), abort, timed, &w2))) {
                         timed_out = true;
                         break;
                     }
@@ -501,48 +415,86 @@ __global__ void __launch_bounds__(kFtThreads, 1) k_fit_tc(const Problem<float> P
             }
         }
     } else {
-        // ---- A^(1) operand chunks ------------------------------------------
+        // ---- loads ---------------------------------------------------------
+        // lane 0: KRP tiles and A^(1) chunks; lane 1: replica blocks, so that
+        // the replica runs ahead while an A^(1) slot waits for its MMAs
+        const uint32_t abytes = (uint32_t)L.aslot, zbytes = (uint32_t)L.zst;
         if (lane == 0) {
-            const uint32_t bytes = (uint32_t)L.aslot;
-            if (resident) {
+            if (resident)
                 for (int c = 0; c < nch; ++c) {
-                    mbar_expect_tx(bar(kBarAFull, c), bytes);
-                    bulk_g2s(smem_u32(smem + L.a + (size_t)c * L.aslot), a.a0op + (size_t)c * (2 * kFtN * Kp), bytes,
+                    mbar_expect_tx(bar(kBarAFull, c), abytes);
+                    bulk_g2s(smem_u32(smem + L.a + (size_t)c * L.aslot), a.a0op + (size_t)c * (2 * kFtN * Kp), abytes,
                              bar(kBarAFull, c));
                 }
-                for (int c = 0; c < nch; ++c) mbar_wait_bounded(bar(kBarAFull, c), 0);
-            } else {
-                long long qi = 0;
-                for (long long t = blockIdx.x; t < ntile && !timed_out; t += gridDim.x)
-                    for (int c = 0; c < nch; ++c, ++qi) {
-                        const int slot = (int)(qi & 1);
-                        if (qi >= 2 &&
-                            !ft_wait(bar(kBarAFree, slot), (uint32_t)(((qi >> 1) + 1) & 1), abort, timed, &w0)) {
-                            timed_out = true;
-                            break;
-                        }
-                        mbar_expect_tx(bar(kBarAFull, slot), bytes);
-                        bulk_g2s(smem_u32(smem + L.a + (size_t)slot * L.aslot), a.a0op + (size_t)c * (2 * kFtN * Kp),
-                                 bytes, bar(kBarAFull, slot));
+            long long nz = 0, na = 0;   // copies issued: KRP tiles, A^(1) chunks (ring)
+            for (long long t = blockIdx.x; t < ntile && !timed_out; t += gridDim.x) {
+                const int s = (int)(nz & 1);
+                if (nz >= 2 && !ft_wait(bar(kBarZFree, s), (uint32_t)(((nz >> 1) + 1) & 1), abort, timed, &w0)) {
+                    timed_out = true;
+                    break;
+                }
+                mbar_expect_tx(bar(kBarZFull, s), zbytes);
+                bulk_g2s(smem_u32(smem + L.z + (size_t)s * L.zst), a.ztiles + (size_t)t * (2 * kFtM * Kp), zbytes,
+                         bar(kBarZFull, s));
+                ++nz;
+                if (resident) continue;
+                for (int c = 0; c < nch; ++c) {
+                    const int slot = (int)(na & 1);
+                    if (na >= 2 && !ft_wait(bar(kBarAFree, slot), (uint32_t)(((na >> 1) + 1) & 1), abort, timed, &w1)) {
+                        timed_out = true;
+                        break;
                     }
-                // the copies in flight land before the CTA's shared memory goes away
-                for (long long r = (qi >= 2 ? qi - 2 : 0); r < qi; ++r)
-                    mbar_wait_bounded(bar(kBarAFull, (int)(r & 1)), (uint32_t)((r >> 1) & 1));
+                    mbar_expect_tx(bar(kBarAFull, slot), abytes);
+                    bulk_g2s(smem_u32(smem + L.a + (size_t)slot * L.aslot), a.a0op + (size_t)c * (2 * kFtN * Kp),
+                             abytes, bar(kBarAFull, slot));
+                    ++na;
+                }
             }
+            // the copies in flight land before the CTA's shared memory goes away
+            if (resident)
+                for (int c = 0; c < nch; ++c) mbar_wait_bounded(bar(kBarAFull, c), 0);
+            for (long long r = (nz >= 2 ? nz - 2 : 0); r < nz; ++r)
+                mbar_wait_bounded(bar(kBarZFull, (int)(r & 1)), (uint32_t)((r >> 1) & 1));
+            for (long long r = (na >= 2 ? na - 2 : 0); r < na; ++r)
+                mbar_wait_bounded(bar(kBarAFull, (int)(r & 1)), (uint32_t)((r >> 1) & 1));
+        } else if (lane == 1) {
+            long long nx = 0;
+            for (long long t = blockIdx.x; t < ntile && !timed_out; t += gridDim.x)
+                for (int c = 0; c < nch; ++c) {
+                    const int xs = (int)(nx % kFtXStages);
+                    if (nx >= kFtXStages &&
+                        !ft_wait(bar(kBarXFree, xs), (uint32_t)(((nx / kFtXStages) + 1) & 1), abort, timed, &w2)) {
+                        timed_out = true;
+                        break;
+                    }
+                    mbar_expect_tx(bar(kBarXFull, xs), kFtXBytes);
+                    const uint32_t dst = smem_u32(smem + L.x + (size_t)xs * kFtXBytes);
+                    tma_load_2d(dst, &xmap, c * kFtN, (int)(t * kFtM), bar(kBarXFull, xs));
+                    tma_load_2d(dst + kFtXBytes / 2, &xmap, c * kFtN + 64, (int)(t * kFtM), bar(kBarXFull, xs));
+                    ++nx;
+                }
+            for (long long r = (nx >= kFtXStages ? nx - kFtXStages : 0); r < nx; ++r)
+                mbar_wait_bounded(bar(kBarXFull, (int)(r % kFtXStages)), (uint32_t)((r / kFtXStages) & 1));
         }
     }
-    if (timed_out && (lane == 0)) atomicOr(P.status, kStTimeout);
-    if (timed && lane == 0) {   // one thread per role: epilogue warps 0 and 4, producer, MMA, loader
-        if (warp == 0) P.trace[46] = w0;
-        if (warp == 4) P.trace[47] = w0;
-        if (warp == kFtProdWarp0) P.trace[48] = w0;
+    if (timed_out) atomicOr(P.status, kStTimeout);
+    if (timed && lane == 0) {   // one thread per role: epilogue warps 0 and 4, MMA, loader
+        if (warp == 0) {
+            P.trace[46] = w0;
+            P.trace[47] = w1;
+        }
+        if (warp == 4) P.trace[48] = w0 + w1;
         if (warp == kFtMmaWarp) {
             P.trace[49] = w0;
             P.trace[50] = w1;
             P.trace[51] = w2;
         }
-        if (warp == kFtMmaWarp + 1) P.trace[52] = w0;
+        if (warp == kFtLoadWarp) {
+            P.trace[52] = w0;
+            P.trace[53] = w1;
+        }
     }
+    if (timed && warp == kFtLoadWarp && lane == 1) P.trace[54] = w2;
     trace_stamp(P.trace, 45, blockIdx.x == 0);
 
     // fixed-order sum: warp tree, then the warps in order
@@ -562,29 +514,61 @@ __global__ void __launch_bounds__(kFtThreads, 1) k_fit_tc(const Problem<float> P
     }
 }
 
-bool fit_tc_supported(const Problem<float> &P)
-{
-    return P.x_dtype == CPD_BF16 && P.R >= 1 && P.R <= 64;
-}
+namespace {
 
 int fit_tc_kp(int R) { return (R + 15) / 16 * 16; }
 
 int fit_tc_chunks(long long I0) { return (int)((I0 + kFtN - 1) / kFtN); }
 
+long long fit_tc_fibers(const Problem<float> &P)
+{
+    long long J = 1;
+    for (int k = 1; k < P.N; ++k) J *= P.dims[k];
+    return J;
+}
+
+// cuTensorMapEncodeTiled from the driver, found once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+}  // namespace
+
+bool fit_tc_supported(const Problem<float> &P)
+{
+    // fibers and tile coordinates stay below 2^31 (32-bit copy coordinates)
+    return P.x_dtype == CPD_BF16 && P.R >= 1 && P.R <= 64 && fit_tc_fibers(P) < (1LL << 31) - kFtM &&
+           encode_tiled() != nullptr;
+}
+
 size_t fit_tc_scratch_bytes(const Problem<float> &P)
 {
     const int Kp = fit_tc_kp(P.R);
+    const long long ntile = (fit_tc_fibers(P) + kFtM - 1) / kFtM;
     size_t b = (size_t)fit_tc_chunks(P.dims[0]) * 2 * kFtN * Kp * 2;
-    for (int k = 1; k < P.N; ++k) b += (size_t)P.dims[k] * Kp * 4 + 64;
+    for (int k = 1; k < P.N; ++k) b += ((size_t)P.dims[k] * Kp * 4 + 64 + 15) / 16 * 16;
+    b += (size_t)ntile * 2 * kFtM * Kp * 2;
     return b + 256;
 }
 
-void fit_tc_args(const Problem<float> &P, void *scratch, double *partials, FitTcArgs &a)
+static void fit_tc_args(const Problem<float> &P, void *scratch, double *partials, FitTcArgs &a)
 {
     a.Kp = fit_tc_kp(P.R);
     a.nchunks = fit_tc_chunks(P.dims[0]);
-    a.J = 1;
-    for (int k = 1; k < P.N; ++k) a.J *= P.dims[k];
+    a.J = fit_tc_fibers(P);
     a.partials = partials;
     char *p = static_cast<char *>(scratch);
     a.a0op = reinterpret_cast<__nv_bfloat16 *>(p);
@@ -594,6 +578,7 @@ void fit_tc_args(const Problem<float> &P, void *scratch, double *partials, FitTc
         a.apad[k] = reinterpret_cast<float *>(p);
         p += ((size_t)P.dims[k] * a.Kp * 4 + 64 + 15) / 16 * 16;
     }
+    a.ztiles = reinterpret_cast<__nv_bfloat16 *>(p);
 }
 
 cudaError_t launch_fit_tc(const Problem<float> &P, void *scratch, double *partials, int sm_count, double *out,
@@ -601,6 +586,17 @@ cudaError_t launch_fit_tc(const Problem<float> &P, void *scratch, double *partia
 {
     FitTcArgs a{};
     fit_tc_args(P, scratch, partials, a);
+    // the mode-1 replica as a 2-D tensor: ld_1 entries (contiguous) x J fibers,
+    // boxes of 64 entries (128 bytes, the swizzle span) x 128 fibers
+    CUtensorMap xmap;
+    const cuuint64_t gdim[2] = {(cuuint64_t)P.ld[0], (cuuint64_t)a.J};
+    const cuuint64_t gstride[1] = {(cuuint64_t)P.ld[0] * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)kFtM};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult r = encode_tiled()(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(P.rep[0]), gdim,
+                                      gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     const FitTcLayout L(a.Kp);
     static size_t raised = 0;
     if (L.total > raised) {
@@ -612,9 +608,10 @@ cudaError_t launch_fit_tc(const Problem<float> &P, void *scratch, double *partia
         raised = L.total;
     }
     k_fit_tc_prep<<<2 * sm_count, kThreads, 0, s>>>(P, a);
+    k_fit_tc_z<<<4 * sm_count, kThreads, 0, s>>>(P, a);
     const long long ntile = (a.J + kFtM - 1) / kFtM;
     const int grid = (int)std::min<long long>(ntile, sm_count);
-    k_fit_tc<<<grid, kFtThreads, L.total, s>>>(P, a);
+    k_fit_tc<<<grid, kFtThreads, L.total, s>>>(P, a, xmap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_fold(partials, grid, out, s);

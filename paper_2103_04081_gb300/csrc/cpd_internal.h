@@ -151,7 +151,8 @@ constexpr long long kSimtStageCap = 2048;
 
 // Tensor-core stop check (cpd_fit_tc.cu): BF16 tensors, float factors, R <= 64.
 struct FitTcArgs {
-    __nv_bfloat16 *a0op;        // A^(1) hi/lo operand, chunks of 256 rows
+    __nv_bfloat16 *a0op;        // A^(1) hi/lo operand, chunks of 128 rows
+    __nv_bfloat16 *ztiles;      // KRP hi/lo operand, tiles of 128 fibers
     float *apad[kMaxModes];     // factors k >= 1 with rows of Kp floats (apad[0] unused)
     double *partials;           // one FP64 partial per CTA
     long long J;                // mode-1 fibers
