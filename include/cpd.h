@@ -83,6 +83,15 @@ enum {
     CPD_CONSTRAINT_NONNEG = 1   /* a <- max(0, a) after the step (NaN kept)  */
 };
 
+/* Where the sampled fibers are read from (cpd_config.x_layout). */
+typedef enum {
+    CPD_LAYOUT_REPLICAS = 0,    /* one mode-major replica per mode: every mode-n
+                                   fiber contiguous (N copies of X)             */
+    CPD_LAYOUT_STRIDED = 1      /* one copy of X in its own column-major layout:
+                                   a mode-n fiber (Eq. (2)) is read with stride
+                                   I_1 ... I_{n-1}; CUDA-core engine only       */
+} cpd_layout;
+
 typedef struct {
     int32_t N;          /* number of modes, 3 <= N <= CPD_MAX_MODES                 */
     int32_t R;          /* CP rank, 1 <= R <= 256                                   */
@@ -115,7 +124,8 @@ typedef struct {
                            of the batch fixes the summation order of the
                            gradient partials.                                   */
     int32_t constraint; /* CPD_CONSTRAINT_*                                     */
-    int32_t reserved;   /* must be 0                                            */
+    int32_t x_layout;   /* CPD_LAYOUT_*: replicas (0) or a single strided copy
+                           (1, N times less memory, slower gathers for n > 1)   */
 } cpd_config;
 
 typedef struct cpd_ctx cpd_ctx;
@@ -367,17 +377,23 @@ typedef struct {
                              lane of same-dtype, same-engine requests; others
                              run on streams of their own. 1: every request on
                              a stream of its own.                             */
-    int32_t reserved;     /* must be 0                                         */
+    int32_t strided_above_mb; /* a request whose mode-major replicas would hold
+                             more than this many MiB runs with one strided copy
+                             of X on the CUDA-core engine (CPD_LAYOUT_STRIDED;
+                             0: only when the replicas exceed the budget)     */
 } cpd_server_config;
 
 typedef struct {
     int32_t status;       /* CPD_OK, or the failure that stopped the request   */
     int32_t done;         /* 1 once the request has stopped                    */
     int32_t reached;      /* 1 when the fit target was reached                 */
-    int32_t pad;
+    int32_t layout;       /* CPD_LAYOUT_* the request runs with (the server
+                             falls back to the strided layout, see cpd_submit) */
     int64_t iters;        /* iterations run                                    */
     double fit, tol;      /* at the last check (Sec. 5.2)                      */
-    double t_submit, t_start, t_done; /* seconds on the server's clock         */
+    double t_submit, t_start, t_done; /* seconds on the server's clock; t_start:
+                             admitted and its own copy of X made (the caller
+                             may release X and A0 from then on)               */
 } cpd_result;
 
 /* cpd_server_create -- a server on the current CUDA device (one worker thread). */
@@ -385,8 +401,13 @@ cpd_status cpd_server_create(const cpd_server_config *cfg, cpd_server **out);
 
 /*
  * cpd_submit -- queue one decomposition: cfg, X and A0 as for cpd_init (X and
- * A0 must stay valid until cpd_poll reports the request done); it stops when
- * fit >= stop_fit or after max_iters iterations. Returns its ticket.
+ * A0 must stay valid until the request has started: cpd_poll reports
+ * t_start > 0); it stops when fit >= stop_fit or after max_iters iterations.
+ * Returns its ticket. A request whose mode-major replicas would exceed the
+ * budget (or cpd_server_config.strided_above_mb) runs with
+ * CPD_LAYOUT_STRIDED on the CUDA-core engine instead (one copy of X; the
+ * decision depends only on the request and the server's configuration, so
+ * a request's arithmetic never depends on the load).
  * CPD_ENOMEM if the request can never fit the budget.
  */
 cpd_status cpd_submit(cpd_server *srv, const cpd_config *cfg, const void *X, int x_loc,
@@ -399,6 +420,12 @@ cpd_status cpd_submit(cpd_server *srv, const cpd_config *cfg, const void *X, int
  * copies its N factor matrices into the host buffers A_out[k] (I_k x R).
  */
 cpd_status cpd_poll(cpd_server *srv, uint64_t ticket, cpd_result *out, void *const *A_out);
+
+/*
+ * cpd_server_stats -- the server's budget, the bytes its admitted requests
+ * hold, and how many requests run and wait (any pointer may be NULL).
+ */
+cpd_status cpd_server_stats(cpd_server *srv, size_t *budget, size_t *held, int32_t *active, int32_t *queued);
 
 /* cpd_server_wait -- block until every submitted request is done, or
  * CPD_EAGAIN after timeout_s seconds (timeout_s <= 0: no limit). */

@@ -23,6 +23,7 @@ HOST, DEVICE = 0, 1
 SAMPLE = {"euclidean": 0, "leverage": 1, "uniform": 2}
 STEP = {"fixed": 0, "adagrad": 1, "decay": 2}
 CONSTRAINT = {"none": 0, "nonneg": 1}
+LAYOUT = {"replicas": 0, "strided": 1}
 XDT = {"f64": 0, "f32": 1, "bf16": 2}
 ENGINE = {"auto": 0, "simt": 1, "tensor": 2, "cluster": 3, "persistent": 4}
 MAX_MODES = 8
@@ -42,19 +43,19 @@ class cpd_config(ctypes.Structure):
         ("alpha", ctypes.c_double), ("eta", ctypes.c_double), ("b", ctypes.c_double),
         ("beta", ctypes.c_double), ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("engine", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
-        ("constraint", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("constraint", ctypes.c_int32), ("x_layout", ctypes.c_int32),
     ]
 
 
 class cpd_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int32),
                 ("fit_every", ctypes.c_int32), ("no_grouping", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("strided_above_mb", ctypes.c_int32)]
 
 
 class cpd_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("done", ctypes.c_int32), ("reached", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("iters", ctypes.c_int64), ("fit", ctypes.c_double),
+                ("layout", ctypes.c_int32), ("iters", ctypes.c_int64), ("fit", ctypes.c_double),
                 ("tol", ctypes.c_double), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
                 ("t_done", ctypes.c_double)]
 
@@ -94,6 +95,8 @@ def _load():
                        ctypes.POINTER(ctypes.c_uint64)],
         "cpd_poll": [P, ctypes.c_uint64, ctypes.POINTER(cpd_result), P],
         "cpd_server_wait": [P, ctypes.c_double],
+        "cpd_server_stats": [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
         "cpd_server_destroy": [P],
         "cpd_grad_variance": [P, I32, P, P, P],
         "cpd_autotune": [ctypes.POINTER(cpd_config), P, I32, P, I32, I64, ctypes.POINTER(cpd_config),
@@ -127,7 +130,7 @@ def _check(st: int) -> None:
 
 def make_config(dims, R, B, sampling="euclidean", step="adagrad", x_dtype="bf16", alpha=0.1,
                 eta=0.1, b=1e-12, beta=1.0, gamma=1.0, seed=0, engine="auto",
-                max_ctas=0, constraint="none") -> cpd_config:
+                max_ctas=0, constraint="none", x_layout="replicas") -> cpd_config:
     c = cpd_config()
     c.N, c.R, c.B = len(dims), int(R), int(B)
     c.sampling, c.step, c.x_dtype = SAMPLE[sampling], STEP[step], XDT[x_dtype]
@@ -138,7 +141,7 @@ def make_config(dims, R, B, sampling="euclidean", step="adagrad", x_dtype="bf16"
     c.engine = ENGINE[engine]
     c.max_ctas = int(max_ctas)
     c.constraint = CONSTRAINT[constraint]
-    c.reserved = 0
+    c.x_layout = LAYOUT[x_layout]
     return c
 
 
@@ -291,10 +294,11 @@ def cpd_tol_noalloc(dims, R: int, x_dtype: str, X: torch.Tensor, A: list, tol_ou
 
 
 def cpd_server_create(hbm_budget: int = 0, max_active: int = 0, fit_every: int = 0,
-                      grouping: bool = True):
+                      grouping: bool = True, strided_above_mb: int = 0):
     cfg = cpd_server_config()
     cfg.hbm_budget, cfg.max_active, cfg.fit_every = int(hbm_budget), int(max_active), int(fit_every)
     cfg.no_grouping = 0 if grouping else 1
+    cfg.strided_above_mb = int(strided_above_mb)
     srv = ctypes.c_void_p()
     _check(_lib.cpd_server_create(ctypes.byref(cfg), ctypes.byref(srv)))
     return srv
@@ -315,9 +319,17 @@ def cpd_poll(srv, ticket: int, A_out: list | None = None):
         msg = _lib.cpd_last_error().decode()
     else:
         msg = ""
-    d = {f: getattr(res, f) for f, _ in cpd_result._fields_ if f != "pad"}
+    d = {f: getattr(res, f) for f, _ in cpd_result._fields_}
     d["message"] = msg
     return st, d
+
+
+def cpd_server_stats(srv) -> dict:
+    """The server's budget, the bytes its requests hold, running and waiting requests."""
+    b, h = ctypes.c_size_t(), ctypes.c_size_t()
+    a, q = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.cpd_server_stats(srv, ctypes.byref(b), ctypes.byref(h), ctypes.byref(a), ctypes.byref(q)))
+    return {"budget": b.value, "held": h.value, "active": a.value, "queued": q.value}
 
 
 def cpd_server_wait(srv, timeout_s: float = 0.0) -> bool:

@@ -137,7 +137,10 @@ static cpd_status validate(const cpd_config *cfg)
     if (cfg->max_ctas < 0) return fail(CPD_EINVAL, "max_ctas must be >= 0");
     if (cfg->constraint != CPD_CONSTRAINT_NONE && cfg->constraint != CPD_CONSTRAINT_NONNEG)
         return fail(CPD_EINVAL, "unknown constraint");
-    if (cfg->reserved != 0) return fail(CPD_EINVAL, "reserved must be 0");
+    if (cfg->x_layout != CPD_LAYOUT_REPLICAS && cfg->x_layout != CPD_LAYOUT_STRIDED)
+        return fail(CPD_EINVAL, "unknown x_layout");
+    if (cfg->x_layout == CPD_LAYOUT_STRIDED && cfg->engine != 0 && cfg->engine != kEngineSimt)
+        return fail(CPD_EINVAL, "the strided x_layout runs on the CUDA-core engine (1)");
     if (cfg->engine < 0 || cfg->engine > 4) return fail(CPD_EINVAL, "unknown engine");
     if (cfg->engine == kEnginePersistent && !pers_supported(*cfg))
         return fail(CPD_EINVAL, "persistent engine needs BF16 tensors, R <= 64, Euclidean or uniform "
@@ -276,9 +279,13 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     P.constraint = g.constraint;
     P.alpha = g.alpha; P.eta = g.eta; P.b = g.b; P.beta = g.beta; P.gamma = g.gamma;
     P.seed = g.seed;
+    P.strided = g.x_layout == CPD_LAYOUT_STRIDED ? 1 : 0;
+    int64_t pre = 1;
     for (int k = 0; k < g.N; ++k) {
         P.dims[k] = g.dims[k];
-        P.ld[k] = round8(g.dims[k]);
+        P.ld[k] = P.strided ? g.dims[k] : round8(g.dims[k]);   // strided: mode-1 fibers I_1 apart
+        P.xpre[k] = pre;
+        pre *= g.dims[k];
         double J = 1.0;
         for (int m = 0; m < g.N; ++m)
             if (m != k) J *= (double)g.dims[m];
@@ -288,7 +295,9 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, c->device);
     c->sm_count = sm_count;
-    if (g.engine == 0) {
+    if (g.engine == 0 && P.strided) {
+        c->engine = kEngineSimt;
+    } else if (g.engine == 0) {
         int64_t imax = 0;
         for (int k = 0; k < g.N; ++k) imax = std::max<int64_t>(imax, g.dims[k]);
         const bool tc = g.x_dtype == CPD_BF16 && tc_supported(g.R, 128) && g.R >= 16;
@@ -304,12 +313,20 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     const size_t xb = (size_t)c->xbytes;
     const void *Xd = X;
     void *staging = nullptr;
-    if (x_loc == CPD_HOST) {
+    if (P.strided) {   // one copy of X, read in place by every mode
+        void *copy;
+        cudaError_t e = dmalloc(c, &copy, (size_t)total * xb);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor allocation");
+        CK(cudaMemcpyAsync(copy, X, total * xb, x_loc == CPD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                           s));
+        for (int k = 0; k < g.N; ++k) P.rep[k] = copy;
+    }
+    if (x_loc == CPD_HOST && !P.strided) {
         CK(cudaMallocAsync(&staging, total * xb, s));
         CK(cudaMemcpyAsync(staging, X, total * xb, cudaMemcpyHostToDevice, s));
         Xd = staging;
     }
-    for (int k = 0; k < g.N; ++k) {
+    for (int k = 0; k < g.N && !P.strided; ++k) {
         const size_t bytes = (size_t)(total / g.dims[k]) * P.ld[k] * xb;
         void *rep;
         cudaError_t e = dmalloc(c, &rep, bytes);
@@ -606,6 +623,7 @@ extern "C" cpd_status cpd_skrp(cpd_ctx *c, int32_t n, int64_t t0, int32_t K, int
 {
     if (!c || K < 1 || t0 < 0) return fail(CPD_EINVAL, "bad argument");
     if (c->fbytes != 4) return fail(CPD_EINVAL, "cpd_skrp takes float factors (F32 or BF16 tensors)");
+    if (c->Pf.strided) return fail(CPD_EINVAL, "cpd_skrp reads the mode-major replicas (x_layout 0)");
     if (n < 0 || n >= c->cfg.N) return fail(CPD_EINVAL, "mode out of range");
     if ((double)K * c->cfg.B > 2.0e9) return fail(CPD_EINVAL, "K B too large");
     cudaStream_t s = (cudaStream_t)stream;
@@ -908,7 +926,7 @@ extern "C" cpd_status cpd_describe(cpd_ctx *c, char *buf, size_t len)
                   "{\"engine\": \"%s\", \"rows_per_cta\": %d, \"fibers_per_cta\": %d, \"fiber_groups\": %d, "
                   "\"grad_grid\": %d, \"update_grid\": %d, \"grad_smem\": %zu, \"graph_chunk\": %d, "
                   "\"cluster\": %d, \"max_clusters\": %d, \"deferred_cdf\": %d, "
-                  "\"fit_pass\": \"%s\", \"xnorm2\": %.17g}",
+                  "\"fit_pass\": \"%s\", \"x_layout\": \"%s\", \"xnorm2\": %.17g}",
                   c->engine == kEnginePersistent       ? "persistent"
                   : c->engine == kEngineTensorCluster ? "cluster"
                   : c->engine == kEngineTensor        ? "tensor"
@@ -916,7 +934,7 @@ extern "C" cpd_status cpd_describe(cpd_ctx *c, char *buf, size_t len)
                   rb, fb, pf, c->grid_grad, c->grid_upd,
                   c->smem_grad, kGraphChunk, c->fbytes == 8 ? 1 : c->Pf.cs, c->max_clusters,
                   c->fbytes == 8 ? c->Pd.defer_cdf : c->Pf.defer_cdf, c->fit_tc ? "tensor" : "cuda_cores",
-                  c->xnorm2);
+                  (c->fbytes == 8 ? c->Pd.strided : c->Pf.strided) ? "strided" : "replicas", c->xnorm2);
     return CPD_OK;
 }
 
@@ -1169,12 +1187,12 @@ extern "C" cpd_status cpd_autotune(const cpd_config *cfg, const void *X, int x_l
         cand.push_back({cfg->engine, cfg->max_ctas});
     } else {
         for (int mc : {0, 16, 64}) cand.push_back({kEngineSimt, mc});
-        if (tc_ok) {
+        if (tc_ok && cfg->x_layout == CPD_LAYOUT_REPLICAS) {
             for (int mc : {0, 16, 64}) cand.push_back({kEngineTensor, mc});
             if (cs <= 8)
                 for (int m : {0, 4, 8, 12}) cand.push_back({kEngineTensorCluster, m * cs});
         }
-        if (pers_supported(*cfg))   // persistent cluster engine: the cluster size is the tile choice
+        if (pers_supported(*cfg) && cfg->x_layout == CPD_LAYOUT_REPLICAS)   // the cluster size is the tile choice
             for (int mc : {2, 4, 8, 16}) cand.push_back({kEnginePersistent, mc});
     }
     cudaStream_t s = (cudaStream_t)stream;

@@ -507,6 +507,25 @@ __device__ __forceinline__ bool cdfs_staged(const Problem<T> &P, int n, long lon
 
 template <class XT, class T>
 __device__ __forceinline__ T load_x(const XT *p) { return (T)to_float<XT>(*p); }
+
+// Element offset of the first entry of mode-n fiber j (Eq. (2) numbering) in
+// the storage the problem reads, and the distance between its entries: the
+// mode-n replica (fibers contiguous, ld[n] apart), or, with the strided
+// layout, X itself in column-major order, where the modes before n give the
+// low part of j and the entries of a fiber are I_1 ... I_{n-1} apart.
+template <class T>
+__device__ __forceinline__ long long fiber_start(const Problem<T> &P, int n, long long j)
+{
+    if (!P.strided) return j * P.ld[n];
+    const long long pre = P.xpre[n];
+    return (j % pre) + (j / pre) * pre * P.dims[n];
+}
+
+template <class T>
+__device__ __forceinline__ long long fiber_step(const Problem<T> &P, int n)
+{
+    return P.strided ? P.xpre[n] : 1;
+}
 template <>
 __device__ __forceinline__ double load_x<double, double>(const double *p) { return *p; }
 

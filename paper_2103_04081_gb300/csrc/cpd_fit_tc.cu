@@ -550,8 +550,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
 bool fit_tc_supported(const Problem<float> &P)
 {
     // fibers and tile coordinates stay below 2^31 (32-bit copy coordinates)
+    // and the copy's row stride (ld_1 entries) is a multiple of 16 bytes
     return P.x_dtype == CPD_BF16 && P.R >= 1 && P.R <= 64 && fit_tc_fibers(P) < (1LL << 31) - kFtM &&
-           encode_tiled() != nullptr;
+           P.ld[0] % 8 == 0 && encode_tiled() != nullptr;
 }
 
 size_t fit_tc_scratch_bytes(const Problem<float> &P)

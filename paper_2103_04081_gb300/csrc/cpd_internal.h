@@ -45,6 +45,11 @@ struct Problem {
     int cs;                   // CTAs per cluster (clustered tensor-core engine)
     int64_t dims[kMaxModes];
     int64_t ld[kMaxModes];    // fiber stride of replica k (elements, multiple of 8)
+    int strided;              // 1: rep[k] is the single column-major copy of X for
+                              // every k: fiber j of mode n starts at
+                              // (j mod xpre[n]) + (j div xpre[n]) xpre[n] I_n and its
+                              // entries are xpre[n] apart (Eq. (2) numbering)
+    int64_t xpre[kMaxModes];  // I_1 ... I_{n-1} (1 for the first mode)
     double Jn[kMaxModes];     // J_n = prod_{k != n} I_k, as a double
     ModeTile tile[kMaxModes];
     const void *rep[kMaxModes];

@@ -64,6 +64,19 @@ __device__ __forceinline__ void gather_rows(const XT *__restrict__ rep, long lon
     }
 }
 
+// The strided layout's gather: rows [r0, r0+rows) of the fibers starting at
+// start[f] with entries `step` apart, one entry per thread (consecutive
+// threads take consecutive rows of a fiber).
+template <class XT, class T>
+__device__ __forceinline__ void gather_rows_strided(const XT *__restrict__ x, long long step, const long long *start,
+                                                    int nf, int r0, int rows, int rb, T *sx)
+{
+    for (int e = threadIdx.x; e < nf * rows; e += blockDim.x) {
+        const int f = e / rows, i = e % rows;
+        sx[f * rb + i] = load_x<XT, T>(x + start[f] + (long long)(r0 + i) * step);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -120,7 +133,7 @@ __device__ __forceinline__ void grad_simt_body(const Problem<T> &P, int bid)
             j += (long long)row[k] * Jp;
             Jp *= P.dims[k];
         }
-        jcol[f] = j;
+        jcol[f] = P.strided ? fiber_start(P, n, j) : j;   // strided: the fiber's first entry
         if constexpr (sizeof(T) == 8)
             ss[f] = __ddiv_rn(1.0, __dmul_rn(__dmul_rn((double)P.B, P.Jn[n]), fiber_prob_staged(P, n, row, staged ? stage : nullptr)));
         else
@@ -142,7 +155,10 @@ __device__ __forceinline__ void grad_simt_body(const Problem<T> &P, int bid)
     __syncthreads();
 
     // 4. fiber gather from the mode-n replica (Alg. 1, X_(n)(:, F_n))
-    gather_rows<XT, T>(reinterpret_cast<const XT *>(P.rep[n]), P.ld[n], jcol, nf, r0, rows, rb, sx);
+    if (P.strided)
+        gather_rows_strided<XT, T>(reinterpret_cast<const XT *>(P.rep[n]), P.xpre[n], jcol, nf, r0, rows, rb, sx);
+    else
+        gather_rows<XT, T>(reinterpret_cast<const XT *>(P.rep[n]), P.ld[n], jcol, nf, r0, rows, rb, sx);
     __syncthreads();
 
     // 5. weighted residuals

@@ -50,24 +50,30 @@ double now_s()
     return std::chrono::duration<double>(clk::now() - t0).count();
 }
 
-// Device bytes a request may hold: the mode-major replicas, factors and their
-// state, the gradient partials (upper bound) and a fixed allowance.
+// Device bytes of a request's copy of X: the mode-major replicas, or the
+// single strided copy.
+double tensor_bytes(const cpd_config &g)
+{
+    const double xb = g.x_dtype == CPD_F64 ? 8 : (g.x_dtype == CPD_F32 ? 4 : 2);
+    double total = 1.0;
+    for (int k = 0; k < g.N; ++k) total *= (double)g.dims[k];
+    if (g.x_layout == CPD_LAYOUT_STRIDED) return total * xb;
+    double bytes = 0.0;
+    for (int k = 0; k < g.N; ++k) bytes += total / (double)g.dims[k] * (double)((g.dims[k] + 7) / 8 * 8) * xb;
+    return bytes;
+}
+
+// Device bytes a request may hold: its copy of X, factors and their state,
+// the gradient partials (upper bound) and a fixed allowance.
 size_t estimate_bytes(const cpd_config &g)
 {
-    const size_t xb = g.x_dtype == CPD_F64 ? 8 : (g.x_dtype == CPD_F32 ? 4 : 2);
     const size_t fb = g.x_dtype == CPD_F64 ? 8 : 4;
-    double total = 1.0;
     int64_t imax = 0, isum = 0;
     for (int k = 0; k < g.N; ++k) {
-        total *= (double)g.dims[k];
         imax = std::max<int64_t>(imax, g.dims[k]);
         isum += g.dims[k];
     }
-    double bytes = 0.0;
-    for (int k = 0; k < g.N; ++k) {
-        const double ld = (double)((g.dims[k] + 7) / 8 * 8);
-        bytes += total / (double)g.dims[k] * ld * (double)xb;
-    }
+    double bytes = tensor_bytes(g);
     bytes += (double)isum * g.R * (fb + 8) + (double)isum * 16;
     bytes += 608.0 * g.R * (double)imax * fb;   // partial slabs, bound of the tile chooser
     bytes += 8.0 * 1024 * 1024;
@@ -294,13 +300,15 @@ static void worker_loop(cpd_server *srv)
             }
         }
         for (auto &r : admit) {
-            {
-                std::lock_guard<std::mutex> lock(srv->mu);
-                r->res.t_start = now_s();
-            }
             cpd_status st = CPD_OK;
             if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess) st = CPD_ECUDA;
             if (st == CPD_OK) st = cpd_init(&r->cfg, r->X, r->x_loc, r->A0.data(), r->a0_loc, r->stream, &r->ctx);
+            {
+                // cpd_init has copied X and A0 (it synchronises its stream):
+                // from here on the caller may release them
+                std::lock_guard<std::mutex> lock(srv->mu);
+                r->res.t_start = now_s();
+            }
             if (st != CPD_OK) {
                 finish(srv, r, st);
                 continue;
@@ -378,9 +386,9 @@ extern "C" cpd_status cpd_server_create(const cpd_server_config *cfg, cpd_server
     }
     auto *srv = new cpd_server();
     if (cfg) srv->cfg = *cfg;
-    if (srv->cfg.reserved || srv->cfg.no_grouping < 0 || srv->cfg.no_grouping > 1) {
+    if (srv->cfg.strided_above_mb < 0 || srv->cfg.no_grouping < 0 || srv->cfg.no_grouping > 1) {
         delete srv;
-        set_error("reserved must be 0 and no_grouping 0 or 1");
+        set_error("strided_above_mb must be >= 0 and no_grouping 0 or 1");
         return CPD_EINVAL;
     }
     if (cudaGetDevice(&srv->device) != cudaSuccess) {
@@ -417,6 +425,16 @@ extern "C" cpd_status cpd_submit(cpd_server *srv, const cpd_config *cfg, const v
     r->stop_fit = stop_fit;
     r->max_iters = max_iters;
     r->bytes = estimate_bytes(*cfg);
+    const double limit = srv->cfg.strided_above_mb > 0 ? (double)((size_t)srv->cfg.strided_above_mb << 20) : 1e300;
+    if (r->cfg.x_layout == CPD_LAYOUT_REPLICAS && (r->bytes > srv->budget || tensor_bytes(r->cfg) > limit)) {
+        // the replicas would not fit: one strided copy of X on the CUDA-core
+        // engine instead (decided from the request and the configuration)
+        r->cfg.x_layout = CPD_LAYOUT_STRIDED;
+        r->cfg.engine = 1;
+        r->cfg.max_ctas = 0;
+        r->bytes = estimate_bytes(r->cfg);
+    }
+    r->res.layout = r->cfg.x_layout;
     if (r->bytes > srv->budget) {
         set_error("request needs " + std::to_string(r->bytes) + " bytes, over the server budget");
         return CPD_ENOMEM;
@@ -429,6 +447,21 @@ extern "C" cpd_status cpd_submit(cpd_server *srv, const cpd_config *cfg, const v
     ++srv->unfinished;
     srv->cv_work.notify_all();
     *ticket = r->ticket;
+    return CPD_OK;
+}
+
+extern "C" cpd_status cpd_server_stats(cpd_server *srv, size_t *budget, size_t *held, int32_t *active,
+                                       int32_t *queued)
+{
+    if (!srv) {
+        set_error("NULL server");
+        return CPD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (budget) *budget = srv->budget;
+    if (held) *held = srv->used;
+    if (active) *active = (int32_t)srv->running;
+    if (queued) *queued = (int32_t)srv->queue.size();
     return CPD_OK;
 }
 

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kThreads) k_variance(const Problem<T> P, int n
         __syncthreads();
         if (own) {
             for (int f = 0; f < nf; ++f) {
-                const float x = xval<XT>(rep[(jb + f) * P.ld[n] + row]);
+                const float x = xval<XT>(rep[fiber_start(P, n, jb + f) + row * fiber_step(P, n)]);
                 float res = -x;
                 for (int r = 0; r < R; ++r) res = fmaf(sA[r * kVarRows + threadIdx.x], sz[f * R + r], res);
                 if (sw[f] == 0.0) continue;   // never drawn

@@ -120,6 +120,36 @@ def cp_tensor(A: list[torch.Tensor], noise: float, seed: int, x_dtype: str = "f6
     return out
 
 
+def cp_tensor_streamed(A: list[torch.Tensor], noise: float, seed: int, x_dtype: str = "bf16",
+                       chunk_entries: int = 1 << 26, out: torch.Tensor | None = None) -> torch.Tensor:
+    """The model of ``cp_tensor`` in one pass, for the serving stream's tensors
+    (up to 400^4 entries), generated on the device as requests are admitted:
+    ||[[A]]||^2 comes from the factors' Gram matrices (the sum of the entries
+    of their Hadamard product), and the noise is scaled by its expected norm
+    sqrt(#entries) instead of its measured one, so no entry is formed twice.
+    The noise of chunk c comes from a generator seeded with (seed, c).
+    ``out``, if given, is a flat tensor of the storage dtype to fill."""
+    device = A[0].device
+    A = [a.to(torch.float32) for a in A]
+    G = torch.ones(A[0].shape[1], A[0].shape[1], dtype=torch.float64, device=device)
+    for a in A:
+        G = G * (a.double().T @ a.double())
+    I0 = A[0].shape[0]
+    J = math.prod(a.shape[0] for a in A[1:])
+    scale = noise * math.sqrt(float(G.sum())) / math.sqrt(I0 * J) if noise else 0.0
+    if out is None:
+        out = torch.empty(I0 * J, dtype=_STORE[x_dtype], device=device)
+    cols = max(1, chunk_entries // I0)
+    for c, j0 in enumerate(range(0, J, cols)):
+        j1 = min(J, j0 + cols)
+        xt = _krp_rows(A[1:], j0, j1) @ A[0].T
+        if scale:
+            xt += scale * torch.randn(xt.shape, generator=_gen(seed * 1_000_003 + c, device), dtype=torch.float32,
+                                      device=device)
+        out[j0 * I0: j1 * I0] = xt.reshape(-1).to(out.dtype)
+    return out
+
+
 def to_numpy_fortran(x_flat: torch.Tensor, dims) -> np.ndarray:
     """Host copy of a flat column-major tensor as a Fortran-ordered ndarray.
 
@@ -176,11 +206,10 @@ def serve_requests(n: int, rate: float = 200.0, seed: int = 0) -> list[dict]:
 
     Arrivals form a Poisson process of ``rate`` per second (exponential gaps
     from ``seed``; the first request arrives at 0). Request i draws, from its
-    own generator (seed, i): 3 or 4 modes with equal odds, mode sizes uniform
-    in [50, 400] for 3-way tensors and in [50, 90] for 4-way ones (so that no
-    4-way tensor is larger than the largest 3-way one, 90^4 ~ 400^3), and a
-    rank uniform in {5, ..., 32}. Its data, initial factors and sampling use
-    seed i.
+    own generator (seed, i): 3 or 4 modes with equal odds, every mode size
+    uniform in [50, 400], and a rank uniform in {5, ..., 32}. Its data,
+    initial factors and sampling use seed i. A 4-way request holds 225^4
+    entries on average (5 GB in BF16) and up to 400^4 (51 GB).
     """
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, n)
@@ -189,8 +218,7 @@ def serve_requests(n: int, rate: float = 200.0, seed: int = 0) -> list[dict]:
     for i in range(n):
         r = np.random.default_rng([seed, i])
         N = 3 if r.random() < 0.5 else 4
-        hi = 400 if N == 3 else 90
-        dims = tuple(int(v) for v in r.integers(50, hi + 1, N))
+        dims = tuple(int(v) for v in r.integers(50, 401, N))
         R = int(r.integers(5, 33))
         out.append(dict(i=i, arrival=float(arrive[i]), N=N, dims=dims, R=R, noise=1e-2,
                         data_seed=i, init_seed=i, sample_seed=i))

@@ -60,9 +60,9 @@ def test_invalid_configs_rejected_on_host(cpd, kw, msg):
     assert msg in err
 
 
-def test_unknown_constraint_and_reserved_rejected(cpd):
+def test_unknown_constraint_and_layout_rejected(cpd):
     import torch
-    for field, value, msg in (("constraint", 7, "constraint"), ("reserved", 1, "reserved"),
+    for field, value, msg in (("constraint", 7, "constraint"), ("x_layout", 2, "x_layout"),
                               ("max_ctas", -1, "max_ctas")):
         cfg = cpd.make_config(dims=(2, 2, 2), R=1, B=1)
         setattr(cfg, field, value)
@@ -88,7 +88,7 @@ def test_server_group_and_variance_reject_bad_arguments_on_host(cpd):
     """Argument checks that come before any device work."""
     import ctypes as C
     cfg = cpd.cpd_server_config()
-    cfg.reserved = 1
+    cfg.strided_above_mb = -1
     srv = C.c_void_p()
     assert cpd.lib().cpd_server_create(C.byref(cfg), C.byref(srv)) == cpd.EINVAL
     cfg = cpd.cpd_server_config()

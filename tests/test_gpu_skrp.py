@@ -111,3 +111,40 @@ def test_skrp_full_size_c4(cpd, orc):
     dec.sgd_iters(30)
     check_batches(cpd, orc, dec, xb, "bf16", w["dims"], w["R"], w["B"], "euclidean", range(3), K=1)
     dec.close()
+
+
+@pytest.mark.parametrize("dims,R,B", [((200, 150, 100), 24, 256), ((64, 50, 40, 30), 16, 96)])
+def test_gradients_match_oracle_per_batch(cpd, orc, dims, R, B):
+    """cpd_gradients: K mini-batch gradients of mode n at the current factors
+    (persistent engine, batches on concurrent clusters), each against the
+    oracle's Eq. (11) for the same draws: whole-matrix and row-scaled errors
+    within the tensor-core tolerances of the teacher-forced tests. The
+    context's state does not move."""
+    from helpers import TOL, grad_row_scale
+    _, X, A0 = make_problem(dims, R, x_dtype="bf16", lognormal_rows=True)
+    dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype="bf16",
+                            sampling="euclidean", step="adagrad", seed=17, engine="persistent")
+    dec.sgd_iters(12)
+    t_before = dec.t
+    A = [a.double().numpy() for a in dec.factors()]
+    xb = oracle_xbuf(X)
+    ocfg = orc.Config(dims=tuple(dims), R=R, B=B, sampling="euclidean", step="adagrad", x_dtype="bf16", seed=17)
+    tol = TOL["bf16_tensor"]
+    K, t0 = 3, 500
+    for n in range(len(dims)):
+        G = torch.empty(K, dims[n], R, dtype=torch.float32, device="cuda")
+        cpd.cpd_gradients(dec.ctx, n, t0, K, G)
+        torch.cuda.synchronize()
+        G = G.cpu().double().numpy()
+        for b in range(K):
+            s = orc.sample_batch(ocfg, n, t0 + b, A, xbuf=xb, want_fibers=False)
+            st, p, Go = orc.gradient_for_batch(ocfg, n, s["idx"], xb, A)
+            assert st == orc.OK
+            np.testing.assert_array_equal(p, s["p"])
+            eg = np.linalg.norm(G[b] - Go) / np.linalg.norm(Go)
+            sc = grad_row_scale(dims, n, s["idx"], s["p"], A, xb, "bf16", B)
+            er = float(np.max(np.linalg.norm(G[b] - Go, axis=1) / sc))
+            assert eg < tol["G"] and er < tol["G_row"], (n, b, eg, er)
+    assert dec.t == t_before
+    assert all(np.array_equal(a, b.double().numpy()) for a, b in zip(A, dec.factors()))
+    dec.close()
