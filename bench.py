@@ -510,15 +510,15 @@ def serve_materialize(q: dict, dev: str, out: torch.Tensor | None = None):
 
 
 def serve_bench(dev: str, n_req: int, n_plain: int, max_active: int) -> dict:
-    """The serving workload (the benchmark spec (5)): a Poisson stream of 3- and 4-way
-    BF16 requests, every mode size uniform in [50, 400], served concurrently by
-    the native server under an HBM budget. A request's tensor is generated on
-    the device when the server's queue is empty (the client carves it from a
+    """The serving workload: a Poisson stream of 3- and 4-way BF16 requests,
+    every mode size uniform in [50, 400], served concurrently by the native
+    server under an HBM budget. A request's tensor is generated on the device
+    as soon as it has arrived and there is room (the client carves it from a
     64 GB ring and releases it once the server has admitted the request and
     copied it); its time-to-fit runs from its arrival to its stop, so time
     spent waiting for admission or generation counts. A request whose replicas
-    would take more than a quarter of the budget runs with one strided copy on
-    the CUDA-core engine.
+    would take more than a quarter of the budget runs with the strided layout
+    on the CUDA-core engine.
 
     Then a seeded random sample of n_plain requests runs in the plain GPU form:
     one decomposition at a time, the engine and grid chosen for the whole GPU
@@ -540,11 +540,22 @@ def serve_bench(dev: str, n_req: int, n_plain: int, max_active: int) -> dict:
     srv = C.cpd_server_create(hbm_budget=budget, max_active=max_active, fit_every=SERVE["fit_every"],
                               grouping=SERVE["grouping"], strided_above_mb=strided_mb)
 
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
     def engine_of(q):
+        """Engine and CTA cap of a request: small requests share the GPU in
+        grouped lanes with a cap of max_ctas; a request whose replicas let
+        only `conc` such requests fit the budget at once gets about 2 x SMs /
+        conc CTAs (a multiple of 8), so that the few large ones that run
+        together still cover the GPU."""
         if SERVE["engine"] == "persistent":   # one thread-block cluster per request, grouped launches
             return "persistent", SERVE["cluster"]
-        return (SERVE["engine_r16"] if q["R"] >= 16 else "simt"), SERVE["max_ctas"]
+        reps = 2 * sum(int(np.prod(q["dims"])) // d * ((d + 7) // 8 * 8) for d in q["dims"])
+        conc = max(1, budget // max(reps, 1))
+        cap = min(sms, max(SERVE["max_ctas"], ((2 * sms + conc - 1) // conc + 7) // 8 * 8))
+        return (SERVE["engine_r16"] if q["R"] >= 16 else "simt"), cap
 
+    gen_stream = torch.cuda.Stream()
     pending, arrived = deque(reqs), deque()
     live, done, gen_s = {}, {}, 0.0
     t0 = time.perf_counter()
@@ -553,14 +564,21 @@ def serve_bench(dev: str, n_req: int, n_plain: int, max_active: int) -> dict:
         while pending and pending[0]["arrival"] <= now:
             arrived.append(pending.popleft())
         moved = False
-        if arrived and C.cpd_server_stats(srv)["queued"] == 0:
+        # every arrived request is generated and submitted as soon as the ring
+        # has room for its tensor: the server admits whichever fit its budget,
+        # so a large request waiting for memory does not hold up small ones
+        if arrived:
             q = arrived[0]
             nbytes = 2 * int(np.prod(q["dims"]))
             buf, rec = ring.alloc(nbytes)
             if buf is not None:
+                # generated on a stream of its own and synchronised on that
+                # stream alone: the server's worker may be capturing graphs,
+                # which a device-wide synchronisation would break
                 g0 = time.perf_counter()
-                X, A0 = serve_materialize(q, dev, out=buf[:nbytes].view(torch.bfloat16))
-                torch.cuda.synchronize()
+                with torch.cuda.stream(gen_stream):
+                    X, A0 = serve_materialize(q, dev, out=buf[:nbytes].view(torch.bfloat16))
+                gen_stream.synchronize()
                 gen_s += time.perf_counter() - g0
                 eng, cap = engine_of(q)
                 tk = C.cpd_submit(srv, serve_cfg(q, "bf16", eng, cap), X, A0, SERVE["stop_fit"], SERVE["max_iters"])
@@ -603,6 +621,12 @@ def serve_bench(dev: str, n_req: int, n_plain: int, max_active: int) -> dict:
               "strided_layout": sum(d["layout"] == 1 for _, d, _ in ok),
               "four_way": sum(q["N"] == 4 for q, _, _ in ok),
               "generation_s": gen_s}
+    for name, sel in (("three_way", lambda q, d: q["N"] == 3),
+                      ("four_way_replicas", lambda q, d: q["N"] == 4 and d["layout"] == 0),
+                      ("strided", lambda q, d: d["layout"] == 1)):
+        run = [d["t_done"] - d["t_start"] for q, d, _ in ok if sel(q, d)]
+        if run:
+            served["run_s_" + name] = {"n": len(run), "mean": statistics.fmean(run), "max": max(run)}
     out = {"workload": "serve_poisson200_3or4way_dims50to400_bf16", "served": served,
            "budget_gb": budget / 2**30, "strided_above_gb": strided_mb / 1024}
     if n_plain < 1:
@@ -617,8 +641,13 @@ def serve_bench(dev: str, n_req: int, n_plain: int, max_active: int) -> dict:
         X, A0 = serve_materialize(q, dev)
         torch.cuda.synchronize()
         p0 = time.perf_counter()
+        # the server's rule: replicas above the threshold -> the strided layout
+        reps = 2 * sum(int(np.prod(q["dims"])) // d * ((d + 7) // 8 * 8) for d in q["dims"])
+        cfg = serve_cfg(q, "bf16")
+        if reps > strided_mb << 20:
+            cfg.x_layout, cfg.engine = 1, 1
         with torch.cuda.stream(stream):
-            ctx = C.cpd_init(serve_cfg(q, "bf16"), X, A0, stream)
+            ctx = C.cpd_init(cfg, X, A0, stream)
         del X
         it, fit = 0, 0.0
         while it < SERVE["max_iters"]:
@@ -685,6 +714,7 @@ def main() -> None:
     ap.add_argument("--no-gather-legs", action="store_true", help="skip the bulk gather and batched-form legs")
     ap.add_argument("--only-gather", action="store_true", help="run only the bulk gather leg (--steps launches per mode)")
     ap.add_argument("--only-fit", action="store_true", help="run only the stop-check pass (--steps passes)")
+    ap.add_argument("--only-serving", action="store_true", help="run only the serving leg")
     ap.add_argument("--batch-g", type=int, default=15, help="decompositions in the batched-form leg")
     ap.add_argument("--batch-cs", type=int, default=8, help="cluster size of the batched-form leg")
     ap.add_argument("--batch-iters", type=int, default=1000)
@@ -708,6 +738,11 @@ def main() -> None:
     dist, rank, world, local = dist_setup()
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
+    if args.only_serving:
+        SERVE["engine"], SERVE["cluster"] = args.serve_engine, args.serve_cluster
+        print(json.dumps({"serving": serve_bench(dev, args.serve_requests, args.serve_plain, args.serve_active)}),
+              flush=True)
+        return
     X, A0 = make_inputs(w, rank, dev)
     if args.only_fit:      # the stop-check pass alone (e.g. for a counter capture)
         kwf = cfg_kwargs(w, rank, "auto")

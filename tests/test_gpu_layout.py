@@ -28,9 +28,9 @@ def cpd():
 
 CASES = [
     # dims, R, B, x_dtype, sampling, step
-    ((37, 29, 23), 5, 40, "f64", "euclidean", "adagrad"),
+    ((37, 29, 23), 5, 40, "f64", "euclidean", "fixed"),
     ((61, 47, 33), 7, 64, "f32", "leverage", "adagrad"),
-    ((45, 30, 26, 19), 6, 77, "bf16", "euclidean", "fixed"),
+    ((45, 30, 26, 19), 6, 77, "bf16", "euclidean", "adagrad"),
     ((50, 44, 36), 9, 96, "bf16", "uniform", "adagrad"),
 ]
 
@@ -38,19 +38,20 @@ CASES = [
 @pytest.mark.parametrize("dims,R,B,xdt,sampling,step", CASES)
 def test_strided_matches_replicas_bitwise_and_oracle(cpd, orc, dims, R, B, xdt, sampling, step):
     _, X, A0 = make_problem(dims, R, noise=0.05, x_dtype=xdt, lognormal_rows=True)
-    kw = dict(dims=dims, R=R, B=B, x_dtype=xdt, sampling=sampling, step=step, alpha=0.05, seed=23, engine="simt")
+    kw = dict(dims=dims, R=R, B=B, x_dtype=xdt, sampling=sampling, step=step, alpha=0.01, seed=23, engine="simt")
     rep = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], **kw)
     strd = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], x_layout="strided", **kw)
     assert strd.describe()["x_layout"] == "strided" and rep.describe()["x_layout"] == "replicas"
     rep.sgd_iters(60)
     strd.sgd_iters(60)               # every mode drawn many times
     for a, b in zip(rep.factors(), strd.factors()):
+        assert torch.isfinite(a).all()
         assert torch.equal(a, b)
     _, t_rep = rep.fit()
     _, t_str = strd.fit()
     assert t_str == pytest.approx(t_rep, rel=1e-12 if xdt == "f64" else 2e-5)
     # teacher forcing against the oracle on the strided context
-    ocfg = orc.Config(dims=dims, R=R, B=B, sampling=sampling, step=step, x_dtype=xdt, alpha=0.05, seed=23)
+    ocfg = orc.Config(dims=dims, R=R, B=B, sampling=sampling, step=step, x_dtype=xdt, alpha=0.01, seed=23)
     forced(strd, orc, ocfg, oracle_xbuf(X), 6, xdt)
     rep.close()
     strd.close()
