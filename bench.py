@@ -764,8 +764,9 @@ def main() -> None:
     if not args.no_autotune and args.engine == "auto" and args.max_ctas == 0:
         best, rate = C.cpd_autotune(C.make_config(**kw), X, [a.to(dev) for a in A0], iters=300, stream=stream)
         tuned = {"engine": {1: "simt", 2: "tensor", 3: "cluster", 4: "persistent"}[best.engine], "max_ctas": best.max_ctas,
-                 "tuning_iters_per_s": rate}
+                 "tile_rows": best.tile_rows, "tile_fibers": best.tile_fibers, "tuning_iters_per_s": rate}
         kw["engine"], kw["max_ctas"] = tuned["engine"], tuned["max_ctas"]
+        kw["tile_rows"], kw["tile_fibers"] = tuned["tile_rows"], tuned["tile_fibers"]
     with torch.cuda.stream(stream):
         dec = C.Decomposition(X, [a.to(dev) for a in A0], stream=stream, **kw)
     desc = dec.describe()

@@ -87,9 +87,11 @@ enum {
 typedef enum {
     CPD_LAYOUT_REPLICAS = 0,    /* one mode-major replica per mode: every mode-n
                                    fiber contiguous (N copies of X)             */
-    CPD_LAYOUT_STRIDED = 1      /* one copy of X in its own column-major layout:
-                                   a mode-n fiber (Eq. (2)) is read with stride
-                                   I_1 ... I_{n-1}; CUDA-core engine only       */
+    CPD_LAYOUT_STRIDED = 1      /* the mode-1 replica alone (X column-major, the
+                                   first mode padded to a multiple of 8): a
+                                   mode-n fiber (Eq. (2)) is read from it with
+                                   stride ld_1 I_2 ... I_{n-1}; CUDA-core engine
+                                   only                                         */
 } cpd_layout;
 
 typedef struct {
@@ -124,8 +126,18 @@ typedef struct {
                            of the batch fixes the summation order of the
                            gradient partials.                                   */
     int32_t constraint; /* CPD_CONSTRAINT_*                                     */
-    int32_t x_layout;   /* CPD_LAYOUT_*: replicas (0) or a single strided copy
-                           (1, N times less memory, slower gathers for n > 1)   */
+    int32_t x_layout;   /* CPD_LAYOUT_*: replicas (0) or the mode-1 replica alone
+                           (1, N times less memory, strided gathers for n > 1)  */
+    int32_t tile_rows;  /* rows of A^(n) per gradient CTA (0 = chosen from the
+                           shape and max_ctas). CUDA-core engine: a multiple of
+                           8 in [8, 512]; tensor-core engines: 0 or 128 (the
+                           MMA's M); persistent engine: 0.                      */
+    int32_t tile_fibers; /* sampled fibers per gradient CTA / fiber group (0 =
+                           chosen). CUDA-core engine: [1, B]; tensor-core
+                           engines: a multiple of 16 (the MMA's K) in [16, 128]
+                           (engine 2) or [16, 256] (engine 3); persistent: 0.
+                           Like max_ctas, part of the arithmetic: the fiber
+                           groups fix the summation order.                      */
 } cpd_config;
 
 typedef struct cpd_ctx cpd_ctx;
@@ -438,17 +450,20 @@ cpd_status cpd_server_destroy(cpd_server *srv);
 cpd_status cpd_destroy(cpd_ctx *ctx);
 
 /*
- * cpd_autotune -- choose the gradient engine and CTA cap for a problem by
- * timing. The paper has no counterpart: the launch shape is this library's
- * choice, and it fixes the summation order of the gradient, so it is made
- * once, explicitly, and handed back as a configuration. Runs built from
- * `best` are reproducible; only the choice itself depends on timing.
+ * cpd_autotune -- choose the gradient engine, CTA cap and tile shape for a
+ * problem by timing. The paper has no counterpart: the launch shape is this
+ * library's choice, and it fixes the summation order of the gradient, so it
+ * is made once, explicitly, and handed back as a configuration. Runs built
+ * from `best` are reproducible; only the choice itself depends on timing.
  *  cfg, X, x_loc, A0, a0_loc: as for cpd_init. If cfg->engine != 0 only
- *    that engine and cfg->max_ctas are timed; otherwise every applicable
- *    engine (CUDA cores; per-CTA and cluster tensor cores for BF16 tensors
- *    with R <= 64) with a few CTA caps.
+ *    that engine is timed, at cfg->max_ctas, over its tile shapes; otherwise
+ *    every applicable engine (CUDA cores; per-CTA and cluster tensor cores
+ *    for BF16 tensors with R <= 64; the persistent cluster engine where it
+ *    applies) with a few CTA caps (cluster sizes) and tile shapes (rows and
+ *    fibers per CTA; fibers per fiber group).
  *  iters: timed iterations per candidate (after iters / 4 warm-up ones).
- *  best: receives cfg with engine and max_ctas set to the fastest candidate;
+ *  best: receives cfg with engine, max_ctas, tile_rows and tile_fibers set to
+ *    the fastest candidate;
  *  best_iters_per_s (may be NULL): its measured rate.
  * Creates and destroys one context per candidate on `stream` (device-wide
  * synchronisation). Errors: those of cpd_init for cfg itself; CPD_ECUDA if

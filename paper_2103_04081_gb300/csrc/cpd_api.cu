@@ -142,6 +142,18 @@ static cpd_status validate(const cpd_config *cfg)
     if (cfg->x_layout == CPD_LAYOUT_STRIDED && cfg->engine != 0 && cfg->engine != kEngineSimt)
         return fail(CPD_EINVAL, "the strided x_layout runs on the CUDA-core engine (1)");
     if (cfg->engine < 0 || cfg->engine > 4) return fail(CPD_EINVAL, "unknown engine");
+    if (cfg->tile_rows < 0 || cfg->tile_fibers < 0 || cfg->tile_fibers > cfg->B)
+        return fail(CPD_EINVAL, "tile_rows and tile_fibers must be >= 0, tile_fibers <= B");
+    if (cfg->tile_rows && (cfg->tile_rows % 8 || cfg->tile_rows > 512))
+        return fail(CPD_EINVAL, "tile_rows must be a multiple of 8 in [8, 512]");
+    if (cfg->engine == kEnginePersistent && (cfg->tile_rows || cfg->tile_fibers))
+        return fail(CPD_EINVAL, "the persistent engine takes no tile_rows / tile_fibers");
+    if ((cfg->engine == kEngineTensor || cfg->engine == kEngineTensorCluster) &&
+        ((cfg->tile_rows && cfg->tile_rows != 128) ||
+         (cfg->tile_fibers && (cfg->tile_fibers % 16 ||
+                               cfg->tile_fibers > (cfg->engine == kEngineTensor ? 128 : 256)))))
+        return fail(CPD_EINVAL, "tensor-core engines: tile_rows 0 or 128, tile_fibers a multiple of 16 "
+                                "up to 128 (engine 2) or 256 (engine 3)");
     if (cfg->engine == kEnginePersistent && !pers_supported(*cfg))
         return fail(CPD_EINVAL, "persistent engine needs BF16 tensors, R <= 64, Euclidean or uniform "
                                 "sampling, sum of the I_k <= 4096 and ceil(I_max / 128) row tiles in tensor memory");
@@ -252,6 +264,10 @@ static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
             else P.rb = std::max(8, P.rb / 2);
         }
     }
+    // an explicit tile shape (validated per engine; its shared memory is
+    // checked after the choice)
+    if (g.tile_rows && c->engine == kEngineSimt) P.rb = (int)std::min<int64_t>(g.tile_rows, round8(imax));
+    if (g.tile_fibers) P.fb = g.tile_fibers;
     P.pf = (g.B + P.fb - 1) / P.fb;
     int maxpr = 0;
     for (int k = 0; k < g.N; ++k) {
@@ -280,12 +296,12 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     P.alpha = g.alpha; P.eta = g.eta; P.b = g.b; P.beta = g.beta; P.gamma = g.gamma;
     P.seed = g.seed;
     P.strided = g.x_layout == CPD_LAYOUT_STRIDED ? 1 : 0;
-    int64_t pre = 1;
+    int64_t q = 1;
     for (int k = 0; k < g.N; ++k) {
         P.dims[k] = g.dims[k];
-        P.ld[k] = P.strided ? g.dims[k] : round8(g.dims[k]);   // strided: mode-1 fibers I_1 apart
-        P.xpre[k] = pre;
-        pre *= g.dims[k];
+        P.ld[k] = round8(g.dims[k]);
+        P.xq[k] = q;                        // prod of dims[1 .. k-1]
+        if (k > 0) q *= g.dims[k];
         double J = 1.0;
         for (int m = 0; m < g.N; ++m)
             if (m != k) J *= (double)g.dims[m];
@@ -306,6 +322,11 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
         c->engine = g.engine;
     }
     choose_tiles(c, P, sm_count);
+    if (g.tile_rows || g.tile_fibers) {   // an explicit tile shape must fit the engine
+        const size_t lim = c->engine == kEngineSimt ? 200 * 1024 : 220 * 1024;
+        if (c->smem_grad > lim || (c->engine == kEngineTensor && P.fb > 128))
+            return fail(CPD_EINVAL, "tile_rows / tile_fibers: the tile does not fit the engine's shared memory");
+    }
 
     // Tensor replicas (one per mode), built from a device copy of X.
     int64_t total = 1;
@@ -313,20 +334,13 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     const size_t xb = (size_t)c->xbytes;
     const void *Xd = X;
     void *staging = nullptr;
-    if (P.strided) {   // one copy of X, read in place by every mode
-        void *copy;
-        cudaError_t e = dmalloc(c, &copy, (size_t)total * xb);
-        if (e != cudaSuccess) return cuda_fail(e, "tensor allocation");
-        CK(cudaMemcpyAsync(copy, X, total * xb, x_loc == CPD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                           s));
-        for (int k = 0; k < g.N; ++k) P.rep[k] = copy;
-    }
-    if (x_loc == CPD_HOST && !P.strided) {
+    if (x_loc == CPD_HOST) {
         CK(cudaMallocAsync(&staging, total * xb, s));
         CK(cudaMemcpyAsync(staging, X, total * xb, cudaMemcpyHostToDevice, s));
         Xd = staging;
     }
-    for (int k = 0; k < g.N && !P.strided; ++k) {
+    // the strided layout keeps the mode-1 replica alone and reads every mode from it
+    for (int k = 0; k < (P.strided ? 1 : g.N); ++k) {
         const size_t bytes = (size_t)(total / g.dims[k]) * P.ld[k] * xb;
         void *rep;
         cudaError_t e = dmalloc(c, &rep, bytes);
@@ -342,6 +356,7 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
         }
         P.rep[k] = rep;
     }
+    for (int k = 1; k < g.N && P.strided; ++k) P.rep[k] = P.rep[0];
     if (staging) CK(cudaFreeAsync(staging, s));
 
     // Factors, AdaGrad state, distributions.
@@ -1182,19 +1197,42 @@ extern "C" cpd_status cpd_autotune(const cpd_config *cfg, const void *X, int x_l
     for (int k = 0; k < cfg->N; ++k) imax = std::max<int64_t>(imax, cfg->dims[k]);
     const bool tc_ok = cfg->x_dtype == CPD_BF16 && tc_supported(cfg->R, 128);
     const int cs = (int)((imax + 127) / 128);
-    std::vector<std::pair<int, int>> cand;   // (engine, max_ctas)
-    if (cfg->engine != 0) {
-        cand.push_back({cfg->engine, cfg->max_ctas});
-    } else {
-        for (int mc : {0, 16, 64}) cand.push_back({kEngineSimt, mc});
-        if (tc_ok && cfg->x_layout == CPD_LAYOUT_REPLICAS) {
-            for (int mc : {0, 16, 64}) cand.push_back({kEngineTensor, mc});
-            if (cs <= 8)
-                for (int m : {0, 4, 8, 12}) cand.push_back({kEngineTensorCluster, m * cs});
-        }
-        if (pers_supported(*cfg) && cfg->x_layout == CPD_LAYOUT_REPLICAS)   // the cluster size is the tile choice
-            for (int mc : {2, 4, 8, 16}) cand.push_back({kEnginePersistent, mc});
+    // candidates: (engine, max_ctas, tile_rows, tile_fibers); 0 = the tile
+    // chooser's own choice for that cap
+    struct Cand {
+        int engine, max_ctas, rows, fibers;
+    };
+    std::vector<Cand> cand;
+    const bool fixed = cfg->engine != 0;
+    auto want = [&](int e) { return !fixed || cfg->engine == e; };
+    if (want(kEngineSimt))
+        for (int mc : {0, 16, 64})
+            for (int rows : {0, 32, 128})
+                for (int fib : {0, 32})
+                    if (fib <= cfg->B) cand.push_back({kEngineSimt, fixed ? cfg->max_ctas : mc, rows, fib});
+    if (tc_ok && cfg->x_layout == CPD_LAYOUT_REPLICAS) {
+        if (want(kEngineTensor))
+            for (int mc : {0, 16, 64})
+                for (int fib : {0, 32, 64})
+                    if (fib <= cfg->B) cand.push_back({kEngineTensor, fixed ? cfg->max_ctas : mc, 0, fib});
+        if (cs <= 8 && want(kEngineTensorCluster))
+            for (int m : {0, 4, 8, 12})
+                for (int fib : {0, 64, 128})
+                    if (fib <= cfg->B)
+                        cand.push_back({kEngineTensorCluster, fixed ? cfg->max_ctas : m * cs, 0, fib});
     }
+    if (pers_supported(*cfg) && cfg->x_layout == CPD_LAYOUT_REPLICAS && want(kEnginePersistent))
+        for (int mc : {2, 4, 8, 16}) cand.push_back({kEnginePersistent, fixed ? cfg->max_ctas : mc, 0, 0});
+    if (cand.empty()) cand.push_back({cfg->engine, cfg->max_ctas, cfg->tile_rows, cfg->tile_fibers});
+    // a fixed engine and cap repeat across the caps' loop: keep one of each
+    std::vector<Cand> uniq;
+    for (const Cand &c : cand) {
+        bool dup = false;
+        for (const Cand &u : uniq)
+            dup = dup || (u.engine == c.engine && u.max_ctas == c.max_ctas && u.rows == c.rows && u.fibers == c.fibers);
+        if (!dup) uniq.push_back(c);
+    }
+    cand.swap(uniq);
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
@@ -1203,8 +1241,10 @@ extern "C" cpd_status cpd_autotune(const cpd_config *cfg, const void *X, int x_l
     cpd_config chosen = *cfg;
     for (const auto &c : cand) {
         cpd_config trial = *cfg;
-        trial.engine = c.first;
-        trial.max_ctas = c.second;
+        trial.engine = c.engine;
+        trial.max_ctas = c.max_ctas;
+        trial.tile_rows = c.rows;
+        trial.tile_fibers = c.fibers;
         cpd_ctx *ctx = nullptr;
         if (cpd_init(&trial, X, x_loc, A0, a0_loc, stream, &ctx) != CPD_OK) continue;   // not applicable
         float ms = 0.f;

@@ -511,20 +511,24 @@ __device__ __forceinline__ T load_x(const XT *p) { return (T)to_float<XT>(*p); }
 // Element offset of the first entry of mode-n fiber j (Eq. (2) numbering) in
 // the storage the problem reads, and the distance between its entries: the
 // mode-n replica (fibers contiguous, ld[n] apart), or, with the strided
-// layout, X itself in column-major order, where the modes before n give the
-// low part of j and the entries of a fiber are I_1 ... I_{n-1} apart.
+// layout, the mode-1 replica alone, X in column-major order with the first
+// mode padded to ld[0]. There (0-based modes), writing
+// j = i_pre + (I_0 ... I_{n-1}) i_post and i_pre = i_0 + I_0 mid, the fiber
+// starts at i_0 + ld[0] (mid + q_n I_n i_post) and its entries are ld[0] q_n
+// apart, q_n = I_1 ... I_{n-1}.
 template <class T>
 __device__ __forceinline__ long long fiber_start(const Problem<T> &P, int n, long long j)
 {
-    if (!P.strided) return j * P.ld[n];
-    const long long pre = P.xpre[n];
-    return (j % pre) + (j / pre) * pre * P.dims[n];
+    if (!P.strided || n == 0) return j * P.ld[n];
+    const long long pre = P.dims[0] * P.xq[n];
+    const long long ipre = j % pre, ipost = j / pre;
+    return (ipre % P.dims[0]) + P.ld[0] * (ipre / P.dims[0] + P.xq[n] * P.dims[n] * ipost);
 }
 
 template <class T>
 __device__ __forceinline__ long long fiber_step(const Problem<T> &P, int n)
 {
-    return P.strided ? P.xpre[n] : 1;
+    return (P.strided && n > 0) ? P.ld[0] * P.xq[n] : 1;
 }
 template <>
 __device__ __forceinline__ double load_x<double, double>(const double *p) { return *p; }

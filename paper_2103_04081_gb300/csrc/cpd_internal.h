@@ -45,11 +45,10 @@ struct Problem {
     int cs;                   // CTAs per cluster (clustered tensor-core engine)
     int64_t dims[kMaxModes];
     int64_t ld[kMaxModes];    // fiber stride of replica k (elements, multiple of 8)
-    int strided;              // 1: rep[k] is the single column-major copy of X for
-                              // every k: fiber j of mode n starts at
-                              // (j mod xpre[n]) + (j div xpre[n]) xpre[n] I_n and its
-                              // entries are xpre[n] apart (Eq. (2) numbering)
-    int64_t xpre[kMaxModes];  // I_1 ... I_{n-1} (1 for the first mode)
+    int strided;              // 1: rep[k] is the mode-1 replica for every k (X in
+                              // column-major order, the first mode padded to ld[0]);
+                              // the other modes' fibers are read from it with a stride
+    int64_t xq[kMaxModes];    // 0-based: prod_{0 < m < n} I_m (1 for modes 0 and 1)
     double Jn[kMaxModes];     // J_n = prod_{k != n} I_k, as a double
     ModeTile tile[kMaxModes];
     const void *rep[kMaxModes];

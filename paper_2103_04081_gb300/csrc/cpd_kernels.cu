@@ -133,7 +133,7 @@ __device__ __forceinline__ void grad_simt_body(const Problem<T> &P, int bid)
             j += (long long)row[k] * Jp;
             Jp *= P.dims[k];
         }
-        jcol[f] = P.strided ? fiber_start(P, n, j) : j;   // strided: the fiber's first entry
+        jcol[f] = (P.strided && n > 0) ? fiber_start(P, n, j) : j;   // strided: the fiber's first entry
         if constexpr (sizeof(T) == 8)
             ss[f] = __ddiv_rn(1.0, __dmul_rn(__dmul_rn((double)P.B, P.Jn[n]), fiber_prob_staged(P, n, row, staged ? stage : nullptr)));
         else
@@ -155,8 +155,9 @@ __device__ __forceinline__ void grad_simt_body(const Problem<T> &P, int bid)
     __syncthreads();
 
     // 4. fiber gather from the mode-n replica (Alg. 1, X_(n)(:, F_n))
-    if (P.strided)
-        gather_rows_strided<XT, T>(reinterpret_cast<const XT *>(P.rep[n]), P.xpre[n], jcol, nf, r0, rows, rb, sx);
+    if (P.strided && n > 0)
+        gather_rows_strided<XT, T>(reinterpret_cast<const XT *>(P.rep[n]), fiber_step(P, n), jcol, nf, r0, rows, rb,
+                                   sx);
     else
         gather_rows<XT, T>(reinterpret_cast<const XT *>(P.rep[n]), P.ld[n], jcol, nf, r0, rows, rb, sx);
     __syncthreads();

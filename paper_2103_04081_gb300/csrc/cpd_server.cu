@@ -57,7 +57,8 @@ double tensor_bytes(const cpd_config &g)
     const double xb = g.x_dtype == CPD_F64 ? 8 : (g.x_dtype == CPD_F32 ? 4 : 2);
     double total = 1.0;
     for (int k = 0; k < g.N; ++k) total *= (double)g.dims[k];
-    if (g.x_layout == CPD_LAYOUT_STRIDED) return total * xb;
+    if (g.x_layout == CPD_LAYOUT_STRIDED)   // the mode-1 replica alone
+        return total / (double)g.dims[0] * (double)((g.dims[0] + 7) / 8 * 8) * xb;
     double bytes = 0.0;
     for (int k = 0; k < g.N; ++k) bytes += total / (double)g.dims[k] * (double)((g.dims[k] + 7) / 8 * 8) * xb;
     return bytes;

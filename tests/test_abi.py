@@ -53,6 +53,12 @@ def _init_status(cpd, **kw):
     (dict(dims=(2, 2, 2), R=1, B=1, step="adagrad", eta=0.0), "eta"),
     (dict(dims=(2, 2, 2), R=1, B=1, step="decay", gamma=0.0), "gamma"),
     (dict(dims=(2, 2, 2), R=1, B=1, x_dtype="f32", engine="tensor"), "tensor-core"),
+    (dict(dims=(8, 8, 8), R=1, B=4, tile_rows=12), "tile_rows must be a multiple of 8"),
+    (dict(dims=(8, 8, 8), R=1, B=4, tile_fibers=5), "tile_fibers <= B"),
+    (dict(dims=(64, 64, 64), R=16, B=64, engine="tensor", tile_fibers=20), "tensor-core engines"),
+    (dict(dims=(64, 64, 64), R=16, B=64, engine="tensor", tile_rows=64), "tensor-core engines"),
+    (dict(dims=(64, 64, 64), R=16, B=64, engine="persistent", tile_fibers=32), "persistent engine takes no"),
+    (dict(dims=(8, 8, 8), R=1, B=4, x_layout="strided", engine="cluster"), "strided x_layout"),
 ])
 def test_invalid_configs_rejected_on_host(cpd, kw, msg):
     st, err = _init_status(cpd, **kw)
