@@ -54,7 +54,9 @@ constexpr int kPHd = 64;          // H is formed 64 x 64 (4 x 4 blocks, upper tr
 constexpr int kPOwnBlock = 64;    // owned rows handled per pass of the step phase
 constexpr long long kPMaxStage = 4096;   // CDF staging entries (sum of all I_k)
 constexpr int kPMaxFpc = 1024;    // fibers per CTA
-constexpr size_t kPSmemMax = 226 * 1024;  // dynamic shared memory per CTA (plus ~1 KB static)
+// dynamic shared memory per CTA: the 227 KB a CTA may opt into, less the
+// kernel's static copy of its launch arguments and flags
+constexpr size_t kPSmemMax = (227 * 1024 - sizeof(PersArgs) - 256) / 1024 * 1024;
 
 __host__ __device__ inline size_t up128(size_t v) { return (v + 127) / 128 * 128; }
 
@@ -923,7 +925,7 @@ static void pers_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr, int 
 int pers_max_clusters(const PersArgs &a)
 {
     const size_t smem = pers_smem_bytes(a);
-    if (smem > 227 * 1024 || a.cs < 1 || a.cs > 16) return 0;
+    if (smem > kPSmemMax || a.cs < 1 || a.cs > 16) return 0;
     if (pers_attrs(a.cs, smem) != cudaSuccess) return 0;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
