@@ -702,7 +702,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=500)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tensor", "cluster", "persistent"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tensor", "cluster", "persistent", "fused"])
     ap.add_argument("--max-ctas", type=int, default=0, help="CTA cap of the gradient launch (0: none)")
     ap.add_argument("--sampling", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -763,7 +763,7 @@ def main() -> None:
     tuned = None
     if not args.no_autotune and args.engine == "auto" and args.max_ctas == 0:
         best, rate = C.cpd_autotune(C.make_config(**kw), X, [a.to(dev) for a in A0], iters=300, stream=stream)
-        tuned = {"engine": {1: "simt", 2: "tensor", 3: "cluster", 4: "persistent"}[best.engine], "max_ctas": best.max_ctas,
+        tuned = {"engine": {1: "simt", 2: "tensor", 3: "cluster", 4: "persistent", 5: "fused"}[best.engine], "max_ctas": best.max_ctas,
                  "tile_rows": best.tile_rows, "tile_fibers": best.tile_fibers, "tuning_iters_per_s": rate}
         kw["engine"], kw["max_ctas"] = tuned["engine"], tuned["max_ctas"]
         kw["tile_rows"], kw["tile_fibers"] = tuned["tile_rows"], tuned["tile_fibers"]
@@ -771,7 +771,7 @@ def main() -> None:
         dec = C.Decomposition(X, [a.to(dev) for a in A0], stream=stream, **kw)
     desc = dec.describe()
     engine = desc["engine"]
-    launches_per_iter = 2 + (2 if w["sampling"] == "leverage" else 0)
+    launches_per_iter = (1 if engine == "fused" else 2) + (2 if w["sampling"] == "leverage" else 0)
     if engine == "persistent":   # one launch per call of cpd_sgd_iters (up to 2^20 iterations)
         launches_per_iter = 1.0 / args.steps
 
@@ -846,12 +846,13 @@ def main() -> None:
         "metric": METRIC, "value": iters_per_s, "unit": "iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if engine in ("tensor", "cluster", "persistent") else ("f64" if w["x_dtype"] == "f64" else "f32"),
+        "dtype": "bf16" if engine in ("tensor", "cluster", "persistent", "fused") else ("f64" if w["x_dtype"] == "f64" else "f32"),
         "data": "synthetic", "config": config_block(w, engine),
         "gather_gbs_in_loop": gather_bytes * args.steps / (ms / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "kernel": {"tensor": "k_grad_tc", "cluster": "k_grad_tcc", "persistent": "k_pers"}.get(engine, "k_grad_simt"),
+                     "kernel": {"tensor": "k_grad_tc", "cluster": "k_grad_tcc", "persistent": "k_pers",
+                                "fused": "k_fused"}.get(engine, "k_grad_simt"),
                      "algorithmic_bytes_per_launch": gather_bytes, "mean_launch_ms": grad_ms,
                      "timed_launches": nlaunch, "peak_source": src + " (hbm_gbs, of " + src + ")",
                      "update_mean_ms": upd_ms},

@@ -116,13 +116,20 @@ typedef struct {
                            whole calls of cpd_sgd_iters in one launch (BF16
                            tensors, R <= 64, Euclidean or uniform sampling,
                            sum of the I_k <= 4096, ceil(I_max/128) accumulator
-                           tiles of <= 64 columns within 512)                   */
+                           tiles of <= 64 columns within 512),
+                           5 = fused: gradient and step in one launch, one
+                           thread-block cluster per 128-row tile of A^(n) whose
+                           CTAs split the batch and sum M and H in distributed
+                           shared memory in rank order (BF16 tensors, R <= 64,
+                           at most 208 fibers per CTA)                          */
     int32_t max_ctas;   /* 0: size the gradient grid for the whole GPU; > 0: use at
                            most about this many CTAs per gradient launch (fewer
                            fiber groups, more fibers per CTA), so that several
                            decompositions share the GPU. Engine 4: the cluster
                            size (1..16; 0 = 8, or less if the device cannot
-                           co-schedule 8). Part of the arithmetic: the grouping
+                           co-schedule 8). Engine 5: the cluster size (0, 1, 2,
+                           4, 8 or 16; 0 = the smallest that leaves a CTA at
+                           most 64 fibers, up to 16). Part of the arithmetic: the grouping
                            of the batch fixes the summation order of the
                            gradient partials.                                   */
     int32_t constraint; /* CPD_CONSTRAINT_*                                     */
@@ -131,11 +138,12 @@ typedef struct {
     int32_t tile_rows;  /* rows of A^(n) per gradient CTA (0 = chosen from the
                            shape and max_ctas). CUDA-core engine: a multiple of
                            8 in [8, 512]; tensor-core engines: 0 or 128 (the
-                           MMA's M); persistent engine: 0.                      */
+                           MMA's M); persistent and fused engines: 0.           */
     int32_t tile_fibers; /* sampled fibers per gradient CTA / fiber group (0 =
                            chosen). CUDA-core engine: [1, B]; tensor-core
                            engines: a multiple of 16 (the MMA's K) in [16, 128]
-                           (engine 2) or [16, 256] (engine 3); persistent: 0.
+                           (engine 2) or [16, 256] (engine 3); persistent and
+                           fused: 0.
                            Like max_ctas, part of the arithmetic: the fiber
                            groups fix the summation order.                      */
 } cpd_config;
@@ -319,6 +327,13 @@ cpd_status cpd_profile_read(cpd_ctx *ctx, int64_t *launches, double *mean_grad_m
  *   H rows summed and sent; 14 all H rows received; 15 H operands converted,
  *   cluster barrier passed; 6 A H_g products issued; 7 accumulator complete;
  *   8 G_g stored; 9 exit.
+ * Fused engine (one launch per iteration), first CTA: 0 entry; 15 set up;
+ *   1 draws done; 2 columns and weights; 16 factor rows landed (the X gather
+ *   in flight); 3 operands built; 4 gather landed; 5 products complete; 6
+ *   partials in shared memory; 7 first cluster barrier; 8 owned rows of H
+ *   summed; 9 second cluster barrier; 10 H complete; 17 owned rows of M
+ *   summed, G and the step written; 11 row weights written; 12 / 13 last
+ *   CTA's bookkeeping start / end; 14 exit.
  * The other gradient engines use slots 0-15 for their own phases in the
  * same spirit. Update kernel: 16 entry, 17 gradient reduced, 18 step
  * applied, 19 row weights written (first CTA); 20 / 21 distribution
@@ -458,7 +473,8 @@ cpd_status cpd_destroy(cpd_ctx *ctx);
  *  cfg, X, x_loc, A0, a0_loc: as for cpd_init. If cfg->engine != 0 only
  *    that engine is timed, at cfg->max_ctas, over its tile shapes; otherwise
  *    every applicable engine (CUDA cores; per-CTA and cluster tensor cores
- *    for BF16 tensors with R <= 64; the persistent cluster engine where it
+ *    for BF16 tensors with R <= 64; the fused engine with clusters of 4, 8
+ *    and 16 CTAs; the persistent cluster engine where it
  *    applies) with a few CTA caps (cluster sizes) and tile shapes (rows and
  *    fibers per CTA; fibers per fiber group).
  *  iters: timed iterations per candidate (after iters / 4 warm-up ones).

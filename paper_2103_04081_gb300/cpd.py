@@ -25,7 +25,7 @@ STEP = {"fixed": 0, "adagrad": 1, "decay": 2}
 CONSTRAINT = {"none": 0, "nonneg": 1}
 LAYOUT = {"replicas": 0, "strided": 1}
 XDT = {"f64": 0, "f32": 1, "bf16": 2}
-ENGINE = {"auto": 0, "simt": 1, "tensor": 2, "cluster": 3, "persistent": 4}
+ENGINE = {"auto": 0, "simt": 1, "tensor": 2, "cluster": 3, "persistent": 4, "fused": 5}
 MAX_MODES = 8
 
 

@@ -141,13 +141,13 @@ static cpd_status validate(const cpd_config *cfg)
         return fail(CPD_EINVAL, "unknown x_layout");
     if (cfg->x_layout == CPD_LAYOUT_STRIDED && cfg->engine != 0 && cfg->engine != kEngineSimt)
         return fail(CPD_EINVAL, "the strided x_layout runs on the CUDA-core engine (1)");
-    if (cfg->engine < 0 || cfg->engine > 4) return fail(CPD_EINVAL, "unknown engine");
+    if (cfg->engine < 0 || cfg->engine > 5) return fail(CPD_EINVAL, "unknown engine");
     if (cfg->tile_rows < 0 || cfg->tile_fibers < 0 || cfg->tile_fibers > cfg->B)
         return fail(CPD_EINVAL, "tile_rows and tile_fibers must be >= 0, tile_fibers <= B");
     if (cfg->tile_rows && (cfg->tile_rows % 8 || cfg->tile_rows > 512))
         return fail(CPD_EINVAL, "tile_rows must be a multiple of 8 in [8, 512]");
-    if (cfg->engine == kEnginePersistent && (cfg->tile_rows || cfg->tile_fibers))
-        return fail(CPD_EINVAL, "the persistent engine takes no tile_rows / tile_fibers");
+    if ((cfg->engine == kEnginePersistent || cfg->engine == kEngineFused) && (cfg->tile_rows || cfg->tile_fibers))
+        return fail(CPD_EINVAL, "the persistent and fused engines take no tile_rows / tile_fibers");
     if ((cfg->engine == kEngineTensor || cfg->engine == kEngineTensorCluster) &&
         ((cfg->tile_rows && cfg->tile_rows != 128) ||
          (cfg->tile_fibers && (cfg->tile_fibers % 16 ||
@@ -172,9 +172,14 @@ static cpd_status validate(const cpd_config *cfg)
         return fail(CPD_EINVAL, "AdaGrad needs eta > 0 and b >= 0");
     if (cfg->step == CPD_STEP_DECAY && !(cfg->gamma > 0.0))
         return fail(CPD_EINVAL, "decreasing step needs gamma > 0");
-    if ((cfg->engine == kEngineTensor || cfg->engine == kEngineTensorCluster) &&
+    if ((cfg->engine == kEngineTensor || cfg->engine == kEngineTensorCluster || cfg->engine == kEngineFused) &&
         (cfg->x_dtype != CPD_BF16 || !tc_supported(cfg->R, 128)))
         return fail(CPD_EINVAL, "tensor-core engine needs BF16 tensors and R <= 64");
+    if (cfg->engine == kEngineFused &&
+        ((cfg->max_ctas & (cfg->max_ctas - 1)) || cfg->max_ctas > 16 || !fused_fits(cfg->N, cfg->R, cfg->B, cfg->max_ctas, 1)))
+        return fail(CPD_EINVAL, "fused engine: max_ctas is the cluster size (0 = chosen, or 1, 2, 4, 8, 16) and "
+                                "a CTA's share of the batch must fit its shared memory (at most 208 fibers; "
+                                "fewer for small clusters and large R)");
     if (cfg->engine == kEngineTensorCluster) {
         int64_t imax = 0;
         for (int k = 0; k < cfg->N; ++k) imax = std::max<int64_t>(imax, cfg->dims[k]);
@@ -213,6 +218,39 @@ static void choose_tiles(cpd_ctx *c, Problem<T> &P, int sm_count)
             c->grid_upd = 0;
             c->smem_grad = pers_smem_bytes(pa);
             c->max_clusters = pers_max_clusters(pa);
+        }
+        return;
+    }
+    if (c->engine == kEngineFused) {
+        if constexpr (sizeof(T) == 4) {
+            // one cluster per tile of 128 rows, or of 256 rows (two MMA tiles)
+            // where the tiles of 128 would outnumber the clusters the device
+            // co-schedules; its CTAs split the batch
+            int cs = 1, fpc = 16;
+            fused_plan(g.N, g.R, g.B, g.max_ctas, &cs, &fpc);
+            P.rb = 128;
+            P.cs = cs;
+            P.fb = fpc;
+            P.pf = 1;
+            c->max_clusters = fused_max_clusters(P);
+            if (c->max_clusters >= 1 && (imax + 127) / 128 > c->max_clusters && fused_fits(g.N, g.R, g.B, cs, 2)) {
+                P.rb = 256;
+                const int m2 = fused_max_clusters(P);
+                if (m2 >= 1) c->max_clusters = m2;
+                else P.rb = 128;
+            }
+            int maxpr = 0;
+            for (int k = 0; k < g.N; ++k) {
+                P.tile[k].pr = (int)((g.dims[k] + P.rb - 1) / P.rb);
+                maxpr = std::max(maxpr, P.tile[k].pr);
+            }
+            c->grid_grad = cs * maxpr;
+            c->grid_upd = 0;
+            c->smem_grad = fused_smem_bytes(P);
+            if (c->max_clusters < 1) {   // no such cluster can be co-scheduled
+                c->engine = imax <= 1024 ? kEngineTensorCluster : kEngineTensor;
+                choose_tiles(c, P, sm_count);
+            }
         }
         return;
     }
@@ -390,6 +428,7 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
         if constexpr (sizeof(T) == 4) {
             if (c->engine == kEngineTensor) cap = tc_stage_cap(P);
             if (c->engine == kEngineTensorCluster) cap = tcc_stage_cap(P);
+            if (c->engine == kEngineFused) cap = fused_stage_cap(P);
         }
         long long need = 0;
         for (int n = 0; n < g.N; ++n) {
@@ -943,6 +982,7 @@ extern "C" cpd_status cpd_describe(cpd_ctx *c, char *buf, size_t len)
                   "\"cluster\": %d, \"max_clusters\": %d, \"deferred_cdf\": %d, "
                   "\"fit_pass\": \"%s\", \"x_layout\": \"%s\", \"xnorm2\": %.17g}",
                   c->engine == kEnginePersistent       ? "persistent"
+                  : c->engine == kEngineFused         ? "fused"
                   : c->engine == kEngineTensorCluster ? "cluster"
                   : c->engine == kEngineTensor        ? "tensor"
                                                       : "simt",
@@ -1221,6 +1261,10 @@ extern "C" cpd_status cpd_autotune(const cpd_config *cfg, const void *X, int x_l
                     if (fib <= cfg->B)
                         cand.push_back({kEngineTensorCluster, fixed ? cfg->max_ctas : m * cs, 0, fib});
     }
+    if (tc_ok && cfg->x_layout == CPD_LAYOUT_REPLICAS && want(kEngineFused))
+        for (int fcs : {4, 8, 16})
+            if (fused_fits(cfg->N, cfg->R, cfg->B, fixed ? cfg->max_ctas : fcs, 1))
+                cand.push_back({kEngineFused, fixed ? cfg->max_ctas : fcs, 0, 0});
     if (pers_supported(*cfg) && cfg->x_layout == CPD_LAYOUT_REPLICAS && want(kEnginePersistent))
         for (int mc : {2, 4, 8, 16}) cand.push_back({kEnginePersistent, fixed ? cfg->max_ctas : mc, 0, 0});
     if (cand.empty()) cand.push_back({cfg->engine, cfg->max_ctas, cfg->tile_rows, cfg->tile_fibers});

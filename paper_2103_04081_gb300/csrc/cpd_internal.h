@@ -29,7 +29,7 @@ constexpr int kThreads = 256;
 enum : int { kStNonFinite = 1, kStDegenerate = 2, kStTimeout = 4 };
 
 // Gradient engines.
-enum : int { kEngineSimt = 1, kEngineTensor = 2, kEngineTensorCluster = 3, kEnginePersistent = 4 };
+enum : int { kEngineSimt = 1, kEngineTensor = 2, kEngineTensorCluster = 3, kEnginePersistent = 4, kEngineFused = 5 };
 
 // Launch tiling of the gradient kernel for one mode n: CTA (gr, gf) handles
 // rows [gr*rb, gr*rb+rb) of A^(n) and fibers [gf*fb, gf*fb+fb) of the batch.
@@ -152,6 +152,17 @@ int tcc_max_clusters(const Problem<float> &P);
 long long tc_stage_cap(const Problem<float> &P);
 long long tcc_stage_cap(const Problem<float> &P);
 constexpr long long kSimtStageCap = 2048;
+
+// Fused iteration engine (cpd_fused.cu): one cluster per tile of P.rb =
+// 128 or 256 rows of A^(n), gradient and step in one launch; BF16 tensors,
+// R <= 64.
+constexpr size_t kFusedSmemMax = 226 * 1024;
+void fused_plan(int N, int R, int B, int cs_req, int *cs, int *fpc);
+bool fused_fits(int N, int R, int B, int cs_req, int tpc);
+cudaError_t launch_fused(const Problem<float> &P, int grid, cudaStream_t stream);
+size_t fused_smem_bytes(const Problem<float> &P);
+long long fused_stage_cap(const Problem<float> &P);
+int fused_max_clusters(const Problem<float> &P);
 
 // Tensor-core stop check (cpd_fit_tc.cu): BF16 tensors, float factors, R <= 64.
 struct FitTcArgs {

@@ -784,9 +784,11 @@ cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd, s
 {
     cudaError_t e = cudaSuccess;
     if (ev0) cudaEventRecord(ev0, s);
-    if (engine == kEngineTensor || engine == kEngineTensorCluster) {
+    if (engine == kEngineTensor || engine == kEngineTensorCluster || engine == kEngineFused) {
         if constexpr (sizeof(T) == 4)
-            e = engine == kEngineTensor ? launch_grad_tc(P, grid_grad, s) : launch_grad_tcc(P, grid_grad, s);
+            e = engine == kEngineTensor          ? launch_grad_tc(P, grid_grad, s)
+                : engine == kEngineTensorCluster ? launch_grad_tcc(P, grid_grad, s)
+                                                 : launch_fused(P, grid_grad, s);
         else
             e = cudaErrorInvalidValue;
     } else {
@@ -799,8 +801,10 @@ cudaError_t launch_iteration(const Problem<T> &P, int grid_grad, int grid_upd, s
     }
     if (ev1) cudaEventRecord(ev1, s);
     if (e != cudaSuccess) return e;
-    k_update<T><<<grid_upd, kThreads, 0, s>>>(P);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (engine != kEngineFused) {   // the fused engine applies the step itself
+        k_update<T><<<grid_upd, kThreads, 0, s>>>(P);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if (P.sampling == CPD_SAMPLE_LEVERAGE) {
         const int npairs = P.R * (P.R + 1) / 2;
         k_gram<T><<<(npairs + 7) / 8, kThreads, lev_smem_bytes(P.R), s>>>(P, -1);

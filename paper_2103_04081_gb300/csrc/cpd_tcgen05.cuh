@@ -127,6 +127,16 @@ __device__ __forceinline__ float ld_cluster_f32(uint32_t addr)
     return v;
 }
 
+__device__ __forceinline__ float4 ld_cluster_v4(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
 // Bulk copies completing on an mbarrier (byte count). Addresses 16-byte
 // aligned, size a multiple of 16. Destination and mbarrier may belong to
 // another CTA of the cluster (shared::cluster addresses from map_shared).

@@ -57,7 +57,11 @@ def _init_status(cpd, **kw):
     (dict(dims=(8, 8, 8), R=1, B=4, tile_fibers=5), "tile_fibers <= B"),
     (dict(dims=(64, 64, 64), R=16, B=64, engine="tensor", tile_fibers=20), "tensor-core engines"),
     (dict(dims=(64, 64, 64), R=16, B=64, engine="tensor", tile_rows=64), "tensor-core engines"),
-    (dict(dims=(64, 64, 64), R=16, B=64, engine="persistent", tile_fibers=32), "persistent engine takes no"),
+    (dict(dims=(64, 64, 64), R=16, B=64, engine="persistent", tile_fibers=32), "take no tile_rows"),
+    (dict(dims=(64, 64, 64), R=16, B=64, engine="fused", tile_fibers=32), "take no tile_rows"),
+    (dict(dims=(64, 64, 64), R=16, B=64, engine="fused", max_ctas=3), "cluster size"),
+    (dict(dims=(64, 64, 64), R=16, B=4000, engine="fused", max_ctas=16), "208 fibers"),
+    (dict(dims=(64, 64, 64), R=16, B=64, x_dtype="f32", engine="fused"), "tensor-core engine"),
     (dict(dims=(8, 8, 8), R=1, B=4, x_layout="strided", engine="cluster"), "strided x_layout"),
 ])
 def test_invalid_configs_rejected_on_host(cpd, kw, msg):

@@ -92,7 +92,7 @@ def free_run_compare(cpd, orc, name, sampling, iters, every, engine="auto", star
     return rec
 
 
-@pytest.mark.parametrize("engine", ["auto", "persistent"])
+@pytest.mark.parametrize("engine", ["auto", "persistent", "fused"])
 def test_free_run_bf16_near_solution(cpd, orc, engine):
     """120^4 BF16 on the tensor cores from a start 10% off the true factors
     (eta = 0.1): the regime where the gradient is small against the terms it
@@ -101,7 +101,7 @@ def test_free_run_bf16_near_solution(cpd, orc, engine):
     floor (fit above 0.99 at noise 1e-3)."""
     rec = free_run_compare(cpd, orc, "c3_120pow4_bf16", "euclidean", 2000, 500, engine=engine,
                            start="perturbed", eta=0.1)
-    assert rec["engine"] in ("tensor", "cluster", "persistent")
+    assert rec["engine"] in ("tensor", "cluster", "persistent", "fused")
     for r in rec["checkpoints"]:
         assert abs(r["fit_diff"]) <= 1e-3, r
     last = rec["checkpoints"][-1]

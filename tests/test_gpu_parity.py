@@ -283,7 +283,7 @@ def _full(cpd, orc, name, sampling, steps, warm, engine="auto", max_ctas=0, auto
     del X
     desc = dec.describe()
     dec.sgd_iters(warm)
-    key = "bf16_tensor" if desc["engine"] in ("tensor", "cluster", "persistent") else xdt
+    key = "bf16_tensor" if desc["engine"] in ("tensor", "cluster", "persistent", "fused") else xdt
     ocfg = _ocfg(orc, dims, R, B, xdt, sampling, w["step"], w["sample_seed"],
                  eta=w.get("eta", 0.1), b=w.get("b", 1e-12))
     worst = forced(dec, orc, ocfg, xb, steps, key)
@@ -411,6 +411,12 @@ def test_full_c4_persistent(cpd, orc, cs):
         if cs == 16 and e.status == cpd.ECUDA and "cannot be scheduled" in str(e):
             pytest.skip("this device does not co-schedule 16-CTA clusters with this layout")
         raise
+
+
+def test_full_c4_fused(cpd, orc):
+    """The 1000^3 workload on the fused engine (a cluster of 16 CTAs per
+    128-row tile, 128 fibers each), teacher-forced at full size."""
+    _full(cpd, orc, "c4_1000cube_bf16", "euclidean", steps=3, warm=50, engine="fused", max_ctas=16)
 
 
 def _krp_mode1(A: list) -> np.ndarray:
