@@ -328,12 +328,15 @@ cpd_status cpd_profile_read(cpd_ctx *ctx, int64_t *launches, double *mean_grad_m
  *   cluster barrier passed; 6 A H_g products issued; 7 accumulator complete;
  *   8 G_g stored; 9 exit.
  * Fused engine (one launch per iteration), first CTA: 0 entry; 15 set up;
- *   1 draws done; 2 columns and weights; 16 factor rows landed (the X gather
- *   in flight); 3 operands built; 4 gather landed; 5 products complete; 6
+ *   1 draws done; 2 columns and weights; 16 X gather issued; 3 operands
+ *   built; 4 gather landed; 5 products complete; 6
  *   partials in shared memory; 7 first cluster barrier; 8 owned rows of H
  *   summed; 9 second cluster barrier; 10 H complete; 17 owned rows of M
- *   summed, G and the step written; 11 row weights written; 12 / 13 last
- *   CTA's bookkeeping start / end; 14 exit.
+ *   summed, G and the step written (18 / 19: the first thread's A^(n) H
+ *   formed / its M summed); 11 row weights written; 12 / 13 last CTA's
+ *   bookkeeping start / end; 14 exit.
+ * Every engine's sampler (first CTA): 29 CDFs staged in shared memory, 30
+ *   deferred CDF rebuilt; the cluster engine: 31 first fiber's weight.
  * The other gradient engines use slots 0-15 for their own phases in the
  * same spirit. Update kernel: 16 entry, 17 gradient reduced, 18 step
  * applied, 19 row weights written (first CTA); 20 / 21 distribution

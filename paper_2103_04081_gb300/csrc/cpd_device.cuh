@@ -261,6 +261,29 @@ __device__ inline bool block_distribution_inplace(unsigned long long *a, long lo
     return Q > 0;
 }
 
+// Copy n words from global into shared memory, eight loads in flight a
+// thread: a loop that stores each word before loading the next pays one
+// memory latency per word it copies. kL2: load through L2 only (words other
+// CTAs of the same launch may have written).
+template <class W, bool kL2>
+__device__ __forceinline__ void stage_words(W *dst, const W *src, long long n)
+{
+    const long long nt = blockDim.x;
+    for (long long i0 = threadIdx.x; i0 < n; i0 += 8 * nt) {
+        W v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const long long i = i0 + u * nt;
+            v[u] = i < n ? (kL2 ? __ldcg(src + i) : __ldg(src + i)) : W(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const long long i = i0 + u * nt;
+            if (i < n) dst[i] = v[u];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The fixed-point distribution of one factor from its FP64 row weights, by
 // one CTA: s = 61 - ceil(log2 I) - floor(log2 max w), q_i = floor(w_i 2^s),
@@ -275,7 +298,7 @@ __device__ inline bool block_distribution(const double *wg, long long I, unsigne
     const int tid = threadIdx.x, nt = blockDim.x;
     const double *w = wg;
     if (wstage && I <= wcap) {   // one coalesced pass through L2, then shared memory
-        for (long long i = tid; i < I; i += nt) wstage[i] = __ldcg(wg + i);
+        stage_words<double, true>(wstage, wg, I);
         __syncthreads();
         w = wstage;
     }
@@ -373,15 +396,14 @@ __device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int
         const int dirty = P.defer_cdf ? *P.dirty : -1;
         for (int k = 0; k < P.N; ++k) {
             if (k == n) continue;
-            if (k == dirty) {
-                const unsigned long long *wb = reinterpret_cast<const unsigned long long *>(P.w[k]);
-                for (long long i = threadIdx.x; i < P.dims[k]; i += blockDim.x) stage[off[k] + i] = __ldcg(wb + i);
-            } else {
-                const unsigned long long *c = P.cdf[k];
-                for (long long i = threadIdx.x; i < P.dims[k]; i += blockDim.x) stage[off[k] + i] = __ldg(c + i);
-            }
+            if (k == dirty)
+                stage_words<unsigned long long, true>(stage + off[k],
+                                                      reinterpret_cast<const unsigned long long *>(P.w[k]), P.dims[k]);
+            else
+                stage_words<unsigned long long, false>(stage + off[k], P.cdf[k], P.dims[k]);
         }
         __syncthreads();
+        trace_stamp(P.trace, 29, blockIdx.x == 0);
         if (dirty >= 0 && dirty != n) {
             unsigned long long *c = stage + off[dirty];
             if (!block_distribution_inplace(c, P.dims[dirty], dsm)) {
@@ -390,6 +412,7 @@ __device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int
                 for (long long i = threadIdx.x; i < P.dims[dirty]; i += blockDim.x) P.cdf[dirty][i] = c[i];
             }
         }
+        trace_stamp(P.trace, 30, blockIdx.x == 0);
     }
     const int chunks = (nf + 31) / 32;
     for (int job = warp; job < chunks * P.N; job += nwarps) {

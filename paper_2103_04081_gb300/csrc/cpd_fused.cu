@@ -62,7 +62,7 @@ __device__ __forceinline__ int kmaj(int row, int k, int Kp)
 
 struct FusedSmem {
     size_t a, bhi, blo, zc, hp, hq, h, arow, srow, snew, jcol, s, idx, bar, tmem, total;
-    size_t abytes, krp_bytes;
+    size_t abytes;
     int fpc, mr, hr;
     __host__ __device__ FusedSmem(int N, int R, int fpc_, int cs, int tpc)
     {
@@ -77,11 +77,9 @@ struct FusedSmem {
         bhi = o;  o += (size_t)fpc * kN * 2;           // Z' hi (K-major, fpc columns)
         blo = o;  o += (size_t)fpc * kN * 2;           // Z' lo
         zc = o;   o += (size_t)fpc * kM * 2;           // z hi (rows 0-63) and z lo (rows 64-127), K-major
-        hp = o;   o += up((size_t)kN * kMs * 4);       // draw scratch, factor rows, then the partial H
-        hq = o;   o += up((size_t)kN * kMs * 4);       // factor rows, then the z-lo half of the partial H
-        h = o;    o += up((size_t)kN * kMs * 4);       // factor rows, then H: owned rows summed, the
-                                                       // rest read from their owners
-        krp_bytes = o - hp;                            // factor-row staging: hp, hq and h
+        hp = o;   o += up((size_t)kN * kMs * 4);       // draw scratch, then the partial H
+        hq = o;   o += up((size_t)kN * kMs * 4);       // the z-lo half of the partial H
+        h = o;    o += up((size_t)kN * kMs * 4);       // H: owned rows summed, the rest read from their owners
         arow = o; o += up((size_t)mr * R * 4);         // owned rows of A^(n)
         srow = o; o += up((size_t)mr * R * 8);         // their AdaGrad state
         snew = o; o += up((size_t)mr * R * 4);         // their new values
@@ -152,8 +150,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused(const Problem<float> P)
     const uint32_t bar_mma = smem_u32(smem + L.bar);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + L.tmem);
 
-    // 0. barrier, tensor memory, and the owned rows of A^(n) (and their
-    //    AdaGrad state) on their way into shared memory
+    // 0. barrier and tensor memory
     if (threadIdx.x == 0) {
         mbar_init(bar_mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -164,18 +161,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused(const Problem<float> P)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
-    {
-        const float *asrc = P.A[n] + i_own * R;
-        for (int e = threadIdx.x; e < own_rows * R; e += kThreads) cp_async4(smem_u32(sArow + e), asrc + e);
-        if (P.step == CPD_STEP_ADAGRAD) {
-            const double *ssrc = P.S[n] + i_own * R;
-            for (int e = threadIdx.x; e < own_rows * R; e += kThreads)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(sSrow + e)), "l"(ssrc + e)
-                             : "memory");
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    }
-
     // 1. own fibers: draws (CDFs staged in the X-tile region), columns, weights
     unsigned long long *stage = reinterpret_cast<unsigned long long *>(sA);
     const long long cap = (long long)(L.abytes / 8);
@@ -205,37 +190,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused(const Problem<float> P)
     __syncthreads();   // the staged CDFs are dead: the region takes the X tile
     trace_stamp(P.trace, 2, tr0);
 
-    // 2a. the factor rows of the own fibers (in chunks of fch fibers that fit
-    //     the partial-H regions, free until the products) by cp.async, one warp
-    //     per (fiber, mode) row; the first chunk is issued before the X gather,
-    //     so that waiting for it leaves the gather in flight
-    float *sRows = sHp;
-    const int per_fiber = (N - 1) * R;
-    int fch = (int)(L.krp_bytes / ((size_t)per_fiber * 4)) / 8 * 8;
-    fch = fch < fpc ? fch : fpc;
-    auto issue_rows = [&](int c0) {
-        const int nf = nown - c0 < 0 ? 0 : (nown - c0 < fch ? nown - c0 : fch);
-        const uint32_t dst0 = smem_u32(sRows);
-        for (int p2 = warp; p2 < nf * (N - 1); p2 += kThreads / 32) {
-            const int fl = p2 / (N - 1), kk = p2 % (N - 1);
-            const int k = kk + (kk >= n ? 1 : 0);
-            const float *src = P.A[k] + (long long)sidx[(c0 + fl) * N + k] * R;
-            const uint32_t dst = dst0 + (uint32_t)(p2 * R * 4);
-            if ((R & 1) == 0) {
-                for (int q = lane; q < R / 2; q += 32)
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst + q * 8), "l"(src + 2 * q)
-                                 : "memory");
-            } else {
-                for (int q = lane; q < R; q += 32) cp_async4(dst + q * 4, src + q);
-            }
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    };
-    issue_rows(0);
-
-    // 2b. the fibers' entries of the cluster's rows -> X operands, one per MMA
+    // 2a. the fibers' entries of the cluster's rows -> X operands, one per MMA
     //     tile (MN-major: core matrix (f/8, i/8) at ((f/8) 16 + i/8) 128 bytes,
-    //     fiber rows of 16 bytes; tile h at h fpc 256 bytes)
+    //     fiber rows of 16 bytes; tile h at h fpc 256 bytes); in flight while
+    //     the operands below are formed
     const uint32_t aBase = smem_u32(sA);
     {
         const __nv_bfloat16 *rep = reinterpret_cast<const __nv_bfloat16 *>(P.rep[n]);
@@ -253,40 +211,67 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused(const Problem<float> P)
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // all but the X gather
-    __syncthreads();
+    {
+        // the owned rows of A^(n) and their AdaGrad state, for the step
+        const float *asrc = P.A[n] + i_own * R;
+        for (int e = threadIdx.x; e < own_rows * R; e += kThreads) cp_async4(smem_u32(sArow + e), asrc + e);
+        if (P.step == CPD_STEP_ADAGRAD) {
+            const double *ssrc = P.S[n] + i_own * R;
+            for (int e = threadIdx.x; e < own_rows * R; e += kThreads)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(sSrow + e)), "l"(ssrc + e)
+                             : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
     trace_stamp(P.trace, 16, tr0);
 
-    // 2c. z_f (products of the factor rows, modes ascending) and the operands:
-    //     Z' hi / lo, z hi / lo (K-major, K = fibers)
-    for (int c0 = 0; c0 < fpc; c0 += fch) {
-        if (c0 > 0) {   // the next chunk of factor rows
-            __syncthreads();
-            issue_rows(c0);
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-            __syncthreads();
+    // 2b. z_f (products of the factor rows, modes ascending) straight from the
+    //     factors, and the operands: Z' hi / lo, z hi / lo (K-major, K = fibers).
+    //     A thread takes up to kJobs (column r, block of 8 fibers) jobs at once
+    //     and issues all their loads of one mode before multiplying, so the
+    //     latency is paid once per mode.
+    constexpr int kJobs = 4;
+    const int njobs = kN * (fpc / 8);
+    for (int j0 = 0; j0 < njobs; j0 += kJobs * kThreads) {
+        float v[kJobs][8];
+#pragma unroll
+        for (int jj = 0; jj < kJobs; ++jj) {
+            const int job = j0 + jj * kThreads + threadIdx.x;
+            const int r = job % kN, b = job / kN;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[jj][u] = (job < njobs && 8 * b + u < nown && r < R) ? 1.f : 0.f;
         }
-        const int nb = ((fpc - c0 < fch) ? fpc - c0 : fch) / 8;
-        for (int job = threadIdx.x; job < kN * nb; job += kThreads) {
-            const int r = job % kN, b = c0 / 8 + job / kN;
-            float v[8];
+        for (int k = 0; k < N; ++k) {
+            if (k == n) continue;
+            const float *Ak = P.A[k];
+            float x[kJobs][8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = (8 * b + u < nown && r < R) ? 1.f : 0.f;
-            if (r < R) {
-                for (int kk = 0; kk < N - 1; ++kk) {
+            for (int jj = 0; jj < kJobs; ++jj) {
+                const int job = j0 + jj * kThreads + threadIdx.x;
+                const int r = job % kN, b = job / kN;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int fl = 8 * b + u;
-                        if (fl < nown) v[u] = v[u] * sRows[((fl - c0) * (N - 1) + kk) * R + r];
-                    }
+                for (int u = 0; u < 8; ++u) {
+                    const int fl = 8 * b + u;
+                    x[jj][u] = (job < njobs && fl < nown && r < R) ? __ldg(Ak + (long long)sidx[fl * N + k] * R + r)
+                                                                    : 0.f;
                 }
             }
+#pragma unroll
+            for (int jj = 0; jj < kJobs; ++jj)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[jj][u] = v[jj][u] * x[jj][u];
+        }
+#pragma unroll
+        for (int jj = 0; jj < kJobs; ++jj) {
+            const int job = j0 + jj * kThreads + threadIdx.x;
+            if (job >= njobs) continue;
+            const int r = job % kN, b = job / kN;
             __nv_bfloat16 zh[8], zl[8], ph[8], pl[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const float zs = v[u] * ss[8 * b + u];
-                zh[u] = __float2bfloat16_rn(v[u]);
-                zl[u] = __float2bfloat16_rn(v[u] - __bfloat162float(zh[u]));
+                const float zs = v[jj][u] * ss[8 * b + u];
+                zh[u] = __float2bfloat16_rn(v[jj][u]);
+                zl[u] = __float2bfloat16_rn(v[jj][u] - __bfloat162float(zh[u]));
                 ph[u] = __float2bfloat16_rn(zs);
                 pl[u] = __float2bfloat16_rn(zs - __bfloat162float(ph[u]));
             }
@@ -447,32 +432,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused(const Problem<float> P)
             acc[2] = __fmaf_rn(a, h.z, acc[2]);
             acc[3] = __fmaf_rn(a, h.w, acc[3]);
         }
+        trace_stamp(P.trace, 18, tr0);
         float4 m = part[0];
 #pragma unroll
         for (int q = 1; q < kMaxCs; ++q)
             if (q < cs) m = add4(m, part[q]);
         const float mv[4] = {m.x, m.y, m.z, m.w};
+        trace_stamp(P.trace, 19, tr0);
+        // the four columns' FP64 AdaGrad updates first, so that their latencies overlap
+        float gv[4];
+        double Sv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            gv[u] = acc[u] - mv[u];
+            Sv[u] = (P.step == CPD_STEP_ADAGRAD && r4 + u < R)
+                        ? __fma_rn((double)gv[u], (double)gv[u], sSrow[rl * R + r4 + u])
+                        : 0.0;
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int r = r4 + u;
-            if (r >= R) break;
-            const int eo = rl * R + r;
-            const float g = acc[u] - mv[u];
-            P.G[i * R + r] = g;
-            float an;
-            if (P.step == CPD_STEP_ADAGRAD) {
-                // S accumulates in FP64; the step factor eta / sqrt(b + S) is formed in FP32
-                const double S = __fma_rn((double)g, (double)g, sSrow[eo]);
-                P.S[n][i * R + r] = S;
-                an = arow[r] - (float)P.eta * g * rsqrtf((float)S + (float)P.b);
-            } else {
-                const float alpha = (float)((P.step == CPD_STEP_DECAY) ? P.beta / ((double)t + P.gamma) : P.alpha);
-                an = arow[r] - alpha * g;
+            if (r < R) {
+                const int eo = rl * R + r;
+                const float g = gv[u];
+                P.G[i * R + r] = g;
+                float an;
+                if (P.step == CPD_STEP_ADAGRAD) {
+                    // S accumulates in FP64; the step factor eta / sqrt(b + S) is formed in FP32
+                    P.S[n][i * R + r] = Sv[u];
+                    an = arow[r] - (float)P.eta * g * rsqrtf((float)Sv[u] + (float)P.b);
+                } else {
+                    const float alpha =
+                        (float)((P.step == CPD_STEP_DECAY) ? P.beta / ((double)t + P.gamma) : P.alpha);
+                    an = arow[r] - alpha * g;
+                }
+                if (P.constraint == CPD_CONSTRAINT_NONNEG && an < 0.f) an = 0.f;   // projection; NaN kept
+                if (!isfinite(an) || !isfinite(g)) atomicOr(P.status, kStNonFinite);
+                An[i * R + r] = an;
+                sNew[eo] = an;
             }
-            if (P.constraint == CPD_CONSTRAINT_NONNEG && an < 0.f) an = 0.f;   // projection; NaN kept
-            if (!isfinite(an) || !isfinite(g)) atomicOr(P.status, kStNonFinite);
-            An[i * R + r] = an;
-            sNew[eo] = an;
         }
     }
     cluster_arrive();   // no more reads of the other CTAs' shared memory; the barrier completes meanwhile

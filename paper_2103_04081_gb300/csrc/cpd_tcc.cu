@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tcc(const Problem<float> P
                 Jp *= P.dims[k];
             }
             w = staged ? fiber_weight_staged(P, n, row, stage) : fiber_weight(P, n, row);
+            trace_stamp(P.trace, 31, tr0 && f == 0);
             for (int k = 0; k < N; ++k) P.idx[(long long)(f0 + fo0 + f) * N + k] = row[k];
         }
         jcol[fo0 + f] = j;
