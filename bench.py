@@ -35,15 +35,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SGD iters/s & fiber-gather GB/s vs HBM peak; batched solves/s, p99 @ equal fit"
 DEFAULT_WORKLOAD = "c4_1000cube_bf16"
-KERNEL_SOURCES = ["paper_2103_04081_gb300/csrc/cpd_kernels.cu", "paper_2103_04081_gb300/csrc/cpd_tc.cu",
-                  "paper_2103_04081_gb300/csrc/cpd_pers.cu",
-                  "paper_2103_04081_gb300/csrc/cpd_tcc.cu", "paper_2103_04081_gb300/csrc/cpd_tcgen05.cuh",
-                  "paper_2103_04081_gb300/csrc/cpd_device.cuh"]
+# The sources each engine's gradient kernel is compiled from: a committed traffic
+# figure applies while their hash is the one recorded beside it.
+_CSRC = "paper_2103_04081_gb300/csrc/"
+_COMMON = [_CSRC + "cpd_device.cuh", _CSRC + "cpd_tcgen05.cuh", _CSRC + "cpd_internal.h"]
+KERNEL_SOURCES = {"cluster": [_CSRC + "cpd_tcc.cu"] + _COMMON, "tensor": [_CSRC + "cpd_tc.cu"] + _COMMON,
+                  "persistent": [_CSRC + "cpd_pers.cu"] + _COMMON, "fused": [_CSRC + "cpd_fused.cu"] + _COMMON,
+                  "simt": [_CSRC + "cpd_kernels.cu"] + _COMMON}
 
 
-def kernel_hash() -> str:
+def kernel_hash(engine: str) -> str:
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in KERNEL_SOURCES.get(engine, KERNEL_SOURCES["simt"]):
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -66,7 +69,7 @@ def ncu_traffic(engine: str) -> float | None:
     txt = open(p).read()
     m_hash = re.search(r"kernel_sources_sha256_16=(\w+)", txt)
     m_b = re.search(r"dram_bytes_per_full_launch=([0-9.eE+]+)", txt)
-    if not m_hash or not m_b or m_hash.group(1) != kernel_hash():
+    if not m_hash or not m_b or m_hash.group(1) != kernel_hash(engine):
         return None
     return float(m_b.group(1))
 

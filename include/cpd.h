@@ -401,8 +401,8 @@ typedef struct {
     int32_t max_active;   /* requests running at once (0: 32)                  */
     int32_t fit_every;    /* iterations between fit checks (0: 250; a multiple
                              of 32 keeps every iteration in replayed graphs)  */
-    int32_t no_grouping;  /* 0: requests that use the CUDA-core or per-CTA
-                             tensor-core engine (and no leverage sampling) run
+    int32_t no_grouping;  /* 0: requests that use the CUDA-core, per-CTA
+                             tensor-core or persistent engine run
                              in grouped launches (cpd_group_*), one group per
                              lane of same-dtype, same-engine requests; others
                              run on streams of their own. 1: every request on
@@ -503,11 +503,12 @@ cpd_status cpd_autotune(const cpd_config *cfg, const void *X, int x_loc, const v
  * cpd_group_create -- group G contexts (array of G distinct handles, borrowed:
  *  they must outlive the group). Members must share the tensor dtype and the
  *  gradient engine, which must be the CUDA-core (1), the per-CTA
- *  tensor-core (2) or the persistent (4) engine, and none may sample by
- *  leverage. Persistent members must share the cluster size; the group then
- *  runs every member's iterations in ONE launch per call, one thread-block
- *  cluster per member (the other engines use one gradient and one update
- *  launch per iteration). The members' launch state is captured at
+ *  tensor-core (2) or the persistent (4) engine. Persistent members must
+ *  share the cluster size; the group then runs every member's iterations in
+ *  ONE launch per call, one thread-block cluster per member. The other
+ *  engines use one gradient and one update launch per iteration, plus one
+ *  Gram and one leverage-row launch when any member samples by leverage
+ *  (members that do not take no CTAs of those). The members' launch state is captured at
  *  creation (later cpd_trace / cpd_profile changes do not reach the group).
  *  Allocates about a kilobyte per member on `stream` and synchronises it.
  *  Errors: CPD_EINVAL (NULL, duplicate or incompatible members), CPD_ENOMEM,

@@ -1054,13 +1054,22 @@ template <class T>
 static cpd_status group_build(cpd_group *g, cudaStream_t s)
 {
     std::vector<Problem<T>> hp(g->G);
-    std::vector<int> cta(2 * (g->G + 1), 0);
-    size_t smem = 0;
+    const int G1 = g->G + 1;
+    std::vector<int> cta(4 * G1, 0);   // gradient, update, Gram, leverage-row CTAs
+    size_t smem = 0, smem_lev = 0;
     for (int q = 0; q < g->G; ++q) {
         cpd_ctx *c = g->members[q];
         hp[q] = problem<T>(c);
         cta[q + 1] = cta[q] + c->grid_grad;
-        cta[g->G + 1 + q + 1] = cta[g->G + 1 + q] + c->grid_upd;
+        cta[G1 + q + 1] = cta[G1 + q] + c->grid_upd;
+        int gram = 0, lev = 0;
+        if (c->cfg.sampling == CPD_SAMPLE_LEVERAGE) {   // the grids launch_iteration uses
+            gram = (c->cfg.R * (c->cfg.R + 1) / 2 + 7) / 8;
+            lev = (int)((c->imax * 32 + kThreads - 1) / kThreads);
+            smem_lev = std::max(smem_lev, lev_smem(c->cfg.R));
+        }
+        cta[2 * G1 + q + 1] = cta[2 * G1 + q] + gram;
+        cta[3 * G1 + q + 1] = cta[3 * G1 + q] + lev;
         smem = std::max(smem, c->smem_grad);
     }
     CK(cudaMallocAsync(&g->dP, sizeof(Problem<T>) * g->G, s));
@@ -1071,10 +1080,15 @@ static cpd_status group_build(cpd_group *g, cudaStream_t s)
     GroupLaunch<T> L{};
     L.P = (const Problem<T> *)g->dP;
     L.cta_grad = g->dcta;
-    L.cta_upd = g->dcta + g->G + 1;
+    L.cta_upd = g->dcta + G1;
+    L.cta_gram = g->dcta + 2 * G1;
+    L.cta_lev = g->dcta + 3 * G1;
     L.G = g->G;
     L.grid_grad = cta[g->G];
-    L.grid_upd = cta[2 * g->G + 1];
+    L.grid_upd = cta[G1 + g->G];
+    L.grid_gram = cta[2 * G1 + g->G];
+    L.grid_lev = cta[3 * G1 + g->G];
+    L.smem_lev = smem_lev;
     L.engine = g->engine;
     L.x_dtype = g->x_dtype;
     L.smem_grad = smem;
@@ -1096,8 +1110,8 @@ extern "C" cpd_status cpd_group_create(cpd_ctx *const *ctxs, int32_t G, void *st
             return fail(CPD_EINVAL, "grouped launches take CUDA-core, per-CTA tensor-core or persistent contexts");
         if (c->engine == kEnginePersistent && c->pers.cs != c0->pers.cs)
             return fail(CPD_EINVAL, "persistent group members must share the cluster size");
-        if (c->cfg.sampling == CPD_SAMPLE_LEVERAGE)
-            return fail(CPD_EINVAL, "grouped launches do not take leverage sampling");
+        if (c->engine == kEnginePersistent && c->cfg.sampling == CPD_SAMPLE_LEVERAGE)
+            return fail(CPD_EINVAL, "persistent group members do not sample by leverage");
         if (c->fbytes != c0->fbytes || c->cfg.x_dtype != c0->cfg.x_dtype || c->engine != c0->engine ||
             c->device != c0->device)
             return fail(CPD_EINVAL, "group members differ in tensor dtype, engine or device");

@@ -84,8 +84,11 @@ struct GroupLaunch {
     const Problem<T> *P;      // device array of G problems
     const int *cta_grad;      // device, G + 1 prefix sums
     const int *cta_upd;       // device, G + 1 prefix sums
-    int G, grid_grad, grid_upd, engine, x_dtype;
+    const int *cta_gram;      // device, G + 1 prefix sums (leverage members only)
+    const int *cta_lev;       // device, G + 1 prefix sums (leverage members only)
+    int G, grid_grad, grid_upd, grid_gram, grid_lev, engine, x_dtype;
     size_t smem_grad;         // largest member's dynamic shared memory
+    size_t smem_lev;          // largest leverage member's (k_gram / k_lev_rows)
 };
 
 // Persistent cluster engine (cpd_pers.cu): one thread-block cluster of cs
@@ -152,6 +155,7 @@ int tcc_max_clusters(const Problem<float> &P);
 long long tc_stage_cap(const Problem<float> &P);
 long long tcc_stage_cap(const Problem<float> &P);
 constexpr long long kSimtStageCap = 2048;
+size_t lev_smem(int R);   // dynamic shared memory of the leverage kernels
 
 // Fused iteration engine (cpd_fused.cu): one cluster per tile of P.rb =
 // 128 or 256 rows of A^(n), gradient and step in one launch; BF16 tensors,

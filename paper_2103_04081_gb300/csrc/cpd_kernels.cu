@@ -326,8 +326,9 @@ __global__ void __launch_bounds__(kThreads) k_update_group(const Problem<T> *__r
 // P.lev_L.
 // k_mode < 0: the mode of the current iteration; else that mode.
 // ---------------------------------------------------------------------------
+// `bid` / `nblk`: the CTA's index among, and the number of, this problem's CTAs.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mode)
+__device__ __forceinline__ void gram_body(const Problem<T> &P, int k_mode, int bid, unsigned nblk)
 {
     const long long t = *P.t_dev;
     const int k = k_mode >= 0 ? k_mode : mode_draw(P.seed, t, P.N);
@@ -336,9 +337,9 @@ __global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mod
     const T *A = P.A[k];
     double *g = P.lev_L + R * R + R;  // Gram scratch after L and inv
     const int lane = threadIdx.x & 31;
-    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int warp_global = (bid * blockDim.x + threadIdx.x) >> 5;
     const int npairs = R * (R + 1) / 2;
-    for (int pr = warp_global; pr < npairs; pr += (gridDim.x * blockDim.x) >> 5) {
+    for (int pr = warp_global; pr < npairs; pr += (int)((nblk * blockDim.x) >> 5)) {
         int r = 0, rem = pr;
         while (rem >= R - r) { rem -= R - r; ++r; }
         const int s = r + rem;
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mod
             g[s * R + r] = acc;
         }
     }
-    if (!last_block(P.counters + 1)) return;
+    if (!last_block(P.counters + 1, nblk)) return;
     double *Lm = P.lev_L, *inv = P.lev_L + R * R;
     __shared__ int s_bad;
     __shared__ double s_col[256];  // column q of L below the diagonal, contiguous
@@ -425,6 +426,24 @@ __global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mod
     }
 }
 
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mode)
+{
+    gram_body<T>(P, k_mode, (int)blockIdx.x, gridDim.x);
+}
+
+// Grouped: the CTAs of problem g are [cta0[g], cta0[g+1]) (none for members
+// that do not sample by leverage); each runs its own problem's arithmetic.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_gram_group(const Problem<T> *__restrict__ Ps,
+                                                         const int *__restrict__ cta0, int G)
+{
+    __shared__ __align__(16) Problem<T> sp;
+    const int g = group_member(Ps, cta0, G, sp);
+    const int b0 = __ldg(cta0 + g);
+    gram_body<T>(sp, -1, (int)blockIdx.x - b0, (unsigned)(__ldg(cta0 + g + 1) - b0));
+}
+
 // l_i = ||L^{-1} a_i||^2 by forward substitution, then the CDF of the mode in
 // the last CTA; advance = 1 closes the iteration (t += 1). One warp per row in
 // right-looking order: lane j % 32 holds the partial v_j (v_j = a_ij at the
@@ -434,7 +453,7 @@ __global__ void __launch_bounds__(kThreads) k_gram(const Problem<T> P, int k_mod
 // ascending order and the sum the squares in ascending order, as in the
 // sequential form, so l_i is the same bits.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k_mode, int advance)
+__device__ __forceinline__ void lev_rows_body(const Problem<T> &P, int k_mode, int advance, int bid, unsigned nblk)
 {
     const long long t = *P.t_dev;
     const int k = k_mode >= 0 ? k_mode : mode_draw(P.seed, t, P.N);
@@ -455,7 +474,7 @@ __global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k
     }
     const double *inv = in_smem ? lev_dyn + R * R : P.lev_L + R * R;
     const int lane = threadIdx.x & 31;
-    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long i = ((long long)bid * blockDim.x + threadIdx.x) >> 5;
     if (!bad && i < I) {
         constexpr int kSlots = 256 / 32;  // v_j of j = lane + 32 s
         const T *a = P.A[k] + i * R;
@@ -485,7 +504,7 @@ __global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k
         }
         if (lane == 0) P.w[k][i] = acc;
     }
-    if (!last_block(P.counters + 2)) return;
+    if (!last_block(P.counters + 2, nblk)) return;
     __shared__ unsigned long long s_dist[2 * kThreads];
     if (!bad) finish_distribution(P, k, s_dist, lev_dyn);
     if (threadIdx.x == 0) {
@@ -495,6 +514,22 @@ __global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k
             *P.t_dev = t + 1;
         }
     }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_lev_rows(const Problem<T> P, int k_mode, int advance)
+{
+    lev_rows_body<T>(P, k_mode, advance, (int)blockIdx.x, gridDim.x);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_lev_rows_group(const Problem<T> *__restrict__ Ps,
+                                                             const int *__restrict__ cta0, int G)
+{
+    __shared__ __align__(16) Problem<T> sp;
+    const int g = group_member(Ps, cta0, G, sp);
+    const int b0 = __ldg(cta0 + g);
+    lev_rows_body<T>(sp, -1, 1, (int)blockIdx.x - b0, (unsigned)(__ldg(cta0 + g + 1) - b0));
 }
 
 // Euclidean or uniform weights of mode k from scratch (initialisation and
@@ -854,6 +889,12 @@ cudaError_t launch_group_iteration(const GroupLaunch<T> &L, cudaStream_t s)
     }
     if (e != cudaSuccess) return e;
     k_update_group<T><<<L.grid_upd, kThreads, 0, s>>>(L.P, L.cta_upd, L.G);
+    if ((e = cudaGetLastError()) != cudaSuccess || L.grid_gram == 0) return e;
+    // leverage members: their modes' Gram factor, then their leverage rows and
+    // distribution (which closes their iteration)
+    k_gram_group<T><<<L.grid_gram, kThreads, L.smem_lev, s>>>(L.P, L.cta_gram, L.G);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_lev_rows_group<T><<<L.grid_lev, kThreads, L.smem_lev, s>>>(L.P, L.cta_lev, L.G);
     return cudaGetLastError();
 }
 
@@ -970,6 +1011,8 @@ template cudaError_t launch_iteration<float>(const Problem<float> &, int, int, s
                                              cudaEvent_t, cudaEvent_t, cudaEvent_t);
 template cudaError_t launch_iteration<double>(const Problem<double> &, int, int, size_t, cudaStream_t, int,
                                               cudaEvent_t, cudaEvent_t, cudaEvent_t);
+size_t lev_smem(int R) { return lev_smem_bytes(R); }
+
 template cudaError_t launch_group_iteration<float>(const GroupLaunch<float> &, cudaStream_t);
 template cudaError_t launch_group_iteration<double>(const GroupLaunch<double> &, cudaStream_t);
 template cudaError_t launch_refresh_mode<float>(const Problem<float> &, int, cudaStream_t);

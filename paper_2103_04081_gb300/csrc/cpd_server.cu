@@ -4,8 +4,8 @@
 // One worker thread owns all device work. Per round it
 //   1. admits queued requests first-fit while the memory budget and the
 //      concurrency limit allow (cpd_init on a fresh non-blocking stream);
-//   2. steps the lanes: requests of one class (tensor dtype and engine, no
-//      leverage sampling; for the persistent engine also the cluster size)
+//   2. steps the lanes: requests of one class (tensor dtype and engine; for
+//      the persistent engine also the cluster size)
 //      share a lane whose rounds advance all members with grouped launches
 //      (one gradient and one update launch per iteration for the whole
 //      lane, or one launch per round for persistent members), then start
@@ -315,7 +315,7 @@ static void worker_loop(cpd_server *srv)
                 continue;
             }
             const int engine = ctx_engine(r->ctx);
-            const bool groupable = !srv->cfg.no_grouping && r->cfg.sampling != CPD_SAMPLE_LEVERAGE &&
+            const bool groupable = !srv->cfg.no_grouping &&
                                    (engine == kEngineSimt || engine == kEngineTensor || engine == kEnginePersistent);
             Lane *lane = groupable ? pick_lane(srv, r, engine) : nullptr;
             if (lane) {

@@ -1,6 +1,7 @@
 """Grouped launches (cpd_group_create / cpd_group_iters): one gradient launch
-and one update launch per iteration advance many decompositions, and every
-member ends bitwise where it ends when run alone."""
+and one update launch per iteration (plus one Gram and one leverage-row
+launch when members sample by leverage) advance many decompositions, and
+every member ends bitwise where it ends when run alone."""
 import pytest
 import torch
 
@@ -26,6 +27,12 @@ CLASSES = {
         ((150, 70, 33), 10, 100, "f32", "uniform", "fixed", 4, dict(alpha=0.002)),
         ((33, 17, 9, 5), 3, 20, "f32", "euclidean", "decay", 2, dict(beta=0.01, gamma=2.0)),
         ((120, 90, 200), 24, 512, "f32", "euclidean", "adagrad", 8, {}),
+        ((90, 130, 40), 7, 64, "f32", "leverage", "adagrad", 0, {}),
+    ],
+    "simt_leverage": [
+        ((80, 70, 60), 6, 48, "f32", "leverage", "adagrad", 0, {}),
+        ((150, 110, 100), 70, 64, "f32", "leverage", "fixed", 8, dict(alpha=0.001)),   # L past shared memory
+        ((40, 36, 30, 28), 12, 100, "f32", "leverage", "decay", 2, dict(beta=0.01, gamma=2.0)),
     ],
     "simt_bf16": [
         ((40, 36, 30, 28), 12, 200, "bf16", "euclidean", "adagrad", 0, {}),
@@ -36,6 +43,7 @@ CLASSES = {
         ((300, 64, 90), 20, 1024, "bf16", "uniform", "adagrad", 8, {}),
         ((60, 70, 55, 40), 16, 512, "bf16", "euclidean", "adagrad", 4, {}),
         ((129, 257, 70), 64, 256, "bf16", "euclidean", "fixed", 2, dict(alpha=0.0005)),
+        ((150, 120, 90), 24, 256, "bf16", "leverage", "adagrad", 4, {}),
     ],
 }
 
@@ -85,12 +93,9 @@ def test_group_rejects_incompatible_members(cpd):
     a = _pair(cpd, 0, CLASSES["simt_f32"][0], "simt")[0]
     b = _pair(cpd, 1, CLASSES["simt_bf16"][0], "simt")[0]
     c = _pair(cpd, 2, CLASSES["tensor_bf16"][0], "cluster")[0]
-    _, X, A0 = make_problem((64, 64, 64), 10, x_dtype="f32", seed=3)
-    lev = cpd.Decomposition(X.cuda(), [x.cuda() for x in A0], dims=(64, 64, 64), R=10, B=64,
-                            x_dtype="f32", sampling="leverage", engine="simt")
-    for members in ([a.ctx, b.ctx], [c.ctx], [a.ctx, lev.ctx], [a.ctx, a.ctx]):
+    for members in ([a.ctx, b.ctx], [c.ctx], [a.ctx, a.ctx]):
         with pytest.raises(cpd.CpdError) as e:
             cpd.cpd_group_create(members)
         assert e.value.status == cpd.EINVAL
-    for d in (a, b, c, lev):
+    for d in (a, b, c):
         d.close()
