@@ -146,6 +146,18 @@ typedef struct {
                            fused: 0.
                            Like max_ctas, part of the arithmetic: the fiber
                            groups fix the summation order.                      */
+    int32_t block;      /* Remark 1, blocks first and then sampling: 0 or 1 =
+                           per-fiber sampling (Alg. 3); bs > 1 = the batch is
+                           B / bs sampled blocks of bs consecutive mode-n
+                           fibers (Eq. (2) order): an aligned range of bs rows
+                           of the first mode other than n, every other index
+                           fixed. A block is drawn with the sum of its fibers'
+                           probabilities (its row of that mode drawn by
+                           Alg. 3 stands for the row's block) and its fibers
+                           carry that probability; Eq. (11)'s 1/B becomes
+                           1/(B / bs). bs must divide B, I_1 and I_2. Not with
+                           the persistent engine, cpd_skrp, cpd_gradients or
+                           cpd_grad_variance.                                    */
 } cpd_config;
 
 typedef struct cpd_ctx cpd_ctx;

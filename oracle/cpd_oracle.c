@@ -57,6 +57,20 @@
  *  - p_k(i) = (double)q_i / (double)Q (both conversions and the quotient
  *    rounded to nearest); p_f = prod_{k != n, k ascending} p_k(i_k).
  *
+ * Blocks first, then sampling (Remark 1), when block > 1: the fibers of the
+ * mode-n unfolding are grouped, in their Eq. (2) order, into blocks of
+ * `block` consecutive columns: an aligned range of the fastest-varying other
+ * mode k0 (the first mode other than n) with every other index fixed; block
+ * must divide I_1, I_2 and B. The batch is B / block sampled blocks, with
+ * replacement. Block beta draws each index of the modes k != n once, from the
+ * word of (t, beta, k), by the draw above; for k0 the drawn row stands for its
+ * block, so the block is drawn with the sum of its rows' probabilities. The
+ * block's fiber u (u < block) takes row (r / block) block + u of k0 and is
+ * batch slot beta block + u. Every fiber of a block carries the block's
+ * probability p_b (k0's factor q_blk / Q with q_blk the block's exact sum of
+ * q_i), and Eq. (11)'s 1/B becomes 1/(B / block), one term per sampled block:
+ * E[G] is still the full gradient / J_n. block = 1 is the per-fiber method.
+ *
  * Conventions (0-based in code, the paper is 1-based):
  *  - X dense, column-major (first index fastest): entry (i_0..i_{N-1}) at
  *    offset sum_k i_k S_k with S_k = prod_{m<k} I_m.  This is the order in
@@ -92,7 +106,7 @@ typedef struct {
     double gamma;  /*   (Thm 9)                                 */
     uint64_t seed;
     int32_t constraint;  /* ORC_CONSTRAINT_*                         */
-    int32_t pad;
+    int32_t block;       /* Remark 1: fibers per sampled block (1: per fiber) */
 } orc_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -401,17 +415,40 @@ static int build_distributions(const orc_cfg *c, int32_t n, const double *const 
     return ORC_OK;
 }
 
-/* Eq. (10): p_f as the product of the per-factor probabilities. */
+/* Blocks (Remark 1): the mode whose rows form the blocks of mode n's fibers. */
+static int32_t block_mode(int32_t n) { return n == 0 ? 1 : 0; }
+
+static int32_t block_of(const orc_cfg *c) { return c->block > 1 ? c->block : 1; }
+
+/* Eq. (10): p_f as the product of the per-factor probabilities; with blocks,
+ * k0's factor is the probability of the block of rows that holds i_k0. */
 static double fiber_probability(const orc_cfg *c, int32_t n, const int64_t *idx,
                                 uint64_t *const *cdf)
 {
+    const int32_t bs = block_of(c), k0 = block_mode(n);
     double p = 1.0;
     for (int32_t k = 0; k < c->N; ++k) {
         if (k == n)
             continue;
-        p = p * orc_prob(cdf[k], c->dims[k], idx[k]);
+        if (bs > 1 && k == k0) {
+            const int64_t b = idx[k] / bs;
+            const uint64_t hi = cdf[k][(b + 1) * bs - 1];
+            const uint64_t lo = b > 0 ? cdf[k][b * bs - 1] : 0;
+            p = p * ((double)(hi - lo) / (double)cdf[k][c->dims[k] - 1]);
+        } else {
+            p = p * orc_prob(cdf[k], c->dims[k], idx[k]);
+        }
     }
     return p;
+}
+
+/* block > 1 must divide B and the two modes whose rows can form blocks. */
+static int blocks_valid(const orc_cfg *c)
+{
+    const int32_t bs = block_of(c);
+    if (c->block < 0)
+        return 0;
+    return bs == 1 || (c->B % bs == 0 && c->dims[0] % bs == 0 && c->dims[1] % bs == 0);
 }
 
 /*
@@ -420,8 +457,18 @@ static double fiber_probability(const orc_cfg *c, int32_t n, const int64_t *idx,
  *   G = (A H - M) / (B J_n),  D = diag(1/p_f).
  * Z_S is B x R row-major, X_S is I_n x B with fiber f contiguous (x_S + f*I_n).
  */
+static void gradient_eq11(int64_t In, int32_t R, int32_t B, int64_t Bterms, int64_t Jn, const double *An,
+                          const double *Zs, const double *Xs, const double *p, double *G);
+
 void orc_gradient(int64_t In, int32_t R, int32_t B, int64_t Jn, const double *An,
                   const double *Zs, const double *Xs, const double *p, double *G)
+{
+    gradient_eq11(In, R, B, B, Jn, An, Zs, Xs, p, G);
+}
+
+/* Eq. (11) over B fibers whose 1/B is 1/Bterms (B / block with blocks). */
+static void gradient_eq11(int64_t In, int32_t R, int32_t B, int64_t Bterms, int64_t Jn, const double *An,
+                          const double *Zs, const double *Xs, const double *p, double *G)
 {
     double *H = (double *)calloc((size_t)R * R, sizeof(double));
     double *M = (double *)calloc((size_t)In * R, sizeof(double));
@@ -441,7 +488,7 @@ void orc_gradient(int64_t In, int32_t R, int32_t B, int64_t Jn, const double *An
             for (int32_t r = 0; r < R; ++r)
                 M[i * R + r] += Xs[f * In + i] * d * Zs[f * R + r];
         }
-    double scale = 1.0 / ((double)B * (double)Jn);
+    double scale = 1.0 / ((double)Bterms * (double)Jn);
 #ifdef ORC_OMP
 #pragma omp parallel for schedule(static)
 #endif
@@ -500,6 +547,8 @@ int orc_gradient_for_batch(const orc_cfg *c, int32_t n, const int64_t *idx,
                            const void *X, const double *const *A, double *p, double *G)
 {
     int32_t N = c->N, R = c->R, B = c->B;
+    if (!blocks_valid(c))
+        return ORC_EINVAL;
     int64_t In = c->dims[n];
     double *w[ORC_MAXN] = {0};
     uint64_t *cdf[ORC_MAXN] = {0};
@@ -517,7 +566,7 @@ int orc_gradient_for_batch(const orc_cfg *c, int32_t n, const int64_t *idx,
             orc_krp_row(N, R, n, A, row, Zs + (int64_t)f * R);
             orc_gather_fiber(X, c->x_dtype, N, c->dims, n, row, Xs + (int64_t)f * In);
         }
-        orc_gradient(In, R, B, j_count(c, n), A[n], Zs, Xs, p, G);
+        gradient_eq11(In, R, B, B / block_of(c), j_count(c, n), A[n], Zs, Xs, p, G);
     }
     free(Zs);
     free(Xs);
@@ -539,7 +588,7 @@ int orc_sample_batch(const orc_cfg *c, int32_t n, int64_t t, const void *X, cons
                      int64_t *idx, double *p, double *Zs, double *Xs)
 {
     int32_t N = c->N, R = c->R, B = c->B;
-    if (N < 2 || N > ORC_MAXN || R < 1 || B < 1 || n < 0 || n >= N)
+    if (N < 2 || N > ORC_MAXN || R < 1 || B < 1 || n < 0 || n >= N || !blocks_valid(c))
         return ORC_EINVAL;
     int64_t In = c->dims[n];
     double *w[ORC_MAXN] = {0};
@@ -550,14 +599,18 @@ int orc_sample_batch(const orc_cfg *c, int32_t n, int64_t t, const void *X, cons
     }
     int st = build_distributions(c, n, A, w, cdf);
     if (st == ORC_OK) {
+        /* block beta = f / bs draws once per mode; its fiber u = f % bs takes
+         * row u of the drawn block of mode k0 (bs = 1: one draw per fiber) */
+        const int32_t bs = block_of(c), k0 = block_mode(n);
         for (int32_t f = 0; f < B; ++f) {
             for (int32_t k = 0; k < N; ++k) {
                 if (k == n) {
                     idx[(int64_t)f * N + k] = -1;
                     continue;
                 }
-                const uint64_t x = orc_fiber_word(c->seed, t, f, k);
-                idx[(int64_t)f * N + k] = orc_draw(cdf[k], c->dims[k], x);
+                const uint64_t x = orc_fiber_word(c->seed, t, f / bs, k);
+                const int64_t r = orc_draw(cdf[k], c->dims[k], x);
+                idx[(int64_t)f * N + k] = (bs > 1 && k == k0) ? r / bs * bs + f % bs : r;
             }
         }
 #ifdef ORC_OMP
@@ -591,7 +644,7 @@ int orc_step(const orc_cfg *c, int64_t t, const void *X, double *const *A,
              double *G_out)
 {
     int32_t N = c->N, R = c->R, B = c->B;
-    if (N < 2 || N > ORC_MAXN || R < 1 || B < 1)
+    if (N < 2 || N > ORC_MAXN || R < 1 || B < 1 || !blocks_valid(c))
         return ORC_EINVAL;
     int32_t n = orc_mode_draw(c->seed, t, N);
     int64_t In = c->dims[n];
@@ -602,7 +655,7 @@ int orc_step(const orc_cfg *c, int64_t t, const void *X, double *const *A,
     double *Xs = (double *)malloc((size_t)B * In * sizeof(double));
     int st = orc_sample_batch(c, n, t, X, (const double *const *)A, idx, p, Zs, Xs);
     if (st == ORC_OK) {
-        orc_gradient(In, R, B, j_count(c, n), A[n], Zs, Xs, p, G);
+        gradient_eq11(In, R, B, B / block_of(c), j_count(c, n), A[n], Zs, Xs, p, G);
         orc_update(c, t, In, A[n], S ? S[n] : NULL, G);
         if (n_out)
             *n_out = n;

@@ -75,7 +75,7 @@ class _Cfg(ctypes.Structure):
         ("alpha", ctypes.c_double), ("eta", ctypes.c_double),
         ("b", ctypes.c_double), ("beta", ctypes.c_double),
         ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64),
-        ("constraint", ctypes.c_int32), ("pad", ctypes.c_int32),
+        ("constraint", ctypes.c_int32), ("block", ctypes.c_int32),
     ]
 
 
@@ -95,6 +95,7 @@ class Config:
     gamma: float = 1.0
     seed: int = 0
     constraint: str = "none"
+    block: int = 1          # Remark 1: fibers per sampled block (1: per-fiber sampling)
     extra: dict = field(default_factory=dict)
 
     def c(self) -> _Cfg:
@@ -110,6 +111,7 @@ class Config:
         cfg.constraint = CONSTRAINT[self.constraint]
         cfg.beta, cfg.gamma = self.beta, self.gamma
         cfg.seed = int(self.seed) & (2**64 - 1)
+        cfg.block = int(self.block)
         return cfg
 
 
@@ -373,18 +375,20 @@ def tol_blas(xbuf: np.ndarray, dims, A: list, x_dtype: str = "f64",
     return res / xx, xx
 
 
-def grad_row_scale(dims, n: int, idx, p, A: list, xbuf: np.ndarray, x_dtype: str, B: int) -> np.ndarray:
+def grad_row_scale(dims, n: int, idx, p, A: list, xbuf: np.ndarray, x_dtype: str, B: int,
+                   terms: int | None = None) -> np.ndarray:
     """Componentwise size of each row of the mini-batch gradient of Eq. (11):
         scale_i = || |A^(n)_i| |H| ||  +  || sum_f s_f |x_f(i)| |z_f| ||,
     |H| = sum_f s_f |z_f| |z_f|^T, s_f = 1 / (B J_n p_f), z_f the sampled KRP
     row (Eq. (3)) and x_f the sampled fiber (Eq. (2)) of batch entry f. These
     are the sizes of the two products whose difference is G_i, against which
     the rounding error of any evaluation of G_i is measured. idx is B x N
-    (column n ignored), A the factors the batch was drawn from."""
+    (column n ignored), A the factors the batch was drawn from. `terms` is the
+    count of Eq. (11)'s 1/B (B / bs with sampled blocks of bs fibers)."""
     N = len(dims)
     strides = np.cumprod([1] + [int(d) for d in dims[:-1]])
     Jn = float(np.prod([float(d) for k, d in enumerate(dims) if k != n]))
-    s = 1.0 / (B * Jn * np.asarray(p, dtype=np.float64))
+    s = 1.0 / ((B if terms is None else terms) * Jn * np.asarray(p, dtype=np.float64))
     Z = np.ones((B, A[0].shape[1]))
     base = np.zeros(B, dtype=np.int64)
     for k in range(N):

@@ -45,6 +45,7 @@ class cpd_config(ctypes.Structure):
         ("engine", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
         ("constraint", ctypes.c_int32), ("x_layout", ctypes.c_int32),
         ("tile_rows", ctypes.c_int32), ("tile_fibers", ctypes.c_int32),
+        ("block", ctypes.c_int32),
     ]
 
 
@@ -132,7 +133,7 @@ def _check(st: int) -> None:
 def make_config(dims, R, B, sampling="euclidean", step="adagrad", x_dtype="bf16", alpha=0.1,
                 eta=0.1, b=1e-12, beta=1.0, gamma=1.0, seed=0, engine="auto",
                 max_ctas=0, constraint="none", x_layout="replicas", tile_rows=0,
-                tile_fibers=0) -> cpd_config:
+                tile_fibers=0, block=1) -> cpd_config:
     c = cpd_config()
     c.N, c.R, c.B = len(dims), int(R), int(B)
     c.sampling, c.step, c.x_dtype = SAMPLE[sampling], STEP[step], XDT[x_dtype]
@@ -145,6 +146,7 @@ def make_config(dims, R, B, sampling="euclidean", step="adagrad", x_dtype="bf16"
     c.constraint = CONSTRAINT[constraint]
     c.x_layout = LAYOUT[x_layout]
     c.tile_rows, c.tile_fibers = int(tile_rows), int(tile_fibers)
+    c.block = int(block)
     return c
 
 

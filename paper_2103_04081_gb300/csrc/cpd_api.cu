@@ -142,6 +142,11 @@ static cpd_status validate(const cpd_config *cfg)
     if (cfg->x_layout == CPD_LAYOUT_STRIDED && cfg->engine != 0 && cfg->engine != kEngineSimt)
         return fail(CPD_EINVAL, "the strided x_layout runs on the CUDA-core engine (1)");
     if (cfg->engine < 0 || cfg->engine > 5) return fail(CPD_EINVAL, "unknown engine");
+    if (cfg->block < 0) return fail(CPD_EINVAL, "block must be >= 0");
+    if (cfg->block > 1 && (cfg->B % cfg->block || cfg->dims[0] % cfg->block || cfg->dims[1] % cfg->block))
+        return fail(CPD_EINVAL, "block (Remark 1) must divide B, I_1 and I_2");
+    if (cfg->block > 1 && cfg->engine == kEnginePersistent)
+        return fail(CPD_EINVAL, "the persistent engine samples fibers one by one (block 0 or 1)");
     if (cfg->tile_rows < 0 || cfg->tile_fibers < 0 || cfg->tile_fibers > cfg->B)
         return fail(CPD_EINVAL, "tile_rows and tile_fibers must be >= 0, tile_fibers <= B");
     if (cfg->tile_rows && (cfg->tile_rows % 8 || cfg->tile_rows > 512))
@@ -334,6 +339,7 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
     P.alpha = g.alpha; P.eta = g.eta; P.b = g.b; P.beta = g.beta; P.gamma = g.gamma;
     P.seed = g.seed;
     P.strided = g.x_layout == CPD_LAYOUT_STRIDED ? 1 : 0;
+    P.block = g.block > 1 ? g.block : 1;
     int64_t q = 1;
     for (int k = 0; k < g.N; ++k) {
         P.dims[k] = g.dims[k];
@@ -344,7 +350,7 @@ static cpd_status init_typed(cpd_ctx *c, const void *X, int x_loc, const void *c
         for (int m = 0; m < g.N; ++m)
             if (m != k) J *= (double)g.dims[m];
         P.Jn[k] = J;
-        P.inv_bj[k] = (float)(1.0 / ((double)g.B * J));
+        P.inv_bj[k] = (float)((double)P.block / ((double)g.B * J));   // 1 / ((B / bs) J_n)
     }
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, c->device);
@@ -678,6 +684,7 @@ extern "C" cpd_status cpd_skrp(cpd_ctx *c, int32_t n, int64_t t0, int32_t K, int
     if (!c || K < 1 || t0 < 0) return fail(CPD_EINVAL, "bad argument");
     if (c->fbytes != 4) return fail(CPD_EINVAL, "cpd_skrp takes float factors (F32 or BF16 tensors)");
     if (c->Pf.strided) return fail(CPD_EINVAL, "cpd_skrp reads the mode-major replicas (x_layout 0)");
+    if (c->Pf.block > 1) return fail(CPD_EINVAL, "cpd_skrp draws fibers one by one (block 0 or 1)");
     if (n < 0 || n >= c->cfg.N) return fail(CPD_EINVAL, "mode out of range");
     if ((double)K * c->cfg.B > 2.0e9) return fail(CPD_EINVAL, "K B too large");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1231,6 +1238,7 @@ extern "C" cpd_status cpd_grad_variance(cpd_ctx *c, int32_t n, double *var, doub
     if (!c || !var) return fail(CPD_EINVAL, "NULL argument");
     if (n < 0 || n >= c->cfg.N) return fail(CPD_EINVAL, "mode out of range");
     if (c->cfg.R > 64) return fail(CPD_EINVAL, "the variance diagnostic takes R <= 64");
+    if (c->cfg.block > 1) return fail(CPD_EINVAL, "the variance diagnostic enumerates single fibers (block 0 or 1)");
     cudaStream_t s = (cudaStream_t)stream;
     return c->fbytes == 8 ? variance_typed<double>(c, n, var, mean_norm2, s)
                           : variance_typed<float>(c, n, var, mean_norm2, s);

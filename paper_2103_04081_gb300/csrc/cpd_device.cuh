@@ -366,6 +366,17 @@ __device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 x)
 }
 
 
+// Blocks (Remark 1): the mode whose rows form the blocks of mode n's fibers
+// (the first mode other than n: the fastest-varying index of Eq. (2)).
+__device__ __forceinline__ int block_mode(int n) { return n == 0 ? 1 : 0; }
+
+// q of row i of a CDF, or of i's whole block of bs rows (its exact sum).
+__device__ __forceinline__ unsigned long long row_mass(const unsigned long long *c, long long i, int bs)
+{
+    const long long b0 = bs > 1 ? i / bs * bs : i, b1 = b0 + bs - 1;
+    return c[b1] - (b0 > 0 ? c[b0 - 1] : 0ULL);
+}
+
 // ---------------------------------------------------------------------------
 // Sampling steps shared by both gradient engines.
 // ---------------------------------------------------------------------------
@@ -424,7 +435,12 @@ __device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int
             continue;
         }
         const long long Ik = P.dims[k];
-        const unsigned long long x = act ? fiber_word(P.seed, t, (long long)(f0 + fl), k) : 0ULL;
+        // blocks (Remark 1): block f / bs draws once per mode from the word of
+        // (t, f / bs, k); for the blocks' mode k0 the drawn row stands for its
+        // block and fiber f takes row f % bs of it (bs = 1: one draw per fiber)
+        const int bs = P.block;
+        const long long f = (long long)(f0 + fl);
+        const unsigned long long x = act ? fiber_word(P.seed, t, bs > 1 ? f / bs : f, k) : 0ULL;
         long long i;
         if (P.sampling == CPD_SAMPLE_UNIFORM) {
             i = (long long)__umul64hi(x, (unsigned long long)Ik);
@@ -435,23 +451,26 @@ __device__ inline void draw_indices(const Problem<T> &P, long long t, int n, int
             const unsigned long long *c = P.cdf[k];
             i = warp_search_cdf(c, Ik, __umul64hi(x, __ldg(c + (Ik - 1))), act);
         }
+        if (bs > 1 && k == block_mode(n)) i = i / bs * bs + f % bs;
         if (act) sidx[fl * P.N + k] = (int)i;
     }
 }
 
 // p_f = prod_{k != n, ascending} q_k(i_k) / Q_k in FP64 (Eq. (10)),
-// for the record of the last batch; uniform: q = 1, Q = I_k.
+// for the record of the last batch; uniform: q = 1, Q = I_k. With blocks,
+// k0's factor is the probability of i_k0's block.
 template <class T>
 __device__ __forceinline__ double fiber_prob(const Problem<T> &P, int n, const int *row)
 {
     double p = 1.0;
     for (int k = 0; k < P.N; ++k) {
         if (k == n) continue;
+        const int bs = k == block_mode(n) ? P.block : 1;
         if (P.sampling == CPD_SAMPLE_UNIFORM) {
-            p = __dmul_rn(p, __ddiv_rn(1.0, (double)P.dims[k]));
+            p = __dmul_rn(p, __ddiv_rn((double)bs, (double)P.dims[k]));
         } else {
             const unsigned long long *c = P.cdf[k];
-            const unsigned long long q = c[row[k]] - (row[k] > 0 ? c[row[k] - 1] : 0ULL);
+            const unsigned long long q = row_mass(c, row[k], bs);
             p = __dmul_rn(p, __ddiv_rn(__ull2double_rn(q), __ull2double_rn(c[P.dims[k] - 1])));
         }
     }
@@ -469,7 +488,7 @@ __device__ __forceinline__ double fiber_prob_staged(const Problem<T> &P, int n, 
     for (int k = 0; k < P.N; ++k) {
         if (k == n) continue;
         const unsigned long long *c = stage + off;
-        const unsigned long long q = c[row[k]] - (row[k] > 0 ? c[row[k] - 1] : 0ULL);
+        const unsigned long long q = row_mass(c, row[k], k == block_mode(n) ? P.block : 1);
         p = __dmul_rn(p, __ddiv_rn(__ull2double_rn(q), __ull2double_rn(c[P.dims[k] - 1])));
         off += P.dims[k];
     }
@@ -477,19 +496,23 @@ __device__ __forceinline__ double fiber_prob_staged(const Problem<T> &P, int n, 
 }
 
 // The fiber's weight in Eq. (11), s_f = 1 / (B J_n p_f), in FP32 (the
-// gradient's own precision): (1/(B J_n)) prod_k Q_k / q_k(i_k).
+// gradient's own precision): (1/(B J_n)) prod_k Q_k / q_k(i_k). With blocks
+// of bs fibers, 1 / ((B / bs) J_n p_b): P.inv_bj carries the factor bs and
+// k0's q is its block's.
 template <class T>
 __device__ __forceinline__ float fiber_weight(const Problem<T> &P, int n, const int *row)
 {
     float s = P.inv_bj[n];
     for (int k = 0; k < P.N; ++k) {
         if (k == n) continue;
+        const int bs = k == block_mode(n) ? P.block : 1;
         if (P.sampling == CPD_SAMPLE_UNIFORM) {
-            s *= (float)P.dims[k];
+            s *= (float)P.dims[k] / (float)bs;
         } else {
             const unsigned long long *c = P.cdf[k];
-            const unsigned long long hi = __ldg(c + row[k]);
-            const unsigned long long lo = row[k] > 0 ? __ldg(c + row[k] - 1) : 0ULL;
+            const long long b0 = bs > 1 ? row[k] / bs * bs : row[k], b1 = b0 + bs - 1;
+            const unsigned long long hi = __ldg(c + b1);
+            const unsigned long long lo = b0 > 0 ? __ldg(c + b0 - 1) : 0ULL;
             s *= __ull2float_rn(__ldg(c + P.dims[k] - 1)) / __ull2float_rn(hi - lo);
         }
     }
@@ -506,12 +529,12 @@ __device__ __forceinline__ float fiber_weight_staged(const Problem<T> &P, int n,
     long long off = 0;
     for (int k = 0; k < P.N; ++k) {
         if (k == n) continue;
+        const int bs = k == block_mode(n) ? P.block : 1;
         if (P.sampling == CPD_SAMPLE_UNIFORM) {
-            s *= (float)P.dims[k];
+            s *= (float)P.dims[k] / (float)bs;
         } else {
             const unsigned long long *c = stage + off;
-            const unsigned long long q = c[row[k]] - (row[k] > 0 ? c[row[k] - 1] : 0ULL);
-            s *= __ull2float_rn(c[P.dims[k] - 1]) / __ull2float_rn(q);
+            s *= __ull2float_rn(c[P.dims[k] - 1]) / __ull2float_rn(row_mass(c, row[k], bs));
         }
         off += P.dims[k];
     }

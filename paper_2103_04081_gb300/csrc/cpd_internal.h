@@ -48,6 +48,7 @@ struct Problem {
     int strided;              // 1: rep[k] is the mode-1 replica for every k (X in
                               // column-major order, the first mode padded to ld[0]);
                               // the other modes' fibers are read from it with a stride
+    int block;                // fibers per sampled block (Remark 1; 1: per-fiber sampling)
     int64_t xq[kMaxModes];    // 0-based: prod_{0 < m < n} I_m (1 for modes 0 and 1)
     double Jn[kMaxModes];     // J_n = prod_{k != n} I_k, as a double
     ModeTile tile[kMaxModes];

@@ -135,7 +135,8 @@ __device__ __forceinline__ void grad_simt_body(const Problem<T> &P, int bid)
         }
         jcol[f] = (P.strided && n > 0) ? fiber_start(P, n, j) : j;   // strided: the fiber's first entry
         if constexpr (sizeof(T) == 8)
-            ss[f] = __ddiv_rn(1.0, __dmul_rn(__dmul_rn((double)P.B, P.Jn[n]), fiber_prob_staged(P, n, row, staged ? stage : nullptr)));
+            ss[f] = __ddiv_rn(1.0, __dmul_rn(__dmul_rn((double)(P.B / P.block), P.Jn[n]),
+                                             fiber_prob_staged(P, n, row, staged ? stage : nullptr)));
         else
             ss[f] = staged ? fiber_weight_staged(P, n, row, stage) : fiber_weight(P, n, row);
         if (gr == 0)

@@ -74,10 +74,10 @@ def rel(a, b) -> float:
     return float(np.linalg.norm(a - b) / (den if den > 0 else 1.0))
 
 
-def grad_row_scale(dims, n, idx, p, A, xbuf, x_dtype, B):
+def grad_row_scale(dims, n, idx, p, A, xbuf, x_dtype, B, terms=None):
     """scale_i of every row of G^(n) for the batch (idx, p) (see the module docstring)."""
     from oracle import oracle as O
-    return O.grad_row_scale(dims, n, idx, p, A, xbuf, x_dtype, B)
+    return O.grad_row_scale(dims, n, idx, p, A, xbuf, x_dtype, B, terms)
 
 
 def row_errors(G_gpu, G_orc, scale, A_gpu, A_orc, A_prev):
@@ -128,7 +128,8 @@ def teacher_forced(dec, orc, ocfg, xbuf, steps, tol_G, tol_A, check_every=1, tol
         for k in range(len(A)):
             if k != n:
                 np.testing.assert_array_equal(A1[k].double().numpy(), A[k])
-        scale = grad_row_scale(dims, n, out["idx"], out["p"], A_prev, xbuf, ocfg.x_dtype, ocfg.B)
+        scale = grad_row_scale(dims, n, out["idx"], out["p"], A_prev, xbuf, ocfg.x_dtype, ocfg.B,
+                               ocfg.B // max(1, ocfg.block))
         eGr, eAr = row_errors(G.numpy(), out["G"], scale, A1[n].double().numpy(), A_step, A_prev[n])
         assert eG <= tol_G, (t, n, eG)
         assert eA <= tol_A, (t, n, eA)

@@ -62,6 +62,10 @@ def _init_status(cpd, **kw):
     (dict(dims=(64, 64, 64), R=16, B=64, engine="fused", max_ctas=3), "cluster size"),
     (dict(dims=(64, 64, 64), R=16, B=4000, engine="fused", max_ctas=16), "208 fibers"),
     (dict(dims=(64, 64, 64), R=16, B=64, x_dtype="f32", engine="fused"), "tensor-core engine"),
+    (dict(dims=(8, 8, 8), R=1, B=4, block=3), "must divide B, I_1 and I_2"),
+    (dict(dims=(6, 8, 8), R=1, B=8, block=4), "must divide B, I_1 and I_2"),
+    (dict(dims=(8, 8, 8), R=1, B=8, block=-1), "block must be >= 0"),
+    (dict(dims=(64, 64, 64), R=16, B=64, block=2, engine="persistent"), "samples fibers one by one"),
     (dict(dims=(8, 8, 8), R=1, B=4, x_layout="strided", engine="cluster"), "strided x_layout"),
 ])
 def test_invalid_configs_rejected_on_host(cpd, kw, msg):

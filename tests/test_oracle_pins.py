@@ -669,3 +669,113 @@ def test_sample_batch_is_the_step_batch(orc):
             j = orc.unfold_col(dims, n, tup)
             np.testing.assert_allclose(sb["Z"][f], Z[j], rtol=1e-15)
             np.testing.assert_array_equal(sb["X"][f], Xn[:, j])
+
+
+# ------------------------------------------------------------------ #
+# Remark 1: blocks of rows first, then sampling blocks                #
+# ------------------------------------------------------------------ #
+
+def _fiber_probs(orc, A, n, sampling):
+    """p_j of every mode-n fiber j (Eq. (2) order), from the per-factor
+    probabilities computed here by numpy from the oracle's exact CDFs."""
+    N = len(A)
+    per = []
+    for k in range(N):
+        if k == n:
+            continue
+        _, w = orc.weights(sampling, A[k])
+        _, cdf = orc.distribution(w)
+        q = np.diff(np.concatenate([[0], cdf.astype(object)])).astype(np.float64)
+        per.append(q / float(cdf[-1]))
+    # Eq. (2): the first other mode varies fastest
+    P = per[0]
+    for pk in per[1:]:
+        P = np.outer(pk, P).reshape(-1)
+    return P
+
+
+@pytest.mark.parametrize("dims,R,bs,sampling", [((4, 6, 3), 2, 2, "euclidean"), ((4, 4, 5), 2, 4, "leverage"),
+                                                 ((6, 3, 2, 3), 2, 3, "euclidean"), ((4, 6, 3), 2, 2, "uniform")])
+def test_block_sampling_unbiased_and_block_probabilities(orc, dims, R, bs, sampling):
+    """Every block of `bs` consecutive mode-n fibers (an aligned range of the
+    first other mode's rows, other indices fixed) as the whole batch: the
+    recorded probability of each of its fibers is the sum of its fibers'
+    per-fiber probabilities (brute force over the explicit Eq. (10) products),
+    the block probabilities sum to 1, and the expectation of Eq. (11) over all
+    blocks is the full gradient / J_n (Thm 5 for blocks)."""
+    A, X = rand_problem(dims, R, 29)
+    N = len(dims)
+    for n in range(N):
+        k0 = 1 if n == 0 else 0
+        others = [k for k in range(N) if k != n]
+        cfg = orc.Config(dims=dims, R=R, B=bs, sampling=sampling, block=bs)
+        Pj = _fiber_probs(orc, A, n, sampling)
+        _, Z, grad = full_gradient(A, X, n)
+        Jn = Z.shape[0]
+        EG = np.zeros_like(grad)
+        total = 0.0
+        ranges = [range(dims[k] // bs) if k == k0 else range(dims[k]) for k in others]
+        for combo in itertools.product(*ranges):
+            idx = np.full((bs, N), -1, dtype=np.int64)
+            for u in range(bs):
+                for k, v in zip(others, combo):
+                    idx[u, k] = v * bs + u if k == k0 else v
+            st, p, G = orc.gradient_for_batch(cfg, n, idx, X, A)
+            assert st == orc.OK
+            assert np.all(p == p[0])
+            # columns of the block's fibers by Eq. (2), their p_j summed
+            cols = []
+            for u in range(bs):
+                j, Jp = 0, 1
+                for k in others:
+                    j += idx[u, k] * Jp
+                    Jp *= dims[k]
+                cols.append(j)
+            assert cols == list(range(cols[0], cols[0] + bs))   # consecutive columns
+            np.testing.assert_allclose(p[0], Pj[cols].sum(), rtol=1e-13)
+            total += p[0]
+            EG += p[0] * G
+        assert abs(total - 1.0) < 1e-12
+        np.testing.assert_allclose(EG, grad / Jn, rtol=1e-11, atol=1e-13 * np.abs(grad).max())
+
+
+def test_block_sampling_draws_and_reduces_to_per_fiber(orc):
+    """block = 1 is the per-fiber method bit for bit; with blocks, the fibers of
+    each sampled block share every other index, run through one aligned block
+    of rows of the first other mode, and the block's rows are drawn with the
+    word of (t, block) -- so the first fiber of block beta repeats the per-fiber
+    draw of slot beta, moved to its block's first row."""
+    dims, R, B, bs = (8, 12, 6), 3, 24, 4
+    A, X = rand_problem(dims, R, 31)
+    base = orc.Config(dims=dims, R=R, B=B, sampling="euclidean", seed=5)
+    one = orc.Config(dims=dims, R=R, B=B, sampling="euclidean", seed=5, block=1)
+    blk = orc.Config(dims=dims, R=R, B=B, sampling="euclidean", seed=5, block=bs)
+    for t in range(6):
+        n = orc.mode_draw(5, t, 3)
+        k0 = 1 if n == 0 else 0
+        s0 = orc.sample_batch(base, n, t, A, X=X)
+        s1 = orc.sample_batch(one, n, t, A, X=X)
+        np.testing.assert_array_equal(s0["idx"], s1["idx"])
+        np.testing.assert_array_equal(s0["p"], s1["p"])
+        sb = orc.sample_batch(blk, n, t, A, X=X)
+        assert sb["status"] == orc.OK
+        idx = sb["idx"]
+        for beta in range(B // bs):
+            rows = idx[beta * bs:(beta + 1) * bs]
+            for k in range(3):
+                if k in (n, k0):
+                    continue
+                assert np.all(rows[:, k] == rows[0, k])
+                assert rows[0, k] == s0["idx"][beta, k]
+            assert rows[0, k0] % bs == 0
+            np.testing.assert_array_equal(rows[:, k0], rows[0, k0] + np.arange(bs))
+            assert rows[0, k0] == s0["idx"][beta, k0] // bs * bs
+            assert np.all(sb["p"][beta * bs:(beta + 1) * bs] == sb["p"][beta * bs])
+
+
+def test_block_sampling_rejects_blocks_that_do_not_tile(orc):
+    A, X = rand_problem((6, 8, 5), 2, 3)
+    for dims_ok, B, bs in (((6, 8, 5), 8, 4), ((6, 8, 5), 6, 2)):
+        cfg = orc.Config(dims=(6, 8, 5), R=2, B=B, sampling="euclidean", block=bs)
+        st = orc.sample_batch(cfg, 2, 0, A, X=X)["status"]
+        assert st == (orc.EINVAL if bs == 4 else orc.OK)   # 4 does not divide I_1 = 6
