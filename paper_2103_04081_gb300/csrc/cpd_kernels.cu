@@ -69,8 +69,19 @@ __device__ __forceinline__ void gather_rows(const XT *__restrict__ rep, long lon
 // threads take consecutive rows of a fiber).
 template <class XT, class T>
 __device__ __forceinline__ void gather_rows_strided(const XT *__restrict__ x, long long step, const long long *start,
-                                                    int nf, int r0, int rows, int rb, T *sx)
+                                                    int nf, int r0, int rows, int rb, int bs, T *sx)
 {
+    if (bs > 1 && nf % bs == 0) {
+        // sampled blocks (Remark 1): the bs fibers of a block start at
+        // consecutive elements, so consecutive threads take them for one row
+        // and each warp reads runs of bs adjacent entries
+        for (int e = threadIdx.x; e < nf * rows; e += blockDim.x) {
+            const int u = e % bs, rest = e / bs;
+            const int i = rest % rows, f = (rest / rows) * bs + u;
+            sx[f * rb + i] = load_x<XT, T>(x + start[f] + (long long)(r0 + i) * step);
+        }
+        return;
+    }
     for (int e = threadIdx.x; e < nf * rows; e += blockDim.x) {
         const int f = e / rows, i = e % rows;
         sx[f * rb + i] = load_x<XT, T>(x + start[f] + (long long)(r0 + i) * step);
@@ -158,7 +169,7 @@ __device__ __forceinline__ void grad_simt_body(const Problem<T> &P, int bid)
     // 4. fiber gather from the mode-n replica (Alg. 1, X_(n)(:, F_n))
     if (P.strided && n > 0)
         gather_rows_strided<XT, T>(reinterpret_cast<const XT *>(P.rep[n]), fiber_step(P, n), jcol, nf, r0, rows, rb,
-                                   sx);
+                                   block_mode(n) == 0 ? P.block : 1, sx);
     else
         gather_rows<XT, T>(reinterpret_cast<const XT *>(P.rep[n]), P.ld[n], jcol, nf, r0, rows, rb, sx);
     __syncthreads();
