@@ -1,7 +1,7 @@
 // Gradient-variance diagnostic (Thm 10, Table 1, Fig. 3).
 //
-// For mode n and the current factors, the mini-batch gradient of Eq.
-// gradient1 is G = (1/(B J_n)) sum_f (1/p_f) r_f z_f^T with r_f = A z_f - x_f
+// For mode n and the current factors, the mini-batch gradient of Eq. (11)
+// is G = (1/(B J_n)) sum_f (1/p_f) r_f z_f^T with r_f = A z_f - x_f
 // (the residual column of fiber f, Eq. (2)) and B draws i.i.d. from p. Its
 // conditional moments are exact sums over all J_n fibers j:
 //   S1 = sum_j ||r_j||^2 ||z_j||^2 / p_j,   M = sum_j r_j z_j^T,
