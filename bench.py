@@ -726,7 +726,10 @@ def main() -> None:
     ap.add_argument("--serve-active", type=int, default=64)
     ap.add_argument("--serve-engine", default=SERVE["engine"], choices=["classic", "persistent"])
     ap.add_argument("--serve-cluster", type=int, default=SERVE["cluster"])
+    ap.add_argument("--serve-strided-fraction", type=float, default=SERVE["strided_fraction"],
+                    help="requests whose replicas need more than this fraction of the budget run strided")
     args = ap.parse_args()
+    SERVE["strided_fraction"] = args.serve_strided_fraction
 
     from paper_2103_04081_gb300 import inputs as IN
     w = dict(IN.WORKLOADS[args.workload])
