@@ -987,7 +987,7 @@ extern "C" cpd_status cpd_describe(cpd_ctx *c, char *buf, size_t len)
                   "{\"engine\": \"%s\", \"rows_per_cta\": %d, \"fibers_per_cta\": %d, \"fiber_groups\": %d, "
                   "\"grad_grid\": %d, \"update_grid\": %d, \"grad_smem\": %zu, \"graph_chunk\": %d, "
                   "\"cluster\": %d, \"max_clusters\": %d, \"deferred_cdf\": %d, "
-                  "\"fit_pass\": \"%s\", \"x_layout\": \"%s\", \"xnorm2\": %.17g}",
+                  "\"fit_pass\": \"%s\", \"x_layout\": \"%s\", \"block\": %d, \"xnorm2\": %.17g}",
                   c->engine == kEnginePersistent       ? "persistent"
                   : c->engine == kEngineFused         ? "fused"
                   : c->engine == kEngineTensorCluster ? "cluster"
@@ -996,7 +996,8 @@ extern "C" cpd_status cpd_describe(cpd_ctx *c, char *buf, size_t len)
                   rb, fb, pf, c->grid_grad, c->grid_upd,
                   c->smem_grad, kGraphChunk, c->fbytes == 8 ? 1 : c->Pf.cs, c->max_clusters,
                   c->fbytes == 8 ? c->Pd.defer_cdf : c->Pf.defer_cdf, c->fit_tc ? "tensor" : "cuda_cores",
-                  (c->fbytes == 8 ? c->Pd.strided : c->Pf.strided) ? "strided" : "replicas", c->xnorm2);
+                  (c->fbytes == 8 ? c->Pd.strided : c->Pf.strided) ? "strided" : "replicas",
+                  c->fbytes == 8 ? c->Pd.block : c->Pf.block, c->xnorm2);
     return CPD_OK;
 }
 

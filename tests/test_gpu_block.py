@@ -40,7 +40,7 @@ def test_teacher_forced_block_sampling(cpd, orc, engine, xdt, dims, R, B, bs, sa
     dec = cpd.Decomposition(X.cuda(), [a.cuda() for a in A0], dims=dims, R=R, B=B, x_dtype=xdt,
                             sampling=sampling, step="adagrad", seed=13, engine=engine, block=bs,
                             x_layout=layout)
-    assert dec.describe()["engine"] == engine
+    assert dec.describe()["engine"] == engine and dec.describe()["block"] == bs
     ocfg = orc.Config(dims=dims, R=R, B=B, sampling=sampling, step="adagrad", x_dtype=xdt, seed=13, block=bs)
     key = "bf16_tensor" if engine in ("tensor", "cluster", "fused") else xdt
     worst = forced(dec, orc, ocfg, oracle_xbuf(X), 9, key)

@@ -28,6 +28,7 @@ CLASSES = {
         ((33, 17, 9, 5), 3, 20, "f32", "euclidean", "decay", 2, dict(beta=0.01, gamma=2.0)),
         ((120, 90, 200), 24, 512, "f32", "euclidean", "adagrad", 8, {}),
         ((90, 130, 40), 7, 64, "f32", "leverage", "adagrad", 0, {}),
+        ((64, 48, 30), 8, 96, "f32", "euclidean", "adagrad", 0, dict(block=4)),      # sampled blocks
     ],
     "simt_leverage": [
         ((80, 70, 60), 6, 48, "f32", "leverage", "adagrad", 0, {}),
@@ -44,6 +45,7 @@ CLASSES = {
         ((60, 70, 55, 40), 16, 512, "bf16", "euclidean", "adagrad", 4, {}),
         ((129, 257, 70), 64, 256, "bf16", "euclidean", "fixed", 2, dict(alpha=0.0005)),
         ((150, 120, 90), 24, 256, "bf16", "leverage", "adagrad", 4, {}),
+        ((128, 96, 60), 24, 256, "bf16", "euclidean", "adagrad", 4, dict(block=8)),
     ],
 }
 
