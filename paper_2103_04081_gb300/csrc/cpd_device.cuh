@@ -207,11 +207,14 @@ __device__ __forceinline__ unsigned long long quantize(double w, int s)
 // In place: `a` holds the bit patterns of the FP64 row weights w[0..I) on
 // entry and the fixed-point CDF (same definition as block_distribution) on
 // exit. Each thread transforms a contiguous chunk, reading every weight
-// before overwriting it. `sm` holds 2 * blockDim.x uint64 slots. Returns
-// false in every thread when the distribution has no mass.
+// before overwriting it. `sm` holds 2 * kThreads uint64 slots. Returns false
+// in every thread when the distribution has no mass. Blocks of kThreads
+// threads: the warps' partials are then combined by unrolled loops whose
+// shared-memory loads are independent.
 __device__ inline bool block_distribution_inplace(unsigned long long *a, long long I, unsigned long long *sm)
 {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    constexpr int nt = kThreads, nw = kThreads / 32;
+    const int tid = threadIdx.x;
     long long mx = 0;
     int bad = 0;
     for (long long i = tid; i < I; i += nt) {
@@ -228,7 +231,8 @@ __device__ inline bool block_distribution_inplace(unsigned long long *a, long lo
     if ((tid & 31) == 0) sm[tid >> 5] = (unsigned long long)mx;
     __syncthreads();
     long long gmx = 0;
-    for (int q = 0; q < (nt >> 5); ++q) gmx = (long long)sm[q] > gmx ? (long long)sm[q] : gmx;
+#pragma unroll
+    for (int q = 0; q < nw; ++q) gmx = (long long)sm[q] > gmx ? (long long)sm[q] : gmx;
     __syncthreads();
     const double wmax = __longlong_as_double(gmx);
     if (bad || !(wmax > 0.0)) return false;
@@ -248,15 +252,18 @@ __device__ inline bool block_distribution_inplace(unsigned long long *a, long lo
     }
     if ((tid & 31) == 31) sm[nt + (tid >> 5)] = inc;
     __syncthreads();
-    unsigned long long acc = 0;
-    for (int q = 0; q < (tid >> 5); ++q) acc += sm[nt + q];
+    unsigned long long acc = 0, Q = 0;
+#pragma unroll
+    for (int q = 0; q < nw; ++q) {
+        const unsigned long long v = sm[nt + q];
+        if (q < (tid >> 5)) acc += v;
+        Q += v;
+    }
     acc += inc - tot;
     for (long long i = i0; i < i1; ++i) {
         acc += quantize(__longlong_as_double((long long)a[i]), s);
         a[i] = acc;
     }
-    unsigned long long Q = 0;
-    for (int q = 0; q < (nt >> 5); ++q) Q += sm[nt + q];
     __syncthreads();
     return Q > 0;
 }
@@ -289,13 +296,14 @@ __device__ __forceinline__ void stage_words(W *dst, const W *src, long long n)
 // one CTA: s = 61 - ceil(log2 I) - floor(log2 max w), q_i = floor(w_i 2^s),
 // cdf = inclusive prefix sum of q (exact, so any summation order gives the
 // same bits). Returns false (in every thread) when a weight is negative or
-// not finite, or when every q_i is 0. `sm` holds 2 * blockDim.x uint64 slots.
+// not finite, or when every q_i is 0. `sm` holds 2 * kThreads uint64 slots.
 // w is read through L2 (other CTAs of the launch may have written it).
 // ---------------------------------------------------------------------------
 __device__ inline bool block_distribution(const double *wg, long long I, unsigned long long *cdf,
                                           unsigned long long *sm, double *wstage, long long wcap)
 {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    constexpr int nt = kThreads, nw = kThreads / 32;   // blocks of kThreads threads
+    const int tid = threadIdx.x;
     const double *w = wg;
     if (wstage && I <= wcap) {   // one coalesced pass through L2, then shared memory
         stage_words<double, true>(wstage, wg, I);
@@ -319,7 +327,8 @@ __device__ inline bool block_distribution(const double *wg, long long I, unsigne
     if ((tid & 31) == 0) sm[tid >> 5] = (unsigned long long)mx;
     __syncthreads();
     long long gmx = 0;
-    for (int q = 0; q < (nt >> 5); ++q) gmx = (long long)sm[q] > gmx ? (long long)sm[q] : gmx;
+#pragma unroll
+    for (int q = 0; q < nw; ++q) gmx = (long long)sm[q] > gmx ? (long long)sm[q] : gmx;
     __syncthreads();
     const double wmax = __longlong_as_double(gmx);
     if (bad || !(wmax > 0.0)) return false;
@@ -342,15 +351,18 @@ __device__ inline bool block_distribution(const double *wg, long long I, unsigne
     }
     if ((tid & 31) == 31) sm[nt + (tid >> 5)] = inc;
     __syncthreads();
-    unsigned long long base = 0;
-    for (int q = 0; q < (tid >> 5); ++q) base += sm[nt + q];
+    unsigned long long base = 0, Q = 0;
+#pragma unroll
+    for (int q = 0; q < nw; ++q) {
+        const unsigned long long v = sm[nt + q];
+        if (q < (tid >> 5)) base += v;
+        Q += v;
+    }
     unsigned long long acc = base + inc - tot;
     for (long long i = i0; i < i1; ++i) {
         acc += quantize(w == wg ? __ldcg(w + i) : w[i], s);
         cdf[i] = acc;
     }
-    unsigned long long Q = 0;
-    for (int q = 0; q < (nt >> 5); ++q) Q += sm[nt + q];
     __syncthreads();
     return Q > 0;
 }
@@ -388,7 +400,7 @@ __device__ __forceinline__ unsigned long long row_mass(const unsigned long long 
 //
 // When CDF rebuilds are deferred (P.defer_cdf), the mode updated last
 // (*P.dirty) has only fresh row weights: its CDF is rebuilt here, in the
-// staging buffer, from those weights (scratch: `dsm`, 2 * blockDim.x uint64),
+// staging buffer, from those weights (scratch: `dsm`, 2 * kThreads uint64),
 // and the one CTA of the launch that passes `writer` stores it for later
 // iterations.
 template <class T>
