@@ -82,9 +82,12 @@ __device__ __forceinline__ unsigned long long fiber_word(unsigned long long seed
 // every lane's candidate range into 32 segments: the warp issues the 32
 // draws' segment-end loads back to back (one memory round trip per level for
 // all 32 draws) and a ballot per draw picks the segment, so an I-entry CDF
-// costs ceil(log32 I) + 1 dependent round trips.
+// costs ceil(log32 I) + 1 dependent round trips. Kept out of line: its
+// unrolled levels are long (about 130 KB of code), run only when the CDFs do
+// not fit the staging buffer, and would otherwise sit inside every sampler's
+// loop and lengthen the code each launch fetches.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ long long warp_search_cdf(const unsigned long long *__restrict__ c, long long I,
+static __device__ __noinline__ long long warp_search_cdf(const unsigned long long *__restrict__ c, long long I,
                                                      unsigned long long target, bool active)
 {
     const unsigned full = 0xffffffffu;
@@ -299,8 +302,10 @@ __device__ __forceinline__ void stage_words(W *dst, const W *src, long long n)
 // not finite, or when every q_i is 0. `sm` holds 2 * kThreads uint64 slots.
 // w is read through L2 (other CTAs of the launch may have written it).
 // ---------------------------------------------------------------------------
-__device__ inline bool block_distribution(const double *wg, long long I, unsigned long long *cdf,
-                                          unsigned long long *sm, double *wstage, long long wcap)
+// Out of line: the iteration kernels call it only where a CDF is rebuilt at
+// once (not deferred), and its body would otherwise lengthen their code.
+static __device__ __noinline__ bool block_distribution(const double *wg, long long I, unsigned long long *cdf,
+                                                       unsigned long long *sm, double *wstage, long long wcap)
 {
     constexpr int nt = kThreads, nw = kThreads / 32;   // blocks of kThreads threads
     const int tid = threadIdx.x;
@@ -511,8 +516,9 @@ __device__ __forceinline__ double fiber_prob_staged(const Problem<T> &P, int n, 
 // gradient's own precision): (1/(B J_n)) prod_k Q_k / q_k(i_k). With blocks
 // of bs fibers, 1 / ((B / bs) J_n p_b): P.inv_bj carries the factor bs and
 // k0's q is its block's.
+// Out of line: it serves only CDFs too long to stage (see warp_search_cdf).
 template <class T>
-__device__ __forceinline__ float fiber_weight(const Problem<T> &P, int n, const int *row)
+static __device__ __noinline__ float fiber_weight(const Problem<T> &P, int n, const int *row)
 {
     float s = P.inv_bj[n];
     for (int k = 0; k < P.N; ++k) {
