@@ -369,6 +369,7 @@ __device__ __forceinline__ void gram_body(const Problem<T> &P, int k_mode, int b
     double *Lm = P.lev_L, *inv = P.lev_L + R * R;
     __shared__ int s_bad;
     __shared__ double s_col[256];  // column q of L below the diagonal, contiguous
+    __shared__ double s_gd[256];   // g_jj, the pivots' degeneracy thresholds
     // Right-looking order: once column q of L is final, every entry (i, j)
     // with q < j <= i takes its update -L_iq L_jq at once. Each entry still
     // receives the fmas of q = 0, 1, ..., j-1 in ascending order, as in the
@@ -382,21 +383,24 @@ __device__ __forceinline__ void gram_body(const Problem<T> &P, int k_mode, int b
     double *W = in_smem ? lev_dyn : Lm;
     double *wi = in_smem ? lev_dyn + R * R : inv;
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) W[e] = __ldcg(g + e);
-    // pivot j: W_jj holds g_jj minus all its updates
-    auto pivot = [&](int j) {
-        const double gjj = __ldcg(g + j * R + j);
-        double d = W[j * R + j];
-        if (!(d > 0x1.0p-40 * gjj)) {
+    for (int j = threadIdx.x; j < R; j += blockDim.x) s_gd[j] = __ldcg(g + j * R + j);
+    // pivot j from d, g_jj minus all its updates. The pivots form the only
+    // dependent chain of the factorisation (R square roots and reciprocals),
+    // so nothing on it goes through memory: the threshold is staged above and
+    // d and L_jj stay in registers.
+    auto pivot = [&](int j, double d) {
+        if (!(d > 0x1.0p-40 * s_gd[j])) {
             s_bad = 1;
             d = 1.0;
         }
-        W[j * R + j] = __dsqrt_rn(d);
-        wi[j] = __drcp_rn(W[j * R + j]);  // 1/L_jj, correctly rounded
+        const double ljj = __dsqrt_rn(d);
+        W[j * R + j] = ljj;
+        wi[j] = __drcp_rn(ljj);  // 1/L_jj, correctly rounded
     };
     __syncthreads();
     if (threadIdx.x == 0) {
         s_bad = 0;
-        pivot(0);
+        pivot(0, W[0]);
     }
     __syncthreads();
     static_assert(kThreads >= 64, "the factorisation needs a pivot warp and an update warp");
@@ -412,9 +416,8 @@ __device__ __forceinline__ void gram_body(const Problem<T> &P, int k_mode, int b
         // factors pivot q+1 while warps 1, 2, ... update rows q+2, q+3, ...
         if (warp == 0) {
             if (lane == 0 && q + 1 < R) {
-                const int d = (q + 1) * (R + 1);
-                W[d] = __fma_rn(-s_col[q + 1], s_col[q + 1], W[d]);
-                pivot(q + 1);
+                const double c = s_col[q + 1];
+                pivot(q + 1, __fma_rn(-c, c, W[(q + 1) * (R + 1)]));
             }
         } else {
             for (int i = q + 2 + (warp - 1); i < R; i += nwarp - 1) {
