@@ -646,6 +646,8 @@ int orc_step(const orc_cfg *c, int64_t t, const void *X, double *const *A,
     int32_t N = c->N, R = c->R, B = c->B;
     if (N < 2 || N > ORC_MAXN || R < 1 || B < 1 || !blocks_valid(c))
         return ORC_EINVAL;
+    if (c->step == ORC_STEP_ADAGRAD && !S)     /* Eq. (13a) needs the accumulators */
+        return ORC_EINVAL;
     int32_t n = orc_mode_draw(c->seed, t, N);
     int64_t In = c->dims[n];
     int64_t *idx = (int64_t *)malloc((size_t)B * N * sizeof(int64_t));

@@ -223,6 +223,8 @@ def test_distribution_degenerate(orc):
     assert orc.distribution(np.zeros(5))[0] == orc.EDEGENERATE
     assert orc.distribution(np.array([1.0, np.nan]))[0] == orc.EDEGENERATE
     assert orc.distribution(np.array([1.0, -2.0]))[0] == orc.EDEGENERATE
+    for w in ([np.inf, 1.0, 2.0], [1.0, 2.0, np.inf], [np.nan, 1.0], [-0.5, 1.0]):   # first and last entries
+        assert orc.distribution(np.array(w))[0] == orc.EDEGENERATE, w
 
 
 def test_draw_matches_bigint(orc):
@@ -779,3 +781,194 @@ def test_block_sampling_rejects_blocks_that_do_not_tile(orc):
         cfg = orc.Config(dims=(6, 8, 5), R=2, B=B, sampling="euclidean", block=bs)
         st = orc.sample_batch(cfg, 2, 0, A, X=X)["status"]
         assert st == (orc.EINVAL if bs == 4 else orc.OK)   # 4 does not divide I_1 = 6
+
+
+# ------------------------------------------------------------------ #
+# Edges: the degeneracy threshold, exact block masses, the step's own  #
+# Eq. (11) with blocks, the limits of the configuration, T iterations  #
+# ------------------------------------------------------------------ #
+
+def test_leverage_degeneracy_threshold(orc):
+    """Def. 3 assumes full column rank; a Cholesky pivot at or below 2^-40 of
+    its Gram diagonal entry reads as rank-deficient. A = [[1, c], [0, c s]]
+    with powers of two makes every Gram entry and pivot exact: g_00 = 1,
+    g_01 = c, g_11 = c^2 (1 + s^2) and the last pivot d = c^2 s^2. With
+    c = 2^10 and s = 2^-21 the pivot 2^-22 lies below 2^-40 g_11 (about 2^-20)
+    but above 2^-40 g_01 and 2^-40 / g_11: only the threshold on the pivot's
+    own diagonal entry calls it degenerate. s = 2^-19 (pivot 2^-18) is full
+    rank, and a zero first column (pivot 0 against threshold 0) is not."""
+    c = 2.0 ** 10
+    for s, want in ((2.0 ** -21, orc.EDEGENERATE), (2.0 ** -19, orc.OK)):
+        A = np.array([[1.0, c], [0.0, c * s]])
+        st, w = orc.weights("leverage", A)
+        assert st == want, (s, st)
+        if want == orc.OK:
+            np.testing.assert_allclose(w, [1.0, 1.0], rtol=1e-12)   # square A: Q is orthogonal
+    A = np.array([[0.0, 1.0], [0.0, 2.0], [0.0, 3.0]])
+    assert orc.weights("leverage", A)[0] == orc.EDEGENERATE
+    # a pivot exactly at the threshold: four unit columns, then a column of
+    # integers whose squares sum to 2^40, so g_44 = 2^40 and the last pivot is
+    # 1 = 2^-40 g_44 exactly (every sum below 2^53)
+    A = np.eye(5)
+    A[:, 4] = [1048575.0, 1447.0, 50.0, 29.0, 1.0]
+    assert orc.weights("leverage", A)[0] == orc.EDEGENERATE
+    A[4, 4] = 2.0        # g_44 = 2^40 + 3, pivot 4, above its threshold 2^-40 (2^40 + 3)
+    assert orc.weights("leverage", A)[0] == orc.OK
+
+
+def test_block_probability_is_the_exact_block_mass(orc):
+    """Remark 1 with Eq. (10): a fiber's recorded probability is its block's
+    mass over the total, (cdf[(b+1) bs - 1] - cdf[b bs - 1]) / Q (cdf[-1] = 0),
+    times the other modes' q_i / Q, in ascending mode order and compared bit
+    for bit. The first block of each factor that can form blocks carries
+    weights 1e-12 times the others, so its mass is a small integer that a
+    wrong lower bound would change."""
+    dims, R, bs = (8, 12, 6), 3, 4
+    A, X = rand_problem(dims, R, 41)
+    A[0][:bs] *= 1e-6
+    A[1][:bs] *= 1e-6
+    cdf = {}
+    for k in range(3):
+        _, w = orc.weights("euclidean", A[k])
+        st, ck = orc.distribution(w)
+        assert st == orc.OK
+        cdf[k] = [0] + [int(v) for v in ck]          # cdf[k][i + 1] = q_0 + ... + q_i
+    small = False
+    for n in range(3):
+        k0 = 1 if n == 0 else 0
+        other = [k for k in range(3) if k not in (n, k0)][0]
+        cfg = orc.Config(dims=dims, R=R, B=bs, sampling="euclidean", block=bs)
+        for b in range(dims[k0] // bs):
+            for v in range(dims[other]):
+                idx = np.full((bs, 3), -1, dtype=np.int64)
+                idx[:, k0] = b * bs + np.arange(bs)
+                idx[:, other] = v
+                st, p, _ = orc.gradient_for_batch(cfg, n, idx, X, A)
+                assert st == orc.OK
+                want = 1.0
+                for k in sorted((k0, other)):
+                    Q = float(cdf[k][-1])
+                    if k == k0:
+                        mass = cdf[k][(b + 1) * bs] - cdf[k][b * bs]
+                        small |= b == 0 and mass < 2 ** 40
+                    else:
+                        mass = cdf[k][v + 1] - cdf[k][v]
+                    want = want * (float(mass) / Q)
+                assert np.all(p == want), (n, b, v, p[0], want)
+    assert small
+
+
+def test_block_step_is_its_batch_gradient(orc):
+    """orc_step with blocks: the batch is sample_batch's, G is Eq. (11) on it
+    with 1/B read as 1/(B / bs) -- equal to gradient_for_batch on the same
+    batch, and, Eq. (11) being linear in its terms, to the mean of the
+    gradients of its blocks taken one at a time (B = bs, the case the
+    enumeration above pins)."""
+    dims, R, B, bs = (8, 12, 6), 3, 12, 4
+    A, X = rand_problem(dims, R, 43)
+    cfg = orc.Config(dims=dims, R=R, B=B, sampling="euclidean", step="fixed", alpha=0.05, block=bs, seed=3)
+    one = orc.Config(dims=dims, R=R, B=bs, sampling="euclidean", block=bs)
+    for t in range(6):
+        A0 = [a.copy() for a in A]
+        out = orc.step(cfg, t, X, A)
+        assert out["status"] == orc.OK
+        n = out["n"]
+        sb = orc.sample_batch(cfg, n, t, A0, X=X)
+        np.testing.assert_array_equal(sb["idx"], out["idx"])
+        st, p, G = orc.gradient_for_batch(cfg, n, out["idx"], X, A0)
+        assert st == orc.OK
+        np.testing.assert_array_equal(p, out["p"])
+        np.testing.assert_array_equal(G, out["G"])
+        blocks = [orc.gradient_for_batch(one, n, out["idx"][q * bs:(q + 1) * bs], X, A0)[2]
+                  for q in range(B // bs)]
+        np.testing.assert_allclose(out["G"], np.mean(blocks, axis=0), rtol=1e-12,
+                                   atol=1e-14 * np.abs(out["G"]).max())
+
+
+@pytest.mark.parametrize("dims,R,B", [((5, 4), 2, 1), ((2,) * 8, 1, 1), ((3, 4, 2), 1, 2)])
+def test_configuration_limits_accepted(orc, dims, R, B):
+    """N = 2 (a matrix), N = 8 (the largest order), R = 1 and B = 1 are in the
+    method's domain: step and sample_batch accept them and draw the same batch,
+    the step's G is Eq. (11) on it, and with B = 1 the expectation over every
+    fiber is the full gradient / J_n with probabilities summing to 1 (Thm 5)."""
+    A, X = rand_problem(dims, R, 47)
+    N = len(dims)
+    cfg = orc.Config(dims=dims, R=R, B=B, sampling="euclidean", step="fixed", alpha=0.01, seed=2)
+    for t in range(3):
+        A0 = [a.copy() for a in A]
+        out = orc.step(cfg, t, X, A)
+        assert out["status"] == orc.OK
+        sb = orc.sample_batch(cfg, out["n"], t, A0, X=X)
+        assert sb["status"] == orc.OK
+        np.testing.assert_array_equal(sb["idx"], out["idx"])
+        st, _, G = orc.gradient_for_batch(cfg, out["n"], out["idx"], X, A0)
+        np.testing.assert_array_equal(G, out["G"])
+    if B != 1:
+        return
+    for n in range(N):
+        _, Z, grad = full_gradient(A, X, n)
+        Jn = Z.shape[0]
+        others = [k for k in range(N) if k != n]
+        EG, total = np.zeros_like(grad), 0.0
+        for combo in itertools.product(*[range(dims[k]) for k in others]):
+            idx = np.full((1, N), -1, dtype=np.int64)
+            idx[0, others] = combo
+            st, p, G = orc.gradient_for_batch(cfg, n, idx, X, A)
+            assert st == orc.OK
+            total += p[0]
+            EG += p[0] * G
+        assert abs(total - 1.0) < 1e-12
+        np.testing.assert_allclose(EG, grad / Jn, rtol=1e-11, atol=1e-13 * np.abs(grad).max())
+
+
+def test_configuration_out_of_range_rejected(orc):
+    """N outside [2, 8], R < 1, B < 1, a mode outside [0, N), a negative or
+    non-tiling block and an AdaGrad step without its accumulators are
+    rejected; block = 0 means per-fiber sampling, like 1."""
+    from dataclasses import replace
+    import ctypes
+    dims = (3, 4, 2)
+    A, X = rand_problem(dims, 2, 5)
+    ok = orc.Config(dims=dims, R=2, B=2, step="fixed")
+    assert orc.step(ok, 0, X, [a.copy() for a in A])["status"] == orc.OK
+    assert orc.step(replace(ok, step="adagrad"), 0, X, [a.copy() for a in A])["status"] == orc.EINVAL  # no S
+    for kw in (dict(R=0), dict(B=0), dict(block=-1), dict(block=3)):     # 3 does not divide I_2 = 4
+        cfg = replace(ok, **kw)
+        assert orc.step(cfg, 0, X, [a.copy() for a in A])["status"] == orc.EINVAL, kw
+        assert orc.sample_batch(cfg, 0, 0, A, X=X, want_fibers=False)["status"] == orc.EINVAL, kw
+    for n in (-1, 3):
+        assert orc.sample_batch(ok, n, 0, A, X=X, want_fibers=False)["status"] == orc.EINVAL, n
+    A1, X1 = rand_problem((5,), 2, 6)
+    c1 = orc.Config(dims=(5,), R=2, B=2, step="fixed")
+    assert orc.step(c1, 0, X1, [a.copy() for a in A1])["status"] == orc.EINVAL
+    assert orc.sample_batch(c1, 0, 0, A1, X=X1, want_fibers=False)["status"] == orc.EINVAL
+    A8, X8 = rand_problem((2,) * 8, 1, 7)
+    c = orc.Config(dims=(2,) * 8, R=1, B=1, step="fixed").c()
+    c.N = 9
+    buf = orc.x_buffer(X8, "f64")
+    idx = np.zeros((1, 9), dtype=np.int64)
+    p, G = np.zeros(1), np.zeros((2, 1))
+    st = orc.lib().orc_step(ctypes.byref(c), 0, orc._ptr(buf), orc._ptr_array(A8), None, None,
+                            orc._ptr(idx), orc._ptr(p), orc._ptr(G))
+    assert st == orc.EINVAL
+    for t in range(3):
+        s0 = orc.sample_batch(replace(ok, block=0), 1, t, A, X=X)
+        s1 = orc.sample_batch(ok, 1, t, A, X=X)
+        assert s0["status"] == s1["status"] == orc.OK
+        np.testing.assert_array_equal(s0["idx"], s1["idx"])
+        np.testing.assert_array_equal(s0["p"], s1["p"])
+
+
+def test_run_is_T_iterations(orc):
+    """orc_run(t0, T) performs the iterations t0, ..., t0 + T - 1: the same
+    factors and AdaGrad state, bit for bit, as T calls of the step."""
+    dims, R, B = (5, 4, 3), 2, 4
+    A, X = rand_problem(dims, R, 7)
+    cfg = orc.Config(dims=dims, R=R, B=B, step="adagrad", eta=0.1, seed=11)
+    A1, S1 = [a.copy() for a in A], [np.zeros_like(a) for a in A]
+    A2, S2 = [a.copy() for a in A], [np.zeros_like(a) for a in A]
+    assert orc.run(cfg, 3, 5, X, A1, S1) == orc.OK
+    for t in range(3, 8):
+        assert orc.step(cfg, t, X, A2, S2)["status"] == orc.OK
+    for a, b in zip(A1 + S1, A2 + S2):
+        np.testing.assert_array_equal(a, b)
