@@ -651,6 +651,53 @@ def test_grad_row_scale_bounds_every_row(orc):
     assert np.all(scale <= 100 * g.max() + 1e-300) and scale.min() > 0
 
 
+@pytest.mark.parametrize("zero,bs", [("X", 1), ("An", 1), ("X", 4), ("An", 4)])
+def test_grad_row_scale_is_tight_on_nonnegative_data(orc, zero, bs):
+    """With nonnegative factors and tensor, |A^(n)| |H| = A^(n) H and the
+    second term is the size of M_i, so when one of the two products of
+    Eq. (11) vanishes -- X = 0 (M = 0), or A^(n) = 0 for the mode the step
+    draws (A H = 0) -- the scale of every row is |G_i| itself (to rounding):
+    an inflated scale would loosen every parity test that uses it. With
+    blocks of bs fibers, Eq. (11)'s 1/B counts B / bs terms."""
+    dims, R, B = ((8, 8, 7), 3, 24) if bs > 1 else ((9, 8, 7), 3, 25)
+    A, X = rand_problem(dims, R, 35, noise=0.0)
+    A = [np.abs(a) + 0.1 for a in A]
+    X = np.abs(X) + 0.2
+    seed, t = 4, 0
+    n = orc.mode_draw(seed, t, 3)
+    if zero == "X":
+        X = np.zeros(dims)
+    else:
+        A[n] = np.zeros_like(A[n])
+    xb = np.asfortranarray(X).ravel(order="F")
+    cfg = orc.Config(dims=dims, R=R, B=B, sampling="euclidean", step="fixed", seed=seed, block=bs)
+    out = orc.step(cfg, t, X, [a.copy() for a in A])
+    assert out["status"] == orc.OK and out["n"] == n
+    scale = orc.grad_row_scale(dims, n, out["idx"], out["p"], A, xb, "f64", B, terms=B // bs)
+    g = np.linalg.norm(out["G"], axis=1)
+    np.testing.assert_allclose(scale, g, rtol=1e-12)
+
+
+def test_grad_row_scale_ignores_signs(orc):
+    """The scale is built from absolute values only: flipping the signs of
+    random entries of every factor and of X (which leaves the Euclidean
+    distributions, hence the batch, unchanged) leaves it bit for bit."""
+    dims, R, B = (9, 8, 7), 3, 25
+    A, X = rand_problem(dims, R, 37, noise=0.5)
+    cfg = orc.Config(dims=dims, R=R, B=B, sampling="euclidean", step="fixed", seed=6)
+    out = orc.step(cfg, 0, X, [a.copy() for a in A])
+    n = out["n"]
+    rng = np.random.default_rng(8)
+    Af = [a * rng.choice([-1.0, 1.0], size=a.shape) for a in A]
+    Xf = X * rng.choice([-1.0, 1.0], size=X.shape)
+    out_f = orc.step(cfg, 0, Xf, [a.copy() for a in Af])
+    np.testing.assert_array_equal(out_f["idx"], out["idx"])
+    np.testing.assert_array_equal(out_f["p"], out["p"])
+    s0 = orc.grad_row_scale(dims, n, out["idx"], out["p"], A, np.asfortranarray(X).ravel(order="F"), "f64", B)
+    s1 = orc.grad_row_scale(dims, n, out["idx"], out["p"], Af, np.asfortranarray(Xf).ravel(order="F"), "f64", B)
+    np.testing.assert_array_equal(s0, s1)
+
+
 def test_sample_batch_is_the_step_batch(orc):
     """orc_sample_batch with the mode of iteration t draws exactly the batch
     orc_step records, and its Z and X rows are the KRP rows and fibers of
