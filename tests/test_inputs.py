@@ -67,3 +67,23 @@ def test_streamed_tensor_follows_the_model():
     assert abs(rel - 0.1) < 0.1 * 5 * (2.0 / n) ** 0.5
     y = IN.cp_tensor_streamed(A, 0.1, 5, "f32", chunk_entries=100)
     assert torch.equal(x, y)                                 # seeded
+
+
+def test_correlated_columns_and_lognormal_rows():
+    """The factor recipe of the 300^3 and 1000^3 workloads: rows of
+    A = G chol(C)^T are N(0, C) with C = (1 - c) I + c 11^T (every pair of
+    columns correlated c), and lognormal row scaling multiplies each row by
+    one exp(N(0, 1)) factor (the first mode, whose entries are drawn before
+    its row scales, compared with the unscaled draw of the same seed)."""
+    I, R, c = 40000, 4, 0.8
+    A = IN.factors((I,), R, seed=9, congruence=c)[0].numpy()
+    corr = np.corrcoef(A.T)
+    off = corr[~np.eye(R, dtype=bool)]
+    assert np.all(np.abs(off - c) < 0.01), corr
+    assert np.all(np.abs(A.std(axis=0) - 1.0) < 0.02)        # unit variances: C has ones on its diagonal
+    plain = IN.factors((I, 30), R, seed=11)[0].numpy()
+    logn = IN.factors((I, 30), R, seed=11, lognormal_rows=True)[0].numpy()
+    ratio = logn / plain
+    np.testing.assert_allclose(ratio, ratio[:, :1] * np.ones((1, R)), rtol=1e-12)   # one scale per row
+    z = np.log(ratio[:, 0])
+    assert abs(z.mean()) < 0.03 and abs(z.std() - 1.0) < 0.03                        # exp(N(0, 1))
