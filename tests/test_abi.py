@@ -67,6 +67,18 @@ def _init_status(cpd, **kw):
     (dict(dims=(8, 8, 8), R=1, B=8, block=-1), "block must be >= 0"),
     (dict(dims=(64, 64, 64), R=16, B=64, block=2, engine="persistent"), "samples fibers one by one"),
     (dict(dims=(8, 8, 8), R=1, B=4, x_layout="strided", engine="cluster"), "strided x_layout"),
+    (dict(dims=(0, 2, 2), R=1, B=1), "every dim must be in [1, 2^31]"),
+    (dict(dims=(2, 2**31 + 1, 2), R=1, B=1), "every dim must be in [1, 2^31]"),
+    (dict(dims=(2**20, 2**20, 2**20), R=1, B=1), "tensor too large"),
+    (dict(dims=(2, 2, 2), R=1, B=1, step="adagrad", eta=0.1, b=-1.0), "AdaGrad needs eta > 0 and b >= 0"),
+    (dict(dims=(8, 8, 8), R=1, B=4, tile_rows=520), "tile_rows must be a multiple of 8"),
+    (dict(dims=(64, 64, 64), R=16, B=512, engine="cluster", tile_fibers=272), "tensor-core engines"),
+    (dict(dims=(64, 64, 64), R=16, B=512, engine="tensor", tile_fibers=144), "tensor-core engines"),
+    (dict(dims=(64, 64, 64), R=80, B=64, engine="cluster"), "R <= 64"),
+    (dict(dims=(1100, 64, 64), R=16, B=64, engine="cluster"), "every I_k <= 1024"),
+    (dict(dims=(64, 64, 64), R=16, B=64, engine="persistent", max_ctas=32), "at most 16"),
+    (dict(dims=(64, 64, 64), R=16, B=64, x_dtype="f32", engine="persistent"), "persistent engine needs BF16"),
+    (dict(dims=(64, 64, 64), R=16, B=64, sampling="leverage", engine="persistent"), "persistent engine needs BF16"),
 ])
 def test_invalid_configs_rejected_on_host(cpd, kw, msg):
     st, err = _init_status(cpd, **kw)
@@ -77,7 +89,10 @@ def test_invalid_configs_rejected_on_host(cpd, kw, msg):
 def test_unknown_constraint_and_layout_rejected(cpd):
     import torch
     for field, value, msg in (("constraint", 7, "constraint"), ("x_layout", 2, "x_layout"),
-                              ("max_ctas", -1, "max_ctas")):
+                              ("max_ctas", -1, "max_ctas"), ("N", 9, "N must"), ("R", 257, "R must"),
+                              ("B", 65537, "B must"), ("sampling", 3, "unknown sampling"),
+                              ("step", 3, "unknown step"), ("x_dtype", 3, "unknown x_dtype"),
+                              ("engine", 6, "unknown engine"), ("engine", -1, "unknown engine")):
         cfg = cpd.make_config(dims=(2, 2, 2), R=1, B=1)
         setattr(cfg, field, value)
         X = torch.zeros(8)
