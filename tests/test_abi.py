@@ -133,3 +133,52 @@ def test_server_group_and_variance_reject_bad_arguments_on_host(cpd):
     v = C.c_double()
     assert cpd.lib().cpd_grad_variance(None, 0, C.byref(v), None, None) == cpd.EINVAL
     assert cpd.lib().cpd_server_destroy(None) == cpd.OK
+
+
+def _header_arity():
+    """Parameter count of every cpd_status function declared in include/*.h."""
+    arity = {}
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", h)).read(), flags=re.S)
+        for m in re.finditer(r"cpd_status\s+(cpd_\w+)\s*\(([^)]*)\)\s*;", txt):
+            params = m.group(2).strip()
+            arity[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return arity
+
+
+def test_binding_signatures_match_the_header(cpd):
+    """The ctypes argument lists of the binding have the header's arity, so no
+    call passes a shifted argument."""
+    arity = _header_arity()
+    assert len(arity) >= 30, sorted(arity)
+    for name, n in sorted(arity.items()):
+        f = getattr(cpd.lib(), name)
+        assert f.argtypes is not None, name
+        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+
+
+def test_null_handles_rejected_on_host(cpd):
+    """Every call on a context, group or server rejects a NULL handle with
+    CPD_EINVAL before any device work; the destroy calls accept NULL."""
+    L = cpd.lib()
+    calls = {
+        "cpd_sgd_iters": (None, 1, None), "cpd_prepare": (None, 1, None),
+        "cpd_gradients": (None, 0, 0, 1, None, None), "cpd_skrp": (None, 0, 0, 1, None, None, None, None, None),
+        "cpd_fit": (None, None, None, None), "cpd_fit_start": (None, None), "cpd_fit_poll": (None, None, None),
+        "cpd_get_factors": (None, None, 0, None), "cpd_set_factors": (None, None, 0, None),
+        "cpd_get_adagrad": (None, None, 0, None), "cpd_set_adagrad": (None, None, 0, None),
+        "cpd_get_iteration": (None, None), "cpd_set_iteration": (None, 0),
+        "cpd_last_sample": (None, None, None, None, None), "cpd_last_gradient": (None, None, None),
+        "cpd_sync": (None, None), "cpd_profile": (None, 1), "cpd_profile_read": (None, None, None, None, None),
+        "cpd_trace": (None, 1), "cpd_trace_read": (None, None, None), "cpd_describe": (None, None, 0),
+        "cpd_grad_variance": (None, 0, None, None, None), "cpd_group_create": (None, 1, None, None),
+        "cpd_group_iters": (None, 1, None), "cpd_submit": (None, None, None, 0, None, 0, 0.0, 1, None),
+        "cpd_poll": (None, 0, None, None), "cpd_server_wait": (None, 1.0),
+        "cpd_server_stats": (None, None, None, None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == cpd.EINVAL, name
+    for name in ("cpd_destroy", "cpd_group_destroy", "cpd_server_destroy"):
+        assert getattr(L, name)(None) == cpd.OK, name
